@@ -1,0 +1,87 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case compiles a copy of the oracle with one planted mistake (a swapped
+operand, a wrong sign or index, a dropped negation) and checks that at least
+one pin of test_oracle_pins fails against it.  Mistakes are planted only in
+the CPU oracle.
+"""
+import pytest
+
+import oracle
+from tests import test_oracle_pins as P
+
+# (name, [(original text, mutated text), ...]); every original must occur once
+MUTANTS = [
+    ("interpolation weights swapped",
+     [("const R vel = (R(1) - s) * ua + s * ub;", "const R vel = s * ua + (R(1) - s) * ub;")]),
+    ("gray point interpolated along the wrong edge",
+     [("u[(size_t)(m.j + 1) * (nx + 1) + m.i], lam, f);",
+       "u[(size_t)m.j * (nx + 1) + m.i + 1], lam, f);")]),
+    ("circle coefficient sign",
+     [("const double al = r2 * qy - q2 * ry;", "const double al = q2 * ry - r2 * qy;")]),
+    ("wrong root of the circle",
+     [("if (a_with_T && !b_with_T) yrel = yb;", "if (!a_with_T && b_with_T) yrel = yb;")]),
+    ("corner flip off by one",
+     [("for (int kk = std::min(i, p.ix) + 1; kk <= std::max(i, p.ix); ++kk) N.k(kk, j) ^= 1;",
+       "for (int kk = std::min(i, p.ix); kk < std::max(i, p.ix); ++kk) N.k(kk, j) ^= 1;")]),
+    ("aligned marker keeps its old fraction",
+     [("land.push_back({p.ix, j, p.fx, i});", "land.push_back({p.ix, j, S.hc(i, j), i});")]),
+    ("centre colour not negated",
+     [("const int vr = lr < 0 ? -1 : !N.kc(k, lr);", "const int vr = lr < 0 ? -1 : N.kc(k, lr);"),
+      ("const int vl = ll < 0 ? -1 : !N.kc(k, ll);", "const int vl = ll < 0 ? -1 : N.kc(k, ll);")]),
+    ("triangle leg measured from the wrong corner",
+     [("case 1: a = 1.0 - s[0]; b = s[1]; break;", "case 1: a = s[0]; b = s[1]; break;")]),
+    ("four-marker fraction inverted",
+     [("return zc == 0 ? Tsum : 1.0 - Tsum;", "return zc == 1 ? Tsum : 1.0 - Tsum;")]),
+    ("trapezoid side swapped",
+     [("return c[0] ? 0.5 * (s[0] + s[2]) : 0.5 * ((1.0 - s[0]) + (1.0 - s[2]));",
+       "return c[0] ? 0.5 * ((1.0 - s[0]) + (1.0 - s[2])) : 0.5 * (s[0] + s[2]);")]),
+    ("second difference sign",
+     [("const R hpp = (h[2] - h[1]) - (h[1] - h[0]);", "const R hpp = (h[2] - h[1]) + (h[1] - h[0]);")]),
+    ("height direction swapped",
+     [("const bool ycol = ax >= ay;", "const bool ycol = ax < ay;")]),
+    ("circle root at initialisation on the wrong side",
+     [("const double root = P.in_circle(o, xi, yj) ? sc->xc[o] + sq : sc->xc[o] - sq;",
+       "const double root = P.in_circle(o, xi, yj) ? sc->xc[o] - sq : sc->xc[o] + sq;")]),
+    ("y sweep maps edges without transposing fractions",
+     [("for (int i = 0; i < S.nx; ++i) T.v(j, i) = S.hc(i, j);",
+       "for (int i = 0; i < S.nx; ++i) T.v(j, i) = R(1) - S.hc(i, j);")]),
+]
+
+BATTERY = [
+    (P.test_fit_exact_on_circle, ()),
+    (P.test_fit_collinear_is_the_line_and_degenerate_cases, ()),
+    (P.test_translation_table1, (32,)),
+    (P.test_aligned_markers_follow_linear_field, (0,)),
+    (P.test_aligned_markers_follow_linear_field, (1,)),
+    (P.test_straight_line_under_shear_stays_straight, (0,)),
+    (P.test_straight_line_under_shear_stays_straight, (1,)),
+    (P.test_merge_when_approaching_along_x, ()),
+    (P.test_diagonal_approach_keeps_two_loops, ()),
+    (P.test_subgrid_drop_disappears, ()),
+    (P.test_fraction_exact_for_half_planes, ()),
+    (P.test_fraction_saddle_cell_follows_centre_colour, ()),
+    (P.test_circle_area_inscribed_polygon_bound, ()),
+    (P.test_hf_straight_line_zero_curvature, ()),
+    (P.test_hf_circle_curvature_converges, ()),
+    (P.test_init_markers_on_shapes, ()),
+    (P.test_vortex_T2_table3, (32,)),
+]
+
+
+@pytest.mark.parametrize("name,edits", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(name, edits, tmp_path):
+    src = oracle.source_text()
+    for old, new in edits:
+        assert src.count(old) == 1, f"mutation site not unique: {old}"
+        src = src.replace(old, new)
+    lib_path = oracle.compile_variant(src, str(tmp_path / "libmutant.so"))
+    failed = []
+    with oracle.use_library(lib_path):
+        for fn, args in BATTERY:
+            try:
+                fn(*args)
+            except Exception as e:  # AssertionError or a numerical blow-up
+                failed.append(fn.__name__)
+                break
+    assert failed, f"no pin caught the planted mistake: {name}"

@@ -1,0 +1,549 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (tests/golden, with the table they come from), closed forms,
+invariants of the method, special cases that reduce to textbook results, and
+brute force on tiny grids.  Together they are chosen so that a dropped term, a
+wrong sign or index, or a swapped operand anywhere in the oracle fails one of
+them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_00338_gb300 import workloads as W
+from tests.conftest import read_golden
+
+
+def run(wl, prec=oracle.FP64, track=None, line_only=False):
+    S = oracle.init(wl.n, wl.n, wl.dx, wl.scene, prec)
+    _, A0 = oracle.fraction(S)
+    tot = np.zeros(oracle.NCOUNTERS, np.int64)
+    for k in range(wl.steps):
+        r = oracle.step(S, wl.field.u, wl.field.v, wl.field.dt_eff(k, wl.dt), line_only=line_only)
+        tot += r["counters"]
+        if track is not None:
+            track(k, S, r)
+    _, A1 = oracle.fraction(S)
+    return S, abs(A1 - A0) / A0, tot
+
+
+# ---------------------------------------------------------------------------
+# circle fit (Sec. 2.2)
+# ---------------------------------------------------------------------------
+def _circle_points(rng, k_line=0.0):
+    """A random circle crossing the grid line x = 0 inside the band [0,1],
+    with four points on it: P1, A (x<0), B (x>0), P4 along the arc."""
+    while True:
+        R = 10 ** rng.uniform(-0.3, 2.0)
+        y_cross = rng.uniform(0.05, 0.95)
+        ang = rng.uniform(-1.2, 1.2)   # direction of the radius at the crossing
+        cx, cy = -R * math.cos(ang), y_cross - R * math.sin(ang)
+        # the crossing point is (0, y_cross); walk along the arc both ways
+        th0 = math.atan2(y_cross - cy, 0.0 - cx)
+        dth = rng.uniform(0.2, 0.9) / R
+        pts = [(cx + R * math.cos(th0 + t * dth), cy + R * math.sin(th0 + t * dth))
+               for t in (-2.5, -0.6, 0.7, 2.4)]
+        xs = [p[0] for p in pts]
+        if xs[1] < 0 < xs[2] or xs[2] < 0 < xs[1]:
+            if xs[1] > xs[2]:
+                pts = pts[::-1]
+            return (cx, cy, R), y_cross, pts
+
+
+def test_fit_exact_on_circle():
+    """Points on a true circle: both circles are that circle, so the new
+    marker is its exact intersection with the grid line (to roundoff)."""
+    rng = W.Xoshiro256ss(11)
+    worst = 0.0
+    for _ in range(300):
+        (cx, cy, R), yc, (P1, A, B, P4) = _circle_points(rng)
+        # input points carry ~1e-16 R rounding; fitting a circle of radius R
+        # through points ~0.5 cell apart amplifies that by ~R, so allow
+        # 1e-13 max(1,R)^2 (cell units)
+        tol = 1e-13 * max(1.0, R) ** 2
+        kind, y = oracle.fit(A, B, P1, P4)
+        assert kind == oracle.FIT_TWO
+        worst = max(worst, abs(y - yc) / tol)
+        kind1, y1 = oracle.fit(A, B, None, P4)
+        assert kind1 == oracle.FIT_ONE and abs(y1 - yc) < tol
+        kind2, y2 = oracle.fit(A, B, P1, None)
+        assert kind2 == oracle.FIT_ONE and abs(y2 - yc) < tol
+    assert worst < 1.0
+
+
+def test_fit_collinear_is_the_line_and_degenerate_cases():
+    # collinear points: the circle degenerates to the straight line
+    A, B = (-0.4, 0.2), (0.6, 0.7)
+    slope = (B[1] - A[1]) / (B[0] - A[0])
+    P1 = (-1.4, 0.2 - slope)
+    P4 = (1.6, 0.7 + slope)
+    kind, y = oracle.fit(A, B, P1, P4)
+    assert abs(y - (0.2 + 0.4 * slope)) < 1e-14
+    # no neighbours: the chord crossing (straight-line fit, first EBIT version)
+    kind, y = oracle.fit(A, B)
+    assert kind == oracle.FIT_LINE and abs(y - (0.2 + 0.4 * slope)) < 1e-15
+    # B exactly on the line: the crossing is B itself
+    kind, y = oracle.fit((-0.5, 0.3), (0.0, 0.8), P1, P4)
+    assert kind == oracle.FIT_ONLINE and y == 0.8
+    # a neighbour coinciding with A gives no circle -> falls back
+    kind, y = oracle.fit(A, B, A, None)
+    assert kind == oracle.FIT_LINE
+    # circle centre (0, 0.55), radius 0.5 through A=(-0.3,0.95), B=(0.3,0.95):
+    # with the third point at the bottom the arc A..B is the top arc, which
+    # crosses x=0 at y=1.05, outside the band -> dropped, chord used
+    A3, B3 = (-0.3, 0.95), (0.3, 0.95)
+    kind, y = oracle.fit(A3, B3, (0.0, 0.05), None)
+    assert kind == oracle.FIT_LINE and abs(y - 0.95) < 1e-15
+    # with the third point at the top the arc A..B is the bottom arc: y=0.05
+    kind, y = oracle.fit(A3, B3, None, (0.0, 1.05))
+    assert kind == oracle.FIT_ONE and abs(y - 0.05) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# whole steps against the paper's tables
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [32, 64])
+def test_translation_table1(n):
+    """Translation (Sec. 3.2): every point moves by the same vector, so the
+    circle fit on points of a circle is exact and the errors stay at roundoff,
+    at or below the paper's Table 1 values."""
+    tab = read_golden("table1_translation.txt")
+    row = tab[tab[:, 0] == n][0]
+    wl = W.translation_workload(n)
+    S, e_area, tot = run(wl)
+    e_shape = oracle.shape_error(S, 0.25, 0.75, 0.15)
+    assert tot[oracle.INVARIANT] == 0
+    assert e_area <= row[1] and e_shape <= row[2]
+    assert e_area < 1e-12 and e_shape < 1e-12
+    assert oracle.loops(S)[:2] == (1, 0)
+
+
+def test_translation_fp32_state():
+    """FP32 state: each step rounds every marker to 2^-24 cell; summed over
+    the 2*pi*R/dx boundary markers and 256 steps this bounds
+    E_area <= 256 * 2*pi*R*2^-24*dx / (pi R^2) ~ 1.3e-5 (worst case)."""
+    wl = W.translation_workload(32)
+    S, e_area, tot = run(wl, prec=oracle.FP32)
+    bound = wl.steps * 2 * math.pi * 0.15 * 2.0 ** -24 * wl.dx / (math.pi * 0.15 ** 2)
+    assert tot[oracle.INVARIANT] == 0
+    assert e_area <= bound
+    assert oracle.shape_error(S, 0.25, 0.75, 0.15) < 1e-5
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_vortex_T2_table3(n):
+    """Single vortex T=2 (Sec. 3.3) with the paper's sign and CFL 0.125:
+    E_area and E_shape within a factor 3 of Table 3."""
+    tab = read_golden("table3_vortex_T2.txt")
+    row = tab[tab[:, 0] == n][0]
+    wl = W.vortex_workload(n, period=2.0, cfl=0.125, paper_sign=True)
+    S, e_area, tot = run(wl)
+    e_shape = oracle.shape_error(S, 0.5, 0.75, 0.15)
+    assert tot[oracle.INVARIANT] == 0
+    assert row[1] / 3 <= e_area <= 3 * row[1]
+    assert row[2] / 3 <= e_shape <= 3 * row[2]
+
+
+def test_vortex_T2_converges():
+    """About first order in area and shape (Sec. 3.3)."""
+    errs = []
+    for n in (32, 64, 128):
+        wl = W.vortex_workload(n, period=2.0, cfl=0.125, paper_sign=True)
+        S, e_area, _ = run(wl)
+        errs.append((e_area, oracle.shape_error(S, 0.5, 0.75, 0.15)))
+    for (a0, s0), (a1, s1) in zip(errs, errs[1:]):
+        assert a1 < a0 and s1 < s0
+    assert errs[0][1] / errs[2][1] > 2.5   # ~4 for first order over two doublings
+
+
+def test_vortex_T8_table4_topology_loss():
+    """T=8 (Table 4): the ligament breaks under the automatic topology change
+    at coarse resolution; the loss falls with N, same order as the paper."""
+    tab = read_golden("table4_vortex_T8.txt")
+    out = []
+    for n in (32, 64):
+        wl = W.vortex_workload(n, period=8.0, cfl=0.125, paper_sign=True)
+        S, e_area, tot = run(wl)
+        assert tot[oracle.INVARIANT] == 0
+        assert tot[oracle.CANCELLED] > 0 and tot[oracle.ZSET] > 0
+        row = tab[tab[:, 0] == n][0]
+        assert row[1] / 3 <= e_area <= 3 * row[1]
+        out.append(e_area)
+    assert out[1] < out[0]
+
+
+def test_vortex_baseline_config_runs_clean():
+    """The 64x64 plain FP64 workload (mirrored vortex, CFL 0.5, 256 steps):
+    invariants hold every step and the shape comes back (time reversal)."""
+    wl = W.vortex_workload(64, period=2.0, cfl=0.5, paper_sign=False)
+    assert wl.steps == 256
+    S, e_area, tot = run(wl)
+    assert tot[oracle.INVARIANT] == 0 and tot[oracle.CFL] == 0
+    assert e_area < 5e-2
+    assert oracle.shape_error(S, 0.5, 0.75, 0.15) < 2e-2
+
+
+# ---------------------------------------------------------------------------
+# advection of aligned and unaligned markers (Sec. 2.1, Eq. 4)
+# ---------------------------------------------------------------------------
+def _markers_by_line(S):
+    out = {}
+    jH, iH = np.nonzero(S.hasH)
+    for j, i in zip(jH, iH):
+        out.setdefault(j, []).append((i + S.sH[j, i]) * S.dx)
+    return {j: np.sort(v) for j, v in out.items()}
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_aligned_markers_follow_linear_field(axis):
+    """A linear field is reproduced exactly by interpolation along an edge,
+    so every aligned marker moves by exactly u(x, y_j) dt (Eq. 4)."""
+    n = 32
+    dx = 1.0 / n
+    scene = W.circle_scene([(0.5, 0.48, 0.3)])
+    S = oracle.init(n, n, dx, scene)
+    f = W.linear_field(n, n, dx, a=(0.3, 0.4, -0.2), b=(-0.25, 0.3, 0.35))
+    dt = 0.45 * dx / f.umax
+    if axis == 1:  # compare on the transposed picture
+        before = {}
+        jV, iV = np.nonzero(S.hasV)
+        for j, i in zip(jV, iV):
+            before.setdefault(i, []).append((j + S.sV[j, i]) * dx)
+    else:
+        before = _markers_by_line(S)
+    ctr, _ = oracle.sweep(S, axis, f.u if axis == 0 else f.v, dt / dx)
+    assert ctr[oracle.INVARIANT] == 0 and ctr[oracle.CANCELLED] == 0
+    if axis == 0:
+        after = _markers_by_line(S)
+        for j, xs in before.items():
+            y = j * dx
+            exp = np.sort(xs + (0.3 + 0.4 * xs - 0.2 * y) * dt)
+            assert np.max(np.abs(after[j] - exp)) < 1e-14
+    else:
+        jV, iV = np.nonzero(S.hasV)
+        after = {}
+        for j, i in zip(jV, iV):
+            after.setdefault(i, []).append((j + S.sV[j, i]) * dx)
+        for i, ys in before.items():
+            x = i * dx
+            ys = np.array(ys)
+            exp = np.sort(ys + (-0.25 + 0.3 * x + 0.35 * ys) * dt)
+            assert np.max(np.abs(np.sort(after[i]) - exp)) < 1e-14
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_straight_line_under_shear_stays_straight(axis):
+    """A shear u = a + c y maps a straight line to a straight line; moved
+    points of the line are collinear, the circles degenerate to that line,
+    so every marker after the sweep lies on the mapped line."""
+    n = 32
+    dx = 1.0 / n
+    # la x + lb y <= lc, meeting only the two walls parallel to the sweep (on
+    # the walls normal to it markers stay put by the wall reading)
+    la, lb, lc = (1.0, 0.6, 0.8) if axis == 0 else (0.6, 1.0, 0.8)
+    S = oracle.init(n, n, dx, {"line": (la, lb, lc)})
+    a, c = 0.2, 0.5
+    dt = 0.4 * dx / (abs(a) + abs(c))
+    if axis == 0:
+        f = W.linear_field(n, n, dx, a=(a, 0.0, c))
+        oracle.sweep(S, 0, f.u, dt / dx)
+        # la (x - (a + c y) dt) + lb y = lc
+        A_, B_, C_ = la, lb - la * c * dt, lc + la * a * dt
+    else:
+        f = W.linear_field(n, n, dx, b=(a, c, 0.0))
+        oracle.sweep(S, 1, f.v, dt / dx)
+        # la x + lb (y - (a + c x) dt) = lc
+        A_, B_, C_ = la - lb * c * dt, lb, lc + lb * a * dt
+    P = oracle.markers(S)
+    assert P.shape[0] > 40
+    res = (A_ * P[:, 0] + B_ * P[:, 1] - C_) / math.hypot(A_, B_)
+    assert np.max(np.abs(res)) < 1e-14
+
+
+def test_corner_colour_flips_when_marker_passes(oracle_lib):
+    """Fig. 5: a corner colour vertex flips when a marker crosses it."""
+    n = 16
+    dx = 1.0 / n
+    S = oracle.init(n, n, dx, {"line": (1.0, 0.0, 0.52)})   # x <= 0.52 (vertical)
+    K0 = S.K.copy()
+    f = W.uniform_field(n, n, dx, 1.0, 0.0)
+    # marker at x=0.52 (edge 8, s=0.32) moves 0.8 cell to x=0.57: passes x_9 = 0.5625
+    oracle.sweep(S, 0, f.u, 0.8)
+    changed = np.argwhere(S.K != K0)
+    assert set(changed[:, 1]) == {9} and len(changed) == n + 1
+    assert np.all(S.K[:, 9] == 1) and np.all(S.hasH.sum(axis=1) == 1)
+    xs = (np.nonzero(S.hasH)[1] + S.sH[S.hasH]) * dx
+    assert np.allclose(xs, 0.52 + 0.8 * dx, atol=1e-15)
+
+
+def test_cfl_violation_is_flagged():
+    n = 16
+    dx = 1.0 / n
+    S = oracle.init(n, n, dx, W.circle_scene([(0.5, 0.5, 0.2)]))
+    f = W.uniform_field(n, n, dx, 1.0, 0.5)
+    r = oracle.step(S, f.u, f.v, 1.5 * dx)
+    assert r["counters"][oracle.CFL] > 0 and r["status"] == 3 and r["max_cfl"] == pytest.approx(1.5)
+
+
+# ---------------------------------------------------------------------------
+# topology change and the colour vertex (Sec. 2.3-2.4)
+# ---------------------------------------------------------------------------
+def test_merge_when_approaching_along_x():
+    """Two drops approaching along x merge when their aligned markers meet on
+    one edge (Sec. 2.4): loops 2 -> 1."""
+    n = 32
+    dx = 1.0 / n
+    S = oracle.init(n, n, dx, W.circle_scene([(0.3, 0.5, 0.1), (0.7, 0.5, 0.1)]))
+    X = np.arange(n + 1) * dx
+    # converging flow whose zero lies inside the edge right of x = 0.5, so both
+    # fronts end up on that edge
+    U = np.tile(np.where(X <= 0.5, 0.5, -0.5), (n + 1, 1))
+    V = np.zeros_like(U)
+    dt = 0.25 * dx / 0.5
+    counts = []
+    tot = np.zeros(oracle.NCOUNTERS, np.int64)
+    for k in range(int(0.3 / dt)):
+        r = oracle.step(S, U, V, dt)
+        tot += r["counters"]
+        counts.append(oracle.loops(S)[0])
+    assert tot[oracle.INVARIANT] == 0
+    assert counts[0] == 2 and counts[-1] == 1 and set(counts) <= {1, 2}
+    assert tot[oracle.CANCELLED] > 0
+
+
+def test_diagonal_approach_keeps_two_loops():
+    """Drops approaching along the diagonal form a saddle cell with four
+    markers; the centre colour vertex keeps them apart as long as their
+    markers are on different edges (Sec. 2.4, Fig. 4)."""
+    n = 32
+    dx = 1.0 / n
+    r0 = 0.12
+    d = 0.5 / math.sqrt(2)
+    S = oracle.init(n, n, dx, W.circle_scene([(0.5 - d * 0.62, 0.5 - d * 0.62, r0),
+                                              (0.5 + d * 0.62, 0.5 + d * 0.62, r0)]))
+    X, Y = np.meshgrid(np.arange(n + 1) * dx, np.arange(n + 1) * dx)
+    s = np.sign((X - 0.5) + (Y - 0.5))
+    U = -0.5 * s
+    V = -0.5 * s
+    dt = 0.2 * dx / 0.5
+    saw_saddle = False
+    cancelled = 0
+    for k in range(400):
+        r = oracle.step(S, U, V, dt)
+        assert r["counters"][oracle.INVARIANT] == 0
+        cancelled += r["counters"][oracle.CANCELLED]
+        if cancelled:
+            break
+        assert oracle.loops(S)[0] == 2
+        if S.four.any():
+            saw_saddle = True
+    assert saw_saddle
+
+
+def test_subgrid_drop_disappears():
+    """A drop smaller than a cell is removed when its two aligned markers meet
+    on one edge (Sec. 2.4)."""
+    n = 16
+    dx = 1.0 / n
+    S = oracle.init(n, n, dx, W.circle_scene([(8 * dx, 8 * dx, 0.3 * dx)]))
+    assert S.hasH.sum() == 2 and S.hasV.sum() == 2
+    f = W.uniform_field(n, n, dx, 1.0, 0.0)
+    for k in range(4):
+        oracle.step(S, f.u, f.v, 0.25 * dx)
+    assert S.hasH.sum() == 0 and S.hasV.sum() == 0 and S.K.sum() == 0
+    assert oracle.fraction(S)[1] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# volume fractions (Sec. 2.5)
+# ---------------------------------------------------------------------------
+def _clip_area(a, b, c):
+    """Area of {a x + b y <= c} within the unit square: Sutherland-Hodgman
+    clipping of the square by the half-plane, then the shoelace formula."""
+    poly = [(0, 0), (1, 0), (1, 1), (0, 1)]
+    out = []
+    for k in range(4):
+        P, Q = poly[k], poly[(k + 1) % 4]
+        fp, fq = a * P[0] + b * P[1] - c, a * Q[0] + b * Q[1] - c
+        if fp <= 0:
+            out.append(P)
+        if (fp < 0) != (fq < 0) and fp != fq:
+            t = fp / (fp - fq)
+            out.append((P[0] + t * (Q[0] - P[0]), P[1] + t * (Q[1] - P[1])))
+    if len(out) < 3:
+        return 0.0
+    s = 0.0
+    for k in range(len(out)):
+        s += out[k][0] * out[(k + 1) % len(out)][1] - out[(k + 1) % len(out)][0] * out[k][1]
+    return abs(s) / 2
+
+
+def test_fraction_exact_for_half_planes():
+    rng = W.Xoshiro256ss(5)
+    n = 16
+    dx = 1.0 / n
+    for _ in range(12):
+        th = rng.uniform(0, 2 * math.pi)
+        a, b = math.cos(th), math.sin(th)
+        c = a * rng.uniform(0.3, 0.7) + b * rng.uniform(0.3, 0.7)
+        S = oracle.init(n, n, dx, {"line": (a, b, c)})
+        C, _ = oracle.fraction(S)
+        for j in range(n):
+            for i in range(n):
+                # cell-local half-plane: a (i+x) dx + b (j+y) dx <= c
+                exp = _clip_area(a, b, c / dx - a * i - b * j)
+                assert abs(C[j, i] - exp) < 1e-12, (i, j, C[j, i], exp)
+
+
+def test_fraction_sum_equals_shoelace_area():
+    """sum C dx^2 equals the area enclosed by the traced marker loops
+    (Green's theorem), also after the interface has been deformed."""
+    rng = W.Xoshiro256ss(9)
+    n = 64
+    circles = W.place_circles(rng, 12, 0.03, 0.12, 2.0 / n, lambda x, y, r: True)
+    wl = W.Workload("t", n, 1.0 / n, W.circle_scene(circles),
+                    W.vortex_field(n, n, 1.0 / n, 2.0), 0.5 / n, 40)
+    S = oracle.init(n, n, wl.dx, wl.scene)
+    for k in range(wl.steps + 1):
+        C, A = oracle.fraction(S)
+        closed, opened, shoe = oracle.loops(S)
+        assert opened == 0
+        assert abs(A - shoe) <= 1e-13 * A
+        if k < wl.steps:
+            oracle.step(S, wl.field.u, wl.field.v, wl.field.dt_eff(k, wl.dt))
+
+
+def test_circle_area_inscribed_polygon_bound():
+    """Markers lie on the circle, so the area is that of an inscribed polygon
+    with sides l <= sqrt(2) dx; each circular segment has area <= l^3/(12R),
+    giving 0 <= pi R^2 - A <= pi dx^2 / 3."""
+    R = 0.3
+    for n in (16, 32, 64, 128, 256):
+        dx = 1.0 / n
+        S = oracle.init(n, n, dx, W.circle_scene([(0.5123, 0.4871, R)]))
+        _, A = oracle.fraction(S)
+        d = math.pi * R * R - A
+        assert -1e-14 <= d <= math.pi * dx * dx / 3
+
+
+def _inside(polys, px, py):
+    """Even-odd ray casting against closed polylines."""
+    inside = np.zeros(px.shape, bool)
+    for P in polys:
+        x0, y0 = P[:-1, 0], P[:-1, 1]
+        x1, y1 = P[1:, 0], P[1:, 1]
+        for a, b, c, d in zip(x0, y0, x1, y1):
+            cond = (b > py) != (d > py)
+            xi = a + (py - b) * (c - a) / np.where(d != b, d - b, 1.0)
+            inside ^= cond & (px < xi)
+    return inside
+
+
+@pytest.mark.parametrize("n", [6, 8, 12])
+def test_fraction_brute_force_tiny_grids(n):
+    """Point sampling of the traced polygons agrees with C per cell; a regular
+    m x m sample grid misclassifies at most ~ (sqrt(2) L m + 4) of m^2 points
+    for a boundary of length L <= 2 sqrt(2) in the cell, i.e. < 0.03 at m=128."""
+    dx = 1.0 / n
+    circles = [(0.37, 0.41, 2.1 * dx), (0.71, 0.69, 1.6 * dx), (0.36, 0.79, 0.8 * dx)]
+    S = oracle.init(n, n, dx, W.circle_scene(circles))
+    C, _ = oracle.fraction(S)
+    closed, opened, _, polys = oracle.loops(S, with_points=True)
+    assert opened == 0 and closed >= 1
+    m = 128
+    t = (np.arange(m) + 0.5) / m
+    for j in range(n):
+        for i in range(n):
+            X, Y = np.meshgrid((i + t) * dx, (j + t) * dx)
+            frac = _inside(polys, X, Y).mean()
+            assert abs(frac - C[j, i]) < 0.03, (i, j, frac, C[j, i])
+
+
+def test_fraction_saddle_cell_follows_centre_colour():
+    """A cell with four markers: the centre colour decides which corners are
+    cut off, and C = T1 + T2 or 1 - T1 - T2 (Sec. 2.3, Fig. 4)."""
+    S = oracle.State(1, 1, 1.0)
+    S.K[...] = [[1, 0], [1, 0]]
+    S.K[0, 0], S.K[0, 1], S.K[1, 1], S.K[1, 0] = 1, 0, 1, 0   # BL=1 BR=0 TR=1 TL=0
+    S.sH[0, 0], S.sV[0, 1], S.sH[1, 0], S.sV[0, 0] = 0.3, 0.4, 0.8, 0.2
+    T_bl = 0.5 * 0.2 * 0.3
+    T_tr = 0.5 * (1 - 0.4) * (1 - 0.8)
+    T_br = 0.5 * (1 - 0.3) * 0.4
+    T_tl = 0.5 * 0.8 * (1 - 0.2)
+    S.Z[0, 0] = 0
+    C, _ = oracle.fraction(S)
+    assert abs(C[0, 0] - (T_bl + T_tr)) < 1e-16
+    S.Z[0, 0] = 1
+    C, _ = oracle.fraction(S)
+    assert abs(C[0, 0] - (1 - T_br - T_tl)) < 1e-16
+
+
+# ---------------------------------------------------------------------------
+# height-function curvature (Sec. 2.5)
+# ---------------------------------------------------------------------------
+def test_hf_straight_line_zero_curvature():
+    """For a straight line the column sums are exactly linear in the column
+    index, so h'' = 0 and kappa = 0 (to roundoff)."""
+    n = 64
+    dx = 1.0 / n
+    for la, lb in ((0.3, 1.0), (1.0, 0.45), (-0.7, 1.0), (1.0, -0.2)):
+        S = oracle.init(n, n, dx, {"line": (la, lb, 0.5 * la + 0.5 * lb)})
+        C, _ = oracle.fraction(S)
+        kap, ninv = oracle.curvature(S, C)
+        iface = ~np.isnan(kap)
+        ncut = (C > 0) & (C < 1)
+        assert iface.sum() > 0.6 * ncut.sum()
+        assert np.max(np.abs(kap[iface])) * dx < 1e-12
+
+
+def _kappa_of_circle(n, R_cells, drop=True):
+    dx = 1.0 / n
+    c = (0.5 + 0.123 * dx, 0.5 - 0.271 * dx, R_cells * dx)
+    scene = W.circle_scene([c])
+    if not drop:
+        scene["line"] = (0.0, 0.0, 1.0)   # everything reference, circle toggles: bubble
+    S = oracle.init(n, n, dx, scene)
+    C, _ = oracle.fraction(S)
+    kap, ninv = oracle.curvature(S, C)
+    v = kap[~np.isnan(kap)]
+    return v * c[2], ninv, v.size
+
+
+def test_hf_circle_curvature_converges():
+    """kappa -> 1/R for a drop and -1/R for a bubble; |kappa R - 1| < 5e-2 at
+    R = 8 cells and decreasing with R/dx."""
+    errs = []
+    for Rc in (8, 16, 32):
+        kr, ninv, nval = _kappa_of_circle(128, Rc, drop=True)
+        assert nval > 0 and np.all(kr > 0)
+        errs.append(np.median(np.abs(kr - 1)))
+        kb, _, _ = _kappa_of_circle(128, Rc, drop=False)
+        assert np.all(kb < 0)
+        assert np.median(np.abs(-kb - 1)) == pytest.approx(errs[-1], rel=0.5)
+    assert errs[0] < 5e-2
+    assert errs[2] < errs[1] < errs[0]
+
+
+# ---------------------------------------------------------------------------
+# initialisation (Sec. 3.2)
+# ---------------------------------------------------------------------------
+def test_init_markers_on_shapes():
+    rng = W.Xoshiro256ss(3)
+    n = 128
+    dx = 1.0 / n
+    circles = W.place_circles(rng, 20, 3 * dx, 12 * dx, 2 * dx, lambda x, y, r: True)
+    curve = W.fourier_curve(rng)
+    S = oracle.init(n, n, dx, {"circles": circles, "curve": curve})
+    X, Y = np.meshgrid(np.arange(n + 1) * dx, np.arange(n + 1) * dx)
+    phase = (Y <= W.curve_height(curve, X)).astype(np.uint8)
+    for (x0, y0, r) in circles:
+        phase ^= (((X - x0) ** 2 + (Y - y0) ** 2) <= r * r).astype(np.uint8)
+    assert np.array_equal(phase, S.K)
+    P = oracle.markers(S)
+    d_circ = np.min(np.abs(np.hypot(P[:, None, 0] - circles[None, :, 0],
+                                    P[:, None, 1] - circles[None, :, 1]) - circles[None, :, 2]), axis=1)
+    d_curve = np.abs(P[:, 1] - W.curve_height(curve, P[:, 0]))
+    assert np.max(np.minimum(d_circ, d_curve)) < 1e-13
