@@ -1,0 +1,165 @@
+/*
+ * ebit.h - C ABI of libebit.so: the Edge-Based Interface Tracking (EBIT) step
+ * of Pan, Long, Chirco, Scardovelli, Popinet & Zaleski (arXiv:2309.00338) on
+ * one GB300 GPU (sm_103a).
+ *
+ * Grid (all arrays row-major, j is the slow index; dx is the cell size):
+ *   vertex (i,j) at (i*dx, j*dx), 0 <= i <= nx, 0 <= j <= ny
+ *   horizontal edge (i,j): (i,j)->(i+1,j), i < nx;  vertical edge (i,j): (i,j)->(i,j+1), j < ny
+ *   a marker on an edge is an edge-local fraction s in [0,1) from the edge's
+ *   first vertex; it exists exactly where the corner colour vertices at the
+ *   two ends of the edge differ (Sec. 2.4).
+ *   colour vertex 1 = reference phase.
+ *
+ * Precision: EBIT_FP64 - everything double.  EBIT_FP32 - marker fractions,
+ * velocities, advection arithmetic, fractions C and curvature stored and
+ * computed in float; circle fit (Sec. 2.2) and fraction areas in double.
+ * Velocity and output buffers have the element type of the context precision.
+ *
+ * Errors: every call returns an ebit_status; no exception crosses the ABI.
+ * Calls are asynchronous on the context's stream unless stated; failures that
+ * kernels detect (CFL > 1, invariant breaks) are recorded in a device status
+ * word and returned by the next synchronising call (ebit_sync,
+ * ebit_fraction/ebit_curvature with a host output, ebit_diagnostics,
+ * ebit_get_state).  ebit_last_error() gives a message for the calling thread.
+ * A context is used by one host thread at a time.
+ */
+#ifndef EBIT_H
+#define EBIT_H
+#include <stddef.h>
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EBIT_OK = 0,
+  EBIT_EAGAIN = 1,       /* result not ready yet (server)                    */
+  EBIT_EINVAL = -1,      /* bad argument                                     */
+  EBIT_ENOMEM = -2,      /* device or host allocation failed                 */
+  EBIT_ECFL = -3,        /* a marker moved more than one cell in a sweep     */
+  EBIT_EINVARIANT = -4,  /* colour/marker parity broken (must not happen)    */
+  EBIT_ECUDA = -5,       /* CUDA runtime error                               */
+  EBIT_ETIMEOUT = -6,    /* a bounded wait ran out                           */
+  EBIT_EFULL = -7        /* request can never fit the server's memory budget */
+} ebit_status;
+
+typedef enum { EBIT_FP64 = 0, EBIT_FP32 = 1 } ebit_precision;
+
+/* flags: EBIT_FIT_LINE places unaligned markers on the chord crossing only
+ * (the straight-line fit of the first EBIT version, Sec. 2.2). */
+#define EBIT_FIT_LINE 1u
+
+typedef struct {
+  int32_t nx, ny;   /* cells; 1 <= nx, ny <= 32768                           */
+  double dx;        /* cell size (> 0)                                       */
+  int32_t prec;     /* ebit_precision                                        */
+  uint32_t flags;
+} ebit_grid;
+
+typedef struct { double xc, yc, r; } ebit_circle;          /* toggles phase where d^2 <= r^2 */
+typedef struct {                                             /* reference phase where y <= h(x) */
+  double y0;                                                 /* h = y0 + sum_k amp[k-1] cos(2 pi k x + phase[k-1]) */
+  int32_t nmodes;
+  const double *amp, *phase;
+} ebit_curve;
+typedef struct { double a, b, c; } ebit_halfplane;          /* toggles phase where a x + b y <= c */
+typedef struct {
+  const ebit_circle* circles;   /* host pointer, ncircles entries (may be NULL if 0) */
+  int32_t ncircles;
+  const ebit_curve* curve;      /* host pointer or NULL                     */
+  const ebit_halfplane* line;   /* host pointer or NULL                     */
+} ebit_scene;
+
+/* Host copy of a state.  K: (ny+1)*(nx+1) bytes, Z: ny*nx bytes (0/1),
+ * sH: (ny+1)*nx doubles, sV: ny*(nx+1) doubles (values where no marker exists
+ * are unspecified on output and ignored on input).  Caller owns the arrays. */
+typedef struct {
+  int32_t nx, ny;
+  uint8_t* K;
+  uint8_t* Z;
+  double* sH;
+  double* sV;
+  int64_t step_index;   /* even: next step sweeps x then y; odd: y then x */
+} ebit_state_host;
+
+/* Diagnostics of the last step (sums over both sweeps). */
+enum {
+  EBIT_D_NH = 0, EBIT_D_NV, EBIT_D_CANCELLED, EBIT_D_ZSET, EBIT_D_ZCONFLICT,
+  EBIT_D_FIT_ONLINE, EBIT_D_FIT_LINE, EBIT_D_FIT_ONE, EBIT_D_FIT_TWO,
+  EBIT_D_WALL_CLAMP, EBIT_D_INVARIANT, EBIT_D_HF_INVALID, EBIT_D_CFL,
+  EBIT_D_COUNT = 16
+};
+typedef struct {
+  int64_t c[EBIT_D_COUNT];
+  double area;      /* sum C dx^2 of the current state                       */
+  double max_cfl;   /* largest |u| dt / dx met by a marker in the last step  */
+} ebit_diag;
+
+typedef struct ebit_ctx ebit_ctx;
+
+/* Initialisation (Sec. 3.2): colour vertices from the scene, markers by root
+ * finding on edges whose end colours differ, then fractions and curvature.
+ * Allocates all device state of the context (owned by it).  stream: a
+ * cudaStream_t (NULL = legacy default stream).  Shapes closer than one cell
+ * to each other are outside the supported input. */
+ebit_status ebit_init(ebit_ctx** out, const ebit_grid* grid, const ebit_scene* scene,
+                      void* stream);
+
+/* An empty context (all colours 0, no markers) to be filled by ebit_load_state. */
+ebit_status ebit_create(ebit_ctx** out, const ebit_grid* grid, void* stream);
+
+/* Copies a host state in (synchronous); recomputes fractions and curvature.
+ * FP32 contexts round the fractions to float. */
+ebit_status ebit_load_state(ebit_ctx* ctx, const ebit_state_host* st);
+
+/* Copies the current state out (synchronous). */
+ebit_status ebit_get_state(ebit_ctx* ctx, ebit_state_host* st);
+
+/* One EBIT time step (Sec. 2.1-2.5): direction-split advection (x then y on
+ * even steps, y then x on odd steps) of the markers by Eq. 4 with the circle
+ * fit (Sec. 2.2), corner and centre colour-vertex update (Sec. 2.3),
+ * automatic topology change (Sec. 2.4), then volume fractions and
+ * height-function curvature (Sec. 2.5).
+ * u, v: DEVICE pointers, (ny+1)*(nx+1) contiguous, context precision,
+ * velocity at the vertices; must stay valid until the step completes on the
+ * stream.  dt: time step (any sign).  Asynchronous. */
+ebit_status ebit_step(ebit_ctx* ctx, const void* u, const void* v, double dt);
+
+/* One sweep only (axis 0 = x with u, 1 = y with v); does not update fractions,
+ * curvature or the step index.  For tests. */
+ebit_status ebit_sweep(ebit_ctx* ctx, int axis, const void* vel, double dt);
+
+/* Volume fractions C (Sec. 2.5) of the current state.  C_dev: DEVICE buffer of
+ * ny*nx elements (context precision) or NULL; area_host: if non-NULL receives
+ * sum C dx^2 (synchronises the stream and reports deferred errors). */
+ebit_status ebit_fraction(ebit_ctx* ctx, void* C_dev, double* area_host);
+
+/* Height-function curvature (Sec. 2.5) of the current state, NaN where the
+ * 7x3 stencil is invalid or the cell holds no interface.  kappa_dev: DEVICE
+ * buffer of ny*nx elements or NULL; n_invalid_host: if non-NULL receives the
+ * number of interface cells without a valid stencil (synchronises). */
+ebit_status ebit_curvature(ebit_ctx* ctx, void* kappa_dev, int32_t* n_invalid_host);
+
+/* Zero-copy access to the context's fraction and curvature buffers (device
+ * pointers, row pitch in elements); valid until the next step or destroy. */
+ebit_status ebit_fields(ebit_ctx* ctx, const void** C, const void** kappa, int64_t* pitch);
+
+/* Counters of the last step (synchronous). */
+ebit_status ebit_diagnostics(ebit_ctx* ctx, ebit_diag* out);
+
+/* Waits for the context's stream; returns and clears a deferred error. */
+ebit_status ebit_sync(ebit_ctx* ctx);
+
+void ebit_destroy(ebit_ctx* ctx);
+
+/* Message of the last failure on the calling thread (never NULL). */
+const char* ebit_last_error(void);
+
+/* Device bytes a context of this grid allocates (for admission control). */
+size_t ebit_footprint(const ebit_grid* grid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

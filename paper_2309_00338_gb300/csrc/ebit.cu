@@ -1,0 +1,516 @@
+// Host side of the C ABI declared in include/ebit.h: context allocation, the
+// launch sequence of one EBIT step, state I/O and error reporting.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ebit.h"
+#include "ebit_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+ebit_status fail(ebit_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define EBIT_CK(call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) return fail(EBIT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kMaxSide = 32768;
+
+struct Layout {
+  ebit::Dims d;
+  size_t esz;
+  size_t k_bytes, z_bytes, h_bytes, v_bytes, field_bytes, verdict_bytes, partial_count;
+  dim3 grid, block;
+  size_t total() const {
+    return 2 * (k_bytes + z_bytes + h_bytes + v_bytes) + 2 * field_bytes + 2 * verdict_bytes +
+           partial_count * sizeof(double) + 4096;
+  }
+};
+
+bool valid_grid(const ebit_grid* g) {
+  return g && g->nx >= 1 && g->ny >= 1 && g->nx <= kMaxSide && g->ny <= kMaxSide && g->dx > 0.0 &&
+         (g->prec == EBIT_FP64 || g->prec == EBIT_FP32) && (g->flags & ~EBIT_FIT_LINE) == 0;
+}
+
+Layout layout_of(const ebit_grid* g) {
+  Layout L;
+  L.d.nx = g->nx;
+  L.d.ny = g->ny;
+  L.d.kw = (g->nx + 1 + 31) / 32;
+  L.d.zw = (g->nx + 31) / 32;
+  L.d.P = ((long long)g->nx + 1 + 31) / 32 * 32;
+  L.esz = g->prec == EBIT_FP32 ? 4 : 8;
+  L.k_bytes = (size_t)(g->ny + 1) * L.d.kw * 4;
+  L.z_bytes = (size_t)g->ny * L.d.zw * 4;
+  L.h_bytes = (size_t)(g->ny + 1) * L.d.P * L.esz;
+  L.v_bytes = (size_t)g->ny * L.d.P * L.esz;
+  L.field_bytes = (size_t)g->ny * L.d.P * L.esz;
+  L.verdict_bytes = (size_t)g->nx * g->ny;
+  L.block = dim3(32, ebit::kBlockY);
+  L.grid = dim3((g->nx + 1 + 31) / 32, (g->ny + 1 + ebit::kBlockY - 1) / ebit::kBlockY);
+  L.partial_count = (size_t)L.grid.x * L.grid.y;
+  return L;
+}
+
+}  // namespace
+
+struct ebit_ctx {
+  ebit_grid grid;
+  Layout L;
+  cudaStream_t stream = nullptr;
+  uint32_t* K[2] = {nullptr, nullptr};
+  uint32_t* Z[2] = {nullptr, nullptr};
+  void* sH[2] = {nullptr, nullptr};
+  void* sV[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* C = nullptr;
+  void* kappa = nullptr;
+  int8_t* from_left = nullptr;
+  int8_t* from_right = nullptr;
+  double* partial = nullptr;
+  double* area = nullptr;
+  unsigned long long* ctr = nullptr;
+  unsigned long long* cfl_bits = nullptr;
+  int* status = nullptr;
+  int64_t step_index = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+ebit_status dalloc(ebit_ctx* c, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EBIT_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  e = cudaMemsetAsync(*p, 0, bytes ? bytes : 16, c->stream);
+  if (e != cudaSuccess) return fail(EBIT_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  return EBIT_OK;
+}
+
+ebit_status alloc_ctx(ebit_ctx* c) {
+  const Layout& L = c->L;
+  ebit_status s;
+#define EBIT_AL(ptr, bytes) \
+  if ((s = dalloc(c, (void**)&(ptr), (bytes))) != EBIT_OK) return s
+  for (int b = 0; b < 2; ++b) {
+    EBIT_AL(c->K[b], L.k_bytes);
+    EBIT_AL(c->Z[b], L.z_bytes);
+    EBIT_AL(c->sH[b], L.h_bytes);
+    EBIT_AL(c->sV[b], L.v_bytes);
+  }
+  EBIT_AL(c->C, L.field_bytes);
+  EBIT_AL(c->kappa, L.field_bytes);
+  EBIT_AL(c->from_left, L.verdict_bytes);
+  EBIT_AL(c->from_right, L.verdict_bytes);
+  EBIT_AL(c->partial, L.partial_count * sizeof(double));
+  EBIT_AL(c->area, sizeof(double));
+  EBIT_AL(c->ctr, ebit::kCounters * sizeof(unsigned long long));
+  EBIT_AL(c->cfl_bits, sizeof(unsigned long long));
+  EBIT_AL(c->status, sizeof(int));
+#undef EBIT_AL
+  return EBIT_OK;
+}
+
+void free_ctx(ebit_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+}
+
+template <typename R>
+ebit_status launch_fields(ebit_ctx* c) {
+  const Layout& L = c->L;
+  const int b = c->cur;
+  ebit::k_fraction<R><<<L.grid, L.block, 0, c->stream>>>(
+      c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], L.d, (R*)c->C, c->partial, c->ctr);
+  ebit::k_area<<<1, 256, 0, c->stream>>>(c->partial, (long long)L.partial_count,
+                                         c->grid.dx * c->grid.dx, c->area);
+  ebit::k_curvature<R><<<L.grid, L.block, 0, c->stream>>>(
+      c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], (const R*)c->C, L.d,
+      (R)c->grid.dx, (R*)c->kappa, c->ctr);
+  EBIT_CK(cudaGetLastError());
+  return EBIT_OK;
+}
+
+ebit_status fields(ebit_ctx* c) {
+  return c->grid.prec == EBIT_FP32 ? launch_fields<float>(c) : launch_fields<double>(c);
+}
+
+template <typename R, int AX>
+ebit_status launch_sweep(ebit_ctx* c, const void* vel, double lam) {
+  const Layout& L = c->L;
+  const int src = c->cur, dst = 1 - c->cur;
+  ebit::View<R, AX> S{c->K[src], c->Z[src], (const R*)c->sH[src], (const R*)c->sV[src],
+                      (const R*)vel, L.d};
+  ebit::Buf<R> out{c->K[dst], c->Z[dst], (R*)c->sH[dst], (R*)c->sV[dst]};
+  ebit::k_sweep<R, AX><<<L.grid, L.block, 0, c->stream>>>(
+      S, out, (R)lam, (c->grid.flags & EBIT_FIT_LINE) ? 1 : 0, c->from_left, c->from_right,
+      c->ctr, c->cfl_bits, c->status);
+  ebit::View<R, AX> Sn{c->K[dst], c->Z[dst], (const R*)c->sH[dst], (const R*)c->sV[dst],
+                       (const R*)vel, L.d};
+  ebit::k_centre<R, AX><<<L.grid, L.block, 0, c->stream>>>(Sn, c->Z[src], c->Z[dst],
+                                                          c->from_left, c->from_right, c->ctr);
+  EBIT_CK(cudaGetLastError());
+  c->cur = dst;
+  return EBIT_OK;
+}
+
+ebit_status sweep(ebit_ctx* c, int axis, const void* vel, double lam) {
+  if (c->grid.prec == EBIT_FP32)
+    return axis == 0 ? launch_sweep<float, 0>(c, vel, lam) : launch_sweep<float, 1>(c, vel, lam);
+  return axis == 0 ? launch_sweep<double, 0>(c, vel, lam) : launch_sweep<double, 1>(c, vel, lam);
+}
+
+ebit_status reset_counters(ebit_ctx* c) {
+  EBIT_CK(cudaMemsetAsync(c->ctr, 0, ebit::kCounters * sizeof(unsigned long long), c->stream));
+  EBIT_CK(cudaMemsetAsync(c->cfl_bits, 0, sizeof(unsigned long long), c->stream));
+  return EBIT_OK;
+}
+
+ebit_status take_status(ebit_ctx* c) {
+  int st = 0;
+  EBIT_CK(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  EBIT_CK(cudaStreamSynchronize(c->stream));
+  if (st) {
+    EBIT_CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    EBIT_CK(cudaStreamSynchronize(c->stream));
+    if (st & ebit::ST_INVARIANT) return fail(EBIT_EINVARIANT, "colour/marker parity broken");
+    if (st & ebit::ST_CFL) return fail(EBIT_ECFL, "a marker moved more than one cell in a sweep");
+  }
+  return EBIT_OK;
+}
+
+ebit_status new_ctx(ebit_ctx** out, const ebit_grid* grid, void* stream) {
+  if (!out) return fail(EBIT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!valid_grid(grid)) return fail(EBIT_EINVAL, "invalid grid");
+  ebit_ctx* c = new (std::nothrow) ebit_ctx;
+  if (!c) return fail(EBIT_ENOMEM, "host allocation failed");
+  c->grid = *grid;
+  c->L = layout_of(grid);
+  c->stream = (cudaStream_t)stream;
+  const ebit_status s = alloc_ctx(c);
+  if (s != EBIT_OK) {
+    free_ctx(c);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return EBIT_OK;
+}
+
+template <typename R>
+ebit_status init_scene(ebit_ctx* c, const ebit_scene* scene) {
+  const Layout& L = c->L;
+  const double dx = c->grid.dx;
+  ebit::SceneDev sc{};
+  std::vector<double> circ;
+  for (int t = 0; t < scene->ncircles; ++t) {
+    circ.push_back(scene->circles[t].xc);
+    circ.push_back(scene->circles[t].yc);
+    circ.push_back(scene->circles[t].r);
+  }
+  std::vector<double> curve;
+  if (scene->curve) {
+    for (int k = 0; k < scene->curve->nmodes; ++k) curve.push_back(scene->curve->amp[k]);
+    for (int k = 0; k < scene->curve->nmodes; ++k) curve.push_back(scene->curve->phase[k]);
+  }
+  // scene arrays and scratch: freed at the end of the call
+  std::vector<void*> tmp;
+  auto talloc = [&](void** p, size_t bytes) -> ebit_status {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(EBIT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)); }
+    tmp.push_back(*p);
+    return EBIT_OK;
+  };
+  auto cleanup = [&]() { cudaStreamSynchronize(c->stream); for (void* p : tmp) cudaFree(p); };
+  double *dcirc = nullptr, *dcurve = nullptr, *hv = nullptr;
+  int *ownH = nullptr, *ownV = nullptr;
+  ebit_status s;
+  if ((s = talloc((void**)&dcirc, circ.size() * sizeof(double))) != EBIT_OK ||
+      (s = talloc((void**)&dcurve, curve.size() * sizeof(double))) != EBIT_OK ||
+      (s = talloc((void**)&hv, (size_t)(c->grid.nx + 1) * sizeof(double))) != EBIT_OK ||
+      (s = talloc((void**)&ownH, (size_t)(c->grid.ny + 1) * L.d.P * sizeof(int))) != EBIT_OK ||
+      (s = talloc((void**)&ownV, (size_t)(c->grid.ny + 1) * L.d.P * sizeof(int))) != EBIT_OK) {
+    cleanup();
+    return s;
+  }
+  auto run = [&]() -> ebit_status {
+    if (!circ.empty())
+      EBIT_CK(cudaMemcpyAsync(dcirc, circ.data(), circ.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (!curve.empty())
+      EBIT_CK(cudaMemcpyAsync(dcurve, curve.data(), curve.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    EBIT_CK(cudaMemsetAsync(ownH, 0x7f, (size_t)(c->grid.ny + 1) * L.d.P * sizeof(int), c->stream));
+    EBIT_CK(cudaMemsetAsync(ownV, 0x7f, (size_t)(c->grid.ny + 1) * L.d.P * sizeof(int), c->stream));
+    sc.circ = dcirc;
+    sc.ncircles = scene->ncircles;
+    if (scene->curve) {
+      sc.has_curve = 1;
+      sc.y0 = scene->curve->y0;
+      sc.nmodes = scene->curve->nmodes;
+      sc.amp = dcurve;
+      sc.phase = dcurve + scene->curve->nmodes;
+    }
+    if (scene->line) {
+      sc.has_line = 1;
+      sc.la = scene->line->a;
+      sc.lb = scene->line->b;
+      sc.lc = scene->line->c;
+    }
+    const int b = c->cur;
+    if (sc.has_curve) ebit::k_curve_cols<<<(c->grid.nx + 1 + 255) / 256, 256, 0, c->stream>>>(sc, c->grid.nx, dx, hv);
+    ebit::k_init_base<<<L.grid, L.block, 0, c->stream>>>(sc, L.d, dx, hv, c->K[b], c->Z[b]);
+    if (sc.ncircles > 0) {
+      ebit::k_init_circles<<<sc.ncircles, 256, 0, c->stream>>>(sc, L.d, dx, c->K[b], c->Z[b]);
+      ebit::k_init_owner<<<sc.ncircles, 256, 0, c->stream>>>(sc, L.d, dx, ownH, ownV);
+    }
+    ebit::k_init_roots<R><<<L.grid, L.block, 0, c->stream>>>(sc, L.d, dx, c->K[b], hv, ownH, ownV,
+                                                            (R*)c->sH[b], (R*)c->sV[b]);
+    EBIT_CK(cudaGetLastError());
+    return EBIT_OK;
+  };
+  s = run();
+  cleanup();
+  return s;
+}
+
+template <typename R>
+ebit_status load_state(ebit_ctx* c, const ebit_state_host* st) {
+  const Layout& L = c->L;
+  const int nx = c->grid.nx, ny = c->grid.ny;
+  const size_t nk = (size_t)(nx + 1) * (ny + 1), nz = (size_t)nx * ny;
+  const size_t nh = (size_t)nx * (ny + 1), nv = (size_t)(nx + 1) * ny;
+  uint8_t *dk = nullptr, *dz = nullptr;
+  double *dh = nullptr, *dv = nullptr;
+  std::vector<void*> tmp;
+  ebit_status s = EBIT_OK;
+  auto talloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) { cudaGetLastError(); return false; }
+    tmp.push_back(*p);
+    return true;
+  };
+  if (!talloc((void**)&dk, nk) || !talloc((void**)&dz, nz) || !talloc((void**)&dh, nh * 8) ||
+      !talloc((void**)&dv, nv * 8)) {
+    s = fail(EBIT_ENOMEM, "cudaMalloc failed in load_state");
+  } else {
+    const int b = c->cur;
+    const int T = 256;
+    cudaMemcpyAsync(dk, st->K, nk, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(dz, st->Z, nz, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(dh, st->sH, nh * 8, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(dv, st->sV, nv * 8, cudaMemcpyHostToDevice, c->stream);
+    ebit::k_pack_bits<<<dim3((nx + 1 + 31) / 32, (ny + 1 + ebit::kBlockY - 1) / ebit::kBlockY), L.block, 0, c->stream>>>(
+        dk, nx + 1, ny + 1, L.d.kw, c->K[b]);
+    ebit::k_pack_bits<<<dim3((nx + 31) / 32, (ny + ebit::kBlockY - 1) / ebit::kBlockY), L.block, 0, c->stream>>>(
+        dz, nx, ny, L.d.zw, c->Z[b]);
+    ebit::k_load_frac<R><<<(unsigned)((nh + T - 1) / T), T, 0, c->stream>>>(dh, nx, ny + 1, L.d.P, (R*)c->sH[b]);
+    ebit::k_load_frac<R><<<(unsigned)((nv + T - 1) / T), T, 0, c->stream>>>(dv, nx + 1, ny, L.d.P, (R*)c->sV[b]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) s = fail(EBIT_ECUDA, "load_state: %s", cudaGetErrorString(e));
+  }
+  cudaStreamSynchronize(c->stream);
+  for (void* p : tmp) cudaFree(p);
+  if (s != EBIT_OK) return s;
+  c->step_index = st->step_index;
+  if ((s = reset_counters(c)) != EBIT_OK) return s;
+  if ((s = fields(c)) != EBIT_OK) return s;
+  EBIT_CK(cudaStreamSynchronize(c->stream));
+  return EBIT_OK;
+}
+
+template <typename R>
+ebit_status get_state(ebit_ctx* c, ebit_state_host* st) {
+  const Layout& L = c->L;
+  const int nx = c->grid.nx, ny = c->grid.ny;
+  const size_t nk = (size_t)(nx + 1) * (ny + 1), nz = (size_t)nx * ny;
+  const size_t nh = (size_t)nx * (ny + 1), nv = (size_t)(nx + 1) * ny;
+  uint8_t *dk = nullptr, *dz = nullptr;
+  double *dh = nullptr, *dv = nullptr;
+  std::vector<void*> tmp;
+  ebit_status s = EBIT_OK;
+  auto talloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) { cudaGetLastError(); return false; }
+    tmp.push_back(*p);
+    return true;
+  };
+  if (!talloc((void**)&dk, nk) || !talloc((void**)&dz, nz) || !talloc((void**)&dh, nh * 8) ||
+      !talloc((void**)&dv, nv * 8)) {
+    s = fail(EBIT_ENOMEM, "cudaMalloc failed in get_state");
+  } else {
+    const int b = c->cur;
+    const int T = 256;
+    ebit::k_unpack_bits<<<(unsigned)((nk + T - 1) / T), T, 0, c->stream>>>(c->K[b], nx + 1, ny + 1, L.d.kw, dk);
+    ebit::k_unpack_bits<<<(unsigned)((nz + T - 1) / T), T, 0, c->stream>>>(c->Z[b], nx, ny, L.d.zw, dz);
+    ebit::k_store_frac<R><<<(unsigned)((nh + T - 1) / T), T, 0, c->stream>>>((const R*)c->sH[b], nx, ny + 1, L.d.P, dh);
+    ebit::k_store_frac<R><<<(unsigned)((nv + T - 1) / T), T, 0, c->stream>>>((const R*)c->sV[b], nx + 1, ny, L.d.P, dv);
+    cudaMemcpyAsync(st->K, dk, nk, cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(st->Z, dz, nz, cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(st->sH, dh, nh * 8, cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(st->sV, dv, nv * 8, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) s = fail(EBIT_ECUDA, "get_state: %s", cudaGetErrorString(e));
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  for (void* p : tmp) cudaFree(p);
+  if (s != EBIT_OK) return s;
+  if (e != cudaSuccess) return fail(EBIT_ECUDA, "get_state: %s", cudaGetErrorString(e));
+  st->step_index = c->step_index;
+  return take_status(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ebit_last_error(void) { return g_err.c_str(); }
+
+size_t ebit_footprint(const ebit_grid* grid) {
+  if (!valid_grid(grid)) return 0;
+  return layout_of(grid).total();
+}
+
+ebit_status ebit_create(ebit_ctx** out, const ebit_grid* grid, void* stream) {
+  ebit_status s = new_ctx(out, grid, stream);
+  if (s != EBIT_OK) return s;
+  if ((s = fields(*out)) != EBIT_OK) return s;
+  return EBIT_OK;
+}
+
+ebit_status ebit_init(ebit_ctx** out, const ebit_grid* grid, const ebit_scene* scene, void* stream) {
+  if (!scene || scene->ncircles < 0 || (scene->ncircles > 0 && !scene->circles) ||
+      (scene->curve && (scene->curve->nmodes < 0 || (scene->curve->nmodes > 0 &&
+                                                     (!scene->curve->amp || !scene->curve->phase)))) ||
+      (scene->line && scene->line->a == 0.0 && scene->line->b == 0.0 && scene->line->c < 0.0))
+    return fail(EBIT_EINVAL, "invalid scene");
+  ebit_status s = new_ctx(out, grid, stream);
+  if (s != EBIT_OK) return s;
+  ebit_ctx* c = *out;
+  s = c->grid.prec == EBIT_FP32 ? init_scene<float>(c, scene) : init_scene<double>(c, scene);
+  if (s == EBIT_OK) s = reset_counters(c);
+  if (s == EBIT_OK) s = fields(c);
+  if (s != EBIT_OK) {
+    ebit_destroy(c);
+    *out = nullptr;
+  }
+  return s;
+}
+
+ebit_status ebit_load_state(ebit_ctx* c, const ebit_state_host* st) {
+  if (!c || !st || !st->K || !st->Z || !st->sH || !st->sV) return fail(EBIT_EINVAL, "NULL argument");
+  if (st->nx != c->grid.nx || st->ny != c->grid.ny) return fail(EBIT_EINVAL, "state size mismatch");
+  return c->grid.prec == EBIT_FP32 ? load_state<float>(c, st) : load_state<double>(c, st);
+}
+
+ebit_status ebit_get_state(ebit_ctx* c, ebit_state_host* st) {
+  if (!c || !st || !st->K || !st->Z || !st->sH || !st->sV) return fail(EBIT_EINVAL, "NULL argument");
+  if (st->nx != c->grid.nx || st->ny != c->grid.ny) return fail(EBIT_EINVAL, "state size mismatch");
+  return c->grid.prec == EBIT_FP32 ? get_state<float>(c, st) : get_state<double>(c, st);
+}
+
+ebit_status ebit_step(ebit_ctx* c, const void* u, const void* v, double dt) {
+  if (!c || !u || !v) return fail(EBIT_EINVAL, "NULL argument");
+  if (!(dt == dt)) return fail(EBIT_EINVAL, "dt is NaN");
+  ebit_status s = reset_counters(c);
+  if (s != EBIT_OK) return s;
+  const double lam = dt / c->grid.dx;
+  const bool x_first = (c->step_index & 1) == 0;
+  if ((s = sweep(c, x_first ? 0 : 1, x_first ? u : v, lam)) != EBIT_OK) return s;
+  if ((s = sweep(c, x_first ? 1 : 0, x_first ? v : u, lam)) != EBIT_OK) return s;
+  if ((s = fields(c)) != EBIT_OK) return s;
+  c->step_index += 1;
+  return EBIT_OK;
+}
+
+ebit_status ebit_sweep(ebit_ctx* c, int axis, const void* vel, double dt) {
+  if (!c || !vel || (axis != 0 && axis != 1)) return fail(EBIT_EINVAL, "bad argument");
+  ebit_status s = reset_counters(c);
+  if (s != EBIT_OK) return s;
+  return sweep(c, axis, vel, dt / c->grid.dx);
+}
+
+ebit_status ebit_fraction(ebit_ctx* c, void* C_dev, double* area_host) {
+  if (!c) return fail(EBIT_EINVAL, "NULL context");
+  const Layout& L = c->L;
+  if (C_dev)
+    EBIT_CK(cudaMemcpy2DAsync(C_dev, (size_t)c->grid.nx * L.esz, c->C, (size_t)L.d.P * L.esz,
+                              (size_t)c->grid.nx * L.esz, c->grid.ny, cudaMemcpyDeviceToDevice,
+                              c->stream));
+  if (area_host) {
+    EBIT_CK(cudaMemcpyAsync(area_host, c->area, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return take_status(c);
+  }
+  return EBIT_OK;
+}
+
+ebit_status ebit_curvature(ebit_ctx* c, void* kappa_dev, int32_t* n_invalid_host) {
+  if (!c) return fail(EBIT_EINVAL, "NULL context");
+  const Layout& L = c->L;
+  if (kappa_dev)
+    EBIT_CK(cudaMemcpy2DAsync(kappa_dev, (size_t)c->grid.nx * L.esz, c->kappa,
+                              (size_t)L.d.P * L.esz, (size_t)c->grid.nx * L.esz, c->grid.ny,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  if (n_invalid_host) {
+    unsigned long long n = 0;
+    EBIT_CK(cudaMemcpyAsync(&n, c->ctr + ebit::D_HF_INVALID, sizeof n, cudaMemcpyDeviceToHost, c->stream));
+    ebit_status s = take_status(c);
+    *n_invalid_host = (int32_t)n;
+    return s;
+  }
+  return EBIT_OK;
+}
+
+ebit_status ebit_fields(ebit_ctx* c, const void** C, const void** kappa, int64_t* pitch) {
+  if (!c) return fail(EBIT_EINVAL, "NULL context");
+  if (C) *C = c->C;
+  if (kappa) *kappa = c->kappa;
+  if (pitch) *pitch = c->L.d.P;
+  return EBIT_OK;
+}
+
+ebit_status ebit_diagnostics(ebit_ctx* c, ebit_diag* out) {
+  if (!c || !out) return fail(EBIT_EINVAL, "NULL argument");
+  unsigned long long ctr[ebit::kCounters], bits = 0;
+  double area = 0.0;
+  EBIT_CK(cudaMemcpyAsync(ctr, c->ctr, sizeof ctr, cudaMemcpyDeviceToHost, c->stream));
+  EBIT_CK(cudaMemcpyAsync(&bits, c->cfl_bits, sizeof bits, cudaMemcpyDeviceToHost, c->stream));
+  EBIT_CK(cudaMemcpyAsync(&area, c->area, sizeof area, cudaMemcpyDeviceToHost, c->stream));
+  EBIT_CK(cudaStreamSynchronize(c->stream));
+  for (int t = 0; t < EBIT_D_COUNT; ++t) out->c[t] = (int64_t)ctr[t];
+  out->area = area;
+  double m;
+  std::memcpy(&m, &bits, sizeof m);
+  out->max_cfl = m;
+  return take_status(c);
+}
+
+ebit_status ebit_sync(ebit_ctx* c) {
+  if (!c) return fail(EBIT_EINVAL, "NULL context");
+  EBIT_CK(cudaStreamSynchronize(c->stream));
+  return take_status(c);
+}
+
+void ebit_destroy(ebit_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,509 @@
+// Device code of the EBIT step (Pan et al., arXiv:2309.00338, Sec. 2.1-2.5).
+//
+// State of one grid in HBM (element pitch P, a multiple of 32, for the edge
+// and cell arrays):
+//   K  corner colour vertices, 1 bit per vertex, rows of kw 32-bit words
+//   Z  centre colour vertices, 1 bit per cell, rows of zw words
+//   sH marker fraction on horizontal edge (i,j), row j, element i
+//   sV marker fraction on vertical edge (i,j),   row j, element i
+// A marker exists exactly where the corner colours at the ends of its edge
+// differ (Sec. 2.4); fractions of edges without a marker are don't-care.
+//
+// One split sweep is written once, for the x direction, on a "view" of the
+// state: AX = 0 reads the grid as it is, AX = 1 reads it transposed (vertex
+// (i,j) is stored vertex (j,i), horizontal and vertical edges swap), which
+// turns the y sweep into an x sweep.  Every decision is taken with the exact
+// integer predicate "left of grid line k" <=> ix < k on moved points stored
+// as (grid line index, fraction), so corner flips and chord crossings agree.
+// The library is compiled with -fmad=false: every expression below is the
+// sequence of IEEE operations it spells.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ebit {
+
+enum {
+  D_NH = 0, D_NV, D_CANCELLED, D_ZSET, D_ZCONFLICT, D_FIT_ONLINE, D_FIT_LINE, D_FIT_ONE,
+  D_FIT_TWO, D_WALL_CLAMP, D_INVARIANT, D_HF_INVALID, D_CFL, D_NUSED
+};
+constexpr int kCounters = 16;
+enum { ST_CFL = 1, ST_INVARIANT = 2 };
+
+// Two points closer than 0.01 cell do not define a usable circle (Sec. 2.2).
+constexpr double kMinSep2 = 1e-4;
+
+template <typename R> __device__ __forceinline__ R below_one();
+template <> __device__ __forceinline__ float below_one<float>() { return __int_as_float(0x3f7fffff); }
+template <> __device__ __forceinline__ double below_one<double>() {
+  return __longlong_as_double(0x3fefffffffffffffLL);
+}
+
+// Pointers of one state buffer.
+template <typename R>
+struct Buf {
+  uint32_t* K;
+  uint32_t* Z;
+  R* sH;
+  R* sV;
+};
+
+struct Dims {
+  int nx, ny;     // cells
+  int kw, zw;     // words per row of K and Z
+  long long P;    // element pitch of sH, sV, C, kappa
+};
+
+// Read view of a state in sweep coordinates (see the file comment).
+template <typename R, int AX>
+struct View {
+  const uint32_t* __restrict__ K;
+  const uint32_t* __restrict__ Z;
+  const R* __restrict__ sH;
+  const R* __restrict__ sV;
+  const R* __restrict__ w;  // velocity component along the sweep, (ny+1)x(nx+1)
+  Dims d;
+  __device__ __forceinline__ int tnx() const { return AX ? d.ny : d.nx; }
+  __device__ __forceinline__ int tny() const { return AX ? d.nx : d.ny; }
+  __device__ __forceinline__ int kreal(int x, int y) const {
+    return (__ldg(&K[(long long)y * d.kw + (x >> 5)]) >> (x & 31)) & 1;
+  }
+  __device__ __forceinline__ int k(int i, int j) const { return AX ? kreal(j, i) : kreal(i, j); }
+  __device__ __forceinline__ int z(int i, int j) const {
+    const int x = AX ? j : i, y = AX ? i : j;
+    return (__ldg(&Z[(long long)y * d.zw + (x >> 5)]) >> (x & 31)) & 1;
+  }
+  __device__ __forceinline__ R h(int i, int j) const {
+    return AX ? __ldg(&sV[(long long)i * d.P + j]) : __ldg(&sH[(long long)j * d.P + i]);
+  }
+  __device__ __forceinline__ R v(int i, int j) const {
+    return AX ? __ldg(&sH[(long long)i * d.P + j]) : __ldg(&sV[(long long)j * d.P + i]);
+  }
+  __device__ __forceinline__ R vel(int i, int j) const {
+    return AX ? __ldg(&w[(long long)i * (d.nx + 1) + j]) : __ldg(&w[(long long)j * (d.nx + 1) + i]);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Cell topology.  Corner c of cell (i,j) counter-clockwise from (i,j); edge e
+// joins corners e and e+1 (0 bottom, 1 right, 2 top, 3 left).
+// ---------------------------------------------------------------------------
+template <typename R, int AX>
+__device__ __forceinline__ int corner_mask(const View<R, AX>& S, int i, int j) {
+  return S.k(i, j) | (S.k(i + 1, j) << 1) | (S.k(i + 1, j + 1) << 2) | (S.k(i, j + 1) << 3);
+}
+__device__ __forceinline__ int edge_mask(int q) { return (q ^ ((q >> 1) | ((q & 1) << 3))) & 15; }
+
+// Segments of the implicit connectivity (Sec. 2.3, Fig. 4): two markers are
+// joined; with four, each corner whose colour differs from the centre colour
+// is cut off by the segment joining the markers of its two edges.
+__device__ __forceinline__ int segments(int q, int zc, int seg[2][2]) {
+  const int em = edge_mask(q);
+  if (em == 0) return 0;
+  if (em != 15) {
+    seg[0][0] = __ffs(em) - 1;
+    seg[0][1] = 31 - __clz(em);
+    return 1;
+  }
+  int m = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    if (((q >> c) & 1) != zc) {
+      seg[m][0] = (c + 3) & 3;
+      seg[m][1] = c;
+      ++m;
+    }
+  return m;
+}
+
+struct Mk {
+  int kind;  // 0 horizontal edge, 1 vertical edge, -1 none
+  int i, j;
+};
+
+__device__ __forceinline__ Mk edge_marker(int ci, int cj, int e) {
+  Mk m;
+  m.kind = e & 1;
+  m.i = ci + (e == 1);
+  m.j = cj + (e == 2);
+  return m;
+}
+
+template <typename R, int AX>
+__device__ __forceinline__ int cell_segments(const View<R, AX>& S, int i, int j, int seg[2][2]) {
+  const int q = corner_mask(S, i, j);
+  return segments(q, edge_mask(q) == 15 ? S.z(i, j) : 0, seg);
+}
+
+template <typename R, int AX>
+__device__ int partner(const View<R, AX>& S, int ci, int cj, int e) {
+  int seg[2][2];
+  const int n = cell_segments(S, ci, cj, seg);
+  for (int t = 0; t < n; ++t) {
+    if (seg[t][0] == e) return seg[t][1];
+    if (seg[t][1] == e) return seg[t][0];
+  }
+  return -1;
+}
+
+// The marker next to m along the interface on the far side of m's edge, seen
+// from cell (ci,cj); writes the cell it lies in.
+template <typename R, int AX>
+__device__ Mk beyond(const View<R, AX>& S, Mk m, int ci, int cj, int* oi_, int* oj_) {
+  int oi, oj, oe;
+  if (m.kind == 0) {
+    oi = m.i;
+    if (cj == m.j) { oj = m.j - 1; oe = 2; } else { oj = m.j; oe = 0; }
+  } else {
+    oj = m.j;
+    if (ci == m.i) { oi = m.i - 1; oe = 1; } else { oi = m.i; oe = 3; }
+  }
+  Mk none{-1, 0, 0};
+  if (oi < 0 || oj < 0 || oi >= S.tnx() || oj >= S.tny()) return none;
+  const int pe = partner(S, oi, oj, oe);
+  if (pe < 0) return none;
+  *oi_ = oi;
+  *oj_ = oj;
+  return edge_marker(oi, oj, pe);
+}
+
+// ---------------------------------------------------------------------------
+// Advection along the sweep (Eq. 4).  A moved point is (ix, fx): grid line at
+// or left of it and a fraction in [0,1); y = jy + fy is unchanged.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct AP {
+  int ix;
+  R fx;
+  int jy;
+  R fy;
+};
+
+struct Flags {
+  int cfl = 0, clamp = 0;
+  double dabs = 0.0;
+};
+
+// Velocity by linear interpolation along the marker's edge (the bilinear
+// interpolation of Sec. 2.1 on a grid line); displacement in cells, clipped to
+// one cell with the CFL flag raised beyond it.
+template <typename R>
+__device__ __forceinline__ R displacement(R s, R ua, R ub, R lam, Flags& f) {
+  const R vel = (R(1) - s) * ua + s * ub;
+  R d = vel * lam;
+  const double ad = fabs((double)d);
+  if (ad == ad && ad > f.dabs) f.dabs = ad;
+  if (!(fabs(d) <= R(1))) {
+    f.cfl = 1;
+    d = (d > R(0)) ? R(1) : R(-1);
+  }
+  return d;
+}
+
+template <typename R, int AX>
+__device__ AP<R> advect(const View<R, AX>& S, R lam, Mk m, Flags& f) {
+  const int nx = S.tnx();
+  AP<R> p;
+  p.jy = m.j;
+  if (m.kind == 0) {
+    // aligned marker: along its own line
+    const R s = S.h(m.i, m.j);
+    const R d = displacement(s, S.vel(m.i, m.j), S.vel(m.i + 1, m.j), lam, f);
+    const R t = s + d;
+    const R fl = floor(t);
+    R fx = t - fl;
+    int sh = (int)fl;
+    if (sh > 1) { sh = 1; fx = below_one<R>(); }
+    if (fx >= R(1)) fx = below_one<R>();
+    int ix = m.i + sh;
+    if (ix < 0) { ix = 0; fx = R(0); f.clamp = 1; }
+    else if (ix > nx - 1) { ix = nx - 1; fx = below_one<R>(); f.clamp = 1; }
+    p.ix = ix;
+    p.fx = fx;
+    p.fy = R(0);
+    return p;
+  }
+  const R s = S.v(m.i, m.j);
+  p.fy = s;
+  if (m.i == 0 || m.i == nx) {  // wall markers normal to the sweep stay
+    p.ix = m.i;
+    p.fx = R(0);
+    return p;
+  }
+  // unaligned marker: the gray point of Fig. 2c
+  const R d = displacement(s, S.vel(m.i, m.j), S.vel(m.i, m.j + 1), lam, f);
+  const R fl = floor(d);
+  R fx = d - fl;
+  if (fx >= R(1)) fx = below_one<R>();
+  p.ix = m.i + (int)fl;
+  p.fx = fx;
+  return p;
+}
+
+template <typename R, int AX>
+__device__ __forceinline__ AP<R> moved(const View<R, AX>& S, R lam, Mk m) {
+  Flags f;
+  return advect(S, lam, m, f);
+}
+
+// New corner colour (Sec. 2.3, Fig. 5): vertex i of line j flips once for each
+// aligned marker that passes it; only markers of edges i-1 and i can.
+template <typename R, int AX>
+__device__ int knew(const View<R, AX>& S, R lam, int i, int j) {
+  const int c = S.k(i, j);
+  int r = c;
+  if (i >= 1 && S.k(i - 1, j) != c && moved(S, lam, Mk{0, i - 1, j}).ix >= i) r ^= 1;
+  if (i < S.tnx() && S.k(i + 1, j) != c && moved(S, lam, Mk{0, i, j}).ix < i) r ^= 1;
+  return r;
+}
+
+// Aligned markers landing on edge (i,j) (Sec. 2.4): kept only where the new
+// end colours differ; an odd count keeps the median by (fraction, source).
+template <typename R>
+struct Landing {
+  int present, kept_src, cancelled, invariant;
+  R kept_fx;
+};
+
+template <typename R, int AX>
+__device__ Landing<R> landing(const View<R, AX>& S, R lam, int i, int j) {
+  R fx[3];
+  int src[3];
+  int n = 0;
+  for (int e = i - 1; e <= i + 1; ++e) {
+    if (e < 0 || e >= S.tnx() || S.k(e, j) == S.k(e + 1, j)) continue;
+    const AP<R> p = moved(S, lam, Mk{0, e, j});
+    if (p.ix == i) { fx[n] = p.fx; src[n] = e; ++n; }
+  }
+  for (int a = 1; a < n; ++a)  // sort by (fx, src)
+    for (int b = a; b > 0 && (fx[b] < fx[b - 1] || (fx[b] == fx[b - 1] && src[b] < src[b - 1])); --b) {
+      const R tf = fx[b]; fx[b] = fx[b - 1]; fx[b - 1] = tf;
+      const int ts = src[b]; src[b] = src[b - 1]; src[b - 1] = ts;
+    }
+  Landing<R> L;
+  L.present = knew(S, lam, i, j) ^ knew(S, lam, i + 1, j);
+  L.kept_src = -1;
+  L.kept_fx = R(0.5);
+  L.cancelled = 0;
+  L.invariant = 0;
+  if (L.present && (n & 1)) {
+    L.kept_src = src[n / 2];
+    L.kept_fx = fx[n / 2];
+  } else if (!L.present && !(n & 1)) {
+    L.cancelled = n / 2;
+  } else {
+    L.invariant = 1;
+    if (L.present && n > 0) {
+      int best = 0;
+      for (int t = 1; t < n; ++t)
+        if (fabs((double)fx[t] - 0.5) < fabs((double)fx[best] - 0.5)) best = t;
+      L.kept_src = src[best];
+      L.kept_fx = fx[best];
+    }
+  }
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// Circle fit (Sec. 2.2, Fig. 3).  Coordinates in cells relative to vertex
+// (k,j): the grid line is x = 0, the edge's band 0 <= y <= 1.  Circle through
+// A, B, T with origin at A: kap (x^2+y^2) + al x + be y = 0 (a line when
+// kap = 0).  The crossing wanted lies on the arc A..B that does not contain
+// T, i.e. on the other side of chord AB from T.
+// ---------------------------------------------------------------------------
+__device__ bool circle_cross(double Ax, double Ay, double Bx, double By, double Tx, double Ty,
+                             double* y) {
+  const double qx = Bx - Ax, qy = By - Ay;
+  const double rx = Tx - Ax, ry = Ty - Ay;
+  const double tx = Tx - Bx, ty = Ty - By;
+  const double q2 = qx * qx + qy * qy;
+  const double r2 = rx * rx + ry * ry;
+  if (r2 < kMinSep2 || tx * tx + ty * ty < kMinSep2) return false;
+  const double kap = qx * ry - qy * rx;
+  const double al = r2 * qy - q2 * ry;
+  const double be = q2 * rx - r2 * qx;
+  const double x0 = -Ax;
+  const double c0 = x0 * (kap * x0 + al);
+  const double disc = be * be - 4.0 * kap * c0;
+  if (!(disc >= 0.0)) return false;
+  const double sq = sqrt(disc);
+  const double h = -0.5 * (be + copysign(sq, be));
+  if (h == 0.0) return false;
+  const double ya = c0 / h;
+  double yrel = ya;
+  if (kap != 0.0) {
+    const double yb = h / kap;
+    const double sa = qx * ya - qy * x0;
+    const double sb = qx * yb - qy * x0;
+    const bool a_with_T = (sa > 0.0 && kap > 0.0) || (sa < 0.0 && kap < 0.0);
+    const bool b_with_T = (sb > 0.0 && kap > 0.0) || (sb < 0.0 && kap < 0.0);
+    if (a_with_T && !b_with_T) yrel = yb;
+  }
+  const double best = Ay + yrel;
+  if (!(best >= 0.0 && best <= 1.0)) return false;
+  *y = best;
+  return true;
+}
+
+// Returns the fit kind (D_FIT_*) and the crossing ordinate.
+__device__ int fit_crossing(double Ax, double Ay, double Bx, double By, bool h1, double P1x,
+                            double P1y, bool h4, double P4x, double P4y, bool line_only,
+                            double* y) {
+  if (Bx == 0.0) {
+    *y = By;
+    return D_FIT_ONLINE;
+  }
+  const double x0 = -Ax;
+  const double ystar = Ay + (x0 * (By - Ay)) / (Bx - Ax);
+  const double cx = Bx - Ax, cy = By - Ay;
+  if (!line_only && cx * cx + cy * cy >= kMinSep2) {
+    double ys0 = 0.0, ys1 = 0.0;
+    int n = 0;
+    if (h1 && circle_cross(Ax, Ay, Bx, By, P1x, P1y, &ys0)) ++n;
+    if (h4) {
+      double t;
+      if (circle_cross(Ax, Ay, Bx, By, P4x, P4y, &t)) {
+        if (n == 0) ys0 = t; else ys1 = t;
+        ++n;
+      }
+    }
+    if (n == 2) { *y = 0.5 * (ys0 + ys1); return D_FIT_TWO; }
+    if (n == 1) { *y = ys0; return D_FIT_ONE; }
+  }
+  *y = ystar;
+  return D_FIT_LINE;
+}
+
+template <typename R>
+__device__ __forceinline__ R to_fraction(double y) {
+  R s = (R)y;
+  if (!(s >= R(0))) s = R(0);
+  if (s >= R(1)) s = below_one<R>();
+  return s;
+}
+
+template <typename R>
+__device__ __forceinline__ void local_xy(const AP<R>& p, int k, int j, double* X, double* Y) {
+  *X = (double)(p.ix - k) + (double)p.fx;
+  *Y = (double)(p.jy - j) + (double)p.fy;
+}
+
+// Centre rule (Sec. 2.3): from the new unaligned marker follow the moved
+// interface through m0 then m1 while they stay in column col; the first
+// aligned marker met that survives the sweep is the partner.  Returns the
+// partner's line, or -1 when no aligned marker is reached.
+template <typename R, int AX>
+__device__ int walk(const View<R, AX>& S, R lam, Mk m0, Mk m1, int col) {
+  Mk pts[2] = {m0, m1};
+  for (int t = 0; t < 2; ++t) {
+    const Mk m = pts[t];
+    if (m.kind < 0) return -1;
+    const AP<R> p = moved(S, lam, m);
+    if (p.ix != col) return -1;
+    if (m.kind == 0) {
+      const Landing<R> L = landing(S, lam, p.ix, m.j);
+      return (L.present && L.kept_src == m.i) ? m.j : -1;
+    }
+  }
+  return -1;
+}
+
+// The next marker along the interface beyond nb (found in cell ci,cj) when
+// nb is closer than the minimum separation to the point (fx,fy).
+template <typename R, int AX>
+__device__ bool far_point(const View<R, AX>& S, R lam, Mk nb, int ci, int cj, int k, int j,
+                          double fx, double fy, double* X, double* Y) {
+  if (nb.kind < 0) return false;
+  local_xy(moved(S, lam, nb), k, j, X, Y);
+  const double ex = *X - fx, ey = *Y - fy;
+  if (ex * ex + ey * ey < kMinSep2) {
+    int oi = 0, oj = 0;
+    const Mk nn = beyond(S, nb, ci, cj, &oi, &oj);
+    if (nn.kind < 0) return false;
+    local_xy(moved(S, lam, nn), k, j, X, Y);
+  }
+  return true;
+}
+
+// New unaligned marker on interior vertical edge (k,j) (Fig. 2c/2d): the
+// moved chords of the old segments of cells k-2..k that cross line k are the
+// candidates; one is kept where the new end colours differ.
+template <typename R>
+struct NewV {
+  int present, vr, vl;
+  R s;
+};
+
+template <typename R, int AX>
+__device__ NewV<R> new_unaligned(const View<R, AX>& S, R lam, bool line_only, int k, int j,
+                                 int* cnt) {
+  double cy[6];
+  int cvr[6], cvl[6], ord[6];
+  int n = 0;
+  for (int c = k - 2; c <= k; ++c) {
+    if (c < 0 || c >= S.tnx()) continue;
+    int seg[2][2];
+    const int ns = cell_segments(S, c, j, seg);
+    for (int t = 0; t < ns; ++t) {
+      const Mk ma = edge_marker(c, j, seg[t][0]);
+      const Mk mb = edge_marker(c, j, seg[t][1]);
+      const AP<R> pa = moved(S, lam, ma), pb = moved(S, lam, mb);
+      const int lo = min(pa.ix, pb.ix), hi = max(pa.ix, pb.ix);
+      if (!(k > lo && k <= hi)) continue;
+      const bool a_left = pa.ix < k;
+      const Mk mA = a_left ? ma : mb, mB = a_left ? mb : ma;
+      const AP<R> A = a_left ? pa : pb, B = a_left ? pb : pa;
+      int c1i = 0, c1j = 0, c4i = 0, c4j = 0;
+      const Mk n1 = beyond(S, mA, c, j, &c1i, &c1j);
+      const Mk n4 = beyond(S, mB, c, j, &c4i, &c4j);
+      double ax, ay, bx, by, p1x = 0, p1y = 0, p4x = 0, p4y = 0;
+      local_xy(A, k, j, &ax, &ay);
+      local_xy(B, k, j, &bx, &by);
+      const bool h1 = far_point(S, lam, n1, c1i, c1j, k, j, ax, ay, &p1x, &p1y);
+      const bool h4 = far_point(S, lam, n4, c4i, c4j, k, j, bx, by, &p4x, &p4y);
+      double y;
+      const int kind = fit_crossing(ax, ay, bx, by, h1, p1x, p1y, h4, p4x, p4y, line_only, &y);
+      cnt[kind] += 1;
+      const int lr = walk(S, lam, mB, n4, k);
+      const int ll = walk(S, lam, mA, n1, k - 1);
+      cy[n] = y;
+      cvr[n] = lr < 0 ? -1 : !knew(S, lam, k, lr);
+      cvl[n] = ll < 0 ? -1 : !knew(S, lam, k, ll);
+      ord[n] = n;
+      ++n;
+    }
+  }
+  for (int a = 1; a < n; ++a)  // sort by (y, generation order)
+    for (int b = a; b > 0 && (cy[b] < cy[b - 1] || (cy[b] == cy[b - 1] && ord[b] < ord[b - 1])); --b) {
+      const double t = cy[b]; cy[b] = cy[b - 1]; cy[b - 1] = t;
+      int u = cvr[b]; cvr[b] = cvr[b - 1]; cvr[b - 1] = u;
+      u = cvl[b]; cvl[b] = cvl[b - 1]; cvl[b - 1] = u;
+      u = ord[b]; ord[b] = ord[b - 1]; ord[b - 1] = u;
+    }
+  NewV<R> out;
+  out.present = knew(S, lam, k, j) ^ knew(S, lam, k, j + 1);
+  out.vr = -1;
+  out.vl = -1;
+  out.s = R(0.5);
+  int pick = -1;
+  if (out.present && (n & 1)) {
+    pick = n / 2;
+  } else if (!out.present && !(n & 1)) {
+    cnt[D_CANCELLED] += n / 2;
+  } else {
+    cnt[D_INVARIANT] += 1;
+    if (out.present && n > 0) {
+      pick = 0;
+      for (int t = 1; t < n; ++t)
+        if (fabs(cy[t] - 0.5) < fabs(cy[pick] - 0.5)) pick = t;
+    }
+  }
+  if (pick >= 0) {
+    out.s = to_fraction<R>(cy[pick]);
+    out.vr = cvr[pick];
+    out.vl = cvl[pick];
+  }
+  return out;
+}
+
+}  // namespace ebit

@@ -1,0 +1,510 @@
+// Kernels of the EBIT step: the two passes of a split sweep, volume
+// fractions, height-function curvature, initialisation and state I/O.
+// Threads map to vertices of the real grid: a warp is 32 consecutive x of one
+// row, aligned to 32, so colour bits pack into 32-bit words with a ballot.
+#pragma once
+#include "ebit_device.cuh"
+
+namespace ebit {
+
+constexpr int kBlockY = 8;  // blocks are 32 x kBlockY threads
+
+__device__ __forceinline__ void flush_counters(const int* cnt, unsigned long long* ctr) {
+#pragma unroll
+  for (int c = 0; c < D_NUSED; ++c) {
+    const int v = __reduce_add_sync(0xffffffffu, cnt[c]);
+    if (v != 0 && (threadIdx.x & 31) == 0) atomicAdd(&ctr[c], (unsigned long long)v);
+  }
+}
+
+__device__ __forceinline__ void raise_status(int* status, const int* cnt) {
+  if (cnt[D_CFL]) atomicOr(status, ST_CFL);
+  if (cnt[D_INVARIANT]) atomicOr(status, ST_INVARIANT);
+}
+
+// Pass 1 of a sweep.  Thread at real vertex (x,y) = sweep vertex (i,j):
+//   new corner colour of vertex (i,j), new aligned marker on edge (i,j),
+//   new unaligned marker on edge (i,j) with the centre-rule verdicts it gives
+//   to the cells right (from_left) and left (from_right) of it.
+template <typename R, int AX>
+__global__ void __launch_bounds__(32 * kBlockY)
+k_sweep(View<R, AX> S, Buf<R> out, R lam, int line_only, int8_t* from_left, int8_t* from_right,
+        unsigned long long* ctr, unsigned long long* cfl_bits, int* status) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.y;
+  const Dims& d = S.d;
+  const bool in = x <= d.nx && y <= d.ny;
+  const int i = AX ? y : x, j = AX ? x : y;
+  const int tnx = S.tnx(), tny = S.tny();
+  int cnt[D_NUSED];
+#pragma unroll
+  for (int c = 0; c < D_NUSED; ++c) cnt[c] = 0;
+  double dmax = 0.0;
+  int kb = 0;
+  if (in) {
+    kb = S.k(i, j);
+    // Anything to do?  Only if a colour changes along vertex rows j, j+1
+    // within columns i-2..i+2 (all markers this thread looks at live there).
+    bool busy = false;
+    const int c0 = max(i - 2, 0), c1 = min(i + 2, tnx);
+    const int ref = S.k(c0, j);
+    for (int r = j; r <= min(j + 1, tny) && !busy; ++r)
+      for (int c = c0; c <= c1; ++c)
+        if (S.k(c, r) != ref) { busy = true; break; }
+    if (busy) {
+      kb = knew(S, lam, i, j);
+      if (i < tnx) {
+        if (S.k(i, j) != S.k(i + 1, j)) {
+          Flags f;
+          advect(S, lam, Mk{0, i, j}, f);
+          cnt[D_CFL] += f.cfl;
+          cnt[D_WALL_CLAMP] += f.clamp;
+          dmax = fmax(dmax, f.dabs);
+        }
+        const Landing<R> L = landing(S, lam, i, j);
+        cnt[D_CANCELLED] += L.cancelled;
+        cnt[D_INVARIANT] += L.invariant;
+        if (L.present) {
+          if (AX) out.sV[(long long)i * d.P + j] = L.kept_fx;
+          else out.sH[(long long)j * d.P + i] = L.kept_fx;
+        }
+      }
+      if (j < tny) {
+        const bool had = S.k(i, j) != S.k(i, j + 1);
+        if (i >= 1 && i <= tnx - 1) {
+          if (had) {
+            Flags f;
+            advect(S, lam, Mk{1, i, j}, f);
+            cnt[D_CFL] += f.cfl;
+            dmax = fmax(dmax, f.dabs);
+          }
+          const NewV<R> nv = new_unaligned(S, lam, line_only != 0, i, j, cnt);
+          if (nv.present) {
+            if (AX) out.sH[(long long)i * d.P + j] = nv.s;
+            else out.sV[(long long)j * d.P + i] = nv.s;
+          }
+          // verdict slots are indexed by real cell
+          const long long cr = AX ? (long long)i * d.nx + j : (long long)j * d.nx + i;
+          const long long cl = AX ? (long long)(i - 1) * d.nx + j : (long long)j * d.nx + (i - 1);
+          from_left[cr] = (int8_t)nv.vr;
+          from_right[cl] = (int8_t)nv.vl;
+        } else if (had) {  // wall marker normal to the sweep stays
+          if (AX) out.sH[(long long)i * d.P + j] = S.v(i, j);
+          else out.sV[(long long)j * d.P + i] = S.v(i, j);
+        }
+      }
+    }
+  }
+  const unsigned word = __ballot_sync(0xffffffffu, in && kb);
+  if (threadIdx.x == 0 && y <= d.ny && x <= d.nx) out.K[(long long)y * d.kw + (x >> 5)] = word;
+  flush_counters(cnt, ctr);
+  raise_status(status, cnt);
+  if (dmax > 0.0) atomicMax(cfl_bits, (unsigned long long)__double_as_longlong(dmax));
+}
+
+// Pass 2 of a sweep: centre colour vertices of cells with four markers after
+// the sweep (Sec. 2.3); the verdict from the cell's left (bottom) edge wins.
+template <typename R, int AX>
+__global__ void __launch_bounds__(32 * kBlockY)
+k_centre(View<R, AX> Snew, const uint32_t* __restrict__ Zold, uint32_t* Zout,
+         const int8_t* __restrict__ from_left, const int8_t* __restrict__ from_right,
+         unsigned long long* ctr) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.y;
+  const Dims& d = Snew.d;
+  const bool in = x < d.nx && y < d.ny;
+  int cnt[D_NUSED];
+#pragma unroll
+  for (int c = 0; c < D_NUSED; ++c) cnt[c] = 0;
+  int zb = 0;
+  if (in) {
+    const long long cell = (long long)y * d.nx + x;
+    zb = (__ldg(&Zold[(long long)y * d.zw + (x >> 5)]) >> (x & 31)) & 1;
+    const int i = AX ? y : x, j = AX ? x : y;
+    const int q = corner_mask(Snew, i, j);
+    if (q == 5 || q == 10) {
+      const int a = (i >= 1) ? from_left[cell] : -1;
+      const int b = (i + 1 <= Snew.tnx() - 1) ? from_right[cell] : -1;
+      if (a >= 0) {
+        zb = a;
+        cnt[D_ZSET] += 1;
+        if (b >= 0 && b != a) cnt[D_ZCONFLICT] += 1;
+      } else if (b >= 0) {
+        zb = b;
+        cnt[D_ZSET] += 1;
+      }
+    }
+  }
+  const unsigned word = __ballot_sync(0xffffffffu, in && zb);
+  if (threadIdx.x == 0 && y < d.ny && x < d.nx) Zout[(long long)y * d.zw + (x >> 5)] = word;
+  flush_counters(cnt, ctr);
+}
+
+// ---------------------------------------------------------------------------
+// Volume fraction (Sec. 2.5), double arithmetic; per-block partial sums in a
+// fixed order; marker counts.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int kbit(const uint32_t* K, const Dims& d, int x, int y) {
+  return (__ldg(&K[(long long)y * d.kw + (x >> 5)]) >> (x & 31)) & 1;
+}
+
+template <typename R>
+__device__ double cell_fraction(const uint32_t* K, const uint32_t* Z, const R* sH, const R* sV,
+                                const Dims& d, int i, int j) {
+  const int q = kbit(K, d, i, j) | (kbit(K, d, i + 1, j) << 1) | (kbit(K, d, i + 1, j + 1) << 2) |
+                (kbit(K, d, i, j + 1) << 3);
+  const int em = edge_mask(q);
+  if (em == 0) return (double)(q & 1);
+  const double s0 = (double)__ldg(&sH[(long long)j * d.P + i]);
+  const double s1 = (double)__ldg(&sV[(long long)j * d.P + i + 1]);
+  const double s2 = (double)__ldg(&sH[(long long)(j + 1) * d.P + i]);
+  const double s3 = (double)__ldg(&sV[(long long)j * d.P + i]);
+  auto tri = [&](int c) {
+    double a, b;
+    switch (c) {
+      case 0: a = s3; b = s0; break;
+      case 1: a = 1.0 - s0; b = s1; break;
+      case 2: a = 1.0 - s1; b = 1.0 - s2; break;
+      default: a = s2; b = 1.0 - s3; break;
+    }
+    return 0.5 * (a * b);
+  };
+  if (em != 15) {
+    const int e1 = __ffs(em) - 1, e2 = 31 - __clz(em);
+    const int c0 = q & 1;
+    if (e2 - e1 == 2) {
+      if (e1 == 0) return c0 ? 0.5 * (s0 + s2) : 0.5 * ((1.0 - s0) + (1.0 - s2));
+      return c0 ? 0.5 * (s3 + s1) : 0.5 * ((1.0 - s3) + (1.0 - s1));
+    }
+    const int c = (e1 == 0 && e2 == 3) ? 0 : e2;
+    const double T = tri(c);
+    return ((q >> c) & 1) ? T : 1.0 - T;
+  }
+  const int zc = (__ldg(&Z[(long long)j * d.zw + (i >> 5)]) >> (i & 31)) & 1;
+  double Tsum = 0.0;
+  bool first = true;
+  for (int c = 0; c < 4; ++c)
+    if (((q >> c) & 1) != zc) {
+      if (first) { Tsum = tri(c); first = false; } else { Tsum = Tsum + tri(c); }
+    }
+  return zc == 0 ? Tsum : 1.0 - Tsum;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(32 * kBlockY)
+k_fraction(const uint32_t* __restrict__ K, const uint32_t* __restrict__ Z,
+           const R* __restrict__ sH, const R* __restrict__ sV, Dims d, R* C, double* partial,
+           unsigned long long* ctr) {
+  __shared__ double red[32 * kBlockY];
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.y;
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  double f = 0.0;
+  int cnt[D_NUSED];
+#pragma unroll
+  for (int c = 0; c < D_NUSED; ++c) cnt[c] = 0;
+  if (x < d.nx && y < d.ny) {
+    f = cell_fraction(K, Z, sH, sV, d, x, y);
+    C[(long long)y * d.P + x] = (R)f;
+  }
+  if (x < d.nx && y <= d.ny) cnt[D_NH] = kbit(K, d, x, y) != kbit(K, d, x + 1, y);
+  if (x <= d.nx && y < d.ny) cnt[D_NV] = kbit(K, d, x, y) != kbit(K, d, x, y + 1);
+  flush_counters(cnt, ctr);
+  red[t] = f;
+  __syncthreads();
+  for (int s = (32 * kBlockY) / 2; s > 0; s >>= 1) {
+    if (t < s) red[t] = red[t] + red[t + s];
+    __syncthreads();
+  }
+  if (t == 0) partial[(long long)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+// Sum of the per-block partials in a fixed order (one block).
+__global__ void k_area(const double* __restrict__ partial, long long n, double scale, double* area) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (long long b = threadIdx.x; b < n; b += 256) acc = acc + partial[b];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *area = red[0] * scale;
+}
+
+// ---------------------------------------------------------------------------
+// Height-function curvature (Sec. 2.5): standard 7x3 heights, orientation
+// from the cell's own segments.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(32 * kBlockY)
+k_curvature(const uint32_t* __restrict__ K, const uint32_t* __restrict__ Z,
+            const R* __restrict__ sH, const R* __restrict__ sV, const R* __restrict__ C, Dims d,
+            R dx, R* kappa, unsigned long long* ctr) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.y;
+  int cnt[D_NUSED];
+#pragma unroll
+  for (int c = 0; c < D_NUSED; ++c) cnt[c] = 0;
+  if (x < d.nx && y < d.ny) {
+    const int i = x, j = y;
+    const int q = kbit(K, d, i, j) | (kbit(K, d, i + 1, j) << 1) | (kbit(K, d, i + 1, j + 1) << 2) |
+                  (kbit(K, d, i, j + 1) << 3);
+    R out = R(NAN);
+    if (q != 0 && q != 15) {
+      const int em = edge_mask(q);
+      const int zc = em == 15 ? (__ldg(&Z[(long long)j * d.zw + (i >> 5)]) >> (i & 31)) & 1 : 0;
+      int seg[2][2];
+      const int ns = segments(q, zc, seg);
+      const R px[4] = {__ldg(&sH[(long long)j * d.P + i]), R(1), __ldg(&sH[(long long)(j + 1) * d.P + i]), R(0)};
+      const R py[4] = {R(0), __ldg(&sV[(long long)j * d.P + i + 1]), R(1), __ldg(&sV[(long long)j * d.P + i])};
+      R ax = R(0), ay = R(0);
+      for (int t = 0; t < ns; ++t) {
+        const int a = seg[t][0], b = seg[t][1];
+        ax = ax + fabs(px[b] - px[a]);
+        ay = ay + fabs(py[b] - py[a]);
+      }
+      const bool ycol = ax >= ay;
+      const bool inside = ycol ? (i - 1 >= 0 && i + 1 <= d.nx - 1 && j - 3 >= 0 && j + 3 <= d.ny - 1)
+                               : (j - 1 >= 0 && j + 1 <= d.ny - 1 && i - 3 >= 0 && i + 3 <= d.nx - 1);
+      bool valid = inside;
+      R h[3];
+      int orient[3] = {0, 0, 0};
+      if (inside) {
+        for (int m = -1; m <= 1; ++m) {
+          R acc = R(0);
+          for (int t = -3; t <= 3; ++t)
+            acc = acc + (ycol ? __ldg(&C[(long long)(j + t) * d.P + i + m])
+                              : __ldg(&C[(long long)(j + m) * d.P + i + t]));
+          h[m + 1] = acc;
+          const R lo = ycol ? __ldg(&C[(long long)(j - 3) * d.P + i + m]) : __ldg(&C[(long long)(j + m) * d.P + i - 3]);
+          const R hi = ycol ? __ldg(&C[(long long)(j + 3) * d.P + i + m]) : __ldg(&C[(long long)(j + m) * d.P + i + 3]);
+          orient[m + 1] = (lo == R(1) && hi == R(0)) ? 1 : (lo == R(0) && hi == R(1)) ? -1 : 0;
+        }
+        valid = orient[0] != 0 && orient[0] == orient[1] && orient[1] == orient[2];
+      }
+      if (valid) {
+        const R hp = (h[2] - h[0]) * R(0.5);
+        const R hpp = (h[2] - h[1]) - (h[1] - h[0]);
+        const R qv = R(1) + hp * hp;
+        const R den = dx * (qv * sqrt(qv));
+        out = -hpp / den;
+      } else {
+        cnt[D_HF_INVALID] = 1;
+      }
+    }
+    kappa[(long long)j * d.P + i] = out;
+  }
+  flush_counters(cnt, ctr);
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation (Sec. 3.2).
+// ---------------------------------------------------------------------------
+struct SceneDev {
+  const double* circ;   // 3 per circle: xc, yc, r
+  int ncircles;
+  int has_curve;
+  double y0;
+  int nmodes;
+  const double* amp;
+  const double* phase;
+  int has_line;
+  double la, lb, lc;
+};
+
+__device__ double curve_h(const SceneDev& sc, double x) {
+  double acc = sc.y0;
+  for (int k = 1; k <= sc.nmodes; ++k) {
+    const double arg = (6.283185307179586 * (double)k) * x + sc.phase[k - 1];
+    acc = acc + sc.amp[k - 1] * cos(arg);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ bool in_circle(const SceneDev& sc, int c, double x, double y) {
+  const double ddx = x - sc.circ[3 * c], ddy = y - sc.circ[3 * c + 1];
+  const double r = sc.circ[3 * c + 2];
+  return ddx * ddx + ddy * ddy <= r * r;
+}
+__device__ __forceinline__ bool in_line(const SceneDev& sc, double x, double y) {
+  return sc.la * x + sc.lb * y <= sc.lc;
+}
+
+// Curve heights at the vertex columns (hv[i], x = i dx).
+__global__ void k_curve_cols(SceneDev sc, int nx, double dx, double* hv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= nx) hv[i] = curve_h(sc, i * dx);
+}
+
+// Base phase of vertices (K) and cell centres (Z) from the curve and line.
+__global__ void __launch_bounds__(32 * kBlockY)
+k_init_base(SceneDev sc, Dims d, double dx, const double* hv, uint32_t* K, uint32_t* Z) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.y;
+  int pk = 0, pz = 0;
+  if (x <= d.nx && y <= d.ny) {
+    if (sc.has_curve) pk ^= (y * dx) <= hv[x];
+    if (sc.has_line) pk ^= in_line(sc, x * dx, y * dx);
+  }
+  if (x < d.nx && y < d.ny) {
+    const double cx = (x + 0.5) * dx, cy = (y + 0.5) * dx;
+    if (sc.has_curve) pz ^= cy <= curve_h(sc, cx);
+    if (sc.has_line) pz ^= in_line(sc, cx, cy);
+  }
+  const unsigned wk = __ballot_sync(0xffffffffu, (x <= d.nx && y <= d.ny) && pk);
+  const unsigned wz = __ballot_sync(0xffffffffu, (x < d.nx && y < d.ny) && pz);
+  if (threadIdx.x == 0 && y <= d.ny && x <= d.nx) K[(long long)y * d.kw + (x >> 5)] = wk;
+  if (threadIdx.x == 0 && y < d.ny && x < d.nx) Z[(long long)y * d.zw + (x >> 5)] = wz;
+}
+
+__device__ __forceinline__ void circle_box(const SceneDev& sc, int c, const Dims& d, double dx,
+                                           int* i0, int* i1, int* j0, int* j1) {
+  const double xc = sc.circ[3 * c], yc = sc.circ[3 * c + 1], r = sc.circ[3 * c + 2];
+  *i0 = max(0, (int)floor((xc - r) / dx) - 1);
+  *i1 = min(d.nx, (int)ceil((xc + r) / dx) + 1);
+  *j0 = max(0, (int)floor((yc - r) / dx) - 1);
+  *j1 = min(d.ny, (int)ceil((yc + r) / dx) + 1);
+}
+
+// One block per circle: toggle the vertices and centres inside it.
+__global__ void k_init_circles(SceneDev sc, Dims d, double dx, uint32_t* K, uint32_t* Z) {
+  const int c = blockIdx.x;
+  int i0, i1, j0, j1;
+  circle_box(sc, c, d, dx, &i0, &i1, &j0, &j1);
+  const int w = i1 - i0 + 1;
+  const long long n = (long long)w * (j1 - j0 + 1);
+  for (long long t = threadIdx.x; t < n; t += blockDim.x) {
+    const int i = i0 + (int)(t % w), j = j0 + (int)(t / w);
+    if (in_circle(sc, c, i * dx, j * dx)) atomicXor(&K[(long long)j * d.kw + (i >> 5)], 1u << (i & 31));
+    if (i < d.nx && j < d.ny && in_circle(sc, c, (i + 0.5) * dx, (j + 0.5) * dx))
+      atomicXor(&Z[(long long)j * d.zw + (i >> 5)], 1u << (i & 31));
+  }
+}
+
+// One block per circle: lowest circle index whose own inside test differs at
+// the two ends of an edge.
+__global__ void k_init_owner(SceneDev sc, Dims d, double dx, int* ownH, int* ownV) {
+  const int c = blockIdx.x;
+  int i0, i1, j0, j1;
+  circle_box(sc, c, d, dx, &i0, &i1, &j0, &j1);
+  const int w = i1 - i0 + 1;
+  const long long n = (long long)w * (j1 - j0 + 1);
+  for (long long t = threadIdx.x; t < n; t += blockDim.x) {
+    const int i = i0 + (int)(t % w), j = j0 + (int)(t / w);
+    const bool here = in_circle(sc, c, i * dx, j * dx);
+    if (i < d.nx && here != in_circle(sc, c, (i + 1) * dx, j * dx))
+      atomicMin(&ownH[(long long)j * d.P + i], c);
+    if (j < d.ny && here != in_circle(sc, c, i * dx, (j + 1) * dx))
+      atomicMin(&ownV[(long long)j * d.P + i], c);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R finish_fraction(double s) {
+  if (!(s >= 0.0)) s = 0.0;
+  if (s >= 1.0) s = below_one<double>();
+  R r = (R)s;
+  if (r >= R(1)) r = below_one<R>();
+  return r;
+}
+
+// Marker fraction of every edge whose end colours differ.
+template <typename R>
+__global__ void __launch_bounds__(32 * kBlockY)
+k_init_roots(SceneDev sc, Dims d, double dx, const uint32_t* __restrict__ K,
+             const double* __restrict__ hv, const int* __restrict__ ownH,
+             const int* __restrict__ ownV, R* sH, R* sV) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.y;
+  if (x > d.nx || y > d.ny) return;
+  const double xi = x * dx, yj = y * dx;
+  if (x < d.nx && kbit(K, d, x, y) != kbit(K, d, x + 1, y)) {
+    double s = 0.5;
+    if (sc.has_curve && ((yj <= hv[x]) != (yj <= hv[x + 1]))) {
+      const bool side0 = yj <= hv[x];
+      double lo = 0.0, hi = 1.0;
+      for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if ((yj <= curve_h(sc, xi + mid * dx)) == side0) lo = mid; else hi = mid;
+      }
+      s = 0.5 * (lo + hi);
+    } else if (sc.has_line && in_line(sc, xi, yj) != in_line(sc, (x + 1) * dx, yj)) {
+      const double xr = (sc.lc - sc.lb * yj) / sc.la;
+      s = (xr - xi) / dx;
+    } else {
+      const int o = ownH[(long long)y * d.P + x];
+      if (o < sc.ncircles) {
+        const double ddy = yj - sc.circ[3 * o + 1];
+        const double r = sc.circ[3 * o + 2];
+        const double disc = r * r - ddy * ddy;
+        const double sq = sqrt(disc > 0.0 ? disc : 0.0);
+        const double root = in_circle(sc, o, xi, yj) ? sc.circ[3 * o] + sq : sc.circ[3 * o] - sq;
+        s = (root - xi) / dx;
+      }
+    }
+    sH[(long long)y * d.P + x] = finish_fraction<R>(s);
+  }
+  if (y < d.ny && kbit(K, d, x, y) != kbit(K, d, x, y + 1)) {
+    double s = 0.5;
+    if (sc.has_curve && ((yj <= hv[x]) != (((y + 1) * dx) <= hv[x]))) {
+      s = (hv[x] - yj) / dx;
+    } else if (sc.has_line && in_line(sc, xi, yj) != in_line(sc, xi, (y + 1) * dx)) {
+      const double yr = (sc.lc - sc.la * xi) / sc.lb;
+      s = (yr - yj) / dx;
+    } else {
+      const int o = ownV[(long long)y * d.P + x];
+      if (o < sc.ncircles) {
+        const double ddx = xi - sc.circ[3 * o];
+        const double r = sc.circ[3 * o + 2];
+        const double disc = r * r - ddx * ddx;
+        const double sq = sqrt(disc > 0.0 ? disc : 0.0);
+        const double root = in_circle(sc, o, xi, yj) ? sc.circ[3 * o + 1] + sq : sc.circ[3 * o + 1] - sq;
+        s = (root - yj) / dx;
+      }
+    }
+    sV[(long long)y * d.P + x] = finish_fraction<R>(s);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// State I/O: bytes <-> packed bits, doubles <-> pitched state fractions.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32 * kBlockY)
+k_pack_bits(const uint8_t* __restrict__ src, int w, int h, int words, uint32_t* dst) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.y;
+  const bool in = x < w && y < h;
+  const unsigned word = __ballot_sync(0xffffffffu, in && src[(long long)y * w + x] != 0);
+  if (threadIdx.x == 0 && y < h && x < w) dst[(long long)y * words + (x >> 5)] = word;
+}
+
+__global__ void k_unpack_bits(const uint32_t* __restrict__ src, int w, int h, int words, uint8_t* dst) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)w * h) return;
+  const int x = (int)(t % w), y = (int)(t / w);
+  dst[t] = (src[(long long)y * words + (x >> 5)] >> (x & 31)) & 1;
+}
+
+template <typename R>
+__global__ void k_load_frac(const double* __restrict__ src, int w, int h, long long P, R* dst) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)w * h) return;
+  const int x = (int)(t % w), y = (int)(t / w);
+  double s = src[t];
+  R r = (R)s;
+  if (!(r >= R(0))) r = R(0);
+  if (r >= R(1)) r = below_one<R>();
+  dst[(long long)y * P + x] = r;
+}
+
+template <typename R>
+__global__ void k_store_frac(const R* __restrict__ src, int w, int h, long long P, double* dst) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)w * h) return;
+  const int x = (int)(t % w), y = (int)(t / w);
+  dst[t] = (double)src[(long long)y * P + x];
+}
+
+}  // namespace ebit

@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libebit.so (include/ebit.h), same names as the C ABI.
+
+Argument marshalling only: every step of the EBIT path runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams (``data_ptr()`` and
+``torch.cuda.current_stream().cuda_stream``).  Loading fails loudly when the
+library has not been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB_PATH
+
+EBIT_OK, EBIT_EAGAIN = 0, 1
+EBIT_EINVAL, EBIT_ENOMEM, EBIT_ECFL, EBIT_EINVARIANT, EBIT_ECUDA, EBIT_ETIMEOUT, EBIT_EFULL = \
+    -1, -2, -3, -4, -5, -6, -7
+EBIT_FP64, EBIT_FP32 = 0, 1
+EBIT_FIT_LINE = 1
+
+# diagnostics indices (include/ebit.h)
+D_NH, D_NV, D_CANCELLED, D_ZSET, D_ZCONFLICT, D_FIT_ONLINE, D_FIT_LINE, D_FIT_ONE, D_FIT_TWO, \
+    D_WALL_CLAMP, D_INVARIANT, D_HF_INVALID, D_CFL = range(13)
+D_COUNT = 16
+
+_STATUS_NAMES = {0: "EBIT_OK", 1: "EBIT_EAGAIN", -1: "EBIT_EINVAL", -2: "EBIT_ENOMEM",
+                 -3: "EBIT_ECFL", -4: "EBIT_EINVARIANT", -5: "EBIT_ECUDA", -6: "EBIT_ETIMEOUT",
+                 -7: "EBIT_EFULL"}
+
+
+class EbitError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__(f"{where}: {_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ebit_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dx", ctypes.c_double),
+                ("prec", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class ebit_circle(ctypes.Structure):
+    _fields_ = [("xc", ctypes.c_double), ("yc", ctypes.c_double), ("r", ctypes.c_double)]
+
+
+class ebit_curve(ctypes.Structure):
+    _fields_ = [("y0", ctypes.c_double), ("nmodes", ctypes.c_int32),
+                ("amp", ctypes.POINTER(ctypes.c_double)), ("phase", ctypes.POINTER(ctypes.c_double))]
+
+
+class ebit_halfplane(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double)]
+
+
+class ebit_scene(ctypes.Structure):
+    _fields_ = [("circles", ctypes.POINTER(ebit_circle)), ("ncircles", ctypes.c_int32),
+                ("curve", ctypes.POINTER(ebit_curve)), ("line", ctypes.POINTER(ebit_halfplane))]
+
+
+class ebit_state_host(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("K", ctypes.c_void_p), ("Z", ctypes.c_void_p),
+                ("sH", ctypes.c_void_p), ("sV", ctypes.c_void_p), ("step_index", ctypes.c_int64)]
+
+
+class ebit_diag(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_int64 * D_COUNT), ("area", ctypes.c_double), ("max_cfl", ctypes.c_double)]
+
+
+_lib = None
+
+# exported symbols and their signatures: (restype, argtypes)
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "ebit_init": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ebit_grid), ctypes.POINTER(ebit_scene), _P]),
+    "ebit_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ebit_grid), _P]),
+    "ebit_load_state": (ctypes.c_int, [_P, ctypes.POINTER(ebit_state_host)]),
+    "ebit_get_state": (ctypes.c_int, [_P, ctypes.POINTER(ebit_state_host)]),
+    "ebit_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
+    "ebit_sweep": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_double]),
+    "ebit_fraction": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "ebit_curvature": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
+    "ebit_fields": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64)]),
+    "ebit_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(ebit_diag)]),
+    "ebit_sync": (ctypes.c_int, [_P]),
+    "ebit_destroy": (None, [_P]),
+    "ebit_last_error": (ctypes.c_char_p, []),
+    "ebit_footprint": (ctypes.c_size_t, [ctypes.POINTER(ebit_grid)]),
+}
+
+
+def lib(path: str | None = None):
+    """Load libebit.so (built by paper_2309_00338_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libebit.so not built ({p}); run __graft_entry__.build() first")
+    L = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(status, where):
+    if status != EBIT_OK:
+        raise EbitError(status, where, lib().ebit_last_error().decode())
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _scene(scene: dict, keep: list):
+    sc = ebit_scene()
+    circles = np.ascontiguousarray(np.asarray(scene.get("circles", np.zeros((0, 3))), np.float64).reshape(-1, 3))
+    keep.append(circles)
+    sc.ncircles = circles.shape[0]
+    sc.circles = circles.ctypes.data_as(ctypes.POINTER(ebit_circle)) if circles.shape[0] else None
+    if scene.get("curve") is not None:
+        cv = scene["curve"]
+        amp = np.ascontiguousarray(cv["amp"], np.float64)
+        ph = np.ascontiguousarray(cv["phase"], np.float64)
+        c = ebit_curve(float(cv["y0"]), int(amp.size), amp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       ph.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        keep += [amp, ph, c]
+        sc.curve = ctypes.pointer(c)
+    if scene.get("line") is not None:
+        hp = ebit_halfplane(*(float(t) for t in scene["line"]))
+        keep.append(hp)
+        sc.line = ctypes.pointer(hp)
+    return sc
+
+
+def ebit_footprint(nx, ny, dx, prec=EBIT_FP64, flags=0) -> int:
+    g = ebit_grid(nx, ny, dx, prec, flags)
+    return int(lib().ebit_footprint(ctypes.byref(g)))
+
+
+def ebit_init(nx, ny, dx, scene: dict, prec=EBIT_FP64, flags=0, stream=None):
+    """ebit_init: returns a context handle (c_void_p)."""
+    g = ebit_grid(nx, ny, dx, prec, flags)
+    keep = []
+    sc = _scene(scene, keep)
+    h = ctypes.c_void_p()
+    _check(lib().ebit_init(ctypes.byref(h), ctypes.byref(g), ctypes.byref(sc), _stream(stream)), "ebit_init")
+    return h
+
+
+def ebit_create(nx, ny, dx, prec=EBIT_FP64, flags=0, stream=None):
+    g = ebit_grid(nx, ny, dx, prec, flags)
+    h = ctypes.c_void_p()
+    _check(lib().ebit_create(ctypes.byref(h), ctypes.byref(g), _stream(stream)), "ebit_create")
+    return h
+
+
+def ebit_load_state(ctx, K, Z, sH, sV, step_index=0):
+    K = np.ascontiguousarray(K, np.uint8)
+    Z = np.ascontiguousarray(Z, np.uint8)
+    sH = np.ascontiguousarray(sH, np.float64)
+    sV = np.ascontiguousarray(sV, np.float64)
+    ny, nx = Z.shape
+    st = ebit_state_host(nx, ny, K.ctypes.data, Z.ctypes.data, sH.ctypes.data, sV.ctypes.data, int(step_index))
+    _check(lib().ebit_load_state(ctx, ctypes.byref(st)), "ebit_load_state")
+
+
+def ebit_get_state(ctx, nx, ny):
+    """Returns dict K, Z, sH, sV (numpy) and step_index."""
+    K = np.zeros((ny + 1, nx + 1), np.uint8)
+    Z = np.zeros((ny, nx), np.uint8)
+    sH = np.zeros((ny + 1, nx), np.float64)
+    sV = np.zeros((ny, nx + 1), np.float64)
+    st = ebit_state_host(nx, ny, K.ctypes.data, Z.ctypes.data, sH.ctypes.data, sV.ctypes.data, 0)
+    _check(lib().ebit_get_state(ctx, ctypes.byref(st)), "ebit_get_state")
+    return {"K": K, "Z": Z, "sH": sH, "sV": sV, "step_index": int(st.step_index)}
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def ebit_step(ctx, u, v, dt):
+    """u, v: contiguous CUDA tensors (ny+1, nx+1) of the context precision."""
+    _check(lib().ebit_step(ctx, _dev_ptr(u), _dev_ptr(v), float(dt)), "ebit_step")
+
+
+def ebit_sweep(ctx, axis, vel, dt):
+    _check(lib().ebit_sweep(ctx, int(axis), _dev_ptr(vel), float(dt)), "ebit_sweep")
+
+
+def ebit_fraction(ctx, C=None, want_area=True):
+    a = ctypes.c_double(0.0)
+    _check(lib().ebit_fraction(ctx, _dev_ptr(C), ctypes.byref(a) if want_area else None), "ebit_fraction")
+    return a.value if want_area else None
+
+
+def ebit_curvature(ctx, kappa=None, want_invalid=True):
+    n = ctypes.c_int32(0)
+    _check(lib().ebit_curvature(ctx, _dev_ptr(kappa), ctypes.byref(n) if want_invalid else None),
+           "ebit_curvature")
+    return n.value if want_invalid else None
+
+
+def ebit_fields(ctx):
+    c, k = ctypes.c_void_p(), ctypes.c_void_p()
+    p = ctypes.c_int64()
+    _check(lib().ebit_fields(ctx, ctypes.byref(c), ctypes.byref(k), ctypes.byref(p)), "ebit_fields")
+    return c.value, k.value, p.value
+
+
+def ebit_diagnostics(ctx):
+    d = ebit_diag()
+    _check(lib().ebit_diagnostics(ctx, ctypes.byref(d)), "ebit_diagnostics")
+    return {"counters": np.array(d.c[:], np.int64), "area": d.area, "max_cfl": d.max_cfl}
+
+
+def ebit_sync(ctx):
+    _check(lib().ebit_sync(ctx), "ebit_sync")
+
+
+def ebit_destroy(ctx):
+    if ctx:
+        lib().ebit_destroy(ctx)

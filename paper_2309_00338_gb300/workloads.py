@@ -4,10 +4,12 @@ velocity fields sampled at grid vertices.
 This module holds none of the EBIT arithmetic.  It only produces inputs, and it
 is the one piece shared by the CUDA path's tests/benchmarks and by the oracle.
 
-Random numbers come from xoshiro256** seeded through SplitMix64, both written
-from their published definitions (Blackman & Vigna); a uniform double is
-(x >> 11) * 2^-53.  No library distribution is used, so the streams are the
-same on every machine.
+Random numbers come from SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) used as a counter-based stream:
+draw n is the SplitMix64 output for state seed + (n+1)*0x9E3779B97F4A7C15,
+written here from that definition and evaluated vectorised with numpy.  A
+uniform double is (x >> 11) * 2^-53.  No library distribution is used, so the
+streams are the same on every machine.
 
 The workloads stand in for the paper's analytic tests (translation, single
 vortex, solid rotation; Sec. 3.2-3.4); no dataset is involved.
@@ -19,41 +21,38 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-_M64 = (1 << 64) - 1
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
 
 
-def _rotl(x, k):
-    return ((x << k) | (x >> (64 - k))) & _M64
+def splitmix64(state):
+    """SplitMix64 output function of a uint64 array of states."""
+    z = np.asarray(state, np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
 
 
-class Xoshiro256ss:
-    """xoshiro256** 1.0 with a SplitMix64-expanded 64-bit seed."""
+class Rng:
+    """Counter-based SplitMix64 stream."""
 
     def __init__(self, seed: int):
-        z = seed & _M64
-        s = []
-        for _ in range(4):
-            z = (z + 0x9E3779B97F4A7C15) & _M64
-            t = z
-            t = ((t ^ (t >> 30)) * 0xBF58476D1CE4E5B9) & _M64
-            t = ((t ^ (t >> 27)) * 0x94D049BB133111EB) & _M64
-            s.append(t ^ (t >> 31))
-        self.s = s
+        self.seed = np.uint64(seed & ((1 << 64) - 1))
+        self.n = 0
 
-    def next_u64(self) -> int:
-        s = self.s
-        result = (_rotl((s[1] * 5) & _M64, 7) * 9) & _M64
-        t = (s[1] << 17) & _M64
-        s[2] ^= s[0]
-        s[3] ^= s[1]
-        s[1] ^= s[2]
-        s[0] ^= s[3]
-        s[2] ^= t
-        s[3] = _rotl(s[3], 45)
-        return result
+    def u64(self, size: int) -> np.ndarray:
+        k = np.arange(self.n + 1, self.n + 1 + size, dtype=np.uint64)
+        self.n += size
+        with np.errstate(over="ignore"):
+            return splitmix64(self.seed + k * _GAMMA)
 
-    def uniform(self, lo=0.0, hi=1.0) -> float:
-        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / 9007199254740992.0))
+    def uniform(self, lo=0.0, hi=1.0, size=None):
+        m = 1 if size is None else int(size)
+        u = (self.u64(m) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+        out = lo + (hi - lo) * u
+        return float(out[0]) if size is None else out
 
     def integer(self, lo: int, hi: int) -> int:
         """Uniform integer in [lo, hi] (inclusive)."""
@@ -163,7 +162,7 @@ def circle_scene(circles):
     return {"circles": np.asarray(circles, np.float64).reshape(-1, 3)}
 
 
-def fourier_curve(rng: Xoshiro256ss, y0=0.5, nmodes=16, amp0=0.01):
+def fourier_curve(rng: Rng, y0=0.5, nmodes=16, amp0=0.01):
     amp = np.array([amp0 / (k * k) for k in range(1, nmodes + 1)])
     phase = np.array([rng.uniform(0.0, 2.0 * math.pi) for _ in range(nmodes)])
     return {"y0": y0, "amp": amp, "phase": phase}
@@ -195,23 +194,22 @@ class _Bins:
         self.b.setdefault(key, []).append(c)
 
 
-def place_circles(rng: Xoshiro256ss, count, rmin, rmax, gap, region, curve=None,
-                  max_tries=1000, max_candidates=10**6, wall_gap=None):
-    """Seeded random sequential placement.  Each candidate draws its radius
-    once, then up to max_tries centres; a centre is accepted when the gap to
-    every placed circle (and to the curve, if any) is at least `gap` and
-    region(x, y, r) holds.  Stops at `count` circles or `max_candidates`
-    candidates.  Returns an (n, 3) array [xc, yc, r] (domain units)."""
+def place_circles(rng: Rng, count, rmin, rmax, gap, region, curve=None, max_tries=1000,
+                  wall_gap=None):
+    """Seeded random sequential placement of `count` attempted circles.  Each
+    attempt draws its radius once, then up to max_tries centres (drawn as one
+    batch); the first centre whose gap to every placed circle (and to the
+    curve, if any) is at least `gap` and for which region(x, y, r) holds is
+    accepted, otherwise the attempt is dropped.  Returns an (n, 3) array
+    [xc, yc, r] (domain units), n <= count."""
     wall_gap = gap if wall_gap is None else wall_gap
     bins = _Bins(2.0 * rmax + gap)
     out = []
-    cands = 0
-    while len(out) < count and cands < max_candidates:
-        cands += 1
+    for _ in range(count):
         r = rng.uniform(rmin, rmax)
-        for _ in range(max_tries):
-            x = rng.uniform(r + wall_gap, 1.0 - r - wall_gap)
-            y = rng.uniform(r + wall_gap, 1.0 - r - wall_gap)
+        xs = rng.uniform(r + wall_gap, 1.0 - r - wall_gap, max_tries)
+        ys = rng.uniform(r + wall_gap, 1.0 - r - wall_gap, max_tries)
+        for x, y in zip(xs.tolist(), ys.tolist()):
             if not region(x, y, r):
                 continue
             ok = True
@@ -220,9 +218,9 @@ def place_circles(rng: Xoshiro256ss, count, rmin, rmax, gap, region, curve=None,
                     ok = False
                     break
             if ok and curve is not None:
-                xs = np.linspace(x - r - gap, x + r + gap, 64)
-                hs = curve_height(curve, xs)
-                if np.min((xs - x) ** 2 + (hs - y) ** 2) < (r + gap) ** 2:
+                cx = np.linspace(x - r - gap, x + r + gap, 64)
+                hs = curve_height(curve, cx)
+                if np.min((cx - x) ** 2 + (hs - y) ** 2) < (r + gap) ** 2:
                     ok = False
             if ok:
                 c = (x, y, r)
@@ -278,7 +276,7 @@ def rotation_disks_workload(n=1024, count=4096, seed=230900338, cfl=0.5, steps=5
     |c - c'| + r <= 0.45, moved by solid rotation (omega = 2 pi) about
     c' = (0.4841, 0.5477), i.e. u = -2 pi (y - 0.5) + 0.3, v = 2 pi (x - 0.5) + 0.1."""
     dx = 1.0 / n
-    rng = Xoshiro256ss(seed)
+    rng = Rng(seed)
     cx, cy = ROT_CENTRE
 
     def region(x, y, r):
@@ -297,7 +295,7 @@ def cellular_curve_workload(n=4096, count=20000, seed=230900339, cfl=0.5, steps=
     plus seeded circles of radius U[3,12] cells (gap >= 2 cells to each other,
     to the curve and to the walls), in the steady cellular flow, dt = 0.5 dx."""
     dx = 1.0 / n
-    rng = Xoshiro256ss(seed)
+    rng = Rng(seed)
     curve = fourier_curve(rng)
     circles = place_circles(rng, count, rmin_cells * dx, rmax_cells * dx, 2.0 * dx,
                             lambda x, y, r: True, curve=curve)
@@ -308,7 +306,7 @@ def cellular_curve_workload(n=4096, count=20000, seed=230900339, cfl=0.5, steps=
                     {"attempted": count, "placed": int(circles.shape[0])})
 
 
-def random_instance(rng: Xoshiro256ss, nmin=32, nmax=512, cmin=1, cmax=64, smin=200, smax=1000,
+def random_instance(rng: Rng, nmin=32, nmax=512, cmin=1, cmax=64, smin=200, smax=1000,
                     cfl=0.5, rmin=0.05, rmax=0.15, rmin_cells=3.0):
     """One instance of the batched workload: side n log-uniform, 1-64 circles
     with r ~ U[0.05, 0.15] (at least 3 cells), a coin flip between the
@@ -319,8 +317,7 @@ def random_instance(rng: Xoshiro256ss, nmin=32, nmax=512, cmin=1, cmax=64, smin=
     steps = rng.integer(smin, smax)
     lo = max(rmin, rmin_cells * dx)
     hi = max(rmax, lo)
-    circles = place_circles(rng, count, lo, hi, 2.0 * dx, lambda x, y, r: True, max_tries=50,
-                            max_candidates=4 * count)
+    circles = place_circles(rng, count, lo, hi, 2.0 * dx, lambda x, y, r: True, max_tries=50)
     dt = cfl * dx
     if rng.uniform() < 0.5:
         f = vortex_field(n, n, dx, steps * dt)

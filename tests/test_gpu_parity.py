@@ -1,0 +1,344 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Both sides start from the same loaded state and take their decisions in the
+same precision, so colour vertices, marker presence and all counters must be
+bit-exact and the FP64 form must agree to 1e-12 (the tolerance the FP64 path
+is held to); the FP32 form stores floats computed by the same sequence of
+operations and must agree exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_00338_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2309_00338_gb300 import ebit  # noqa: E402
+
+TOL64 = 1e-12
+COMPARED = [oracle.CANCELLED, oracle.ZSET, oracle.ZCONFLICT, oracle.FIT_ONLINE, oracle.FIT_LINE,
+            oracle.FIT_ONE, oracle.FIT_TWO, oracle.WALL_CLAMP, oracle.INVARIANT, oracle.CFL]
+
+
+def dev(a, prec):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float64 if prec == 0 else np.float32)).cuda()
+
+
+def gpu_from(S):
+    ctx = ebit.ebit_create(S.nx, S.ny, S.dx, S.prec)
+    ebit.ebit_load_state(ctx, S.K, S.Z, S.sH, S.sV, S.step_index)
+    return ctx
+
+
+def assert_same_state(g, S, prec):
+    assert np.array_equal(g["K"], S.K), f"corner colours differ at {np.argwhere(g['K'] != S.K)[:8]}"
+    four = S.four
+    assert np.array_equal(g["Z"][four], S.Z[four]), "centre colours of four-marker cells differ"
+    for name, mask in (("sH", S.hasH), ("sV", S.hasV)):
+        a, b = g[name][mask], getattr(S, name)[mask]
+        if prec == oracle.FP32:
+            assert np.array_equal(a, b), f"{name}: {np.max(np.abs(a - b))}"
+        else:
+            assert np.max(np.abs(a - b), initial=0.0) <= TOL64, f"{name}: {np.max(np.abs(a - b))}"
+
+
+def assert_same_fields(ctx, S, r, prec):
+    n = S.nx * S.ny
+    dt = torch.float64 if prec == 0 else torch.float32
+    C = torch.empty((S.ny, S.nx), dtype=dt, device="cuda")
+    kap = torch.empty((S.ny, S.nx), dtype=dt, device="cuda")
+    area = ebit.ebit_fraction(ctx, C)
+    ninv = ebit.ebit_curvature(ctx, kap)
+    C = C.double().cpu().numpy()
+    kap = kap.double().cpu().numpy()
+    if prec == oracle.FP32:
+        assert np.array_equal(C, r["C"])
+    else:
+        assert np.max(np.abs(C - r["C"])) <= TOL64
+    assert abs(area - r["area"]) <= TOL64 * max(1.0, abs(r["area"]))
+    nan_g, nan_o = np.isnan(kap), np.isnan(r["kappa"])
+    assert np.array_equal(nan_g, nan_o)
+    d = np.abs(kap[~nan_g] - r["kappa"][~nan_o]) * S.dx
+    if prec == oracle.FP32:
+        assert np.array_equal(kap[~nan_g], r["kappa"][~nan_o])
+    else:
+        assert np.max(d, initial=0.0) <= TOL64
+    assert ninv == r["counters"][oracle.HF_INVALID]
+    assert n > 0
+
+
+# ---------------------------------------------------------------------------
+# scenes: (nx, ny, dx, scene, field) -- ragged sizes spanning several tiles
+# ---------------------------------------------------------------------------
+def scene_disks(prec):
+    nx, ny = 97, 83
+    dx = 1.0 / 97
+    rng = W.Rng(41)
+    circles = W.place_circles(rng, 40, 2 * dx, 9 * dx, 2 * dx, lambda x, y, r: y + r < ny * dx)
+    f = W.rotation_field(nx, ny, dx, 2 * math.pi, (0.5, 0.43), (0.3, 0.1))
+    dt = 0.5 * dx / f.umax
+    return oracle.init(nx, ny, dx, W.circle_scene(circles), prec), f, dt
+
+
+def scene_curve(prec):
+    nx, ny = 130, 70
+    dx = 1.0 / 130
+    rng = W.Rng(7)
+    curve = W.fourier_curve(rng, y0=0.27, amp0=0.02)
+    circles = W.place_circles(rng, 30, 2 * dx, 7 * dx, 2 * dx, lambda x, y, r: y + r < ny * dx - 2 * dx,
+                              curve=curve)
+    f = W.cellular_field(nx, ny, dx)
+    return oracle.init(nx, ny, dx, {"circles": circles, "curve": curve}, prec), f, 0.7 * dx
+
+
+def scene_vortex(prec):
+    n = 64
+    wl = W.vortex_workload(n, period=2.0, cfl=0.5)
+    S = oracle.init(n, n, wl.dx, wl.scene, prec)
+    for k in range(90):   # a stretched, strongly curved interface
+        oracle.step(S, wl.field.u, wl.field.v, wl.field.dt_eff(k, wl.dt))
+    return S, wl.field, wl.dt
+
+
+def scene_saddle(prec):
+    """Two drops approaching along the diagonal until a saddle cell forms."""
+    n = 40
+    dx = 1.0 / n
+    d = 0.5 / math.sqrt(2) * 0.62
+    S = oracle.init(n, n, dx, W.circle_scene([(0.5 - d, 0.5 - d, 0.12), (0.5 + d, 0.5 + d, 0.12)]), prec)
+    X, Y = np.meshgrid(np.arange(n + 1) * dx, np.arange(n + 1) * dx)
+    s = np.sign((X - 0.5) + (Y - 0.5))
+    f = W.Field("converge", -0.5 * s, -0.5 * s, 0.0, "steady", 0.5)
+    dt = 0.2 * dx / 0.5
+    for k in range(400):
+        oracle.step(S, f.u, f.v, dt)
+        if S.four.any():
+            break
+    assert S.four.any()
+    return S, f, dt
+
+
+SCENES = {"disks": scene_disks, "curve": scene_curve, "vortex": scene_vortex, "saddle": scene_saddle}
+
+
+@pytest.mark.parametrize("prec", [oracle.FP64, oracle.FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("name", list(SCENES))
+@pytest.mark.parametrize("axis", [0, 1])
+def test_sweep_parity(name, prec, axis):
+    S, f, dt = SCENES[name](prec)
+    ctx = gpu_from(S)
+    try:
+        vel = f.u if axis == 0 else f.v
+        ebit.ebit_sweep(ctx, axis, dev(vel, prec), dt)
+        d = ebit.ebit_diagnostics(ctx)
+        ctr, _ = oracle.sweep(S, axis, vel, dt / S.dx)
+        g = ebit.ebit_get_state(ctx, S.nx, S.ny)
+        assert_same_state(g, S, prec)
+        assert np.array_equal(d["counters"][COMPARED], ctr[COMPARED]), (d["counters"][:13], ctr[:13])
+    finally:
+        ebit.ebit_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [oracle.FP64, oracle.FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("name", list(SCENES))
+def test_step_parity(name, prec):
+    S, f, dt = SCENES[name](prec)
+    ctx = gpu_from(S)
+    try:
+        u, v = dev(f.u, prec), dev(f.v, prec)
+        for k in range(2):  # both split orders
+            ebit.ebit_step(ctx, u, v, dt)
+            r = oracle.step(S, f.u, f.v, dt)
+            d = ebit.ebit_diagnostics(ctx)
+            assert np.array_equal(d["counters"][:13], r["counters"][:13]), (d["counters"][:13], r["counters"][:13])
+            assert d["max_cfl"] == pytest.approx(r["max_cfl"], rel=1e-6)
+            g = ebit.ebit_get_state(ctx, S.nx, S.ny)
+            assert g["step_index"] == S.step_index
+            assert_same_state(g, S, prec)
+            assert_same_fields(ctx, S, r, prec)
+    finally:
+        ebit.ebit_destroy(ctx)
+
+
+def test_vortex_64_fp64_trajectory():
+    """The plain FP64 64x64 vortex workload (256 steps, CFL 0.5, alternating
+    split order): GPU and oracle stay identical along the whole trajectory."""
+    wl = W.vortex_workload(64, period=2.0, cfl=0.5)
+    S = oracle.init(64, 64, wl.dx, wl.scene)
+    ctx = ebit.ebit_init(64, 64, wl.dx, wl.scene)
+    try:
+        g = ebit.ebit_get_state(ctx, 64, 64)
+        assert_same_state(g, S, 0)
+        u, v = dev(wl.field.u, 0), dev(wl.field.v, 0)
+        _, A0 = oracle.fraction(S)
+        for k in range(wl.steps):
+            dt = wl.field.dt_eff(k, wl.dt)
+            ebit.ebit_step(ctx, u, v, dt)
+            r = oracle.step(S, wl.field.u, wl.field.v, dt)
+            if k % 32 == 31:
+                assert_same_state(ebit.ebit_get_state(ctx, 64, 64), S, 0)
+                assert_same_fields(ctx, S, r, 0)
+        ebit.ebit_sync(ctx)
+        area = ebit.ebit_fraction(ctx)
+        assert abs(area - r["area"]) <= 1e-12
+        e_area = abs(area - A0) / A0
+        assert e_area < 5e-2
+    finally:
+        ebit.ebit_destroy(ctx)
+
+
+def test_init_parity_circles_bit_exact():
+    rng = W.Rng(13)
+    nx, ny = 150, 110
+    dx = 1.0 / 150
+    circles = W.place_circles(rng, 60, 2 * dx, 12 * dx, 2 * dx, lambda x, y, r: y + r < ny * dx)
+    scene = {"circles": circles, "line": (0.2, 1.0, 0.66)}
+    for prec in (0, 1):
+        S = oracle.init(nx, ny, dx, scene, prec)
+        ctx = ebit.ebit_init(nx, ny, dx, scene, prec)
+        try:
+            g = ebit.ebit_get_state(ctx, nx, ny)
+            assert np.array_equal(g["Z"], S.Z)
+            assert_same_state(g, S, 1)  # exact, in both forms
+        finally:
+            ebit.ebit_destroy(ctx)
+
+
+def test_init_parity_curve():
+    """The Fourier curve uses cos on both sides (1-2 ulp apart): colours match
+    except at vertices within 1e-12 of the curve, fractions to 1e-11."""
+    rng = W.Rng(17)
+    n = 256
+    dx = 1.0 / n
+    curve = W.fourier_curve(rng)
+    S = oracle.init(n, n, dx, {"curve": curve})
+    ctx = ebit.ebit_init(n, n, dx, {"curve": curve})
+    try:
+        g = ebit.ebit_get_state(ctx, n, n)
+        X, Y = np.meshgrid(np.arange(n + 1) * dx, np.arange(n + 1) * dx)
+        near = np.abs(Y - W.curve_height(curve, X)) < 1e-12
+        assert np.array_equal(g["K"][~near], S.K[~near])
+        if not near.any():
+            for name, mask in (("sH", S.hasH), ("sV", S.hasV)):
+                assert np.max(np.abs(g[name][mask] - getattr(S, name)[mask])) < 1e-11
+    finally:
+        ebit.ebit_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_full_size_rotating_disks_step(prec):
+    """1024^2 rotating disks (the workload's own size and launch shape), one
+    step from the same state, every output compared."""
+    wl = W.rotation_disks_workload()
+    S = oracle.init(wl.n, wl.n, wl.dx, wl.scene, prec)
+    ctx = ebit.ebit_init(wl.n, wl.n, wl.dx, wl.scene, prec)
+    try:
+        assert_same_state(ebit.ebit_get_state(ctx, wl.n, wl.n), S, 1)
+        ebit.ebit_step(ctx, dev(wl.field.u, prec), dev(wl.field.v, prec), wl.dt)
+        r = oracle.step(S, wl.field.u, wl.field.v, wl.dt)
+        d = ebit.ebit_diagnostics(ctx)
+        assert np.array_equal(d["counters"][:13], r["counters"][:13])
+        assert_same_state(ebit.ebit_get_state(ctx, wl.n, wl.n), S, prec)
+        assert_same_fields(ctx, S, r, prec)
+    finally:
+        ebit.ebit_destroy(ctx)
+
+
+def test_full_size_cellular_curve_fp32_step():
+    """4096^2 cellular flow with the Fourier curve and 20000 circles in the
+    FP32 form: one step from the same loaded state, every output compared."""
+    wl = W.cellular_curve_workload()
+    S = oracle.init(wl.n, wl.n, wl.dx, wl.scene, oracle.FP32)
+    ctx = gpu_from(S)
+    try:
+        ebit.ebit_step(ctx, dev(wl.field.u, 1), dev(wl.field.v, 1), wl.dt)
+        r = oracle.step(S, wl.field.u, wl.field.v, wl.dt)
+        d = ebit.ebit_diagnostics(ctx)
+        assert np.array_equal(d["counters"][:13], r["counters"][:13])
+        assert_same_state(ebit.ebit_get_state(ctx, wl.n, wl.n), S, 1)
+        assert_same_fields(ctx, S, r, 1)
+    finally:
+        ebit.ebit_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny", [(1, 1), (2, 3), (33, 1), (1, 40), (64, 9)])
+def test_tiny_and_degenerate_grids(nx, ny):
+    dx = 1.0 / max(nx, ny)
+    scene = {"line": (1.0, 0.3, 0.41 * nx * dx)}
+    for prec in (0, 1):
+        S = oracle.init(nx, ny, dx, scene, prec)
+        ctx = gpu_from(S)
+        try:
+            f = W.linear_field(nx, ny, dx, a=(0.2, 0.1, -0.1), b=(-0.1, 0.05, 0.1))
+            for k in range(3):
+                ebit.ebit_step(ctx, dev(f.u, prec), dev(f.v, prec), 0.9 * dx / 0.4)
+                r = oracle.step(S, f.u, f.v, 0.9 * dx / 0.4)
+            assert_same_state(ebit.ebit_get_state(ctx, nx, ny), S, prec)
+            assert_same_fields(ctx, S, r, prec)
+        finally:
+            ebit.ebit_destroy(ctx)
+
+
+def test_empty_and_full_domains():
+    for scene, val in (({}, 0.0), ({"line": (0.0, 0.0, 1.0)}, 1.0)):
+        ctx = ebit.ebit_init(50, 37, 0.02, scene)
+        try:
+            f = W.cellular_field(50, 37, 0.02)
+            ebit.ebit_step(ctx, dev(f.u, 0), dev(f.v, 0), 0.01)
+            C = torch.empty((37, 50), dtype=torch.float64, device="cuda")
+            area = ebit.ebit_fraction(ctx, C)
+            assert torch.all(C == val) and area == pytest.approx(val * 50 * 37 * 0.02 ** 2)
+            assert ebit.ebit_curvature(ctx) == 0
+            d = ebit.ebit_diagnostics(ctx)
+            assert d["counters"][ebit.D_NH] == 0 and d["counters"][ebit.D_NV] == 0
+        finally:
+            ebit.ebit_destroy(ctx)
+
+
+def test_cfl_violation_reported_and_context_survives():
+    n = 32
+    dx = 1.0 / n
+    S = oracle.init(n, n, dx, W.circle_scene([(0.5, 0.5, 0.2)]))
+    ctx = gpu_from(S)
+    try:
+        f = W.uniform_field(n, n, dx, 1.0, 0.5)
+        ebit.ebit_step(ctx, dev(f.u, 0), dev(f.v, 0), 1.5 * dx)
+        with pytest.raises(ebit.EbitError) as e:
+            ebit.ebit_sync(ctx)
+        assert e.value.status == ebit.EBIT_ECFL
+        r = oracle.step(S, f.u, f.v, 1.5 * dx)
+        assert r["status"] == 3
+        ebit.ebit_sync(ctx)  # the error was reported once and cleared
+        assert_same_state(ebit.ebit_get_state(ctx, n, n), S, 0)
+    finally:
+        ebit.ebit_destroy(ctx)
+
+
+def test_fp32_form_mass_error_on_translation():
+    """Stated mass-conservation error of the FP32 form: translation (Sec. 3.2)
+    at 64^2; FP64 stays at roundoff, FP32 within the storage-rounding bound."""
+    wl = W.translation_workload(64)
+    out = {}
+    for prec in (0, 1):
+        ctx = ebit.ebit_init(wl.n, wl.n, wl.dx, wl.scene, prec)
+        try:
+            a0 = ebit.ebit_fraction(ctx)
+            u, v = dev(wl.field.u, prec), dev(wl.field.v, prec)
+            for k in range(wl.steps):
+                ebit.ebit_step(ctx, u, v, wl.field.dt_eff(k, wl.dt))
+            out[prec] = abs(ebit.ebit_fraction(ctx) - a0) / a0
+        finally:
+            ebit.ebit_destroy(ctx)
+    assert out[0] < 1e-12
+    bound = wl.steps * 2 * math.pi * 0.15 * 2.0 ** -24 * wl.dx / (math.pi * 0.15 ** 2)
+    assert out[1] <= bound

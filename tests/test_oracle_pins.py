@@ -56,7 +56,7 @@ def _circle_points(rng, k_line=0.0):
 def test_fit_exact_on_circle():
     """Points on a true circle: both circles are that circle, so the new
     marker is its exact intersection with the grid line (to roundoff)."""
-    rng = W.Xoshiro256ss(11)
+    rng = W.Rng(11)
     worst = 0.0
     for _ in range(300):
         (cx, cy, R), yc, (P1, A, B, P4) = _circle_points(rng)
@@ -382,7 +382,7 @@ def _clip_area(a, b, c):
 
 
 def test_fraction_exact_for_half_planes():
-    rng = W.Xoshiro256ss(5)
+    rng = W.Rng(5)
     n = 16
     dx = 1.0 / n
     for _ in range(12):
@@ -401,7 +401,7 @@ def test_fraction_exact_for_half_planes():
 def test_fraction_sum_equals_shoelace_area():
     """sum C dx^2 equals the area enclosed by the traced marker loops
     (Green's theorem), also after the interface has been deformed."""
-    rng = W.Xoshiro256ss(9)
+    rng = W.Rng(9)
     n = 64
     circles = W.place_circles(rng, 12, 0.03, 0.12, 2.0 / n, lambda x, y, r: True)
     wl = W.Workload("t", n, 1.0 / n, W.circle_scene(circles),
@@ -531,7 +531,7 @@ def test_hf_circle_curvature_converges():
 # initialisation (Sec. 3.2)
 # ---------------------------------------------------------------------------
 def test_init_markers_on_shapes():
-    rng = W.Xoshiro256ss(3)
+    rng = W.Rng(3)
     n = 128
     dx = 1.0 / n
     circles = W.place_circles(rng, 20, 3 * dx, 12 * dx, 2 * dx, lambda x, y, r: True)
