@@ -156,6 +156,17 @@ void ebit_destroy(ebit_ctx* ctx);
 /* Message of the last failure on the calling thread (never NULL). */
 const char* ebit_last_error(void);
 
+/* Per-kernel timing for profiling.  When on, the context records a pair of
+ * CUDA events on its stream around every kernel it launches for a step;
+ * ebit_timings (synchronous) returns, per kernel kind, the summed duration in
+ * milliseconds and the number of launches since the last call, then resets.
+ * Kinds: EBIT_K_SWEEP (sweep pass 1), EBIT_K_CENTRE (sweep pass 2),
+ * EBIT_K_FRACTION, EBIT_K_AREA, EBIT_K_CURVATURE. */
+enum { EBIT_K_SWEEP = 0, EBIT_K_CENTRE, EBIT_K_FRACTION, EBIT_K_AREA, EBIT_K_CURVATURE,
+       EBIT_K_COUNT = 8 };
+ebit_status ebit_set_timing(ebit_ctx* ctx, int on);
+ebit_status ebit_timings(ebit_ctx* ctx, double* ms, int64_t* launches);
+
 /* Device bytes a context of this grid allocates (for admission control). */
 size_t ebit_footprint(const ebit_grid* grid);
 

@@ -89,9 +89,34 @@ struct ebit_ctx {
   int* status = nullptr;
   int64_t step_index = 0;
   std::vector<void*> allocs;
+  // per-kernel event timing (off unless ebit_set_timing)
+  bool timing = false;
+  struct Mark { cudaEvent_t a, b; int kind; };
+  std::vector<Mark> marks;
+  size_t marks_used = 0;
 };
 
 namespace {
+
+// Brackets a launch with events when timing is on.
+struct Timed {
+  ebit_ctx* c;
+  ebit_ctx::Mark* m = nullptr;
+  Timed(ebit_ctx* c_, int kind) : c(c_) {
+    if (!c->timing) return;
+    if (c->marks_used == c->marks.size()) {
+      ebit_ctx::Mark k{};
+      if (cudaEventCreate(&k.a) != cudaSuccess || cudaEventCreate(&k.b) != cudaSuccess) return;
+      c->marks.push_back(k);
+    }
+    m = &c->marks[c->marks_used++];
+    m->kind = kind;
+    cudaEventRecord(m->a, c->stream);
+  }
+  ~Timed() {
+    if (m) cudaEventRecord(m->b, c->stream);
+  }
+};
 
 ebit_status dalloc(ebit_ctx* c, void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
@@ -138,13 +163,22 @@ template <typename R>
 ebit_status launch_fields(ebit_ctx* c) {
   const Layout& L = c->L;
   const int b = c->cur;
-  ebit::k_fraction<R><<<L.grid, L.block, 0, c->stream>>>(
-      c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], L.d, (R*)c->C, c->partial, c->ctr);
-  ebit::k_area<<<1, 256, 0, c->stream>>>(c->partial, (long long)L.partial_count,
-                                         c->grid.dx * c->grid.dx, c->area);
-  ebit::k_curvature<R><<<L.grid, L.block, 0, c->stream>>>(
-      c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], (const R*)c->C, L.d,
-      (R)c->grid.dx, (R*)c->kappa, c->ctr);
+  {
+    Timed t(c, EBIT_K_FRACTION);
+    ebit::k_fraction<R><<<L.grid, L.block, 0, c->stream>>>(
+        c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], L.d, (R*)c->C, c->partial, c->ctr);
+  }
+  {
+    Timed t(c, EBIT_K_AREA);
+    ebit::k_area<<<1, 256, 0, c->stream>>>(c->partial, (long long)L.partial_count,
+                                           c->grid.dx * c->grid.dx, c->area);
+  }
+  {
+    Timed t(c, EBIT_K_CURVATURE);
+    ebit::k_curvature<R><<<L.grid, L.block, 0, c->stream>>>(
+        c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], (const R*)c->C, L.d,
+        (R)c->grid.dx, (R*)c->kappa, c->ctr);
+  }
   EBIT_CK(cudaGetLastError());
   return EBIT_OK;
 }
@@ -160,13 +194,19 @@ ebit_status launch_sweep(ebit_ctx* c, const void* vel, double lam) {
   ebit::View<R, AX> S{c->K[src], c->Z[src], (const R*)c->sH[src], (const R*)c->sV[src],
                       (const R*)vel, L.d};
   ebit::Buf<R> out{c->K[dst], c->Z[dst], (R*)c->sH[dst], (R*)c->sV[dst]};
-  ebit::k_sweep<R, AX><<<L.grid, L.block, 0, c->stream>>>(
-      S, out, (R)lam, (c->grid.flags & EBIT_FIT_LINE) ? 1 : 0, c->from_left, c->from_right,
-      c->ctr, c->cfl_bits, c->status);
+  {
+    Timed t(c, EBIT_K_SWEEP);
+    ebit::k_sweep<R, AX><<<L.grid, L.block, 0, c->stream>>>(
+        S, out, (R)lam, (c->grid.flags & EBIT_FIT_LINE) ? 1 : 0, c->from_left, c->from_right,
+        c->ctr, c->cfl_bits, c->status);
+  }
   ebit::View<R, AX> Sn{c->K[dst], c->Z[dst], (const R*)c->sH[dst], (const R*)c->sV[dst],
                        (const R*)vel, L.d};
-  ebit::k_centre<R, AX><<<L.grid, L.block, 0, c->stream>>>(Sn, c->Z[src], c->Z[dst],
-                                                          c->from_left, c->from_right, c->ctr);
+  {
+    Timed t(c, EBIT_K_CENTRE);
+    ebit::k_centre<R, AX><<<L.grid, L.block, 0, c->stream>>>(Sn, c->Z[src], c->Z[dst],
+                                                            c->from_left, c->from_right, c->ctr);
+  }
   EBIT_CK(cudaGetLastError());
   c->cur = dst;
   return EBIT_OK;
@@ -506,9 +546,33 @@ ebit_status ebit_sync(ebit_ctx* c) {
   return take_status(c);
 }
 
+ebit_status ebit_set_timing(ebit_ctx* c, int on) {
+  if (!c) return fail(EBIT_EINVAL, "NULL context");
+  c->timing = on != 0;
+  return EBIT_OK;
+}
+
+ebit_status ebit_timings(ebit_ctx* c, double* ms, int64_t* launches) {
+  if (!c || !ms || !launches) return fail(EBIT_EINVAL, "NULL argument");
+  EBIT_CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < EBIT_K_COUNT; ++k) { ms[k] = 0.0; launches[k] = 0; }
+  for (size_t t = 0; t < c->marks_used; ++t) {
+    float e = 0.0f;
+    EBIT_CK(cudaEventElapsedTime(&e, c->marks[t].a, c->marks[t].b));
+    ms[c->marks[t].kind] += e;
+    launches[c->marks[t].kind] += 1;
+  }
+  c->marks_used = 0;
+  return EBIT_OK;
+}
+
 void ebit_destroy(ebit_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (auto& m : c->marks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
   free_ctx(c);
   delete c;
 }

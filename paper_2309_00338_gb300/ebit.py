@@ -88,7 +88,13 @@ SIGNATURES = {
     "ebit_destroy": (None, [_P]),
     "ebit_last_error": (ctypes.c_char_p, []),
     "ebit_footprint": (ctypes.c_size_t, [ctypes.POINTER(ebit_grid)]),
+    "ebit_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ebit_timings": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }
+
+K_SWEEP, K_CENTRE, K_FRACTION, K_AREA, K_CURVATURE = range(5)
+K_COUNT = 8
+KERNEL_NAMES = ["sweep", "centre", "fraction", "area", "curvature"]
 
 
 def lib(path: str | None = None):
@@ -238,3 +244,15 @@ def ebit_sync(ctx):
 def ebit_destroy(ctx):
     if ctx:
         lib().ebit_destroy(ctx)
+
+
+def ebit_set_timing(ctx, on=True):
+    _check(lib().ebit_set_timing(ctx, int(bool(on))), "ebit_set_timing")
+
+
+def ebit_timings(ctx):
+    """{kernel name: (total ms, launches)} since the last call."""
+    ms = (ctypes.c_double * K_COUNT)()
+    n = (ctypes.c_int64 * K_COUNT)()
+    _check(lib().ebit_timings(ctx, ms, n), "ebit_timings")
+    return {KERNEL_NAMES[k]: (ms[k], n[k]) for k in range(len(KERNEL_NAMES))}
