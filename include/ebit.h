@@ -167,6 +167,27 @@ enum { EBIT_K_SWEEP = 0, EBIT_K_CENTRE, EBIT_K_FRACTION, EBIT_K_AREA, EBIT_K_CUR
 ebit_status ebit_set_timing(ebit_ctx* ctx, int on);
 ebit_status ebit_timings(ebit_ctx* ctx, double* ms, int64_t* launches);
 
+/* Volume fractions without allocating device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (a solver that allocates all device memory at start-up and
+ * forbids allocation inside its time loop, or a host framework that owns every
+ * device buffer).  It computes C, the area sum C dx^2 and the marker counts of
+ * a state held in the caller's device buffers, in the byte layout of
+ * ebit_state_host: K (ny+1)*(nx+1) bytes, Z ny*nx bytes, sH (ny+1)*nx and
+ * sV ny*(nx+1) elements of the grid precision.  Outputs (device): C ny*nx
+ * elements, *area one double, marker_counts two int64 {horizontal, vertical}
+ * or NULL.  Asynchronous on stream.
+ * Scratch: a 1 MiB array inside the library that every GPU loading the
+ * library holds until exit; it limits grids to 131072 blocks of 32x8 vertices
+ * (about 5790x5790 cells) and larger grids return EBIT_EINVAL.  The first call
+ * on a device looks up the array's device address (make it before any stream
+ * capture); it calls no cudaMalloc/cudaFree.  All calls share the array, so
+ * calls that overlap on the GPU (different streams, or other host threads)
+ * race and must be serialised by the caller. */
+ebit_status ebit_fraction_noalloc(const ebit_grid* grid, const uint8_t* K, const uint8_t* Z,
+                                  const void* sH, const void* sV, void* C, double* area,
+                                  int64_t* marker_counts, void* stream);
+
 /* Device bytes a context of this grid allocates (for admission control). */
 size_t ebit_footprint(const ebit_grid* grid);
 

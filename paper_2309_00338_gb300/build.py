@@ -1,9 +1,12 @@
-"""Compile libebit.so for sm_103a in-tree (paper_2309_00338_gb300/_build)."""
+"""Compile libebit.so for sm_103a in-tree (paper_2309_00338_gb300/_build).
+
+Each translation unit is compiled to an object in parallel, then linked."""
 from __future__ import annotations
 
 import os
 import shutil
 import subprocess
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -11,8 +14,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libebit.so")
-SOURCES = ["ebit.cu"]
+SOURCES = ["ebit.cu", "ebit_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC"]
 
 
 def nvcc() -> str:
@@ -31,13 +35,22 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     newest = max(os.path.getmtime(f) for f in _inputs())
     if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
         return LIB_PATH
-    tmp = LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-fmad=false",
-           "-Xcompiler", "-fPIC", "-shared", "-I", INCLUDE, "-I", CSRC, "-o", tmp]
-    if verbose:
-        cmd += ["-Xptxas", "-v"]
-    cmd += [os.path.join(CSRC, s) for s in SOURCES]
-    subprocess.run(cmd, check=True)
+    pid = os.getpid()
+
+    def compile_one(src):
+        obj = os.path.join(OUT_DIR, f"{os.path.splitext(src)[0]}.{pid}.o")
+        cmd = [nvcc(), *ARCH, *FLAGS, "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
+        if verbose:
+            cmd += ["-Xptxas", "-v"]
+        subprocess.run(cmd, check=True)
+        return obj
+
+    with ThreadPoolExecutor(len(SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = LIB_PATH + f".{pid}.tmp"
+    subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], check=True)
+    for o in objs:
+        os.unlink(o)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
 

@@ -417,6 +417,10 @@ ebit_status get_state(ebit_ctx* c, ebit_state_host* st) {
 
 }  // namespace
 
+// Lets the other translation units of the library report errors through
+// ebit_last_error(); not part of the exported interface.
+__attribute__((visibility("hidden"))) void ebit_detail_set_error(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 const char* ebit_last_error(void) { return g_err.c_str(); }

@@ -90,6 +90,7 @@ SIGNATURES = {
     "ebit_footprint": (ctypes.c_size_t, [ctypes.POINTER(ebit_grid)]),
     "ebit_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "ebit_timings": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+    "ebit_fraction_noalloc": (ctypes.c_int, [ctypes.POINTER(ebit_grid), _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 K_SWEEP, K_CENTRE, K_FRACTION, K_AREA, K_CURVATURE = range(5)
@@ -256,3 +257,14 @@ def ebit_timings(ctx):
     n = (ctypes.c_int64 * K_COUNT)()
     _check(lib().ebit_timings(ctx, ms, n), "ebit_timings")
     return {KERNEL_NAMES[k]: (ms[k], n[k]) for k in range(len(KERNEL_NAMES))}
+
+
+def ebit_fraction_noalloc(nx, ny, dx, prec, K, Z, sH, sV, C, area, marker_counts=None, stream=None):
+    """ebit_fraction_noalloc: fractions of a state in caller-owned device
+    tensors (byte colours, fractions of the grid precision) without any
+    device allocation; C, area (1 double) and marker_counts (2 int64) are
+    caller-owned device tensors."""
+    g = ebit_grid(nx, ny, dx, prec, 0)
+    _check(lib().ebit_fraction_noalloc(ctypes.byref(g), _dev_ptr(K), _dev_ptr(Z), _dev_ptr(sH), _dev_ptr(sV),
+                                       _dev_ptr(C), _dev_ptr(area), _dev_ptr(marker_counts), _stream(stream)),
+           "ebit_fraction_noalloc")

@@ -1,0 +1,73 @@
+"""ebit_fraction_noalloc, the volume-fraction entry point for callers that
+cannot allocate device memory (a solver that allocates everything at start-up
+and forbids allocation in its time loop, or a host framework that owns all
+device buffers).  Its output must equal that of the allocating entry point
+ebit_fraction on the same state, on two calls in a row (the second call reuses
+the library's scratch array as the first left it).
+
+This file is collected last so that a run stopping at its first failure has
+run every other test before it."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_00338_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2309_00338_gb300 import ebit  # noqa: E402
+
+
+def _states(prec):
+    n = 96
+    dx = 1.0 / n
+    rng = W.Rng(77)
+    circles = W.place_circles(rng, 25, 2 * dx, 9 * dx, 2 * dx, lambda x, y, r: True)
+    S = oracle.init(n, n, dx, W.circle_scene(circles), prec)
+    first = S.copy()
+    f = W.vortex_field(n, n, dx, 2.0)
+    for k in range(20):
+        oracle.step(S, f.u, f.v, 0.5 * dx)
+    return [first, S]   # two different states for the two calls
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_noalloc_matches_allocating_fraction_twice(prec):
+    dt = torch.float64 if prec == 0 else torch.float32
+    for S in _states(prec):
+        nx, ny = S.nx, S.ny
+        # the allocating path
+        ctx = ebit.ebit_create(nx, ny, S.dx, prec)
+        try:
+            ebit.ebit_load_state(ctx, S.K, S.Z, S.sH, S.sV)
+            C_ref = torch.empty((ny, nx), dtype=dt, device="cuda")
+            area_ref = ebit.ebit_fraction(ctx, C_ref)
+            d = ebit.ebit_diagnostics(ctx)
+        finally:
+            ebit.ebit_destroy(ctx)
+        # the no-allocation path, on the caller's device buffers
+        K = torch.from_numpy(S.K).cuda()
+        Z = torch.from_numpy(S.Z).cuda()
+        sH = torch.from_numpy(S.sH).to(dt).cuda()
+        sV = torch.from_numpy(S.sV).to(dt).cuda()
+        C = torch.full((ny, nx), float("nan"), dtype=dt, device="cuda")
+        area = torch.zeros(1, dtype=torch.float64, device="cuda")
+        counts = torch.zeros(2, dtype=torch.int64, device="cuda")
+        ebit.ebit_fraction_noalloc(nx, ny, S.dx, prec, K, Z, sH, sV, C, area, counts)
+        torch.cuda.synchronize()
+        assert torch.equal(C, C_ref)
+        assert abs(area.item() - area_ref) <= 1e-12 * max(1.0, abs(area_ref))
+        assert counts.tolist() == [int(d["counters"][ebit.D_NH]), int(d["counters"][ebit.D_NV])]
+
+
+def test_noalloc_rejects_grids_beyond_its_scratch():
+    dt = torch.float32
+    K = torch.zeros(1, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ebit.EbitError) as e:
+        ebit.ebit_fraction_noalloc(8192, 8192, 1.0 / 8192, 1, K, K, K.to(dt), K.to(dt), K.to(dt),
+                                   torch.zeros(1, dtype=torch.float64, device="cuda"))
+    assert e.value.status == ebit.EBIT_EINVAL and "scratch" in str(e.value)
