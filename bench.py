@@ -65,11 +65,9 @@ def kernel_bytes_per_cell(kind: str, esz: int) -> float:
         "sweep": (2 * bits + 3 * esz) + (bits + 2 * esz + 2.0),
         # reads new K, old Z, verdicts; writes Z
         "centre": 2 * bits + 2.0 + bits,
-        # reads K, Z, sH, sV; writes C
-        "fraction": 2 * bits + 2 * esz + esz,
+        # reads K, Z, sH, sV; writes C and kappa
+        "fields": 2 * bits + 2 * esz + 2 * esz,
         "area": 0.0,
-        # reads K, Z, sH, sV, C; writes kappa
-        "curvature": 2 * bits + 3 * esz + esz,
     }[kind]
 
 

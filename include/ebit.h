@@ -160,10 +160,10 @@ const char* ebit_last_error(void);
  * CUDA events on its stream around every kernel it launches for a step;
  * ebit_timings (synchronous) returns, per kernel kind, the summed duration in
  * milliseconds and the number of launches since the last call, then resets.
- * Kinds: EBIT_K_SWEEP (sweep pass 1), EBIT_K_CENTRE (sweep pass 2),
- * EBIT_K_FRACTION, EBIT_K_AREA, EBIT_K_CURVATURE. */
-enum { EBIT_K_SWEEP = 0, EBIT_K_CENTRE, EBIT_K_FRACTION, EBIT_K_AREA, EBIT_K_CURVATURE,
-       EBIT_K_COUNT = 8 };
+ * Kinds: EBIT_K_SWEEP (a split sweep), EBIT_K_CENTRE (second pass of the
+ * gather sweep, when selected), EBIT_K_FIELDS (fractions, curvature and area
+ * partials), EBIT_K_AREA (area sum). */
+enum { EBIT_K_SWEEP = 0, EBIT_K_CENTRE, EBIT_K_FIELDS, EBIT_K_AREA, EBIT_K_COUNT = 8 };
 ebit_status ebit_set_timing(ebit_ctx* ctx, int on);
 ebit_status ebit_timings(ebit_ctx* ctx, double* ms, int64_t* launches);
 

@@ -2,12 +2,15 @@
 // launch sequence of one EBIT step, state I/O and error reporting.
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "ebit.h"
 #include "ebit_kernels.cuh"
+#include "ebit_tile.cuh"
+#include "ebit_fields.cuh"
 
 namespace {
 
@@ -89,6 +92,9 @@ struct ebit_ctx {
   int* status = nullptr;
   int64_t step_index = 0;
   std::vector<void*> allocs;
+  // EBIT_SWEEP=gather in the environment selects the thread-per-vertex gather
+  // kernels instead of the tiled one (kept for differential testing)
+  bool gather = false;
   // per-kernel event timing (off unless ebit_set_timing)
   bool timing = false;
   struct Mark { cudaEvent_t a, b; int kind; };
@@ -163,21 +169,17 @@ template <typename R>
 ebit_status launch_fields(ebit_ctx* c) {
   const Layout& L = c->L;
   const int b = c->cur;
+  const dim3 fgrid((L.d.nx + 1 + ebit::kFX - 1) / ebit::kFX, (L.d.ny + 1 + ebit::kFY - 1) / ebit::kFY);
   {
-    Timed t(c, EBIT_K_FRACTION);
-    ebit::k_fraction<R><<<L.grid, L.block, 0, c->stream>>>(
-        c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], L.d, (R*)c->C, c->partial, c->ctr);
+    Timed t(c, EBIT_K_FIELDS);
+    ebit::k_fields_tile<R><<<fgrid, ebit::kFieldThreads, 0, c->stream>>>(
+        c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], L.d, (R)c->grid.dx, (R*)c->C,
+        (R*)c->kappa, c->partial, c->ctr);
   }
   {
     Timed t(c, EBIT_K_AREA);
-    ebit::k_area<<<1, 256, 0, c->stream>>>(c->partial, (long long)L.partial_count,
+    ebit::k_area<<<1, 256, 0, c->stream>>>(c->partial, (long long)fgrid.x * fgrid.y,
                                            c->grid.dx * c->grid.dx, c->area);
-  }
-  {
-    Timed t(c, EBIT_K_CURVATURE);
-    ebit::k_curvature<R><<<L.grid, L.block, 0, c->stream>>>(
-        c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], (const R*)c->C, L.d,
-        (R)c->grid.dx, (R*)c->kappa, c->ctr);
   }
   EBIT_CK(cudaGetLastError());
   return EBIT_OK;
@@ -191,21 +193,36 @@ template <typename R, int AX>
 ebit_status launch_sweep(ebit_ctx* c, const void* vel, double lam) {
   const Layout& L = c->L;
   const int src = c->cur, dst = 1 - c->cur;
-  ebit::View<R, AX> S{c->K[src], c->Z[src], (const R*)c->sH[src], (const R*)c->sV[src],
-                      (const R*)vel, L.d};
+  const int line_only = (c->grid.flags & EBIT_FIT_LINE) ? 1 : 0;
+  ebit::GView<R, AX> S{c->K[src], c->Z[src], (const R*)c->sH[src], (const R*)c->sV[src],
+                       (const R*)vel, L.d, (R)lam};
   ebit::Buf<R> out{c->K[dst], c->Z[dst], (R*)c->sH[dst], (R*)c->sV[dst]};
-  {
+  if (c->gather) {
+    {
+      Timed t(c, EBIT_K_SWEEP);
+      ebit::k_sweep<R, AX><<<L.grid, L.block, 0, c->stream>>>(
+          S, out, line_only, c->from_left, c->from_right, c->ctr, c->cfl_bits, c->status);
+    }
+    ebit::GView<R, AX> Sn{c->K[dst], c->Z[dst], (const R*)c->sH[dst], (const R*)c->sV[dst],
+                          (const R*)vel, L.d, (R)lam};
+    {
+      Timed t(c, EBIT_K_CENTRE);
+      ebit::k_centre<R, AX><<<L.grid, L.block, 0, c->stream>>>(Sn, c->Z[src], c->Z[dst],
+                                                              c->from_left, c->from_right, c->ctr);
+    }
+  } else {
+    constexpr size_t smem = ebit::tile_smem_bytes<R>();
+    static bool attr = false;  // once per instantiation and process
+    if (!attr) {
+      EBIT_CK(cudaFuncSetAttribute(ebit::k_sweep_tile<R, AX>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr = true;
+    }
+    const int tnx = AX ? L.d.ny : L.d.nx, tny = AX ? L.d.nx : L.d.ny;
+    const dim3 grid((tnx + 1 + ebit::kTI - 1) / ebit::kTI, (tny + 1 + ebit::kTJ - 1) / ebit::kTJ);
     Timed t(c, EBIT_K_SWEEP);
-    ebit::k_sweep<R, AX><<<L.grid, L.block, 0, c->stream>>>(
-        S, out, (R)lam, (c->grid.flags & EBIT_FIT_LINE) ? 1 : 0, c->from_left, c->from_right,
-        c->ctr, c->cfl_bits, c->status);
-  }
-  ebit::View<R, AX> Sn{c->K[dst], c->Z[dst], (const R*)c->sH[dst], (const R*)c->sV[dst],
-                       (const R*)vel, L.d};
-  {
-    Timed t(c, EBIT_K_CENTRE);
-    ebit::k_centre<R, AX><<<L.grid, L.block, 0, c->stream>>>(Sn, c->Z[src], c->Z[dst],
-                                                            c->from_left, c->from_right, c->ctr);
+    ebit::k_sweep_tile<R, AX><<<grid, ebit::kTileThreads, smem, c->stream>>>(
+        S, out, line_only, c->ctr, c->cfl_bits, c->status);
   }
   EBIT_CK(cudaGetLastError());
   c->cur = dst;
@@ -246,6 +263,8 @@ ebit_status new_ctx(ebit_ctx** out, const ebit_grid* grid, void* stream) {
   c->grid = *grid;
   c->L = layout_of(grid);
   c->stream = (cudaStream_t)stream;
+  const char* impl = std::getenv("EBIT_SWEEP");
+  c->gather = impl && std::strcmp(impl, "gather") == 0;
   const ebit_status s = alloc_ctx(c);
   if (s != EBIT_OK) {
     free_ctx(c);

@@ -9,14 +9,21 @@
 // A marker exists exactly where the corner colours at the ends of its edge
 // differ (Sec. 2.4); fractions of edges without a marker are don't-care.
 //
-// One split sweep is written once, for the x direction, on a "view" of the
-// state: AX = 0 reads the grid as it is, AX = 1 reads it transposed (vertex
-// (i,j) is stored vertex (j,i), horizontal and vertical edges swap), which
-// turns the y sweep into an x sweep.  Every decision is taken with the exact
-// integer predicate "left of grid line k" <=> ix < k on moved points stored
-// as (grid line index, fraction), so corner flips and chord crossings agree.
-// The library is compiled with -fmad=false: every expression below is the
-// sequence of IEEE operations it spells.
+// One split sweep is written once, for the x direction, in "sweep
+// coordinates": AX = 0 reads the grid as it is, AX = 1 reads it transposed
+// (vertex (i,j) is stored vertex (j,i), horizontal and vertical edges swap),
+// which turns the y sweep into an x sweep.  Every decision is taken with the
+// exact integer predicate "left of grid line k" <=> ix < k on moved points
+// stored as (grid line index, fraction), so corner flips and chord crossings
+// agree.  The library is compiled with -fmad=false: every expression below is
+// the sequence of IEEE operations it spells.
+//
+// The sweep logic (segments, neighbours, centre rule, circle fit, candidate
+// selection) is written against an accessor A that answers, in sweep
+// coordinates: tnx/tny, old colours k/z, moved(marker), knew (new corner
+// colour) and landing (aligned markers landing on an edge).  GView answers
+// from global memory by recomputation; TView from a shared-memory tile where
+// each answer was computed once.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -54,44 +61,40 @@ struct Dims {
   long long P;    // element pitch of sH, sV, C, kappa
 };
 
-// Read view of a state in sweep coordinates (see the file comment).
-template <typename R, int AX>
-struct View {
-  const uint32_t* __restrict__ K;
-  const uint32_t* __restrict__ Z;
-  const R* __restrict__ sH;
-  const R* __restrict__ sV;
-  const R* __restrict__ w;  // velocity component along the sweep, (ny+1)x(nx+1)
-  Dims d;
-  __device__ __forceinline__ int tnx() const { return AX ? d.ny : d.nx; }
-  __device__ __forceinline__ int tny() const { return AX ? d.nx : d.ny; }
-  __device__ __forceinline__ int kreal(int x, int y) const {
-    return (__ldg(&K[(long long)y * d.kw + (x >> 5)]) >> (x & 31)) & 1;
-  }
-  __device__ __forceinline__ int k(int i, int j) const { return AX ? kreal(j, i) : kreal(i, j); }
-  __device__ __forceinline__ int z(int i, int j) const {
-    const int x = AX ? j : i, y = AX ? i : j;
-    return (__ldg(&Z[(long long)y * d.zw + (x >> 5)]) >> (x & 31)) & 1;
-  }
-  __device__ __forceinline__ R h(int i, int j) const {
-    return AX ? __ldg(&sV[(long long)i * d.P + j]) : __ldg(&sH[(long long)j * d.P + i]);
-  }
-  __device__ __forceinline__ R v(int i, int j) const {
-    return AX ? __ldg(&sH[(long long)i * d.P + j]) : __ldg(&sV[(long long)j * d.P + i]);
-  }
-  __device__ __forceinline__ R vel(int i, int j) const {
-    return AX ? __ldg(&w[(long long)i * (d.nx + 1) + j]) : __ldg(&w[(long long)j * (d.nx + 1) + i]);
-  }
+struct Mk {
+  int kind;  // 0 horizontal edge, 1 vertical edge, -1 none
+  int i, j;
+};
+
+// A moved point: grid line ix at or left of it and fraction fx in [0,1);
+// y = jy + fy is unchanged by the sweep.
+template <typename R>
+struct AP {
+  int ix;
+  R fx;
+  int jy;
+  R fy;
+};
+
+// CFL and wall flags of one moved marker; dabs is |d| in the state precision
+// (a float |d| converts to double exactly, so the largest one is the same).
+struct Flags {
+  int cfl = 0, clamp = 0;
+  float dabs = 0.0f;
+  double dabs64 = 0.0;
+};
+
+// Aligned markers landing on an edge (Sec. 2.4).
+template <typename R>
+struct Landing {
+  int present, kept_src, cancelled, invariant;
+  R kept_fx;
 };
 
 // ---------------------------------------------------------------------------
 // Cell topology.  Corner c of cell (i,j) counter-clockwise from (i,j); edge e
 // joins corners e and e+1 (0 bottom, 1 right, 2 top, 3 left).
 // ---------------------------------------------------------------------------
-template <typename R, int AX>
-__device__ __forceinline__ int corner_mask(const View<R, AX>& S, int i, int j) {
-  return S.k(i, j) | (S.k(i + 1, j) << 1) | (S.k(i + 1, j + 1) << 2) | (S.k(i, j + 1) << 3);
-}
 __device__ __forceinline__ int edge_mask(int q) { return (q ^ ((q >> 1) | ((q & 1) << 3))) & 15; }
 
 // Segments of the implicit connectivity (Sec. 2.3, Fig. 4): two markers are
@@ -116,11 +119,6 @@ __device__ __forceinline__ int segments(int q, int zc, int seg[2][2]) {
   return m;
 }
 
-struct Mk {
-  int kind;  // 0 horizontal edge, 1 vertical edge, -1 none
-  int i, j;
-};
-
 __device__ __forceinline__ Mk edge_marker(int ci, int cj, int e) {
   Mk m;
   m.kind = e & 1;
@@ -129,14 +127,19 @@ __device__ __forceinline__ Mk edge_marker(int ci, int cj, int e) {
   return m;
 }
 
-template <typename R, int AX>
-__device__ __forceinline__ int cell_segments(const View<R, AX>& S, int i, int j, int seg[2][2]) {
+template <class A>
+__device__ __forceinline__ int corner_mask(const A& S, int i, int j) {
+  return S.k(i, j) | (S.k(i + 1, j) << 1) | (S.k(i + 1, j + 1) << 2) | (S.k(i, j + 1) << 3);
+}
+
+template <class A>
+__device__ __forceinline__ int cell_segments(const A& S, int i, int j, int seg[2][2]) {
   const int q = corner_mask(S, i, j);
   return segments(q, edge_mask(q) == 15 ? S.z(i, j) : 0, seg);
 }
 
-template <typename R, int AX>
-__device__ int partner(const View<R, AX>& S, int ci, int cj, int e) {
+template <class A>
+__device__ int partner(const A& S, int ci, int cj, int e) {
   int seg[2][2];
   const int n = cell_segments(S, ci, cj, seg);
   for (int t = 0; t < n; ++t) {
@@ -148,8 +151,8 @@ __device__ int partner(const View<R, AX>& S, int ci, int cj, int e) {
 
 // The marker next to m along the interface on the far side of m's edge, seen
 // from cell (ci,cj); writes the cell it lies in.
-template <typename R, int AX>
-__device__ Mk beyond(const View<R, AX>& S, Mk m, int ci, int cj, int* oi_, int* oj_) {
+template <class A>
+__device__ Mk beyond(const A& S, Mk m, int ci, int cj, int* oi_, int* oj_) {
   int oi, oj, oe;
   if (m.kind == 0) {
     oi = m.i;
@@ -168,21 +171,13 @@ __device__ Mk beyond(const View<R, AX>& S, Mk m, int ci, int cj, int* oi_, int* 
 }
 
 // ---------------------------------------------------------------------------
-// Advection along the sweep (Eq. 4).  A moved point is (ix, fx): grid line at
-// or left of it and a fraction in [0,1); y = jy + fy is unchanged.
+// Advection along the sweep (Eq. 4).
 // ---------------------------------------------------------------------------
-template <typename R>
-struct AP {
-  int ix;
-  R fx;
-  int jy;
-  R fy;
-};
 
-struct Flags {
-  int cfl = 0, clamp = 0;
-  double dabs = 0.0;
-};
+template <typename R>
+__device__ __forceinline__ R dabs_of(const Flags& f) {
+  return sizeof(R) == 4 ? (R)f.dabs : (R)f.dabs64;
+}
 
 // Velocity by linear interpolation along the marker's edge (the bilinear
 // interpolation of Sec. 2.1 on a grid line); displacement in cells, clipped to
@@ -191,8 +186,12 @@ template <typename R>
 __device__ __forceinline__ R displacement(R s, R ua, R ub, R lam, Flags& f) {
   const R vel = (R(1) - s) * ua + s * ub;
   R d = vel * lam;
-  const double ad = fabs((double)d);
-  if (ad == ad && ad > f.dabs) f.dabs = ad;
+  const R ad = fabs(d);
+  if (sizeof(R) == 4) {
+    if (ad == ad && (float)ad > f.dabs) f.dabs = (float)ad;
+  } else {
+    if (ad == ad && (double)ad > f.dabs64) f.dabs64 = (double)ad;
+  }
   if (!(fabs(d) <= R(1))) {
     f.cfl = 1;
     d = (d > R(0)) ? R(1) : R(-1);
@@ -200,100 +199,75 @@ __device__ __forceinline__ R displacement(R s, R ua, R ub, R lam, Flags& f) {
   return d;
 }
 
-template <typename R, int AX>
-__device__ AP<R> advect(const View<R, AX>& S, R lam, Mk m, Flags& f) {
-  const int nx = S.tnx();
+// Moved point of an aligned marker on edge (i, line) with fraction s, given the
+// velocities at the edge's ends; nx = number of cells along the sweep.
+template <typename R>
+__device__ __forceinline__ AP<R> move_aligned(int i, int line, R s, R ua, R ub, R lam, int nx,
+                                               Flags& f) {
+  const R d = displacement(s, ua, ub, lam, f);
+  const R t = s + d;
+  const R fl = floor(t);
+  R fx = t - fl;
+  int sh = (int)fl;
+  if (sh > 1) { sh = 1; fx = below_one<R>(); }
+  if (fx >= R(1)) fx = below_one<R>();
+  int ix = i + sh;
+  // markers cannot leave the domain: they stop at the wall
+  if (ix < 0) { ix = 0; fx = R(0); f.clamp = 1; }
+  else if (ix > nx - 1) { ix = nx - 1; fx = below_one<R>(); f.clamp = 1; }
   AP<R> p;
-  p.jy = m.j;
-  if (m.kind == 0) {
-    // aligned marker: along its own line
-    const R s = S.h(m.i, m.j);
-    const R d = displacement(s, S.vel(m.i, m.j), S.vel(m.i + 1, m.j), lam, f);
-    const R t = s + d;
-    const R fl = floor(t);
-    R fx = t - fl;
-    int sh = (int)fl;
-    if (sh > 1) { sh = 1; fx = below_one<R>(); }
-    if (fx >= R(1)) fx = below_one<R>();
-    int ix = m.i + sh;
-    if (ix < 0) { ix = 0; fx = R(0); f.clamp = 1; }
-    else if (ix > nx - 1) { ix = nx - 1; fx = below_one<R>(); f.clamp = 1; }
-    p.ix = ix;
-    p.fx = fx;
-    p.fy = R(0);
-    return p;
-  }
-  const R s = S.v(m.i, m.j);
+  p.ix = ix;
+  p.fx = fx;
+  p.jy = line;
+  p.fy = R(0);
+  return p;
+}
+
+// Moved point (the gray point of Fig. 2c) of an unaligned marker on vertical
+// edge (i, row); markers on the two walls normal to the sweep stay.
+template <typename R>
+__device__ __forceinline__ AP<R> move_unaligned(int i, int row, R s, R ua, R ub, R lam, int nx,
+                                                 Flags& f) {
+  AP<R> p;
+  p.jy = row;
   p.fy = s;
-  if (m.i == 0 || m.i == nx) {  // wall markers normal to the sweep stay
-    p.ix = m.i;
+  if (i == 0 || i == nx) {
+    p.ix = i;
     p.fx = R(0);
     return p;
   }
-  // unaligned marker: the gray point of Fig. 2c
-  const R d = displacement(s, S.vel(m.i, m.j), S.vel(m.i, m.j + 1), lam, f);
+  const R d = displacement(s, ua, ub, lam, f);
   const R fl = floor(d);
   R fx = d - fl;
   if (fx >= R(1)) fx = below_one<R>();
-  p.ix = m.i + (int)fl;
+  p.ix = i + (int)fl;
   p.fx = fx;
   return p;
 }
 
-template <typename R, int AX>
-__device__ __forceinline__ AP<R> moved(const View<R, AX>& S, R lam, Mk m) {
-  Flags f;
-  return advect(S, lam, m, f);
-}
-
-// New corner colour (Sec. 2.3, Fig. 5): vertex i of line j flips once for each
-// aligned marker that passes it; only markers of edges i-1 and i can.
-template <typename R, int AX>
-__device__ int knew(const View<R, AX>& S, R lam, int i, int j) {
-  const int c = S.k(i, j);
-  int r = c;
-  if (i >= 1 && S.k(i - 1, j) != c && moved(S, lam, Mk{0, i - 1, j}).ix >= i) r ^= 1;
-  if (i < S.tnx() && S.k(i + 1, j) != c && moved(S, lam, Mk{0, i, j}).ix < i) r ^= 1;
-  return r;
-}
-
-// Aligned markers landing on edge (i,j) (Sec. 2.4): kept only where the new
-// end colours differ; an odd count keeps the median by (fraction, source).
+// Aligned markers landing on edge (i, j): kept only where the new end colours
+// differ; an odd count keeps the median by (fraction, source edge).
 template <typename R>
-struct Landing {
-  int present, kept_src, cancelled, invariant;
-  R kept_fx;
-};
-
-template <typename R, int AX>
-__device__ Landing<R> landing(const View<R, AX>& S, R lam, int i, int j) {
-  R fx[3];
-  int src[3];
-  int n = 0;
-  for (int e = i - 1; e <= i + 1; ++e) {
-    if (e < 0 || e >= S.tnx() || S.k(e, j) == S.k(e + 1, j)) continue;
-    const AP<R> p = moved(S, lam, Mk{0, e, j});
-    if (p.ix == i) { fx[n] = p.fx; src[n] = e; ++n; }
-  }
-  for (int a = 1; a < n; ++a)  // sort by (fx, src)
+__device__ __forceinline__ Landing<R> choose_landing(int n, R* fx, int* src, int present) {
+  for (int a = 1; a < n; ++a)
     for (int b = a; b > 0 && (fx[b] < fx[b - 1] || (fx[b] == fx[b - 1] && src[b] < src[b - 1])); --b) {
       const R tf = fx[b]; fx[b] = fx[b - 1]; fx[b - 1] = tf;
       const int ts = src[b]; src[b] = src[b - 1]; src[b - 1] = ts;
     }
   Landing<R> L;
-  L.present = knew(S, lam, i, j) ^ knew(S, lam, i + 1, j);
+  L.present = present;
   L.kept_src = -1;
   L.kept_fx = R(0.5);
   L.cancelled = 0;
   L.invariant = 0;
-  if (L.present && (n & 1)) {
+  if (present && (n & 1)) {
     L.kept_src = src[n / 2];
     L.kept_fx = fx[n / 2];
-  } else if (!L.present && !(n & 1)) {
+  } else if (!present && !(n & 1)) {
     L.cancelled = n / 2;
   } else {
     L.invariant = 1;
-    if (L.present && n > 0) {
+    if (present && n > 0) {
       int best = 0;
       for (int t = 1; t < n; ++t)
         if (fabs((double)fx[t] - 0.5) < fabs((double)fx[best] - 0.5)) best = t;
@@ -311,8 +285,8 @@ __device__ Landing<R> landing(const View<R, AX>& S, R lam, int i, int j) {
 // kap = 0).  The crossing wanted lies on the arc A..B that does not contain
 // T, i.e. on the other side of chord AB from T.
 // ---------------------------------------------------------------------------
-__device__ bool circle_cross(double Ax, double Ay, double Bx, double By, double Tx, double Ty,
-                             double* y) {
+__device__ inline bool circle_cross(double Ax, double Ay, double Bx, double By, double Tx,
+                                    double Ty, double* y) {
   const double qx = Bx - Ax, qy = By - Ay;
   const double rx = Tx - Ax, ry = Ty - Ay;
   const double tx = Tx - Bx, ty = Ty - By;
@@ -332,12 +306,15 @@ __device__ bool circle_cross(double Ax, double Ay, double Bx, double By, double 
   const double ya = c0 / h;
   double yrel = ya;
   if (kap != 0.0) {
-    const double yb = h / kap;
+    // the far root is formed only when the near one lies on T's side
     const double sa = qx * ya - qy * x0;
-    const double sb = qx * yb - qy * x0;
     const bool a_with_T = (sa > 0.0 && kap > 0.0) || (sa < 0.0 && kap < 0.0);
-    const bool b_with_T = (sb > 0.0 && kap > 0.0) || (sb < 0.0 && kap < 0.0);
-    if (a_with_T && !b_with_T) yrel = yb;
+    if (a_with_T) {
+      const double yb = h / kap;
+      const double sb = qx * yb - qy * x0;
+      const bool b_with_T = (sb > 0.0 && kap > 0.0) || (sb < 0.0 && kap < 0.0);
+      if (!b_with_T) yrel = yb;
+    }
   }
   const double best = Ay + yrel;
   if (!(best >= 0.0 && best <= 1.0)) return false;
@@ -346,15 +323,13 @@ __device__ bool circle_cross(double Ax, double Ay, double Bx, double By, double 
 }
 
 // Returns the fit kind (D_FIT_*) and the crossing ordinate.
-__device__ int fit_crossing(double Ax, double Ay, double Bx, double By, bool h1, double P1x,
-                            double P1y, bool h4, double P4x, double P4y, bool line_only,
-                            double* y) {
+__device__ inline int fit_crossing(double Ax, double Ay, double Bx, double By, bool h1,
+                                   double P1x, double P1y, bool h4, double P4x, double P4y,
+                                   bool line_only, double* y) {
   if (Bx == 0.0) {
     *y = By;
     return D_FIT_ONLINE;
   }
-  const double x0 = -Ax;
-  const double ystar = Ay + (x0 * (By - Ay)) / (Bx - Ax);
   const double cx = Bx - Ax, cy = By - Ay;
   if (!line_only && cx * cx + cy * cy >= kMinSep2) {
     double ys0 = 0.0, ys1 = 0.0;
@@ -370,7 +345,9 @@ __device__ int fit_crossing(double Ax, double Ay, double Bx, double By, bool h1,
     if (n == 2) { *y = 0.5 * (ys0 + ys1); return D_FIT_TWO; }
     if (n == 1) { *y = ys0; return D_FIT_ONE; }
   }
-  *y = ystar;
+  // no circle: the chord's own crossing
+  const double x0 = -Ax;
+  *y = Ay + (x0 * (By - Ay)) / (Bx - Ax);
   return D_FIT_LINE;
 }
 
@@ -392,16 +369,16 @@ __device__ __forceinline__ void local_xy(const AP<R>& p, int k, int j, double* X
 // interface through m0 then m1 while they stay in column col; the first
 // aligned marker met that survives the sweep is the partner.  Returns the
 // partner's line, or -1 when no aligned marker is reached.
-template <typename R, int AX>
-__device__ int walk(const View<R, AX>& S, R lam, Mk m0, Mk m1, int col) {
+template <class A>
+__device__ int walk(const A& S, Mk m0, Mk m1, int col) {
   Mk pts[2] = {m0, m1};
   for (int t = 0; t < 2; ++t) {
     const Mk m = pts[t];
     if (m.kind < 0) return -1;
-    const AP<R> p = moved(S, lam, m);
+    const auto p = S.moved(m);
     if (p.ix != col) return -1;
     if (m.kind == 0) {
-      const Landing<R> L = landing(S, lam, p.ix, m.j);
+      const auto L = S.landing(p.ix, m.j);
       return (L.present && L.kept_src == m.i) ? m.j : -1;
     }
   }
@@ -410,70 +387,38 @@ __device__ int walk(const View<R, AX>& S, R lam, Mk m0, Mk m1, int col) {
 
 // The next marker along the interface beyond nb (found in cell ci,cj) when
 // nb is closer than the minimum separation to the point (fx,fy).
-template <typename R, int AX>
-__device__ bool far_point(const View<R, AX>& S, R lam, Mk nb, int ci, int cj, int k, int j,
-                          double fx, double fy, double* X, double* Y) {
+template <class A>
+__device__ bool far_point(const A& S, Mk nb, int ci, int cj, int k, int j, double fx, double fy,
+                          double* X, double* Y) {
   if (nb.kind < 0) return false;
-  local_xy(moved(S, lam, nb), k, j, X, Y);
+  local_xy(S.moved(nb), k, j, X, Y);
   const double ex = *X - fx, ey = *Y - fy;
   if (ex * ex + ey * ey < kMinSep2) {
     int oi = 0, oj = 0;
     const Mk nn = beyond(S, nb, ci, cj, &oi, &oj);
     if (nn.kind < 0) return false;
-    local_xy(moved(S, lam, nn), k, j, X, Y);
+    local_xy(S.moved(nn), k, j, X, Y);
   }
   return true;
 }
 
 // New unaligned marker on interior vertical edge (k,j) (Fig. 2c/2d): the
 // moved chords of the old segments of cells k-2..k that cross line k are the
-// candidates; one is kept where the new end colours differ.
+// candidates; one is kept where the new end colours differ.  cnt (nullable)
+// receives the fit kinds, cancellations and invariant breaks.
 template <typename R>
 struct NewV {
   int present, vr, vl;
   R s;
 };
 
-template <typename R, int AX>
-__device__ NewV<R> new_unaligned(const View<R, AX>& S, R lam, bool line_only, int k, int j,
-                                 int* cnt) {
-  double cy[6];
-  int cvr[6], cvl[6], ord[6];
-  int n = 0;
-  for (int c = k - 2; c <= k; ++c) {
-    if (c < 0 || c >= S.tnx()) continue;
-    int seg[2][2];
-    const int ns = cell_segments(S, c, j, seg);
-    for (int t = 0; t < ns; ++t) {
-      const Mk ma = edge_marker(c, j, seg[t][0]);
-      const Mk mb = edge_marker(c, j, seg[t][1]);
-      const AP<R> pa = moved(S, lam, ma), pb = moved(S, lam, mb);
-      const int lo = min(pa.ix, pb.ix), hi = max(pa.ix, pb.ix);
-      if (!(k > lo && k <= hi)) continue;
-      const bool a_left = pa.ix < k;
-      const Mk mA = a_left ? ma : mb, mB = a_left ? mb : ma;
-      const AP<R> A = a_left ? pa : pb, B = a_left ? pb : pa;
-      int c1i = 0, c1j = 0, c4i = 0, c4j = 0;
-      const Mk n1 = beyond(S, mA, c, j, &c1i, &c1j);
-      const Mk n4 = beyond(S, mB, c, j, &c4i, &c4j);
-      double ax, ay, bx, by, p1x = 0, p1y = 0, p4x = 0, p4y = 0;
-      local_xy(A, k, j, &ax, &ay);
-      local_xy(B, k, j, &bx, &by);
-      const bool h1 = far_point(S, lam, n1, c1i, c1j, k, j, ax, ay, &p1x, &p1y);
-      const bool h4 = far_point(S, lam, n4, c4i, c4j, k, j, bx, by, &p4x, &p4y);
-      double y;
-      const int kind = fit_crossing(ax, ay, bx, by, h1, p1x, p1y, h4, p4x, p4y, line_only, &y);
-      cnt[kind] += 1;
-      const int lr = walk(S, lam, mB, n4, k);
-      const int ll = walk(S, lam, mA, n1, k - 1);
-      cy[n] = y;
-      cvr[n] = lr < 0 ? -1 : !knew(S, lam, k, lr);
-      cvl[n] = ll < 0 ? -1 : !knew(S, lam, k, ll);
-      ord[n] = n;
-      ++n;
-    }
-  }
-  for (int a = 1; a < n; ++a)  // sort by (y, generation order)
+// One marker per edge (Sec. 2.4): candidates sorted by (position, generation
+// order); an odd count on an edge whose new end colours differ keeps the
+// median, an even count on an edge whose colours agree cancels in pairs.
+template <typename R>
+__device__ NewV<R> select_candidates(int n, double* cy, int* cvr, int* cvl, int* ord, int present,
+                                     int* cnt) {
+  for (int a = 1; a < n; ++a)
     for (int b = a; b > 0 && (cy[b] < cy[b - 1] || (cy[b] == cy[b - 1] && ord[b] < ord[b - 1])); --b) {
       const double t = cy[b]; cy[b] = cy[b - 1]; cy[b - 1] = t;
       int u = cvr[b]; cvr[b] = cvr[b - 1]; cvr[b - 1] = u;
@@ -481,18 +426,18 @@ __device__ NewV<R> new_unaligned(const View<R, AX>& S, R lam, bool line_only, in
       u = ord[b]; ord[b] = ord[b - 1]; ord[b - 1] = u;
     }
   NewV<R> out;
-  out.present = knew(S, lam, k, j) ^ knew(S, lam, k, j + 1);
+  out.present = present;
   out.vr = -1;
   out.vl = -1;
   out.s = R(0.5);
   int pick = -1;
-  if (out.present && (n & 1)) {
+  if (present && (n & 1)) {
     pick = n / 2;
-  } else if (!out.present && !(n & 1)) {
-    cnt[D_CANCELLED] += n / 2;
+  } else if (!present && !(n & 1)) {
+    if (cnt) cnt[D_CANCELLED] += n / 2;
   } else {
-    cnt[D_INVARIANT] += 1;
-    if (out.present && n > 0) {
+    if (cnt) cnt[D_INVARIANT] += 1;
+    if (present && n > 0) {
       pick = 0;
       for (int t = 1; t < n; ++t)
         if (fabs(cy[t] - 0.5) < fabs(cy[pick] - 0.5)) pick = t;
@@ -505,5 +450,169 @@ __device__ NewV<R> new_unaligned(const View<R, AX>& S, R lam, bool line_only, in
   }
   return out;
 }
+
+template <typename R, class A>
+__device__ NewV<R> new_unaligned(const A& S, bool line_only, int k, int j, int* cnt) {
+  double cy[6];
+  int cvr[6], cvl[6], ord[6];
+  int n = 0;
+  for (int c = k - 2; c <= k; ++c) {
+    if (c < 0 || c >= S.tnx()) continue;
+    int seg[2][2];
+    const int ns = cell_segments(S, c, j, seg);
+    for (int t = 0; t < ns; ++t) {
+      const Mk ma = edge_marker(c, j, seg[t][0]);
+      const Mk mb = edge_marker(c, j, seg[t][1]);
+      const AP<R> pa = S.moved(ma), pb = S.moved(mb);
+      const int lo = min(pa.ix, pb.ix), hi = max(pa.ix, pb.ix);
+      if (!(k > lo && k <= hi)) continue;
+      const bool a_left = pa.ix < k;
+      const Mk mA = a_left ? ma : mb, mB = a_left ? mb : ma;
+      const AP<R> A_ = a_left ? pa : pb, B_ = a_left ? pb : pa;
+      int c1i = 0, c1j = 0, c4i = 0, c4j = 0;
+      const Mk n1 = beyond(S, mA, c, j, &c1i, &c1j);
+      const Mk n4 = beyond(S, mB, c, j, &c4i, &c4j);
+      double ax, ay, bx, by, p1x = 0, p1y = 0, p4x = 0, p4y = 0;
+      local_xy(A_, k, j, &ax, &ay);
+      local_xy(B_, k, j, &bx, &by);
+      const bool h1 = far_point(S, n1, c1i, c1j, k, j, ax, ay, &p1x, &p1y);
+      const bool h4 = far_point(S, n4, c4i, c4j, k, j, bx, by, &p4x, &p4y);
+      double y;
+      const int kind = fit_crossing(ax, ay, bx, by, h1, p1x, p1y, h4, p4x, p4y, line_only, &y);
+      if (cnt) cnt[kind] += 1;
+      const int lr = walk(S, mB, n4, k);
+      const int ll = walk(S, mA, n1, k - 1);
+      cy[n] = y;
+      cvr[n] = lr < 0 ? -1 : !S.knew(k, lr);
+      cvl[n] = ll < 0 ? -1 : !S.knew(k, ll);
+      ord[n] = n;
+      ++n;
+    }
+  }
+  return select_candidates<R>(n, cy, cvr, cvl, ord, S.knew(k, j) ^ S.knew(k, j + 1), cnt);
+}
+
+// ---------------------------------------------------------------------------
+// Accessor over a state in global memory (sweep coordinates), recomputing.
+// ---------------------------------------------------------------------------
+template <typename R, int AX>
+struct GView {
+  const uint32_t* __restrict__ K;
+  const uint32_t* __restrict__ Z;
+  const R* __restrict__ sH;
+  const R* __restrict__ sV;
+  const R* __restrict__ w;  // velocity component along the sweep, (ny+1)x(nx+1)
+  Dims d;
+  R lam;
+  __device__ __forceinline__ int tnx() const { return AX ? d.ny : d.nx; }
+  __device__ __forceinline__ int tny() const { return AX ? d.nx : d.ny; }
+  __device__ __forceinline__ int kreal(int x, int y) const {
+    return (__ldg(&K[(long long)y * d.kw + (x >> 5)]) >> (x & 31)) & 1;
+  }
+  __device__ __forceinline__ int k(int i, int j) const { return AX ? kreal(j, i) : kreal(i, j); }
+  __device__ __forceinline__ int z(int i, int j) const {
+    const int x = AX ? j : i, y = AX ? i : j;
+    return (__ldg(&Z[(long long)y * d.zw + (x >> 5)]) >> (x & 31)) & 1;
+  }
+  __device__ __forceinline__ R h(int i, int j) const {
+    return AX ? __ldg(&sV[(long long)i * d.P + j]) : __ldg(&sH[(long long)j * d.P + i]);
+  }
+  __device__ __forceinline__ R v(int i, int j) const {
+    return AX ? __ldg(&sH[(long long)i * d.P + j]) : __ldg(&sV[(long long)j * d.P + i]);
+  }
+  __device__ __forceinline__ R vel(int i, int j) const {
+    return AX ? __ldg(&w[(long long)i * (d.nx + 1) + j]) : __ldg(&w[(long long)j * (d.nx + 1) + i]);
+  }
+  __device__ AP<R> advect(Mk m, Flags& f) const {
+    if (m.kind == 0)
+      return move_aligned(m.i, m.j, h(m.i, m.j), vel(m.i, m.j), vel(m.i + 1, m.j), lam, tnx(), f);
+    if (m.i == 0 || m.i == tnx())  // wall: no velocity needed
+      return move_unaligned(m.i, m.j, v(m.i, m.j), R(0), R(0), lam, tnx(), f);
+    return move_unaligned(m.i, m.j, v(m.i, m.j), vel(m.i, m.j), vel(m.i, m.j + 1), lam, tnx(), f);
+  }
+  __device__ AP<R> moved(Mk m) const {
+    Flags f;
+    return advect(m, f);
+  }
+  // New corner colour (Sec. 2.3, Fig. 5): vertex i of line j flips once for
+  // each aligned marker that passes it; only markers of edges i-1 and i can.
+  __device__ int knew(int i, int j) const {
+    const int c = k(i, j);
+    int r = c;
+    if (i >= 1 && k(i - 1, j) != c && moved(Mk{0, i - 1, j}).ix >= i) r ^= 1;
+    if (i < tnx() && k(i + 1, j) != c && moved(Mk{0, i, j}).ix < i) r ^= 1;
+    return r;
+  }
+  __device__ Landing<R> landing(int i, int j) const {
+    R fx[3];
+    int src[3];
+    int n = 0;
+    for (int e = i - 1; e <= i + 1; ++e) {
+      if (e < 0 || e >= tnx() || k(e, j) == k(e + 1, j)) continue;
+      const AP<R> p = moved(Mk{0, e, j});
+      if (p.ix == i) { fx[n] = p.fx; src[n] = e; ++n; }
+    }
+    return choose_landing(n, fx, src, knew(i, j) ^ knew(i + 1, j));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Accessor over a shared-memory tile of the state (sweep coordinates).  The
+// region covers vertices [ri0, ri0+RXn) x [rj0, rj0+RYn); every per-vertex or
+// per-edge answer was computed once by the tile kernel.  Indices are clamped
+// into the region (the tile kernel only asks inside it).
+// ---------------------------------------------------------------------------
+constexpr int8_t kNoSrc = -128;
+
+template <typename R, int RXn, int RYn>
+struct TView {
+  const uint8_t* kb;    // old corner colour
+  const uint8_t* kn;    // new corner colour
+  const uint8_t* zb;    // old centre colour of the cell at this vertex
+  const int16_t* hix;   // moved aligned marker: ix - ri0
+  const R* hfx;
+  const int16_t* vix;   // moved unaligned marker: ix - ri0
+  const R* vfx;
+  const R* vfy;
+  const uint8_t* lpres; // landing: presence, kept source - i (kNoSrc: none), kept fraction
+  const int8_t* lsrc;
+  const R* lfx;
+  int ri0, rj0, nx_, ny_;
+  __device__ __forceinline__ int tnx() const { return nx_; }
+  __device__ __forceinline__ int tny() const { return ny_; }
+  __device__ __forceinline__ int id(int i, int j) const {
+    const int lx = min(max(i - ri0, 0), RXn - 1);
+    const int ly = min(max(j - rj0, 0), RYn - 1);
+    return ly * RXn + lx;
+  }
+  __device__ __forceinline__ int k(int i, int j) const { return kb[id(i, j)]; }
+  __device__ __forceinline__ int z(int i, int j) const { return zb[id(i, j)]; }
+  __device__ __forceinline__ int knew(int i, int j) const { return kn[id(i, j)]; }
+  __device__ __forceinline__ AP<R> moved(Mk m) const {
+    const int t = id(m.i, m.j);
+    AP<R> p;
+    p.jy = m.j;
+    if (m.kind == 0) {
+      p.ix = hix[t] + ri0;
+      p.fx = hfx[t];
+      p.fy = R(0);
+    } else {
+      p.ix = vix[t] + ri0;
+      p.fx = vfx[t];
+      p.fy = vfy[t];
+    }
+    return p;
+  }
+  __device__ __forceinline__ Landing<R> landing(int i, int j) const {
+    const int t = id(i, j);
+    Landing<R> L;
+    L.present = lpres[t];
+    L.kept_src = lsrc[t] == kNoSrc ? -1 : i + lsrc[t];
+    L.kept_fx = lfx[t];
+    L.cancelled = 0;
+    L.invariant = 0;
+    return L;
+  }
+};
 
 }  // namespace ebit

@@ -1,5 +1,6 @@
-// Kernels of the EBIT step: the two passes of a split sweep, volume
-// fractions, height-function curvature, initialisation and state I/O.
+// Kernels of the EBIT step besides the tiled sweep and the fused fields: the
+// thread-per-vertex gather sweep (two passes, kept for differential testing),
+// the area sum, initialisation and state I/O.
 // Threads map to vertices of the real grid: a warp is 32 consecutive x of one
 // row, aligned to 32, so colour bits pack into 32-bit words with a ballot.
 #pragma once
@@ -28,7 +29,7 @@ __device__ __forceinline__ void raise_status(int* status, const int* cnt) {
 //   to the cells right (from_left) and left (from_right) of it.
 template <typename R, int AX>
 __global__ void __launch_bounds__(32 * kBlockY)
-k_sweep(View<R, AX> S, Buf<R> out, R lam, int line_only, int8_t* from_left, int8_t* from_right,
+k_sweep(GView<R, AX> S, Buf<R> out, int line_only, int8_t* from_left, int8_t* from_right,
         unsigned long long* ctr, unsigned long long* cfl_bits, int* status) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * kBlockY + threadIdx.y;
@@ -52,16 +53,16 @@ k_sweep(View<R, AX> S, Buf<R> out, R lam, int line_only, int8_t* from_left, int8
       for (int c = c0; c <= c1; ++c)
         if (S.k(c, r) != ref) { busy = true; break; }
     if (busy) {
-      kb = knew(S, lam, i, j);
+      kb = S.knew(i, j);
       if (i < tnx) {
         if (S.k(i, j) != S.k(i + 1, j)) {
           Flags f;
-          advect(S, lam, Mk{0, i, j}, f);
+          S.advect(Mk{0, i, j}, f);
           cnt[D_CFL] += f.cfl;
           cnt[D_WALL_CLAMP] += f.clamp;
-          dmax = fmax(dmax, f.dabs);
+          dmax = fmax(dmax, (double)dabs_of<R>(f));
         }
-        const Landing<R> L = landing(S, lam, i, j);
+        const Landing<R> L = S.landing(i, j);
         cnt[D_CANCELLED] += L.cancelled;
         cnt[D_INVARIANT] += L.invariant;
         if (L.present) {
@@ -74,11 +75,11 @@ k_sweep(View<R, AX> S, Buf<R> out, R lam, int line_only, int8_t* from_left, int8
         if (i >= 1 && i <= tnx - 1) {
           if (had) {
             Flags f;
-            advect(S, lam, Mk{1, i, j}, f);
+            S.advect(Mk{1, i, j}, f);
             cnt[D_CFL] += f.cfl;
-            dmax = fmax(dmax, f.dabs);
+            dmax = fmax(dmax, (double)dabs_of<R>(f));
           }
-          const NewV<R> nv = new_unaligned(S, lam, line_only != 0, i, j, cnt);
+          const NewV<R> nv = new_unaligned<R>(S, line_only != 0, i, j, cnt);
           if (nv.present) {
             if (AX) out.sH[(long long)i * d.P + j] = nv.s;
             else out.sV[(long long)j * d.P + i] = nv.s;
@@ -106,7 +107,7 @@ k_sweep(View<R, AX> S, Buf<R> out, R lam, int line_only, int8_t* from_left, int8
 // the sweep (Sec. 2.3); the verdict from the cell's left (bottom) edge wins.
 template <typename R, int AX>
 __global__ void __launch_bounds__(32 * kBlockY)
-k_centre(View<R, AX> Snew, const uint32_t* __restrict__ Zold, uint32_t* Zout,
+k_centre(GView<R, AX> Snew, const uint32_t* __restrict__ Zold, uint32_t* Zout,
          const int8_t* __restrict__ from_left, const int8_t* __restrict__ from_right,
          unsigned long long* ctr) {
   const int x = blockIdx.x * 32 + threadIdx.x;
@@ -140,83 +141,8 @@ k_centre(View<R, AX> Snew, const uint32_t* __restrict__ Zold, uint32_t* Zout,
   flush_counters(cnt, ctr);
 }
 
-// ---------------------------------------------------------------------------
-// Volume fraction (Sec. 2.5), double arithmetic; per-block partial sums in a
-// fixed order; marker counts.
-// ---------------------------------------------------------------------------
 __device__ __forceinline__ int kbit(const uint32_t* K, const Dims& d, int x, int y) {
   return (__ldg(&K[(long long)y * d.kw + (x >> 5)]) >> (x & 31)) & 1;
-}
-
-template <typename R>
-__device__ double cell_fraction(const uint32_t* K, const uint32_t* Z, const R* sH, const R* sV,
-                                const Dims& d, int i, int j) {
-  const int q = kbit(K, d, i, j) | (kbit(K, d, i + 1, j) << 1) | (kbit(K, d, i + 1, j + 1) << 2) |
-                (kbit(K, d, i, j + 1) << 3);
-  const int em = edge_mask(q);
-  if (em == 0) return (double)(q & 1);
-  const double s0 = (double)__ldg(&sH[(long long)j * d.P + i]);
-  const double s1 = (double)__ldg(&sV[(long long)j * d.P + i + 1]);
-  const double s2 = (double)__ldg(&sH[(long long)(j + 1) * d.P + i]);
-  const double s3 = (double)__ldg(&sV[(long long)j * d.P + i]);
-  auto tri = [&](int c) {
-    double a, b;
-    switch (c) {
-      case 0: a = s3; b = s0; break;
-      case 1: a = 1.0 - s0; b = s1; break;
-      case 2: a = 1.0 - s1; b = 1.0 - s2; break;
-      default: a = s2; b = 1.0 - s3; break;
-    }
-    return 0.5 * (a * b);
-  };
-  if (em != 15) {
-    const int e1 = __ffs(em) - 1, e2 = 31 - __clz(em);
-    const int c0 = q & 1;
-    if (e2 - e1 == 2) {
-      if (e1 == 0) return c0 ? 0.5 * (s0 + s2) : 0.5 * ((1.0 - s0) + (1.0 - s2));
-      return c0 ? 0.5 * (s3 + s1) : 0.5 * ((1.0 - s3) + (1.0 - s1));
-    }
-    const int c = (e1 == 0 && e2 == 3) ? 0 : e2;
-    const double T = tri(c);
-    return ((q >> c) & 1) ? T : 1.0 - T;
-  }
-  const int zc = (__ldg(&Z[(long long)j * d.zw + (i >> 5)]) >> (i & 31)) & 1;
-  double Tsum = 0.0;
-  bool first = true;
-  for (int c = 0; c < 4; ++c)
-    if (((q >> c) & 1) != zc) {
-      if (first) { Tsum = tri(c); first = false; } else { Tsum = Tsum + tri(c); }
-    }
-  return zc == 0 ? Tsum : 1.0 - Tsum;
-}
-
-template <typename R>
-__global__ void __launch_bounds__(32 * kBlockY)
-k_fraction(const uint32_t* __restrict__ K, const uint32_t* __restrict__ Z,
-           const R* __restrict__ sH, const R* __restrict__ sV, Dims d, R* C, double* partial,
-           unsigned long long* ctr) {
-  __shared__ double red[32 * kBlockY];
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * kBlockY + threadIdx.y;
-  const int t = threadIdx.y * 32 + threadIdx.x;
-  double f = 0.0;
-  int cnt[D_NUSED];
-#pragma unroll
-  for (int c = 0; c < D_NUSED; ++c) cnt[c] = 0;
-  if (x < d.nx && y < d.ny) {
-    f = cell_fraction(K, Z, sH, sV, d, x, y);
-    C[(long long)y * d.P + x] = (R)f;
-  }
-  if (x < d.nx && y <= d.ny) cnt[D_NH] = kbit(K, d, x, y) != kbit(K, d, x + 1, y);
-  if (x <= d.nx && y < d.ny) cnt[D_NV] = kbit(K, d, x, y) != kbit(K, d, x, y + 1);
-  flush_counters(cnt, ctr);
-  red[t] = f;
-  __syncthreads();
-  for (int s = (32 * kBlockY) / 2; s > 0; s >>= 1) {
-    if (t < s) red[t] = red[t] + red[t + s];
-    __syncthreads();
-  }
-  if (t == 0) partial[(long long)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
 }
 
 // Sum of the per-block partials in a fixed order (one block).
@@ -231,72 +157,6 @@ __global__ void k_area(const double* __restrict__ partial, long long n, double s
     __syncthreads();
   }
   if (threadIdx.x == 0) *area = red[0] * scale;
-}
-
-// ---------------------------------------------------------------------------
-// Height-function curvature (Sec. 2.5): standard 7x3 heights, orientation
-// from the cell's own segments.
-// ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(32 * kBlockY)
-k_curvature(const uint32_t* __restrict__ K, const uint32_t* __restrict__ Z,
-            const R* __restrict__ sH, const R* __restrict__ sV, const R* __restrict__ C, Dims d,
-            R dx, R* kappa, unsigned long long* ctr) {
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * kBlockY + threadIdx.y;
-  int cnt[D_NUSED];
-#pragma unroll
-  for (int c = 0; c < D_NUSED; ++c) cnt[c] = 0;
-  if (x < d.nx && y < d.ny) {
-    const int i = x, j = y;
-    const int q = kbit(K, d, i, j) | (kbit(K, d, i + 1, j) << 1) | (kbit(K, d, i + 1, j + 1) << 2) |
-                  (kbit(K, d, i, j + 1) << 3);
-    R out = R(NAN);
-    if (q != 0 && q != 15) {
-      const int em = edge_mask(q);
-      const int zc = em == 15 ? (__ldg(&Z[(long long)j * d.zw + (i >> 5)]) >> (i & 31)) & 1 : 0;
-      int seg[2][2];
-      const int ns = segments(q, zc, seg);
-      const R px[4] = {__ldg(&sH[(long long)j * d.P + i]), R(1), __ldg(&sH[(long long)(j + 1) * d.P + i]), R(0)};
-      const R py[4] = {R(0), __ldg(&sV[(long long)j * d.P + i + 1]), R(1), __ldg(&sV[(long long)j * d.P + i])};
-      R ax = R(0), ay = R(0);
-      for (int t = 0; t < ns; ++t) {
-        const int a = seg[t][0], b = seg[t][1];
-        ax = ax + fabs(px[b] - px[a]);
-        ay = ay + fabs(py[b] - py[a]);
-      }
-      const bool ycol = ax >= ay;
-      const bool inside = ycol ? (i - 1 >= 0 && i + 1 <= d.nx - 1 && j - 3 >= 0 && j + 3 <= d.ny - 1)
-                               : (j - 1 >= 0 && j + 1 <= d.ny - 1 && i - 3 >= 0 && i + 3 <= d.nx - 1);
-      bool valid = inside;
-      R h[3];
-      int orient[3] = {0, 0, 0};
-      if (inside) {
-        for (int m = -1; m <= 1; ++m) {
-          R acc = R(0);
-          for (int t = -3; t <= 3; ++t)
-            acc = acc + (ycol ? __ldg(&C[(long long)(j + t) * d.P + i + m])
-                              : __ldg(&C[(long long)(j + m) * d.P + i + t]));
-          h[m + 1] = acc;
-          const R lo = ycol ? __ldg(&C[(long long)(j - 3) * d.P + i + m]) : __ldg(&C[(long long)(j + m) * d.P + i - 3]);
-          const R hi = ycol ? __ldg(&C[(long long)(j + 3) * d.P + i + m]) : __ldg(&C[(long long)(j + m) * d.P + i + 3]);
-          orient[m + 1] = (lo == R(1) && hi == R(0)) ? 1 : (lo == R(0) && hi == R(1)) ? -1 : 0;
-        }
-        valid = orient[0] != 0 && orient[0] == orient[1] && orient[1] == orient[2];
-      }
-      if (valid) {
-        const R hp = (h[2] - h[0]) * R(0.5);
-        const R hpp = (h[2] - h[1]) - (h[1] - h[0]);
-        const R qv = R(1) + hp * hp;
-        const R den = dx * (qv * sqrt(qv));
-        out = -hpp / den;
-      } else {
-        cnt[D_HF_INVALID] = 1;
-      }
-    }
-    kappa[(long long)j * d.P + i] = out;
-  }
-  flush_counters(cnt, ctr);
 }
 
 // ---------------------------------------------------------------------------

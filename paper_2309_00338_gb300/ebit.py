@@ -93,9 +93,9 @@ SIGNATURES = {
     "ebit_fraction_noalloc": (ctypes.c_int, [ctypes.POINTER(ebit_grid), _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
-K_SWEEP, K_CENTRE, K_FRACTION, K_AREA, K_CURVATURE = range(5)
+K_SWEEP, K_CENTRE, K_FIELDS, K_AREA = range(4)
 K_COUNT = 8
-KERNEL_NAMES = ["sweep", "centre", "fraction", "area", "curvature"]
+KERNEL_NAMES = ["sweep", "centre", "fields", "area"]
 
 
 def lib(path: str | None = None):
