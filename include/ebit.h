@@ -188,6 +188,79 @@ ebit_status ebit_fraction_noalloc(const ebit_grid* grid, const uint8_t* K, const
                                   const void* sH, const void* sV, void* C, double* area,
                                   int64_t* marker_counts, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched steps and serving.  A server owns one CUDA stream and one worker
+ * thread on its device.  Requests (an n x n unit-square grid of circles, an
+ * analytic velocity field and a number of steps) are admitted while the sum
+ * of their device footprints stays within the budget; every admitted grid
+ * advances one EBIT step per batch step, in one captured launch sequence for
+ * all of them (continuous batching: requests join and leave between batch
+ * steps).  The results stay on the server until polled.  Submit and poll are
+ * thread-safe.
+ * ------------------------------------------------------------------------ */
+typedef enum {
+  EBIT_FIELD_VORTEX = 0,    /* u = -sin^2(pi x) sin(2 pi y), v = sin^2(pi y) sin(2 pi x),
+                               times cos(pi t / period): time-reversed at t = period */
+  EBIT_FIELD_CELLULAR = 1,  /* u = sin(pi x) cos(pi y), v = -cos(pi x) sin(pi y) */
+  EBIT_FIELD_ROTATION = 2   /* u = -omega (y - cy) + drift_u, v = omega (x - cx) + drift_v */
+} ebit_field_kind;
+
+typedef struct {
+  int32_t n;                   /* grid side, n x n cells, dx = 1/n */
+  int32_t prec;                /* ebit_precision */
+  uint32_t flags;              /* EBIT_FIT_LINE or 0 */
+  const ebit_circle* circles;  /* host array, copied by ebit_submit */
+  int32_t ncircles;
+  int32_t field;               /* ebit_field_kind */
+  double period;               /* vortex period T (> 0 for EBIT_FIELD_VORTEX) */
+  double omega, cx, cy, drift_u, drift_v;  /* rotation parameters */
+  int32_t steps;
+  double cfl;                  /* dt = cfl dx / max|u| at t = 0, 0 < cfl <= 1 */
+  void* C_out;                 /* optional HOST buffer of n*n elements (request
+                                  precision) receiving the final fractions; must
+                                  stay valid until the result has been polled */
+} ebit_request;
+
+typedef struct {
+  int32_t status;              /* EBIT_OK, or why the request failed */
+  int64_t steps;               /* steps done */
+  double area0, area;          /* sum C dx^2 at admission and at the end */
+  double e_area;               /* |area - area0| / area0 (Eq. 13) */
+  double queue_ms;             /* submission to admission */
+  double run_ms;               /* admission to completion */
+  double step_p50_ms, step_p99_ms;  /* latency of the batch steps it took part in */
+  int64_t counters[EBIT_D_COUNT];   /* diagnostics summed over its steps */
+  int64_t cell_updates;        /* n*n*steps */
+} ebit_result;
+
+typedef struct {
+  int32_t max_instances;       /* 0: no limit besides the budget */
+  int32_t use_graphs;          /* replay each batch step as a CUDA graph */
+  int32_t device;              /* CUDA device ordinal */
+} ebit_server_opts;
+
+typedef struct {
+  int64_t queued, running, batch_steps, cell_updates;
+  double busy_ms;              /* GPU time of the batch steps */
+  size_t bytes_in_use;
+} ebit_server_stats;
+
+typedef struct ebit_server ebit_server;
+
+/* hbm_budget: device bytes the admitted requests may use together.  opts may
+ * be NULL (graphs on, device 0).  No CUDA call happens before the first
+ * admissible submission. */
+ebit_status ebit_server_create(ebit_server** out, size_t hbm_budget, const ebit_server_opts* opts);
+/* EBIT_EINVAL for a malformed request; EBIT_EFULL if it can never fit the
+ * budget.  Otherwise queues it and returns its ticket. */
+ebit_status ebit_submit(ebit_server* s, const ebit_request* req, uint64_t* ticket);
+/* EBIT_EAGAIN while the request is queued or running; EBIT_OK with the result
+ * once (the result is then released); EBIT_EINVAL for an unknown ticket. */
+ebit_status ebit_poll(ebit_server* s, uint64_t ticket, ebit_result* out);
+ebit_status ebit_server_stats_get(ebit_server* s, ebit_server_stats* out);
+/* Cancels queued requests, finishes nothing further, frees everything. */
+void ebit_server_destroy(ebit_server* s);
+
 /* Device bytes a context of this grid allocates (for admission control). */
 size_t ebit_footprint(const ebit_grid* grid);
 

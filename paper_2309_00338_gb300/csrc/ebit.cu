@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "ebit.h"
+#include "ebit_ctx.hpp"
 #include "ebit_kernels.cuh"
 #include "ebit_tile.cuh"
 #include "ebit_fields.cuh"
@@ -32,75 +33,9 @@ ebit_status fail(ebit_status s, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(EBIT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-constexpr int kMaxSide = 32768;
-
-struct Layout {
-  ebit::Dims d;
-  size_t esz;
-  size_t k_bytes, z_bytes, h_bytes, v_bytes, field_bytes, verdict_bytes, partial_count;
-  dim3 grid, block;
-  size_t total() const {
-    return 2 * (k_bytes + z_bytes + h_bytes + v_bytes) + 2 * field_bytes + 2 * verdict_bytes +
-           partial_count * sizeof(double) + 4096;
-  }
-};
-
-bool valid_grid(const ebit_grid* g) {
-  return g && g->nx >= 1 && g->ny >= 1 && g->nx <= kMaxSide && g->ny <= kMaxSide && g->dx > 0.0 &&
-         (g->prec == EBIT_FP64 || g->prec == EBIT_FP32) && (g->flags & ~EBIT_FIT_LINE) == 0;
-}
-
-Layout layout_of(const ebit_grid* g) {
-  Layout L;
-  L.d.nx = g->nx;
-  L.d.ny = g->ny;
-  L.d.kw = (g->nx + 1 + 31) / 32;
-  L.d.zw = (g->nx + 31) / 32;
-  L.d.P = ((long long)g->nx + 1 + 31) / 32 * 32;
-  L.esz = g->prec == EBIT_FP32 ? 4 : 8;
-  L.k_bytes = (size_t)(g->ny + 1) * L.d.kw * 4;
-  L.z_bytes = (size_t)g->ny * L.d.zw * 4;
-  L.h_bytes = (size_t)(g->ny + 1) * L.d.P * L.esz;
-  L.v_bytes = (size_t)g->ny * L.d.P * L.esz;
-  L.field_bytes = (size_t)g->ny * L.d.P * L.esz;
-  L.verdict_bytes = (size_t)g->nx * g->ny;
-  L.block = dim3(32, ebit::kBlockY);
-  L.grid = dim3((g->nx + 1 + 31) / 32, (g->ny + 1 + ebit::kBlockY - 1) / ebit::kBlockY);
-  L.partial_count = (size_t)L.grid.x * L.grid.y;
-  return L;
-}
+using namespace ebit_detail;
 
 }  // namespace
-
-struct ebit_ctx {
-  ebit_grid grid;
-  Layout L;
-  cudaStream_t stream = nullptr;
-  uint32_t* K[2] = {nullptr, nullptr};
-  uint32_t* Z[2] = {nullptr, nullptr};
-  void* sH[2] = {nullptr, nullptr};
-  void* sV[2] = {nullptr, nullptr};
-  int cur = 0;
-  void* C = nullptr;
-  void* kappa = nullptr;
-  int8_t* from_left = nullptr;
-  int8_t* from_right = nullptr;
-  double* partial = nullptr;
-  double* area = nullptr;
-  unsigned long long* ctr = nullptr;
-  unsigned long long* cfl_bits = nullptr;
-  int* status = nullptr;
-  int64_t step_index = 0;
-  std::vector<void*> allocs;
-  // EBIT_SWEEP=gather in the environment selects the thread-per-vertex gather
-  // kernels instead of the tiled one (kept for differential testing)
-  bool gather = false;
-  // per-kernel event timing (off unless ebit_set_timing)
-  bool timing = false;
-  struct Mark { cudaEvent_t a, b; int kind; };
-  std::vector<Mark> marks;
-  size_t marks_used = 0;
-};
 
 namespace {
 
@@ -436,9 +371,7 @@ ebit_status get_state(ebit_ctx* c, ebit_state_host* st) {
 
 }  // namespace
 
-// Lets the other translation units of the library report errors through
-// ebit_last_error(); not part of the exported interface.
-__attribute__((visibility("hidden"))) void ebit_detail_set_error(const char* msg) { g_err = msg; }
+void ebit_detail_set_error(const char* msg) { g_err = msg; }
 
 extern "C" {
 

@@ -62,11 +62,13 @@ __device__ double fraction_of(int q, int zc, const R* __restrict__ sH, const R* 
   return zc == 0 ? Tsum : 1.0 - Tsum;
 }
 
+// The tile (bx, by) of one grid; its area partial goes to partial[slot].
 template <typename R>
-__global__ void __launch_bounds__(kFieldThreads)
-k_fields_tile(const uint32_t* __restrict__ K, const uint32_t* __restrict__ Z,
-              const R* __restrict__ sH, const R* __restrict__ sV, Dims d, R dx, R* C, R* kappa,
-              double* partial, unsigned long long* ctr) {
+__device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
+                                            const uint32_t* __restrict__ Z,
+                                            const R* __restrict__ sH, const R* __restrict__ sV,
+                                            const Dims& d, R dx, R* C, R* kappa, double* partial,
+                                            long long slot, unsigned long long* ctr, int bx, int by) {
   __shared__ uint8_t kb[kFVY * kFVX];
   __shared__ uint8_t zb[kFRY * kFRX];
   __shared__ R cs[kFRY * kFRX];
@@ -77,7 +79,7 @@ k_fields_tile(const uint32_t* __restrict__ K, const uint32_t* __restrict__ Z,
   __shared__ int s_nlist;
   __shared__ unsigned long long s_full;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int i0 = blockIdx.x * kFX, j0 = blockIdx.y * kFY;
+  const int i0 = bx * kFX, j0 = by * kFY;
   const int rx0 = i0 - kFH, ry0 = j0 - kFH;
   if (tid < D_NUSED) s_cnt[tid] = 0;
   if (tid == 0) {
@@ -231,9 +233,47 @@ k_fields_tile(const uint32_t* __restrict__ K, const uint32_t* __restrict__ Z,
     double p = 0.0;
     for (int w = 0; w < kFieldThreads / 32; ++w) p = p + s_wsum[w];
     if (s_full) p = p + (double)s_full;
-    partial[(long long)blockIdx.y * gridDim.x + blockIdx.x] = p;
+    partial[slot] = p;
   }
   if (tid < D_NUSED && s_cnt[tid] != 0) atomicAdd(&ctr[tid], (unsigned long long)s_cnt[tid]);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kFieldThreads)
+k_fields_tile(const uint32_t* __restrict__ K, const uint32_t* __restrict__ Z,
+              const R* __restrict__ sH, const R* __restrict__ sV, Dims d, R dx, R* C, R* kappa,
+              double* partial, unsigned long long* ctr) {
+  fields_tile<R>(K, Z, sH, sV, d, dx, C, kappa, partial,
+                 (long long)blockIdx.y * gridDim.x + blockIdx.x, ctr, blockIdx.x, blockIdx.y);
+}
+
+// Many grids in one launch (work items: grid, tile).
+template <typename R>
+struct FieldDesc {
+  const uint32_t* K;
+  const uint32_t* Z;
+  const R* sH;
+  const R* sV;
+  Dims d;
+  R dx;
+  R* C;
+  R* kappa;
+  double* partial;
+  unsigned long long* ctr;
+  int tiles_x;
+};
+
+struct FieldItem {
+  int grid, tx, ty;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kFieldThreads)
+k_fields_tile_batch(const FieldDesc<R>* __restrict__ descs, const FieldItem* __restrict__ items) {
+  const FieldItem it = items[blockIdx.x];
+  const FieldDesc<R>& D = descs[it.grid];
+  fields_tile<R>(D.K, D.Z, D.sH, D.sV, D.d, D.dx, D.C, D.kappa, D.partial,
+                 (long long)it.ty * D.tiles_x + it.tx, D.ctr, it.tx, it.ty);
 }
 
 }  // namespace ebit

@@ -1,0 +1,588 @@
+// Batched EBIT steps over many grids and the request-serving loop
+// (ebit_server_create / ebit_submit / ebit_poll / ebit_server_destroy).
+//
+// A batch step advances every admitted grid by one EBIT step with a fixed
+// launch sequence per precision: a copy of the per-grid sweep descriptors
+// from pinned host memory, four sweep launches (x-first grids' first sweep,
+// y-first grids' first sweep, then the two second sweeps; a grid that is not
+// due in a launch is skipped by its blocks), the fields launch and the area
+// launch.  Work items are (grid, tile) pairs, largest grids first.  The
+// sequence is captured once per set of admitted grids as a CUDA graph and
+// replayed every step.  Grids keep their state in the same buffer across a
+// step (first sweep A->B, second B->A).
+//
+// Serving: one worker thread owns the GPU.  Between batch steps it retires
+// finished grids (results copied to the host, memory freed) and admits queued
+// requests, first come first served among those that fit, while the sum of
+// their device footprints stays within the budget: continuous batching.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "ebit.h"
+#include "ebit_ctx.hpp"
+#include "ebit_fields.cuh"
+#include "ebit_tile.cuh"
+
+namespace {
+
+ebit_status fail_s(ebit_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  ebit_detail_set_error(buf);
+  return s;
+}
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// Analytic velocity fields at the vertices of an n x n unit-square grid.
+template <typename R>
+__global__ void k_velocity(int kind, int n, double dx, double omega, double cx, double cy,
+                           double du, double dv, R* u, R* v) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long m = (long long)(n + 1) * (n + 1);
+  if (t >= m) return;
+  const int i = (int)(t % (n + 1)), j = (int)(t / (n + 1));
+  const double x = i * dx, y = j * dx;
+  double a, b;
+  if (kind == EBIT_FIELD_VORTEX) {
+    const double sx = sinpi(x), sy = sinpi(y);
+    a = -(sx * sx) * sinpi(2.0 * y);
+    b = (sy * sy) * sinpi(2.0 * x);
+  } else if (kind == EBIT_FIELD_CELLULAR) {
+    a = sinpi(x) * cospi(y);
+    b = -cospi(x) * sinpi(y);
+  } else {
+    a = -omega * (y - cy) + du;
+    b = omega * (x - cx) + dv;
+  }
+  u[t] = (R)a;
+  v[t] = (R)b;
+}
+
+struct AreaDesc {
+  const double* partial;
+  long long n;
+  double scale;
+  double* area;
+};
+
+__global__ void k_area_batch(const AreaDesc* __restrict__ descs) {
+  const AreaDesc D = descs[blockIdx.x];
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (long long b = threadIdx.x; b < D.n; b += 256) acc = acc + D.partial[b];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *D.area = red[0] * D.scale;
+}
+
+struct Instance {
+  uint64_t ticket = 0;
+  ebit_request req{};
+  std::vector<ebit_circle> circles;
+  ebit_ctx* ctx = nullptr;
+  void* u = nullptr;
+  void* v = nullptr;
+  size_t bytes = 0;
+  int64_t done = 0;
+  double dt = 0.0, dx = 0.0;
+  double area0 = 0.0;
+  double t_submit = 0.0, t_admit = 0.0;
+  std::vector<float> lat_ms;
+  ebit_status failed = EBIT_OK;  // set when a batch step it took part in failed
+};
+
+size_t request_bytes(const ebit_request& r) {
+  ebit_grid g{r.n, r.n, 1.0 / r.n, r.prec, r.flags};
+  const size_t esz = r.prec == EBIT_FP32 ? 4 : 8;
+  return ebit_footprint(&g) + 2 * (size_t)(r.n + 1) * (r.n + 1) * esz + (1u << 20);
+}
+
+double field_umax(const ebit_request& r) {
+  if (r.field == EBIT_FIELD_VORTEX || r.field == EBIT_FIELD_CELLULAR) return 1.0;
+  double m = 0.0;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      m = std::max(m, std::fabs(-r.omega * (b - r.cy) + r.drift_u));
+      m = std::max(m, std::fabs(r.omega * (a - r.cx) + r.drift_v));
+    }
+  return m > 0.0 ? m : 1.0;
+}
+
+// Launch plan of one precision for the current set of grids.
+template <typename R>
+struct Group {
+  std::vector<Instance*> inst;
+  ebit::SweepDesc<R, 0>* h_s0 = nullptr;  // pinned: [first-x | second-x] descriptors
+  ebit::SweepDesc<R, 1>* h_s1 = nullptr;  // pinned: [first-y | second-y]
+  ebit::SweepDesc<R, 0>* d_s0 = nullptr;
+  ebit::SweepDesc<R, 1>* d_s1 = nullptr;
+  ebit::WorkItem* d_items0 = nullptr;
+  ebit::WorkItem* d_items1 = nullptr;
+  ebit::FieldDesc<R>* d_fd = nullptr;
+  ebit::FieldItem* d_fitems = nullptr;
+  AreaDesc* d_ad = nullptr;
+  int n_items0 = 0, n_items1 = 0, n_fitems = 0;
+
+  void release() {
+    if (h_s0) cudaFreeHost(h_s0);
+    if (h_s1) cudaFreeHost(h_s1);
+    for (void* p : {(void*)d_s0, (void*)d_s1, (void*)d_items0, (void*)d_items1, (void*)d_fd,
+                    (void*)d_fitems, (void*)d_ad})
+      if (p) cudaFree(p);
+    *this = Group<R>();
+  }
+
+  ebit_status build(const std::vector<Instance*>& all, int prec, cudaStream_t st) {
+    release();
+    for (Instance* in : all)
+      if (in->req.prec == prec) inst.push_back(in);
+    if (inst.empty()) return EBIT_OK;
+    // largest grids first so their many tiles start early
+    std::stable_sort(inst.begin(), inst.end(),
+                     [](const Instance* a, const Instance* b) { return a->req.n > b->req.n; });
+    const size_t n = inst.size();
+    std::vector<ebit::WorkItem> it0, it1;
+    std::vector<ebit::FieldItem> fit;
+    std::vector<ebit::FieldDesc<R>> fd(n);
+    std::vector<AreaDesc> ad(n);
+    for (size_t g = 0; g < n; ++g) {
+      const ebit_ctx* c = inst[g]->ctx;
+      const ebit::Dims& d = c->L.d;
+      for (int ty = 0; ty < (d.ny + 1 + ebit::kTJ - 1) / ebit::kTJ; ++ty)
+        for (int tx = 0; tx < (d.nx + 1 + ebit::kTI - 1) / ebit::kTI; ++tx) it0.push_back({(int)g, tx, ty});
+      for (int ty = 0; ty < (d.nx + 1 + ebit::kTJ - 1) / ebit::kTJ; ++ty)
+        for (int tx = 0; tx < (d.ny + 1 + ebit::kTI - 1) / ebit::kTI; ++tx) it1.push_back({(int)g, tx, ty});
+      const int fx = (d.nx + 1 + ebit::kFX - 1) / ebit::kFX, fy = (d.ny + 1 + ebit::kFY - 1) / ebit::kFY;
+      for (int ty = 0; ty < fy; ++ty)
+        for (int tx = 0; tx < fx; ++tx) fit.push_back({(int)g, tx, ty});
+      const int b = c->cur;
+      fd[g] = ebit::FieldDesc<R>{c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], d,
+                                 (R)c->grid.dx, (R*)c->C, (R*)c->kappa, c->partial, c->ctr, fx};
+      ad[g] = AreaDesc{c->partial, (long long)fx * fy, c->grid.dx * c->grid.dx, c->area};
+    }
+    n_items0 = (int)it0.size();
+    n_items1 = (int)it1.size();
+    n_fitems = (int)fit.size();
+    auto dput = [&](void** p, const void* src, size_t bytes) -> ebit_status {
+      if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); return fail_s(EBIT_ENOMEM, "cudaMalloc (batch plan)"); }
+      if (src && cudaMemcpyAsync(*p, src, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return fail_s(EBIT_ECUDA, "cudaMemcpyAsync (batch plan)");
+      return EBIT_OK;
+    };
+    ebit_status s;
+    if ((s = dput((void**)&d_items0, it0.data(), it0.size() * sizeof(ebit::WorkItem))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_items1, it1.data(), it1.size() * sizeof(ebit::WorkItem))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_fitems, fit.data(), fit.size() * sizeof(ebit::FieldItem))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_fd, fd.data(), n * sizeof(ebit::FieldDesc<R>))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_ad, ad.data(), n * sizeof(AreaDesc))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_s0, nullptr, 2 * n * sizeof(ebit::SweepDesc<R, 0>))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_s1, nullptr, 2 * n * sizeof(ebit::SweepDesc<R, 1>))) != EBIT_OK) return s;
+    if (cudaMallocHost((void**)&h_s0, 2 * n * sizeof(ebit::SweepDesc<R, 0>)) != cudaSuccess ||
+        cudaMallocHost((void**)&h_s1, 2 * n * sizeof(ebit::SweepDesc<R, 1>)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail_s(EBIT_ENOMEM, "cudaMallocHost (batch plan)");
+    }
+    return cudaStreamSynchronize(st) == cudaSuccess ? EBIT_OK : fail_s(EBIT_ECUDA, "plan upload");
+  }
+
+  // Descriptors of the coming step: lam and the split order of every grid.
+  void fill() {
+    const size_t n = inst.size();
+    for (size_t g = 0; g < n; ++g) {
+      Instance* in = inst[g];
+      ebit_ctx* c = in->ctx;
+      const int A = c->cur, B = 1 - c->cur;
+      const double t = in->done * in->dt;
+      const double dte = in->req.field == EBIT_FIELD_VORTEX ? in->dt * std::cos(M_PI * t / in->req.period) : in->dt;
+      const R lam = (R)(dte / c->grid.dx);
+      const int x_first = ((c->step_index & 1) == 0);
+      const int lo = (c->grid.flags & EBIT_FIT_LINE) ? 1 : 0;
+      auto gv0 = [&](int s) {
+        return ebit::GView<R, 0>{c->K[s], c->Z[s], (const R*)c->sH[s], (const R*)c->sV[s], (const R*)in->u, c->L.d, lam};
+      };
+      auto gv1 = [&](int s) {
+        return ebit::GView<R, 1>{c->K[s], c->Z[s], (const R*)c->sH[s], (const R*)c->sV[s], (const R*)in->v, c->L.d, lam};
+      };
+      auto buf = [&](int s) { return ebit::Buf<R>{c->K[s], c->Z[s], (R*)c->sH[s], (R*)c->sV[s]}; };
+      // first sweep A -> B, second sweep B -> A
+      h_s0[g] = ebit::SweepDesc<R, 0>{gv0(A), buf(B), c->ctr, c->cfl_bits, c->status, lo, x_first};
+      h_s1[g] = ebit::SweepDesc<R, 1>{gv1(A), buf(B), c->ctr, c->cfl_bits, c->status, lo, !x_first};
+      h_s1[n + g] = ebit::SweepDesc<R, 1>{gv1(B), buf(A), c->ctr, c->cfl_bits, c->status, lo, x_first};
+      h_s0[n + g] = ebit::SweepDesc<R, 0>{gv0(B), buf(A), c->ctr, c->cfl_bits, c->status, lo, !x_first};
+    }
+  }
+
+  // The launch sequence of one step on stream st.
+  ebit_status launch(cudaStream_t st) {
+    if (inst.empty()) return EBIT_OK;
+    const size_t n = inst.size();
+    constexpr size_t smem = ebit::tile_smem_bytes<R>();
+    cudaMemcpyAsync(d_s0, h_s0, 2 * n * sizeof(ebit::SweepDesc<R, 0>), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_s1, h_s1, 2 * n * sizeof(ebit::SweepDesc<R, 1>), cudaMemcpyHostToDevice, st);
+    ebit::k_sweep_tile_batch<R, 0><<<n_items0, ebit::kTileThreads, smem, st>>>(d_s0, d_items0);
+    ebit::k_sweep_tile_batch<R, 1><<<n_items1, ebit::kTileThreads, smem, st>>>(d_s1, d_items1);
+    ebit::k_sweep_tile_batch<R, 1><<<n_items1, ebit::kTileThreads, smem, st>>>(d_s1 + n, d_items1);
+    ebit::k_sweep_tile_batch<R, 0><<<n_items0, ebit::kTileThreads, smem, st>>>(d_s0 + n, d_items0);
+    ebit::k_fields_tile_batch<R><<<n_fitems, ebit::kFieldThreads, 0, st>>>(d_fd, d_fitems);
+    k_area_batch<<<(unsigned)n, 256, 0, st>>>(d_ad);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EBIT_OK : fail_s(EBIT_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+  }
+};
+
+template <typename R>
+ebit_status set_batch_attributes() {
+  constexpr size_t smem = ebit::tile_smem_bytes<R>();
+  if (cudaFuncSetAttribute(ebit::k_sweep_tile_batch<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(ebit::k_sweep_tile_batch<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return fail_s(EBIT_ECUDA, "cudaFuncSetAttribute (batch)");
+  }
+  return EBIT_OK;
+}
+
+}  // namespace
+
+struct ebit_server {
+  size_t budget = 0, in_use = 0;
+  ebit_server_opts opts{};
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  std::deque<std::unique_ptr<Instance>> queue;
+  std::vector<std::unique_ptr<Instance>> active;
+  std::map<uint64_t, ebit_result> done;
+  std::map<uint64_t, int> pending;  // tickets queued or running
+  std::thread worker;
+  bool started = false;
+  // statistics
+  int64_t batch_steps = 0, cell_updates = 0;
+  double busy_ms = 0.0;
+  // worker-only
+  cudaStream_t stream = nullptr;
+  Group<float> g32;
+  Group<double> g64;
+  bool dirty = true;
+  cudaGraphExec_t graph = nullptr;
+
+  void run();
+  ebit_status admit(Instance* in);
+  void retire(size_t idx);
+  ebit_status step();
+};
+
+ebit_status ebit_server::admit(Instance* in) {
+  const ebit_request& r = in->req;
+  ebit_grid g{r.n, r.n, 1.0 / r.n, r.prec, r.flags};
+  ebit_scene sc{in->circles.empty() ? nullptr : in->circles.data(), (int32_t)in->circles.size(), nullptr, nullptr};
+  ebit_status s = ebit_init(&in->ctx, &g, &sc, stream);
+  if (s != EBIT_OK) return s;
+  const size_t esz = r.prec == EBIT_FP32 ? 4 : 8;
+  const size_t vb = (size_t)(r.n + 1) * (r.n + 1) * esz;
+  if (cudaMalloc(&in->u, vb) != cudaSuccess || cudaMalloc(&in->v, vb) != cudaSuccess) {
+    cudaGetLastError();
+    return fail_s(EBIT_ENOMEM, "velocity allocation");
+  }
+  const int nb = (int)(((long long)(r.n + 1) * (r.n + 1) + 255) / 256);
+  if (r.prec == EBIT_FP32)
+    k_velocity<float><<<nb, 256, 0, stream>>>(r.field, r.n, 1.0 / r.n, r.omega, r.cx, r.cy, r.drift_u, r.drift_v, (float*)in->u, (float*)in->v);
+  else
+    k_velocity<double><<<nb, 256, 0, stream>>>(r.field, r.n, 1.0 / r.n, r.omega, r.cx, r.cy, r.drift_u, r.drift_v, (double*)in->u, (double*)in->v);
+  in->dx = 1.0 / r.n;
+  in->dt = r.cfl * in->dx / field_umax(r);
+  if ((s = ebit_fraction(in->ctx, nullptr, &in->area0)) != EBIT_OK) return s;
+  cudaMemsetAsync(in->ctx->ctr, 0, ebit::kCounters * sizeof(unsigned long long), stream);
+  in->t_admit = now_ms();
+  return EBIT_OK;
+}
+
+void ebit_server::retire(size_t idx) {
+  Instance* in = active[idx].get();
+  ebit_result res{};
+  res.status = EBIT_OK;
+  res.steps = in->done;
+  res.area0 = in->area0;
+  unsigned long long ctr[ebit::kCounters] = {0};
+  ebit_status s = ebit_fraction(in->ctx, nullptr, &res.area);
+  if (s == EBIT_OK) {
+    cudaMemcpyAsync(ctr, in->ctx->ctr, sizeof ctr, cudaMemcpyDeviceToHost, stream);
+    if (in->req.C_out)
+      cudaMemcpy2DAsync(in->req.C_out, (size_t)in->req.n * (in->req.prec == EBIT_FP32 ? 4 : 8),
+                        in->ctx->C, (size_t)in->ctx->L.d.P * in->ctx->L.esz,
+                        (size_t)in->req.n * in->ctx->L.esz, in->req.n, cudaMemcpyDeviceToHost, stream);
+    if (cudaStreamSynchronize(stream) != cudaSuccess) s = EBIT_ECUDA;
+  }
+  res.status = in->failed != EBIT_OK ? in->failed : s;
+  for (int t = 0; t < EBIT_D_COUNT; ++t) res.counters[t] = (int64_t)ctr[t];
+  res.e_area = in->area0 != 0.0 ? std::fabs(res.area - in->area0) / in->area0 : 0.0;
+  res.run_ms = now_ms() - in->t_admit;
+  res.queue_ms = in->t_admit - in->t_submit;
+  res.cell_updates = (int64_t)in->req.n * in->req.n * in->done;
+  std::vector<float> l = in->lat_ms;
+  if (!l.empty()) {
+    std::sort(l.begin(), l.end());
+    res.step_p50_ms = l[(size_t)(0.50 * (l.size() - 1))];
+    res.step_p99_ms = l[(size_t)(0.99 * (l.size() - 1))];
+  }
+  ebit_destroy(in->ctx);
+  cudaFree(in->u);
+  cudaFree(in->v);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    done[in->ticket] = res;
+    pending.erase(in->ticket);
+    in_use -= in->bytes;
+  }
+  active.erase(active.begin() + idx);
+  dirty = true;
+  cv.notify_all();
+}
+
+ebit_status ebit_server::step() {
+  std::vector<Instance*> all;
+  for (auto& p : active) all.push_back(p.get());
+  ebit_status s;
+  if (dirty) {
+    if (graph) {
+      cudaGraphExecDestroy(graph);
+      graph = nullptr;
+    }
+    if ((s = g32.build(all, EBIT_FP32, stream)) != EBIT_OK) return s;
+    if ((s = g64.build(all, EBIT_FP64, stream)) != EBIT_OK) return s;
+    if (opts.use_graphs) {
+      cudaGraph_t gr = nullptr;
+      if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail_s(EBIT_ECUDA, "begin capture");
+      const ebit_status s1 = g32.launch(stream), s2 = g64.launch(stream);
+      if (cudaStreamEndCapture(stream, &gr) != cudaSuccess || s1 != EBIT_OK || s2 != EBIT_OK)
+        return fail_s(EBIT_ECUDA, "capture of the batch step");
+      const cudaError_t e = cudaGraphInstantiate(&graph, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) return fail_s(EBIT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    dirty = false;
+  }
+  g32.fill();
+  g64.fill();
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, stream);
+  if (graph) {
+    if (cudaGraphLaunch(graph, stream) != cudaSuccess) return fail_s(EBIT_ECUDA, "graph launch");
+  } else {
+    if ((s = g32.launch(stream)) != EBIT_OK) return s;
+    if ((s = g64.launch(stream)) != EBIT_OK) return s;
+  }
+  cudaEventRecord(b, stream);
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_s(EBIT_ECUDA, "batch step");
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  int64_t cells = 0;
+  for (Instance* in : all) {
+    in->lat_ms.push_back(ms);
+    in->done += 1;
+    in->ctx->step_index += 1;
+    cells += (int64_t)in->req.n * in->req.n;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  batch_steps += 1;
+  cell_updates += cells;
+  busy_ms += ms;
+  return EBIT_OK;
+}
+
+void ebit_server::run() {
+  cudaSetDevice(opts.device);
+  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+      set_batch_attributes<float>() != EBIT_OK || set_batch_attributes<double>() != EBIT_OK) {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& q : queue) {
+      ebit_result r{};
+      r.status = EBIT_ECUDA;
+      done[q->ticket] = r;
+      pending.erase(q->ticket);
+    }
+    queue.clear();
+    stop = true;
+    cv.notify_all();
+    return;
+  }
+  for (;;) {
+    // admission: first come first served among the requests that fit
+    std::vector<std::unique_ptr<Instance>> admitted;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      if (active.empty())
+        cv.wait(lk, [&] { return stop || !queue.empty(); });
+      if (stop && queue.empty() && active.empty()) break;
+      if (stop) {
+        // cancel what is queued; finish nothing further
+        for (auto& q : queue) {
+          ebit_result r{};
+          r.status = EBIT_ETIMEOUT;
+          done[q->ticket] = r;
+          pending.erase(q->ticket);
+        }
+        queue.clear();
+      }
+      for (auto it = queue.begin(); it != queue.end();) {
+        const bool room = in_use + (*it)->bytes <= budget &&
+                          (opts.max_instances <= 0 ||
+                           (int)(active.size() + admitted.size()) < opts.max_instances);
+        if (room) {
+          in_use += (*it)->bytes;
+          admitted.push_back(std::move(*it));
+          it = queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    for (auto& in : admitted) {
+      const ebit_status s = admit(in.get());
+      if (s != EBIT_OK) {
+        ebit_result r{};
+        r.status = s;
+        if (in->ctx) ebit_destroy(in->ctx);
+        if (in->u) cudaFree(in->u);
+        if (in->v) cudaFree(in->v);
+        std::lock_guard<std::mutex> lk(mu);
+        done[in->ticket] = r;
+        pending.erase(in->ticket);
+        in_use -= in->bytes;
+        cv.notify_all();
+        continue;
+      }
+      active.push_back(std::move(in));
+      dirty = true;
+    }
+    if (stop) {
+      while (!active.empty()) retire(active.size() - 1);
+      continue;
+    }
+    if (active.empty()) continue;
+    const ebit_status s = step();
+    if (s != EBIT_OK) {
+      // fail every running request and carry on with an empty set
+      for (auto& in : active) {
+        in->failed = s;
+        in->req.steps = (int32_t)in->done;
+      }
+    }
+    for (size_t i = active.size(); i-- > 0;)
+      if (active[i]->done >= active[i]->req.steps) retire(i);
+  }
+  if (graph) cudaGraphExecDestroy(graph);
+  g32.release();
+  g64.release();
+  cudaStreamDestroy(stream);
+}
+
+extern "C" {
+
+ebit_status ebit_server_create(ebit_server** out, size_t hbm_budget, const ebit_server_opts* opts) {
+  if (!out) return fail_s(EBIT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (hbm_budget == 0) return fail_s(EBIT_EINVAL, "zero memory budget");
+  ebit_server* s = new (std::nothrow) ebit_server;
+  if (!s) return fail_s(EBIT_ENOMEM, "host allocation failed");
+  s->budget = hbm_budget;
+  if (opts) s->opts = *opts;
+  else s->opts.use_graphs = 1;
+  *out = s;
+  return EBIT_OK;
+}
+
+ebit_status ebit_submit(ebit_server* s, const ebit_request* r, uint64_t* ticket) {
+  if (!s || !r || !ticket) return fail_s(EBIT_EINVAL, "NULL argument");
+  if (r->n < 1 || r->n > ebit_detail::kMaxSide || (r->prec != EBIT_FP32 && r->prec != EBIT_FP64) ||
+      r->steps < 0 || !(r->cfl > 0.0 && r->cfl <= 1.0) || r->ncircles < 0 ||
+      (r->ncircles > 0 && !r->circles) ||
+      (r->field != EBIT_FIELD_VORTEX && r->field != EBIT_FIELD_CELLULAR && r->field != EBIT_FIELD_ROTATION) ||
+      (r->field == EBIT_FIELD_VORTEX && !(r->period > 0.0)) || (r->flags & ~EBIT_FIT_LINE))
+    return fail_s(EBIT_EINVAL, "invalid request");
+  auto in = std::make_unique<Instance>();
+  in->req = *r;
+  in->circles.assign(r->circles, r->circles + r->ncircles);
+  in->req.circles = nullptr;
+  in->bytes = request_bytes(*r);
+  if (in->bytes > s->budget)
+    return fail_s(EBIT_EFULL, "request needs %zu bytes, more than the whole budget (%zu)", in->bytes, s->budget);
+  in->t_submit = now_ms();
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) return fail_s(EBIT_EINVAL, "server is shutting down");
+  in->ticket = s->next_ticket++;
+  *ticket = in->ticket;
+  s->pending[in->ticket] = 1;
+  s->queue.push_back(std::move(in));
+  if (!s->started) {
+    s->started = true;
+    s->worker = std::thread([s] { s->run(); });
+  }
+  s->cv.notify_all();
+  return EBIT_OK;
+}
+
+ebit_status ebit_poll(ebit_server* s, uint64_t ticket, ebit_result* out) {
+  if (!s || !out) return fail_s(EBIT_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->done.find(ticket);
+  if (it != s->done.end()) {
+    *out = it->second;
+    s->done.erase(it);
+    return EBIT_OK;
+  }
+  if (s->pending.count(ticket)) return EBIT_EAGAIN;
+  return fail_s(EBIT_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+}
+
+ebit_status ebit_server_stats_get(ebit_server* s, ebit_server_stats* out) {
+  if (!s || !out) return fail_s(EBIT_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  out->queued = (int64_t)s->queue.size();
+  out->running = (int64_t)s->pending.size() - (int64_t)s->queue.size();
+  out->batch_steps = s->batch_steps;
+  out->cell_updates = s->cell_updates;
+  out->busy_ms = s->busy_ms;
+  out->bytes_in_use = s->in_use;
+  return EBIT_OK;
+}
+
+void ebit_server_destroy(ebit_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  delete s;
+}
+
+}  // extern "C"

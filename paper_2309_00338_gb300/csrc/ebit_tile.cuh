@@ -76,10 +76,11 @@ constexpr size_t tile_smem_bytes() {
          (5 * kRN + 4 * kNVE);
 }
 
+// The tile with origin (i0, j0) of one grid (one block runs it).
 template <typename R, int AX>
-__global__ void __launch_bounds__(kTileThreads)
-k_sweep_tile(GView<R, AX> G, Buf<R> out, int line_only, unsigned long long* ctr,
-             unsigned long long* cfl_bits, int* status) {
+__device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& out, int line_only,
+                                           unsigned long long* ctr, unsigned long long* cfl_bits,
+                                           int* status, const int i0, const int j0) {
   extern __shared__ __align__(16) unsigned char smem[];
   Cand<R>* cand = reinterpret_cast<Cand<R>*>(smem);
   R* hfx = reinterpret_cast<R*>(cand + kCandCap);
@@ -106,7 +107,6 @@ k_sweep_tile(GView<R, AX> G, Buf<R> out, int line_only, unsigned long long* ctr,
 
   const int tid = threadIdx.x;
   const int tnx = G.tnx(), tny = G.tny();
-  const int i0 = blockIdx.x * kTI, j0 = blockIdx.y * kTJ;
   const int ri0 = i0 - 4, rj0 = j0 - 2;
   if (tid < D_NUSED) s_cnt[tid] = 0;
   if (tid == 0) {
@@ -435,6 +435,41 @@ k_sweep_tile(GView<R, AX> G, Buf<R> out, int line_only, unsigned long long* ctr,
     if (s_cnt[D_CFL]) atomicOr(status, ST_CFL);
     if (s_cnt[D_INVARIANT]) atomicOr(status, ST_INVARIANT);
   }
+}
+
+// One grid: block (bx, by) runs the tile at (64 bx, 32 by).
+template <typename R, int AX>
+__global__ void __launch_bounds__(kTileThreads)
+k_sweep_tile(GView<R, AX> G, Buf<R> out, int line_only, unsigned long long* ctr,
+             unsigned long long* cfl_bits, int* status) {
+  sweep_tile<R, AX>(G, out, line_only, ctr, cfl_bits, status, blockIdx.x * kTI, blockIdx.y * kTJ);
+}
+
+// Many grids in one launch: per-grid sweep descriptors and a list of work
+// items (grid, tile); a grid whose descriptor is inactive for this launch
+// (its split order puts the other direction first this step) is skipped.
+template <typename R, int AX>
+struct SweepDesc {
+  GView<R, AX> G;
+  Buf<R> out;
+  unsigned long long* ctr;
+  unsigned long long* cfl_bits;
+  int* status;
+  int line_only;
+  int active;
+};
+
+struct WorkItem {
+  int grid, tx, ty;
+};
+
+template <typename R, int AX>
+__global__ void __launch_bounds__(kTileThreads)
+k_sweep_tile_batch(const SweepDesc<R, AX>* __restrict__ descs, const WorkItem* __restrict__ items) {
+  const WorkItem it = items[blockIdx.x];
+  const SweepDesc<R, AX>& D = descs[it.grid];
+  if (!D.active) return;
+  sweep_tile<R, AX>(D.G, D.out, D.line_only, D.ctr, D.cfl_bits, D.status, it.tx * kTI, it.ty * kTJ);
 }
 
 }  // namespace ebit

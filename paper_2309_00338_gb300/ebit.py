@@ -268,3 +268,126 @@ def ebit_fraction_noalloc(nx, ny, dx, prec, K, Z, sH, sV, C, area, marker_counts
     _check(lib().ebit_fraction_noalloc(ctypes.byref(g), _dev_ptr(K), _dev_ptr(Z), _dev_ptr(sH), _dev_ptr(sV),
                                        _dev_ptr(C), _dev_ptr(area), _dev_ptr(marker_counts), _stream(stream)),
            "ebit_fraction_noalloc")
+
+
+# ---------------------------------------------------------------------------
+# batched steps and serving
+# ---------------------------------------------------------------------------
+EBIT_FIELD_VORTEX, EBIT_FIELD_CELLULAR, EBIT_FIELD_ROTATION = 0, 1, 2
+
+
+class ebit_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("prec", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("circles", ctypes.POINTER(ebit_circle)), ("ncircles", ctypes.c_int32),
+                ("field", ctypes.c_int32), ("period", ctypes.c_double),
+                ("omega", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("drift_u", ctypes.c_double), ("drift_v", ctypes.c_double),
+                ("steps", ctypes.c_int32), ("cfl", ctypes.c_double), ("C_out", ctypes.c_void_p)]
+
+
+class ebit_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_int64),
+                ("area0", ctypes.c_double), ("area", ctypes.c_double), ("e_area", ctypes.c_double),
+                ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("step_p50_ms", ctypes.c_double), ("step_p99_ms", ctypes.c_double),
+                ("counters", ctypes.c_int64 * D_COUNT), ("cell_updates", ctypes.c_int64)]
+
+
+class ebit_server_opts(ctypes.Structure):
+    _fields_ = [("max_instances", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+                ("device", ctypes.c_int32)]
+
+
+class ebit_server_stats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("batch_steps", ctypes.c_int64), ("cell_updates", ctypes.c_int64),
+                ("busy_ms", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t)]
+
+
+SIGNATURES.update({
+    "ebit_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_size_t, ctypes.POINTER(ebit_server_opts)]),
+    "ebit_submit": (ctypes.c_int, [_P, ctypes.POINTER(ebit_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "ebit_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(ebit_result)]),
+    "ebit_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(ebit_server_stats)]),
+    "ebit_server_destroy": (None, [_P]),
+})
+if _lib is not None:  # signatures added after an earlier load
+    for _n in ("ebit_server_create", "ebit_submit", "ebit_poll", "ebit_server_stats_get", "ebit_server_destroy"):
+        _f = getattr(_lib, _n)
+        _f.restype, _f.argtypes = SIGNATURES[_n]
+
+
+def ebit_server_create(hbm_budget, max_instances=0, use_graphs=True, device=0):
+    o = ebit_server_opts(int(max_instances), int(bool(use_graphs)), int(device))
+    h = ctypes.c_void_p()
+    _check(lib().ebit_server_create(ctypes.byref(h), int(hbm_budget), ctypes.byref(o)), "ebit_server_create")
+    return h
+
+
+def make_request(n, circles, field=EBIT_FIELD_CELLULAR, steps=10, cfl=0.5, prec=EBIT_FP64, period=1.0,
+                 omega=0.0, centre=(0.5, 0.5), drift=(0.0, 0.0), C_out=None, flags=0):
+    """Build an ebit_request; returns (request, keep-alive list)."""
+    circ = np.ascontiguousarray(np.asarray(circles, np.float64).reshape(-1, 3))
+    keep = [circ]
+    r = ebit_request()
+    r.n, r.prec, r.flags = int(n), int(prec), int(flags)
+    r.circles = circ.ctypes.data_as(ctypes.POINTER(ebit_circle)) if circ.shape[0] else None
+    r.ncircles = circ.shape[0]
+    r.field, r.period, r.omega = int(field), float(period), float(omega)
+    r.cx, r.cy = (float(t) for t in centre)
+    r.drift_u, r.drift_v = (float(t) for t in drift)
+    r.steps, r.cfl = int(steps), float(cfl)
+    if C_out is not None:
+        assert C_out.flags["C_CONTIGUOUS"] and C_out.size == n * n
+        r.C_out = C_out.ctypes.data
+        keep.append(C_out)
+    return r, keep
+
+
+def ebit_submit(server, request):
+    """Returns the ticket, or raises EbitError (EBIT_EINVAL / EBIT_EFULL)."""
+    t = ctypes.c_uint64()
+    _check(lib().ebit_submit(server, ctypes.byref(request), ctypes.byref(t)), "ebit_submit")
+    return t.value
+
+
+def ebit_poll(server, ticket):
+    """The result dict once done, None while queued or running."""
+    r = ebit_result()
+    st = lib().ebit_poll(server, ctypes.c_uint64(ticket), ctypes.byref(r))
+    if st == EBIT_EAGAIN:
+        return None
+    _check(st, "ebit_poll")
+    return {"status": r.status, "steps": r.steps, "area0": r.area0, "area": r.area, "e_area": r.e_area,
+            "queue_ms": r.queue_ms, "run_ms": r.run_ms, "step_p50_ms": r.step_p50_ms,
+            "step_p99_ms": r.step_p99_ms, "counters": np.array(r.counters[:], np.int64),
+            "cell_updates": r.cell_updates}
+
+
+def ebit_server_stats_get(server):
+    s = ebit_server_stats()
+    _check(lib().ebit_server_stats_get(server, ctypes.byref(s)), "ebit_server_stats_get")
+    return {"queued": s.queued, "running": s.running, "batch_steps": s.batch_steps,
+            "cell_updates": s.cell_updates, "busy_ms": s.busy_ms, "bytes_in_use": s.bytes_in_use}
+
+
+def ebit_server_destroy(server):
+    if server:
+        lib().ebit_server_destroy(server)
+
+
+def wait_all(server, tickets, timeout_s=600.0, poll_s=0.002):
+    """Poll until every ticket has a result; returns {ticket: result}."""
+    import time
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t not in out:
+                r = ebit_poll(server, t)
+                if r is not None:
+                    out[t] = r
+        if time.time() - t0 > timeout_s:
+            raise TimeoutError(f"{len(tickets) - len(out)} requests still running")
+        time.sleep(poll_s)
+    return out

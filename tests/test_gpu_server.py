@@ -1,0 +1,128 @@
+"""Batched steps and serving on the GPU.
+
+* every result is the same alone and in the mix (continuous batching with a
+  budget that forces queueing, FP32 and FP64 requests together, ragged sizes);
+* a served request equals the oracle run of the same steps (rotation field,
+  which both sides evaluate with the same IEEE operations);
+* graph replay and plain launches give identical results."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_00338_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2309_00338_gb300 import ebit  # noqa: E402
+
+
+def _mix():
+    rng = W.Rng(2024)
+    reqs = []
+    specs = [(48, ebit.EBIT_FIELD_VORTEX, 0, 40), (64, ebit.EBIT_FIELD_CELLULAR, 1, 30),
+             (97, ebit.EBIT_FIELD_ROTATION, 0, 25), (130, ebit.EBIT_FIELD_VORTEX, 1, 20),
+             (33, ebit.EBIT_FIELD_CELLULAR, 0, 50), (80, ebit.EBIT_FIELD_ROTATION, 1, 35)]
+    for n, field, prec, steps in specs:
+        dx = 1.0 / n
+        circles = W.place_circles(rng, 6, 3 * dx, 0.12, 2 * dx, lambda x, y, r: True, max_tries=50)
+        reqs.append(dict(n=n, circles=circles, field=field, prec=prec, steps=steps, cfl=0.5,
+                         period=steps * 0.5 * dx, omega=2 * math.pi, centre=(0.5, 0.5), drift=(0.1, -0.05)))
+    return reqs
+
+
+def _run(specs, budget, use_graphs=True):
+    s = ebit.ebit_server_create(budget, use_graphs=use_graphs)
+    keep, outs, tickets = [], [], []
+    try:
+        for sp in specs:
+            C = np.zeros(sp["n"] * sp["n"], np.float64 if sp["prec"] == 0 else np.float32)
+            r, k = ebit.make_request(C_out=C, **sp)
+            keep.append(k)
+            outs.append(C)
+            tickets.append(ebit.ebit_submit(s, r))
+        res = ebit.wait_all(s, tickets)
+        stats = ebit.ebit_server_stats_get(s)
+    finally:
+        ebit.ebit_server_destroy(s)
+    return [res[t] for t in tickets], outs, stats
+
+
+def test_alone_equals_in_the_mix():
+    specs = _mix()
+    fps = [ebit.ebit_footprint(sp["n"], sp["n"], 1.0 / sp["n"], sp["prec"]) for sp in specs]
+    budget = int(2.5 * max(fps)) + (8 << 20)       # only a few fit at once: requests queue
+    mixed, Cm, stats = _run(specs, budget)
+    assert stats["batch_steps"] < sum(sp["steps"] for sp in specs)   # steps were shared
+    assert any(r["queue_ms"] > 0.0 for r in mixed)
+    for sp, rm, cm in zip(specs, mixed, Cm):
+        assert rm["status"] == 0 and rm["steps"] == sp["steps"]
+        alone, Ca, _ = _run([sp], budget)
+        ra = alone[0]
+        assert ra["area"] == rm["area"] and ra["area0"] == rm["area0"]
+        assert np.array_equal(Ca[0], cm)
+        assert np.array_equal(ra["counters"], rm["counters"])
+        assert rm["counters"][ebit.D_INVARIANT] == 0 and rm["counters"][ebit.D_CFL] == 0
+
+
+def test_graphs_and_plain_launches_agree():
+    specs = _mix()[:3]
+    a, Ca, _ = _run(specs, 8 << 30, use_graphs=True)
+    b, Cb, _ = _run(specs, 8 << 30, use_graphs=False)
+    for ra, rb, ca, cb in zip(a, b, Ca, Cb):
+        assert ra["area"] == rb["area"] and np.array_equal(ca, cb)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_served_rotation_matches_oracle(prec):
+    n, steps, cfl = 72, 30, 0.5
+    omega, centre, drift = 2 * math.pi, (0.5, 0.5), (0.3, 0.1)
+    circles = np.array([[0.42, 0.55, 0.11], [0.6, 0.3, 0.07]])
+    C = np.zeros(n * n, np.float64 if prec == 0 else np.float32)
+    s = ebit.ebit_server_create(4 << 30)
+    try:
+        r, keep = ebit.make_request(n, circles, ebit.EBIT_FIELD_ROTATION, steps, cfl, prec,
+                                    omega=omega, centre=centre, drift=drift, C_out=C)
+        res = ebit.wait_all(s, [ebit.ebit_submit(s, r)])
+        res = list(res.values())[0]
+    finally:
+        ebit.ebit_server_destroy(s)
+    dx = 1.0 / n
+    umax = 0.0
+    for a in (0, 1):
+        for b in (0, 1):
+            umax = max(umax, abs(-omega * (b - centre[1]) + drift[0]), abs(omega * (a - centre[0]) + drift[1]))
+    dt = cfl * dx / umax
+    f = W.rotation_field(n, n, dx, omega, centre, drift)
+    S = oracle.init(n, n, dx, W.circle_scene(circles), prec)
+    _, A0 = oracle.fraction(S)
+    for k in range(steps):
+        out = oracle.step(S, f.u, f.v, dt)
+    assert res["status"] == 0
+    assert abs(res["area0"] - A0) <= 1e-12 * A0
+    assert abs(res["area"] - out["area"]) <= 1e-12 * out["area"]
+    got = C.reshape(n, n).astype(np.float64)
+    if prec == 1:
+        assert np.array_equal(got, out["C"])
+    else:
+        assert np.max(np.abs(got - out["C"])) <= 1e-12
+
+
+def test_vortex_request_returns_to_its_shape():
+    """A time-reversed vortex request (period = steps * dt) comes back with a
+    small area error, as in the single-grid tests."""
+    n = 64
+    steps = 128
+    s = ebit.ebit_server_create(4 << 30)
+    try:
+        r, keep = ebit.make_request(n, [(0.5, 0.75, 0.15)], ebit.EBIT_FIELD_VORTEX, steps, 0.5, 0,
+                                    period=steps * 0.5 / n)
+        res = list(ebit.wait_all(s, [ebit.ebit_submit(s, r)]).values())[0]
+    finally:
+        ebit.ebit_server_destroy(s)
+    assert res["status"] == 0 and res["e_area"] < 5e-2
