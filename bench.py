@@ -44,6 +44,13 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="cellular_curve_4096",
+                   choices=["cellular_curve_4096", "batched", "serving"],
+                   help="batched: 512 uneven grids in one batch; serving: Poisson arrivals")
+    p.add_argument("--instances", type=int, default=512, help="batched: number of grids")
+    p.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
+    p.add_argument("--serve-seconds", type=float, default=2.0, help="serving: arrival window")
+    p.add_argument("--serve-cap", type=float, default=90.0, help="serving: wall-clock cap (s)")
     return p.parse_args()
 
 
@@ -348,9 +355,141 @@ def run_ours(args, wl, world, rank, local):
         tdist.destroy_process_group()
 
 
+def _batched_requests(count, seed=230900340):
+    """Grids of side log-uniform in [32, 512], 1-64 circles of radius
+    U[0.05, 0.15] (at least 3 cells), a coin flip between the time-reversed
+    vortex (period = steps * dt) and the cellular flow, 200-1000 steps, CFL 0.5."""
+    from paper_2309_00338_gb300 import workloads as W
+    rng = W.Rng(seed)
+    out = []
+    for _ in range(count):
+        wl = W.random_instance(rng)
+        vortex = wl.field.name == "vortex"
+        out.append(dict(n=wl.n, circles=wl.scene["circles"], steps=wl.steps, cfl=0.5,
+                        field=0 if vortex else 1, period=wl.steps * wl.dt if vortex else 1.0,
+                        vortex=vortex))
+    return out
+
+
+def _serve(ebit, specs, prec, budget, max_instances=0, arrivals=None, cap_s=None):
+    """Submit specs (at arrival times if given), wait; returns results + stats."""
+    s = ebit.ebit_server_create(budget, max_instances=max_instances)
+    keep, tickets = [], []
+    t0 = time.perf_counter()
+    res = {}
+    try:
+        for k, sp in enumerate(specs):
+            if arrivals is not None:
+                delay = arrivals[k] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+            r, kk = ebit.make_request(sp["n"], sp["circles"], sp["field"], sp["steps"], sp["cfl"], prec,
+                                      period=sp["period"], omega=sp.get("omega", 0.0),
+                                      centre=sp.get("centre", (0.5, 0.5)), drift=sp.get("drift", (0.0, 0.0)))
+            keep.append(kk)
+            tickets.append(ebit.ebit_submit(s, r))
+        while len(res) < len(tickets):
+            for t in tickets:
+                if t not in res:
+                    r = ebit.ebit_poll(s, t)
+                    if r is not None:
+                        res[t] = r
+            if cap_s is not None and time.perf_counter() - t0 > cap_s:
+                break
+            time.sleep(0.002)
+        wall = time.perf_counter() - t0
+        stats = ebit.ebit_server_stats_get(s)
+    finally:
+        ebit.ebit_server_destroy(s)
+    return [res.get(t) for t in tickets], stats, wall
+
+
+def run_batched(args):
+    """512 uneven grids advanced together (one captured launch sequence per
+    batch step) in FP32 and FP64, against one-grid-at-a-time plain FP64."""
+    from paper_2309_00338_gb300 import ebit
+    import torch
+    torch.cuda.set_device(0)
+    specs = _batched_requests(args.instances)
+    budget = 200 << 30
+    out = {}
+    for name, prec in (("fp32", 1), ("fp64", 0)):
+        res, st, wall = _serve(ebit, specs, prec, budget)
+        lat = [r["step_p50_ms"] for r in res if r]
+        ea = [r["e_area"] for r, sp in zip(res, specs) if r and sp["vortex"]]
+        out[name] = {"cell_updates": st["cell_updates"], "gpu_ms": st["busy_ms"], "wall_s": wall,
+                     "value": st["cell_updates"] / (st["busy_ms"] / 1e3),
+                     "batch_steps": st["batch_steps"],
+                     "step_p50_ms": float(np.percentile(lat, 50)), "step_p99_ms": float(np.percentile(lat, 99)),
+                     "e_area_reversed_median": float(np.median(ea)) if ea else None,
+                     "e_area_reversed_max": float(np.max(ea)) if ea else None}
+    sub = specs[:16]
+    res, st, wall = _serve(ebit, sub, 0, budget, max_instances=1)
+    out["fp64_one_at_a_time"] = {"instances": len(sub), "cell_updates": st["cell_updates"],
+                                 "gpu_ms": st["busy_ms"], "value": st["cell_updates"] / (st["busy_ms"] / 1e3)}
+    total = sum(sp["n"] ** 2 * sp["steps"] for sp in specs)
+    line = {"metric": "EBIT cell-updates/s, batched uneven grids", "value": out["fp32"]["value"],
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"batched_{len(specs)}_grids_32-512", "cell_updates": total,
+                       "seed": 230900340},
+            "fp32": out["fp32"], "fp64": out["fp64"], "fp64_one_at_a_time": out["fp64_one_at_a_time"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Poisson arrivals: grids of side log-uniform in [64, 2048], 1-500
+    circles of radius U[3, 30] cells, 50-2000 steps of the vortex, the
+    cellular flow or a solid rotation; FP32 requests."""
+    from paper_2309_00338_gb300 import ebit
+    from paper_2309_00338_gb300 import workloads as W
+    import torch
+    torch.cuda.set_device(0)
+    rng = W.Rng(230900341)
+    specs, arrivals = [], []
+    t = 0.0
+    while True:
+        t += -math.log(1.0 - rng.uniform()) / args.rate
+        if t > args.serve_seconds:
+            break
+        n = int(round(math.exp(rng.uniform(math.log(64), math.log(2048)))))
+        dx = 1.0 / n
+        count = rng.integer(1, 500)
+        steps = rng.integer(50, 2000)
+        kind = rng.integer(0, 2)
+        circles = W.place_circles(rng, count, 3 * dx, 30 * dx, 2 * dx, lambda x, y, r: True, max_tries=20)
+        sp = dict(n=n, circles=circles, steps=steps, cfl=0.5, field=kind, period=steps * 0.5 * dx,
+                  omega=2 * math.pi, centre=(0.5, 0.5), drift=(0.3, 0.1))
+        specs.append(sp)
+        arrivals.append(t)
+    # a 16 GiB admission budget bounds the batch (and so the step latency)
+    res, st, wall = _serve(ebit, specs, 1, 16 << 30, arrivals=arrivals, cap_s=args.serve_cap)
+    done = [r for r in res if r is not None]
+    lat50 = [r["step_p50_ms"] for r in done]
+    lat99 = [r["step_p99_ms"] for r in done]
+    qw = [r["queue_ms"] for r in done]
+    offered = sum(sp["n"] ** 2 * sp["steps"] for sp in specs) / args.serve_seconds
+    line = {"metric": "EBIT served cell-updates/s (continuous batching)", "value": st["cell_updates"] / wall,
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving_poisson", "rate_per_s": args.rate, "arrival_window_s": args.serve_seconds,
+                       "requests": len(specs), "offered_cell_updates_per_s": offered, "wall_cap_s": args.serve_cap},
+            "completed": len(done), "wall_s": wall, "gpu_busy_s": st["busy_ms"] / 1e3,
+            "batch_steps": st["batch_steps"],
+            "gpu_value": st["cell_updates"] / (st["busy_ms"] / 1e3) if st["busy_ms"] else None,
+            "step_p50_ms": float(np.median(lat50)) if lat50 else None,
+            "step_p99_ms": float(np.percentile(lat99, 99)) if lat99 else None,
+            "queue_ms_p50": float(np.median(qw)) if qw else None,
+            "queue_ms_p99": float(np.percentile(qw, 99)) if qw else None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist()
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     from paper_2309_00338_gb300 import workloads as W
     wl = W.cellular_curve_workload()
     if args.impl == "reference":
