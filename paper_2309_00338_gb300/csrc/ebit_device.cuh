@@ -22,8 +22,8 @@
 // selection) is written against an accessor A that answers, in sweep
 // coordinates: tnx/tny, old colours k/z, moved(marker), knew (new corner
 // colour) and landing (aligned markers landing on an edge).  GView answers
-// from global memory by recomputation; TView from a shared-memory tile where
-// each answer was computed once.
+// from global memory by recomputation; the tiled sweep kernel's accessor
+// from shared memory, where each answer was computed once.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -409,6 +409,7 @@ __device__ bool far_point(const A& S, Mk nb, int ci, int cj, int k, int j, doubl
 template <typename R>
 struct NewV {
   int present, vr, vl;
+  int cancelled, invariant;  // candidate pairs cancelled; 1 if the count breaks parity
   R s;
 };
 
@@ -416,8 +417,7 @@ struct NewV {
 // order); an odd count on an edge whose new end colours differ keeps the
 // median, an even count on an edge whose colours agree cancels in pairs.
 template <typename R>
-__device__ NewV<R> select_candidates(int n, double* cy, int* cvr, int* cvl, int* ord, int present,
-                                     int* cnt) {
+__device__ NewV<R> select_candidates(int n, double* cy, int* cvr, int* cvl, int* ord, int present) {
   for (int a = 1; a < n; ++a)
     for (int b = a; b > 0 && (cy[b] < cy[b - 1] || (cy[b] == cy[b - 1] && ord[b] < ord[b - 1])); --b) {
       const double t = cy[b]; cy[b] = cy[b - 1]; cy[b - 1] = t;
@@ -430,13 +430,15 @@ __device__ NewV<R> select_candidates(int n, double* cy, int* cvr, int* cvl, int*
   out.vr = -1;
   out.vl = -1;
   out.s = R(0.5);
+  out.cancelled = 0;
+  out.invariant = 0;
   int pick = -1;
   if (present && (n & 1)) {
     pick = n / 2;
   } else if (!present && !(n & 1)) {
-    if (cnt) cnt[D_CANCELLED] += n / 2;
+    out.cancelled = n / 2;
   } else {
-    if (cnt) cnt[D_INVARIANT] += 1;
+    out.invariant = 1;
     if (present && n > 0) {
       pick = 0;
       for (int t = 1; t < n; ++t)
@@ -489,7 +491,12 @@ __device__ NewV<R> new_unaligned(const A& S, bool line_only, int k, int j, int* 
       ++n;
     }
   }
-  return select_candidates<R>(n, cy, cvr, cvl, ord, S.knew(k, j) ^ S.knew(k, j + 1), cnt);
+  const NewV<R> out = select_candidates<R>(n, cy, cvr, cvl, ord, S.knew(k, j) ^ S.knew(k, j + 1));
+  if (cnt) {
+    cnt[D_CANCELLED] += out.cancelled;
+    cnt[D_INVARIANT] += out.invariant;
+  }
+  return out;
 }
 
 // ---------------------------------------------------------------------------
@@ -556,63 +563,6 @@ struct GView {
   }
 };
 
-// ---------------------------------------------------------------------------
-// Accessor over a shared-memory tile of the state (sweep coordinates).  The
-// region covers vertices [ri0, ri0+RXn) x [rj0, rj0+RYn); every per-vertex or
-// per-edge answer was computed once by the tile kernel.  Indices are clamped
-// into the region (the tile kernel only asks inside it).
-// ---------------------------------------------------------------------------
-constexpr int8_t kNoSrc = -128;
-
-template <typename R, int RXn, int RYn>
-struct TView {
-  const uint8_t* kb;    // old corner colour
-  const uint8_t* kn;    // new corner colour
-  const uint8_t* zb;    // old centre colour of the cell at this vertex
-  const int16_t* hix;   // moved aligned marker: ix - ri0
-  const R* hfx;
-  const int16_t* vix;   // moved unaligned marker: ix - ri0
-  const R* vfx;
-  const R* vfy;
-  const uint8_t* lpres; // landing: presence, kept source - i (kNoSrc: none), kept fraction
-  const int8_t* lsrc;
-  const R* lfx;
-  int ri0, rj0, nx_, ny_;
-  __device__ __forceinline__ int tnx() const { return nx_; }
-  __device__ __forceinline__ int tny() const { return ny_; }
-  __device__ __forceinline__ int id(int i, int j) const {
-    const int lx = min(max(i - ri0, 0), RXn - 1);
-    const int ly = min(max(j - rj0, 0), RYn - 1);
-    return ly * RXn + lx;
-  }
-  __device__ __forceinline__ int k(int i, int j) const { return kb[id(i, j)]; }
-  __device__ __forceinline__ int z(int i, int j) const { return zb[id(i, j)]; }
-  __device__ __forceinline__ int knew(int i, int j) const { return kn[id(i, j)]; }
-  __device__ __forceinline__ AP<R> moved(Mk m) const {
-    const int t = id(m.i, m.j);
-    AP<R> p;
-    p.jy = m.j;
-    if (m.kind == 0) {
-      p.ix = hix[t] + ri0;
-      p.fx = hfx[t];
-      p.fy = R(0);
-    } else {
-      p.ix = vix[t] + ri0;
-      p.fx = vfx[t];
-      p.fy = vfy[t];
-    }
-    return p;
-  }
-  __device__ __forceinline__ Landing<R> landing(int i, int j) const {
-    const int t = id(i, j);
-    Landing<R> L;
-    L.present = lpres[t];
-    L.kept_src = lsrc[t] == kNoSrc ? -1 : i + lsrc[t];
-    L.kept_fx = lfx[t];
-    L.cancelled = 0;
-    L.invariant = 0;
-    return L;
-  }
-};
+constexpr int8_t kNoSrc = -128;  // no landing source kept
 
 }  // namespace ebit
