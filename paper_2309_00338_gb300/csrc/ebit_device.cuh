@@ -108,15 +108,18 @@ __device__ __forceinline__ int segments(int q, int zc, int seg[2][2]) {
     seg[0][1] = 31 - __clz(em);
     return 1;
   }
-  int m = 0;
-#pragma unroll
-  for (int c = 0; c < 4; ++c)
-    if (((q >> c) & 1) != zc) {
-      seg[m][0] = (c + 3) & 3;
-      seg[m][1] = c;
-      ++m;
-    }
-  return m;
+  // four markers: q is 5 or 10.  The corners of the other colour than the
+  // centre are cut off, in corner order: corners 1 and 3 (segments 0-1, 2-3)
+  // when corner 0 has the centre's colour, else corners 0 and 2 (segments
+  // 3-0, 1-2).
+  if ((q & 1) == zc) {
+    seg[0][0] = 0; seg[0][1] = 1;
+    seg[1][0] = 2; seg[1][1] = 3;
+  } else {
+    seg[0][0] = 3; seg[0][1] = 0;
+    seg[1][0] = 1; seg[1][1] = 2;
+  }
+  return 2;
 }
 
 __device__ __forceinline__ Mk edge_marker(int ci, int cj, int e) {
@@ -142,7 +145,9 @@ template <class A>
 __device__ int partner(const A& S, int ci, int cj, int e) {
   int seg[2][2];
   const int n = cell_segments(S, ci, cj, seg);
-  for (int t = 0; t < n; ++t) {
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    if (t >= n) break;
     if (seg[t][0] == e) return seg[t][1];
     if (seg[t][1] == e) return seg[t][0];
   }
@@ -245,38 +250,117 @@ __device__ __forceinline__ AP<R> move_unaligned(int i, int row, R s, R ua, R ub,
   return p;
 }
 
-// Aligned markers landing on edge (i, j): kept only where the new end colours
-// differ; an odd count keeps the median by (fraction, source edge).
+// Order-preserving integer keys of a float / double (-0 and +0 equal).
+__device__ __forceinline__ long long okey(double x) {
+  const long long b = __double_as_longlong(x);
+  if (b >= 0) return b;
+  return b == (long long)(1ull << 63) ? 0 : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ long long okey(float x) {
+  const int b = __float_as_int(x);
+  if (b >= 0) return b;
+  return b == (int)0x80000000 ? 0 : (long long)(b ^ 0x7fffffff);
+}
+
+// Aligned markers landing on edge (i, j), from edges i-1, i, i+1 (slot q for
+// edge i-1+q, present in valid): kept only where the new end colours differ;
+// an odd count keeps the median by (fraction, source edge).  Ranks in
+// registers instead of a sort.
 template <typename R>
-__device__ __forceinline__ Landing<R> choose_landing(int n, R* fx, int* src, int present) {
-  for (int a = 1; a < n; ++a)
-    for (int b = a; b > 0 && (fx[b] < fx[b - 1] || (fx[b] == fx[b - 1] && src[b] < src[b - 1])); --b) {
-      const R tf = fx[b]; fx[b] = fx[b - 1]; fx[b - 1] = tf;
-      const int ts = src[b]; src[b] = src[b - 1]; src[b - 1] = ts;
-    }
+__device__ __forceinline__ Landing<R> choose_landing3(const bool valid[3], const R fx[3], int i,
+                                                      int present) {
+  const int n = (int)valid[0] + (int)valid[1] + (int)valid[2];
+  long long key[3];
+  int rank[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) key[t] = okey(fx[t]);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    int r = 0;
+#pragma unroll
+    for (int u = 0; u < 3; ++u)  // sources are distinct: ties in fraction go by source edge
+      if (u != t && valid[u] && (key[u] < key[t] || (key[u] == key[t] && u < t))) ++r;
+    rank[t] = r;
+  }
   Landing<R> L;
   L.present = present;
   L.kept_src = -1;
   L.kept_fx = R(0.5);
   L.cancelled = 0;
   L.invariant = 0;
+  int want = -1;
   if (present && (n & 1)) {
-    L.kept_src = src[n / 2];
-    L.kept_fx = fx[n / 2];
+    want = n / 2;
   } else if (!present && !(n & 1)) {
     L.cancelled = n / 2;
   } else {
     L.invariant = 1;
-    if (present && n > 0) {
-      int best = 0;
-      for (int t = 1; t < n; ++t)
-        if (fabs((double)fx[t] - 0.5) < fabs((double)fx[best] - 0.5)) best = t;
-      L.kept_src = src[best];
-      L.kept_fx = fx[best];
+    if (present && n > 0) {  // nearest the edge's middle, first in rank order
+      double bd = 0.0;
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        if (valid[t]) {
+          const double d = fabs((double)fx[t] - 0.5);
+          if (want < 0 || d < bd || (d == bd && rank[t] < want)) {
+            bd = d;
+            want = rank[t];
+          }
+        }
     }
+  }
+  if (want >= 0) {
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+      if (valid[t] && rank[t] == want) {
+        L.kept_src = i - 1 + t;
+        L.kept_fx = fx[t];
+      }
   }
   return L;
 }
+
+// ---------------------------------------------------------------------------
+// IEEE predicates on finite doubles, evaluated on the bit pattern so that they
+// run on the integer pipe rather than the (narrow) FP64 pipe: x > 0, x < 0,
+// x == 0, 0 <= x <= 1, and s < kMinSep2 for s >= +0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool d_gt0(double x) { return dbits(x) > 0; }
+__device__ __forceinline__ bool d_lt0(double x) { return (dbits(x) ^ (long long)(1ull << 63)) > 0; }
+__device__ __forceinline__ bool d_eq0(double x) { return (dbits(x) << 1) == 0; }
+__device__ __forceinline__ bool d_in01(double x) {
+  const unsigned long long b = (unsigned long long)dbits(x);
+  return b <= 0x3ff0000000000000ull || b == 0x8000000000000000ull;
+}
+__device__ __forceinline__ bool d_below_sep(double s) { return dbits(s) < dbits(kMinSep2); }
+
+// Exact conversions to double by integer operations: a float (any finite
+// value) and a small integer.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  int e = (int)((u >> 23) & 0xffu);
+  unsigned m = u & 0x7fffffu;
+  if (e == 0) {
+    if (m == 0) return __longlong_as_double((long long)sign);
+    const int sh = __clz(m) - 8;  // bring the leading one to bit 23
+    m = (m << sh) & 0x7fffffu;
+    e = 1 - sh;
+  }
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)(e + 896) << 52) | ((unsigned long long)m << 29)));
+}
+__device__ __forceinline__ double i2d(int n) {
+  if (n == 0) return 0.0;
+  const unsigned long long sign = n < 0 ? (1ull << 63) : 0ull;
+  const unsigned a = n < 0 ? (unsigned)(-n) : (unsigned)n;
+  const int p = 31 - __clz(a);
+  const unsigned long long mant = ((unsigned long long)a << (52 - p)) & 0xfffffffffffffull;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(1023 + p) << 52) | mant));
+}
+template <typename R> __device__ __forceinline__ double to_d(R x);
+template <> __device__ __forceinline__ double to_d<float>(float x) { return f2d(x); }
+template <> __device__ __forceinline__ double to_d<double>(double x) { return x; }
 
 // ---------------------------------------------------------------------------
 // Circle fit (Sec. 2.2, Fig. 3).  Coordinates in cells relative to vertex
@@ -285,69 +369,91 @@ __device__ __forceinline__ Landing<R> choose_landing(int n, R* fx, int* src, int
 // kap = 0).  The crossing wanted lies on the arc A..B that does not contain
 // T, i.e. on the other side of chord AB from T.
 // ---------------------------------------------------------------------------
-__device__ inline bool circle_cross(double Ax, double Ay, double Bx, double By, double Tx,
-                                    double Ty, double* y) {
-  const double qx = Bx - Ax, qy = By - Ay;
-  const double rx = Tx - Ax, ry = Ty - Ay;
-  const double tx = Tx - Bx, ty = Ty - By;
-  const double q2 = qx * qx + qy * qy;
-  const double r2 = rx * rx + ry * ry;
-  if (r2 < kMinSep2 || tx * tx + ty * ty < kMinSep2) return false;
+
+// A third point T of a circle through A and B with its offsets r = T - A and
+// t = T - B and their squared lengths.
+struct FitPt {
+  double rx, ry, r2, tx, ty, t2;
+};
+
+__device__ __forceinline__ FitPt fit_pt(double X, double Y, double Ax, double Ay, double Bx,
+                                        double By) {
+  FitPt p;
+  p.rx = X - Ax;
+  p.ry = Y - Ay;
+  p.r2 = p.rx * p.rx + p.ry * p.ry;
+  p.tx = X - Bx;
+  p.ty = Y - By;
+  p.t2 = p.tx * p.tx + p.ty * p.ty;
+  return p;
+}
+
+// q = B - A, q2 = |q|^2.
+__device__ __forceinline__ bool circle_cross(double Ay, double x0, double qx, double qy, double q2,
+                                             const FitPt& T, double* y) {
+  if (d_below_sep(T.r2) || d_below_sep(T.t2)) return false;
+  const double rx = T.rx, ry = T.ry, r2 = T.r2;
   const double kap = qx * ry - qy * rx;
   const double al = r2 * qy - q2 * ry;
   const double be = q2 * rx - r2 * qx;
-  const double x0 = -Ax;
   const double c0 = x0 * (kap * x0 + al);
   const double disc = be * be - 4.0 * kap * c0;
-  if (!(disc >= 0.0)) return false;
+  if (d_lt0(disc)) return false;
   const double sq = sqrt(disc);
   const double h = -0.5 * (be + copysign(sq, be));
-  if (h == 0.0) return false;
+  if (d_eq0(h)) return false;
   const double ya = c0 / h;
   double yrel = ya;
-  if (kap != 0.0) {
+  if (!d_eq0(kap)) {
     // the far root is formed only when the near one lies on T's side
+    const bool kpos = d_gt0(kap);
     const double sa = qx * ya - qy * x0;
-    const bool a_with_T = (sa > 0.0 && kap > 0.0) || (sa < 0.0 && kap < 0.0);
-    if (a_with_T) {
+    if (kpos ? d_gt0(sa) : d_lt0(sa)) {
       const double yb = h / kap;
       const double sb = qx * yb - qy * x0;
-      const bool b_with_T = (sb > 0.0 && kap > 0.0) || (sb < 0.0 && kap < 0.0);
-      if (!b_with_T) yrel = yb;
+      if (!(kpos ? d_gt0(sb) : d_lt0(sb))) yrel = yb;
     }
   }
   const double best = Ay + yrel;
-  if (!(best >= 0.0 && best <= 1.0)) return false;
+  if (!d_in01(best)) return false;
   *y = best;
   return true;
 }
 
-// Returns the fit kind (D_FIT_*) and the crossing ordinate.
-__device__ inline int fit_crossing(double Ax, double Ay, double Bx, double By, bool h1,
-                                   double P1x, double P1y, bool h4, double P4x, double P4y,
-                                   bool line_only, double* y) {
-  if (Bx == 0.0) {
+// Returns the fit kind (D_FIT_*) and the crossing ordinate; T1 (point 1) is
+// used when h1, T4 (point 4) when h4.
+__device__ __forceinline__ int fit_crossing(double Ax, double Ay, double Bx, double By, bool h1,
+                                            const FitPt& T1, bool h4, const FitPt& T4,
+                                            bool line_only, double* y) {
+  if (d_eq0(Bx)) {
     *y = By;
     return D_FIT_ONLINE;
   }
   const double cx = Bx - Ax, cy = By - Ay;
-  if (!line_only && cx * cx + cy * cy >= kMinSep2) {
+  const double x0 = -Ax;
+  const double c2 = cx * cx + cy * cy;
+  if (!line_only && !d_below_sep(c2)) {
     double ys0 = 0.0, ys1 = 0.0;
     int n = 0;
-    if (h1 && circle_cross(Ax, Ay, Bx, By, P1x, P1y, &ys0)) ++n;
+    if (h1 && circle_cross(Ay, x0, cx, cy, c2, T1, &ys0)) ++n;
     if (h4) {
       double t;
-      if (circle_cross(Ax, Ay, Bx, By, P4x, P4y, &t)) {
+      if (circle_cross(Ay, x0, cx, cy, c2, T4, &t)) {
         if (n == 0) ys0 = t; else ys1 = t;
         ++n;
       }
     }
-    if (n == 2) { *y = 0.5 * (ys0 + ys1); return D_FIT_TWO; }
-    if (n == 1) { *y = ys0; return D_FIT_ONE; }
+    if (n == 2) {
+      *y = 0.5 * (ys0 + ys1);
+      return D_FIT_TWO;
+    }
+    if (n == 1) {
+      *y = ys0;
+      return D_FIT_ONE;
+    }
   }
   // no circle: the chord's own crossing
-  const double x0 = -Ax;
-  *y = Ay + (x0 * (By - Ay)) / (Bx - Ax);
+  *y = Ay + (x0 * cy) / cx;
   return D_FIT_LINE;
 }
 
@@ -361,8 +467,8 @@ __device__ __forceinline__ R to_fraction(double y) {
 
 template <typename R>
 __device__ __forceinline__ void local_xy(const AP<R>& p, int k, int j, double* X, double* Y) {
-  *X = (double)(p.ix - k) + (double)p.fx;
-  *Y = (double)(p.jy - j) + (double)p.fy;
+  *X = i2d(p.ix - k) + to_d<R>(p.fx);
+  *Y = i2d(p.jy - j) + to_d<R>(p.fy);
 }
 
 // Centre rule (Sec. 2.3): from the new unaligned marker follow the moved
@@ -385,19 +491,22 @@ __device__ int walk(const A& S, Mk m0, Mk m1, int col) {
   return -1;
 }
 
-// The next marker along the interface beyond nb (found in cell ci,cj) when
-// nb is closer than the minimum separation to the point (fx,fy).
+// Point 1 (near = A) or 4 (near = B) of a fit: the moved marker nb next to
+// the chord (found in cell ci,cj), or the marker beyond it when nb is closer
+// than the minimum separation to the near end.
 template <class A>
-__device__ bool far_point(const A& S, Mk nb, int ci, int cj, int k, int j, double fx, double fy,
-                          double* X, double* Y) {
+__device__ bool far_point(const A& S, Mk nb, int ci, int cj, int k, int j, double ax, double ay,
+                          double bx, double by, bool near_a, FitPt* T) {
   if (nb.kind < 0) return false;
-  local_xy(S.moved(nb), k, j, X, Y);
-  const double ex = *X - fx, ey = *Y - fy;
-  if (ex * ex + ey * ey < kMinSep2) {
+  double X, Y;
+  local_xy(S.moved(nb), k, j, &X, &Y);
+  *T = fit_pt(X, Y, ax, ay, bx, by);
+  if (d_below_sep(near_a ? T->r2 : T->t2)) {
     int oi = 0, oj = 0;
     const Mk nn = beyond(S, nb, ci, cj, &oi, &oj);
     if (nn.kind < 0) return false;
-    local_xy(S.moved(nn), k, j, X, Y);
+    local_xy(S.moved(nn), k, j, &X, &Y);
+    *T = fit_pt(X, Y, ax, ay, bx, by);
   }
   return true;
 }
@@ -474,13 +583,14 @@ __device__ NewV<R> new_unaligned(const A& S, bool line_only, int k, int j, int* 
       int c1i = 0, c1j = 0, c4i = 0, c4j = 0;
       const Mk n1 = beyond(S, mA, c, j, &c1i, &c1j);
       const Mk n4 = beyond(S, mB, c, j, &c4i, &c4j);
-      double ax, ay, bx, by, p1x = 0, p1y = 0, p4x = 0, p4y = 0;
+      double ax, ay, bx, by;
       local_xy(A_, k, j, &ax, &ay);
       local_xy(B_, k, j, &bx, &by);
-      const bool h1 = far_point(S, n1, c1i, c1j, k, j, ax, ay, &p1x, &p1y);
-      const bool h4 = far_point(S, n4, c4i, c4j, k, j, bx, by, &p4x, &p4y);
+      FitPt t1{}, t4{};
+      const bool h1 = far_point(S, n1, c1i, c1j, k, j, ax, ay, bx, by, true, &t1);
+      const bool h4 = far_point(S, n4, c4i, c4j, k, j, ax, ay, bx, by, false, &t4);
       double y;
-      const int kind = fit_crossing(ax, ay, bx, by, h1, p1x, p1y, h4, p4x, p4y, line_only, &y);
+      const int kind = fit_crossing(ax, ay, bx, by, h1, t1, h4, t4, line_only, &y);
       if (cnt) cnt[kind] += 1;
       const int lr = walk(S, mB, n4, k);
       const int ll = walk(S, mA, n1, k - 1);
@@ -551,15 +661,21 @@ struct GView {
     return r;
   }
   __device__ Landing<R> landing(int i, int j) const {
+    bool valid[3];
     R fx[3];
-    int src[3];
-    int n = 0;
-    for (int e = i - 1; e <= i + 1; ++e) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int e = i - 1 + q;
+      valid[q] = false;
+      fx[q] = R(0);
       if (e < 0 || e >= tnx() || k(e, j) == k(e + 1, j)) continue;
       const AP<R> p = moved(Mk{0, e, j});
-      if (p.ix == i) { fx[n] = p.fx; src[n] = e; ++n; }
+      if (p.ix == i) {
+        valid[q] = true;
+        fx[q] = p.fx;
+      }
     }
-    return choose_landing(n, fx, src, knew(i, j) ^ knew(i + 1, j));
+    return choose_landing3<R>(valid, fx, i, knew(i, j) ^ knew(i + 1, j));
   }
 };
 

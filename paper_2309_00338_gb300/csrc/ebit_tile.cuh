@@ -138,6 +138,63 @@ __device__ __forceinline__ uint8_t verdicts(int vr, int vl) {
   return (uint8_t)((vr + 1) | ((vl + 1) << 2));
 }
 
+constexpr unsigned kFull = 0xffffffffu;
+
+// Exclusive offset of this lane's n in a block-shared list counter; one
+// shared atomic per warp.  All 32 lanes call it.
+__device__ __forceinline__ int warp_alloc(int n, int* count, int lane) {
+  int incl = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  int base = 0;
+  if (lane == 31 && total) base = atomicAdd(count, total);
+  return __shfl_sync(kFull, base, 31) + incl - n;
+}
+
+// push_bits for a whole warp (all 32 lanes call it).
+__device__ __forceinline__ void push_bits_warp(uint32_t bits, int t, uint16_t* list, int* count,
+                                               int lane) {
+  int base = warp_alloc(__popc(bits), count, lane);
+  const int row0 = (t / kRW) * kRX + 32 * (t % kRW);
+  while (bits) {
+    const int b = __ffs(bits) - 1;
+    bits &= bits - 1;
+    list[base++] = (uint16_t)(row0 + b);
+  }
+}
+
+// 32 x 32 bit transpose across a warp: lane r holds row r (bit c = element
+// (r, c)); returns column `lane` (bit r = element (r, lane)).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const int s = 16 >> q;
+    const uint32_t m = q == 0 ? 0x0000ffffu : q == 1 ? 0x00ff00ffu : q == 2 ? 0x0f0f0f0fu
+                     : q == 3 ? 0x33333333u : 0x55555555u;
+    const uint32_t y = __shfl_xor_sync(kFull, x, s);
+    x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+  }
+  return x;
+}
+
+// Bits c0 .. c0+31 of region row ly (c0 + 32 < 32 kRW).
+__device__ __forceinline__ uint32_t bits32(const uint32_t* w, int ly, int c0) {
+  const int q = c0 >> 5, r = c0 & 31;
+  const uint32_t a = w[ly * kRW + q];
+  return r ? ((a >> r) | (w[ly * kRW + q + 1] << (32 - r))) : a;
+}
+
+// Bits b of a 32-column window starting at column c0 with c0 + b <= last.
+__device__ __forceinline__ uint32_t upto32(int c0, int last) {
+  const int n = last - c0 + 1;
+  return n <= 0 ? 0u : (n >= 32 ? kFull : ((1u << n) - 1u));
+}
+
+
 // Accessor of the tile for the shared sweep logic (beyond, walk,
 // new_unaligned).  Indices are clamped into the region; the kernel only asks
 // inside it.
@@ -187,15 +244,95 @@ struct TViewB {
   // Moved point of a referenced marker relative to vertex (k, j).
   __device__ __forceinline__ void xy(uint16_t r, int k, int j, double* X, double* Y) const {
     const int t = r & (kKindV - 1), ly = t / kRX;
+    // the same values as (double)n + (double)f; the conversions run on the
+    // integer pipe and an aligned marker's y needs no addition
     if (r & kKindV) {
-      *X = (double)(m->vix[t] + ri0 - k) + (double)m->vfx[t];
-      *Y = (double)(rj0 + ly - j) + (double)m->vfy[t];
+      *X = i2d(m->vix[t] + ri0 - k) + to_d<R>(m->vfx[t]);
+      *Y = i2d(rj0 + ly - j) + to_d<R>(m->vfy[t]);
     } else {
-      *X = (double)(m->hix[t] + ri0 - k) + (double)m->hfx[t];
-      *Y = (double)(rj0 + ly - j) + 0.0;
+      *X = i2d(m->hix[t] + ri0 - k) + to_d<R>(m->hfx[t]);
+      *Y = i2d(rj0 + ly - j);
     }
   }
 };
+
+// One marker per edge from its linked candidates (the rule of
+// select_candidates, Sec. 2.4), in registers: candidates ranked by (position,
+// generation order).
+template <typename R>
+__device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int present) {
+  double cy[6];
+  long long key[6];
+  int ord[6], cvr[6], cvl[6];
+  int n = 0;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (s >= 0) {
+      const Cand& C = M.cand[s];
+      cy[q] = C.y;
+      key[q] = okey(C.y);
+      ord[q] = C.ord;
+      cvr[q] = C.vr;
+      cvl[q] = C.vl;
+      n = q + 1;
+      s = M.next[s];
+    } else {
+      cy[q] = 0.0;
+      key[q] = 0;
+      ord[q] = 0;
+      cvr[q] = -1;
+      cvl[q] = -1;
+    }
+  }
+  int rank[6];
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    int r = 0;
+#pragma unroll
+    for (int u = 0; u < 6; ++u)
+      if (u != t && u < n && (key[u] < key[t] || (key[u] == key[t] && ord[u] < ord[t]))) ++r;
+    rank[t] = r;
+  }
+  NewV<R> out;
+  out.present = present;
+  out.vr = -1;
+  out.vl = -1;
+  out.s = R(0.5);
+  out.cancelled = 0;
+  out.invariant = 0;
+  int want = -1;  // rank of the kept candidate
+  if (present && (n & 1)) {
+    want = n / 2;
+  } else if (!present && !(n & 1)) {
+    out.cancelled = n / 2;
+  } else {
+    out.invariant = 1;
+    if (present && n > 0) {  // the candidate nearest the edge's middle, first in rank order
+      double bd = 0.0;
+#pragma unroll
+      for (int t = 0; t < 6; ++t)
+        if (t < n) {
+          const double d = fabs(cy[t] - 0.5);
+          if (want < 0 || d < bd || (d == bd && rank[t] < want)) {
+            bd = d;
+            want = rank[t];
+          }
+        }
+    }
+  }
+  if (want >= 0) {
+    double ysel = 0.0;
+#pragma unroll
+    for (int t = 0; t < 6; ++t)
+      if (t < n && rank[t] == want) {
+        ysel = cy[t];
+        out.vr = cvr[t];
+        out.vl = cvl[t];
+      }
+    out.s = to_fraction<R>(ysel);
+  }
+  return out;
+}
 
 // The tile with origin (i0, j0) of one grid (one block runs it).
 template <typename R, int AX>
@@ -244,31 +381,28 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       (zpl ? M.zb : M.kb)[u] = v;
     }
   } else {
-    // region column lx is stored row ri0 + lx and region row ly stored
-    // column rj0 + ly: a warp reads 32 stored rows and transposes by ballots
-    const int c0 = rj0 >> 5;  // first stored word of the region's rows
+    // region column lx is stored row ri0 + lx and region row ly stored column
+    // rj0 + ly: a warp reads three words of 32 stored rows and transposes them
+    const int c0 = rj0 >> 5;  // stored word holding region rows 0 and 1
     for (int g = warp; g < 2 * kRW; g += kWarps) {
       const int zpl = g >= kRW, gw = zpl ? g - kRW : g;
       const int lx = 32 * gw + lane, yr = ri0 + lx;
       const uint32_t* base = zpl ? G.Z : G.K;
       const int nw = zpl ? G.d.zw : G.d.kw;
-      const bool col_ok = lx >= vx0 && lx <= (zpl ? ex1 : vx1);
       const int row1 = zpl ? ey1 : vy1;
-      uint32_t w0 = 0u, w1 = 0u, w2 = 0u;
-      if (col_ok) {
+      uint32_t w[3] = {0u, 0u, 0u};
+      if (lx >= vx0 && lx <= (zpl ? ex1 : vx1)) {
         const uint32_t* r = base + (long long)yr * nw;
-        if (c0 >= 0 && c0 < nw) w0 = __ldg(&r[c0]);
-        if (c0 + 1 >= 0 && c0 + 1 < nw) w1 = __ldg(&r[c0 + 1]);
-        if (c0 + 2 >= 0 && c0 + 2 < nw) w2 = __ldg(&r[c0 + 2]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          if (c0 + q >= 0 && c0 + q < nw) w[q] = __ldg(&r[c0 + q]);
       }
       uint32_t* dst = zpl ? M.zb : M.kb;
-      for (int ly = 0; ly < kRY; ++ly) {
-        const int xr = rj0 + ly;
-        const int q = (xr >> 5) - c0, b = xr & 31;
-        const uint32_t wq = q == 0 ? w0 : (q == 1 ? w1 : w2);
-        const int bit = (ly >= vy0 && ly <= row1) ? (int)((wq >> b) & 1u) : 0;
-        const uint32_t word = __ballot_sync(0xffffffffu, bit);
-        if (lane == 0) dst[ly * kRW + gw] = word;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const uint32_t col = transpose32(w[q], lane);
+        const int ly = 32 * (c0 + q) + lane - rj0;
+        if (ly >= 0 && ly < kRY) dst[ly * kRW + gw] = (ly >= vy0 && ly <= row1) ? col : 0u;
       }
     }
   }
@@ -293,9 +427,10 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
   const TViewB<R> TV{&M, ri0, rj0, tnx, tny};
 
   if (busy) {
-    for (int t = tid; t < kRB; t += kTileThreads) {
-      push_bits(M.hm[t], t, M.lh, &s_nh);
-      push_bits(M.vm[t], t, M.lv, &s_nv);
+    for (int t0 = warp * 32; t0 < kRB; t0 += kTileThreads) {
+      const int t = t0 + lane;
+      push_bits_warp(t < kRB ? M.hm[t] : 0u, t, M.lh, &s_nh, lane);
+      push_bits_warp(t < kRB ? M.vm[t] : 0u, t, M.lv, &s_nv, lane);
     }
     for (int e = tid; e < kNVE; e += kTileThreads) {
       M.head[e] = -1;
@@ -303,46 +438,57 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     }
     __syncthreads();
 
-    // P2: moved points, corner flips, landing claims
-    const int nh = s_nh, nv = s_nv;
-    for (int w = tid; w < nh; w += kTileThreads) {
-      const int id = M.lh[w], lx = id % kRX, ly = id / kRX;
-      const int x = ri0 + lx, y = rj0 + ly;
-      Flags f;
-      const AP<R> p = G.advect(Mk{0, x, y}, f);
-      M.hix[id] = (int8_t)(p.ix - ri0);
-      M.hfx[id] = p.fx;
-      if (owned(x, y)) {
-        cnt[D_CFL] += f.cfl;
-        cnt[D_WALL_CLAMP] += f.clamp;
-        dmax = fmax(dmax, dabs_of<R>(f));
-      }
-      // a marker moving right passes vertex x+1, one moving left vertex x
-      if (p.ix == x + 1) atomicXor(&M.kn[ly * kRW + ((lx + 1) >> 5)], 1u << ((lx + 1) & 31));
-      else if (p.ix == x - 1) atomicXor(&M.kn[ly * kRW + (lx >> 5)], 1u << (lx & 31));
-      const int dl = p.ix - ri0;
-      if (dl >= 1 && dl <= kRX - 3) {
-        const uint32_t bit = 1u << (dl & 31);
-        if (!(atomicOr(&M.claim[ly * kRW + (dl >> 5)], bit) & bit))
-          M.ld[atomicAdd(&s_nd, 1)] = (uint16_t)(ly * kRX + dl);
-      }
-    }
-    for (int w = tid; w < nv; w += kTileThreads) {
-      const int id = M.lv[w], lx = id % kRX, ly = id / kRX;
-      const int x = ri0 + lx, y = rj0 + ly;
-      Flags f;
-      const AP<R> p = G.advect(Mk{1, x, y}, f);
-      M.vix[id] = (int8_t)(p.ix - ri0);
-      M.vfx[id] = p.fx;
-      M.vfy[id] = p.fy;
-      if (owned(x, y)) {
-        if (x >= 1 && x <= tnx - 1) {
+    // P2: moved points (aligned and unaligned markers in one pass), corner
+    // flips, landing claims
+    const int nh = s_nh, nm = s_nh + s_nv;
+    for (int w0 = warp * 32; w0 < nm; w0 += kTileThreads) {
+      const int w = w0 + lane;
+      int claimed = -1;
+      if (w < nh) {
+        const int id = M.lh[w], lx = id % kRX, ly = id / kRX;
+        const int x = ri0 + lx, y = rj0 + ly;
+        Flags f;
+        const AP<R> p = G.advect(Mk{0, x, y}, f);
+        M.hix[id] = (int8_t)(p.ix - ri0);
+        M.hfx[id] = p.fx;
+        if (owned(x, y)) {
           cnt[D_CFL] += f.cfl;
+          cnt[D_WALL_CLAMP] += f.clamp;
           dmax = fmax(dmax, dabs_of<R>(f));
-        } else {  // a wall marker normal to the sweep stays
-          if (AX) out.sH[(long long)x * P + y] = p.fy;
-          else out.sV[(long long)y * P + x] = p.fy;
         }
+        // a marker moving right passes vertex x+1, one moving left vertex x
+        if (p.ix == x + 1) atomicXor(&M.kn[ly * kRW + ((lx + 1) >> 5)], 1u << ((lx + 1) & 31));
+        else if (p.ix == x - 1) atomicXor(&M.kn[ly * kRW + (lx >> 5)], 1u << (lx & 31));
+        const int dl = p.ix - ri0;
+        if (dl >= 1 && dl <= kRX - 3) {
+          const uint32_t bit = 1u << (dl & 31);
+          if (!(atomicOr(&M.claim[ly * kRW + (dl >> 5)], bit) & bit)) claimed = ly * kRX + dl;
+        }
+      } else if (w < nm) {
+        const int id = M.lv[w - nh], lx = id % kRX, ly = id / kRX;
+        const int x = ri0 + lx, y = rj0 + ly;
+        Flags f;
+        const AP<R> p = G.advect(Mk{1, x, y}, f);
+        M.vix[id] = (int8_t)(p.ix - ri0);
+        M.vfx[id] = p.fx;
+        M.vfy[id] = p.fy;
+        if (owned(x, y)) {
+          if (x >= 1 && x <= tnx - 1) {
+            cnt[D_CFL] += f.cfl;
+            dmax = fmax(dmax, dabs_of<R>(f));
+          } else {  // a wall marker normal to the sweep stays
+            if (AX) out.sH[(long long)x * P + y] = p.fy;
+            else out.sV[(long long)y * P + x] = p.fy;
+          }
+        }
+      }
+      const unsigned cm = __ballot_sync(kFull, claimed >= 0);
+      if (cm) {
+        const int leader = __ffs(cm) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&s_nd, __popc(cm));
+        base = __shfl_sync(kFull, base, leader);
+        if (claimed >= 0) M.ld[base + __popc(cm & ((1u << lane) - 1u))] = (uint16_t)claimed;
       }
     }
     __syncthreads();
@@ -352,19 +498,16 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     for (int w = tid; w < nd; w += kTileThreads) {
       const int id = M.ld[w], dl = id % kRX, ly = id / kRX;
       const int x = ri0 + dl, y = rj0 + ly;
+      bool valid[3];
       R fx[3];
-      int src[3];
-      int n = 0;
-      for (int e = dl - 1; e <= dl + 1; ++e) {
-        if (!getb(M.hm, e, ly)) continue;
-        const int ie = ly * kRX + e;
-        if (M.hix[ie] == dl) {
-          fx[n] = M.hfx[ie];
-          src[n] = ri0 + e;
-          ++n;
-        }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int e = dl - 1 + q, ie = ly * kRX + e;
+        valid[q] = getb(M.hm, e, ly) && M.hix[ie] == dl;
+        fx[q] = valid[q] ? M.hfx[ie] : R(0);
       }
-      const Landing<R> L = choose_landing(n, fx, src, getb(M.kn, dl, ly) ^ getb(M.kn, dl + 1, ly));
+      const Landing<R> L =
+          choose_landing3<R>(valid, fx, x, getb(M.kn, dl, ly) ^ getb(M.kn, dl + 1, ly));
       M.lsrc[id] = L.kept_src < 0 ? kNoSrc : (int8_t)(L.kept_src - x);
       if (owned(x, y)) {
         cnt[D_CANCELLED] += L.cancelled;
@@ -375,7 +518,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         }
       }
     }
-    for (int t = tid; t < kTJ * kRW; t += kTileThreads) {
+    for (int t0 = warp * 32; t0 < kTJ * kRW; t0 += kTileThreads) {
+      const int t = t0 + lane;  // kTJ * kRW is a multiple of 32
       const int ly = 2 + t / kRW, wi = t % kRW, u = ly * kRW + wi;
       // owned aligned edges that gain a marker none landed on (the colour
       // bookkeeping excludes it): counted, fraction 0.5
@@ -393,38 +537,55 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       }
       // interface cells (corner colours not all equal) whose chords can
       // cross a grid line k in [i0, i0+64]: cells k-2..k
+      uint32_t ic = 0u;
       if (ly <= ty1) {
         const uint32_t a = M.kb[u], b = M.kb[u + kRW];
-        const uint32_t ic = ((a ^ shr1(M.kb, ly, wi)) | (b ^ shr1(M.kb, ly + 1, wi)) | (a ^ b)) &
-                            span_mask(wi, max(2, vx0), min(kTI + 4, ex1));
-        push_bits(ic, u, M.lh, &s_nc);
+        ic = ((a ^ shr1(M.kb, ly, wi)) | (b ^ shr1(M.kb, ly + 1, wi)) | (a ^ b)) &
+             span_mask(wi, max(2, vx0), min(kTI + 4, ex1));
       }
+      push_bits_warp(ic, u, M.lh, &s_nc, lane);
     }
     __syncthreads();
 
-    // P4: candidates
+    // P4: candidates.  A thread takes one interface cell: counts the grid
+    // lines its moved chords cross, takes that many slots, then fills them.
     const int nc = s_nc;
     const int kmin = max(1, i0), kmax = min(tnx - 1, i0 + kTI);
-    for (int w = tid; w < nc; w += kTileThreads) {
-      const int id = M.lh[w], lx = id % kRX, ly = id / kRX;
-      const int c = ri0 + lx, j = rj0 + ly;
-      int seg[2][2];
-      const int ns = cell_segments(TV, c, j, seg);
-      for (int t = 0; t < ns; ++t) {
+    for (int w0 = warp * 32; w0 < nc; w0 += kTileThreads) {
+      const int w = w0 + lane;
+      int c = 0, j = 0, ly = 0, ns = 0, ncross = 0;
+      int seg[2][2] = {{0, 0}, {0, 0}};
+      int ia[2] = {0, 0}, ib[2] = {0, 0};
+      if (w < nc) {
+        const int id = M.lh[w], lx = id % kRX;
+        ly = id / kRX;
+        c = ri0 + lx;
+        j = rj0 + ly;
+        ns = cell_segments(TV, c, j, seg);
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+          if (t < ns) {
+            ia[t] = TV.moved(edge_marker(c, j, seg[t][0])).ix;
+            ib[t] = TV.moved(edge_marker(c, j, seg[t][1])).ix;
+            ncross += max(0, min(max(ia[t], ib[t]), kmax) - max(min(ia[t], ib[t]) + 1, kmin) + 1);
+          }
+      }
+      int slot = warp_alloc(ncross, &s_ncand, lane);
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        if (t >= ns) continue;
         const Mk ma = edge_marker(c, j, seg[t][0]);
         const Mk mb = edge_marker(c, j, seg[t][1]);
-        const int ia = TV.moved(ma).ix, ib = TV.moved(mb).ix;
-        const int klo = max(min(ia, ib) + 1, kmin), khi = min(max(ia, ib), kmax);
-        for (int k = klo; k <= khi; ++k) {
+        const int klo = max(min(ia[t], ib[t]) + 1, kmin), khi = min(max(ia[t], ib[t]), kmax);
+        for (int k = klo; k <= khi; ++k, ++slot) {
           const int e = (j - j0) * (kTI + 1) + (k - i0);
           const int ex = k - ri0, eu = ly * kRW + (ex >> 5);
           const uint32_t ebit = 1u << (ex & 31);
-          const int slot = atomicAdd(&s_ncand, 1);
           if (slot >= kCandCap) {
             atomicOr(&M.ovf[eu], ebit);
             continue;
           }
-          const bool a_left = ia < k;
+          const bool a_left = ia[t] < k;
           const Mk mA = a_left ? ma : mb, mB = a_left ? mb : ma;
           Cand& C = M.cand[slot];
           C.a = TV.ref(mA);
@@ -461,49 +622,90 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
           C.vr = (int8_t)(lr < 0 ? -1 : !TV.knew(k, lr));
           C.vl = (int8_t)(ll < 0 ? -1 : !TV.knew(k, ll));
           M.next[slot] = (int16_t)atomicExch(&M.head[e], slot);
-          if (!(atomicOr(&M.hc[eu], ebit) & ebit)) M.le[atomicAdd(&s_ne, 1)] = (uint16_t)e;
+          atomicOr(&M.hc[eu], ebit);
         }
       }
     }
     __syncthreads();
 
-    // P5: circle fits, one candidate per thread
+    // P5: circle fits (Sec. 2.2).  Lanes 2m and 2m+1 fit the circles through
+    // point 1 and point 4 of one candidate and the even lane combines them,
+    // as fit_crossing does; the warps that take candidates rotate with the
+    // block so that the FP64 work spreads over the SM's sub-partitions.  The
+    // last three warps first list the edges with linked candidates.
     const int ncand = min(s_ncand, kCandCap);
-    for (int ci = tid; ci < ncand; ci += kTileThreads) {
-      Cand& C = M.cand[ci];
-      const int k = i0 + C.edge % (kTI + 1), j = j0 + C.edge / (kTI + 1);
-      if (getb(M.ovf, k - ri0, j - rj0)) continue;  // the edge is done in place
-      double ax, ay, bx, by, p1x = 0.0, p1y = 0.0, p4x = 0.0, p4y = 0.0;
-      TV.xy(C.a, k, j, &ax, &ay);
-      TV.xy(C.b, k, j, &bx, &by);
-      bool h1 = false, h4 = false;
-      if (C.fl & CF_P1) {
-        TV.xy(C.p1, k, j, &p1x, &p1y);
-        h1 = true;
-        const double ex = p1x - ax, ey = p1y - ay;
-        if (ex * ex + ey * ey < kMinSep2) {
-          if (C.fl & CF_Q1) TV.xy(C.q1, k, j, &p1x, &p1y);
-          else h1 = false;
+    if (warp >= kWarps - 3) {
+      const int t = (warp - (kWarps - 3)) * 32 + lane;  // kTJ * kRW = 96 words
+      const int u = (2 + t / kRW) * kRW + t % kRW;
+      push_bits_warp(M.hc[u], u, M.le, &s_ne, lane);
+    }
+    const int rot = (int)((blockIdx.x + blockIdx.y) & 3u);
+    const int vt = (((warp + rot) & (kWarps - 1)) << 5) | lane;
+    for (int b0 = 0; b0 < 2 * ncand; b0 += kTileThreads) {
+      const int item = b0 + vt, side = item & 1;
+      Cand& C = M.cand[min(item >> 1, kCandCap - 1)];
+      int k = 0, j = 0;
+      bool act = item < 2 * ncand;
+      if (act) {
+        k = i0 + C.edge % (kTI + 1);
+        j = j0 + C.edge / (kTI + 1);
+        act = !getb(M.ovf, k - ri0, j - rj0);  // else the edge is done in place
+      }
+      double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0, cx = 1.0, cy = 0.0, x0 = 0.0, ys = 0.0;
+      bool online = false, ok = false;
+      if (act) {
+        TV.xy(C.a, k, j, &ax, &ay);
+        TV.xy(C.b, k, j, &bx, &by);
+        online = d_eq0(bx);
+        if (!online) {
+          cx = bx - ax;
+          cy = by - ay;
+          x0 = -ax;
+          const double c2 = cx * cx + cy * cy;
+          const uint8_t fl = C.fl;
+          if (!line_only && !d_below_sep(c2) && (fl & (side ? CF_P4 : CF_P1))) {
+            double X, Y;
+            TV.xy(side ? C.p4 : C.p1, k, j, &X, &Y);
+            FitPt T = fit_pt(X, Y, ax, ay, bx, by);
+            bool use = true;
+            if (d_below_sep(side ? T.t2 : T.r2)) {  // too close to A (B): the next marker
+              if (fl & (side ? CF_Q4 : CF_Q1)) {
+                TV.xy(side ? C.q4 : C.q1, k, j, &X, &Y);
+                T = fit_pt(X, Y, ax, ay, bx, by);
+              } else {
+                use = false;
+              }
+            }
+            if (use) ok = circle_cross(ay, x0, cx, cy, c2, T, &ys);
+          }
         }
       }
-      if (C.fl & CF_P4) {
-        TV.xy(C.p4, k, j, &p4x, &p4y);
-        h4 = true;
-        const double ex = p4x - bx, ey = p4y - by;
-        if (ex * ex + ey * ey < kMinSep2) {
-          if (C.fl & CF_Q4) TV.xy(C.q4, k, j, &p4x, &p4y);
-          else h4 = false;
+      const double yo = __shfl_xor_sync(kFull, ys, 1);
+      const bool oko = __shfl_xor_sync(kFull, (int)ok, 1) != 0;
+      if (act && side == 0) {
+        double y;
+        int kind;
+        if (online) {
+          y = by;
+          kind = D_FIT_ONLINE;
+        } else if (ok && oko) {
+          y = 0.5 * (ys + yo);
+          kind = D_FIT_TWO;
+        } else if (ok || oko) {
+          y = ok ? ys : yo;
+          kind = D_FIT_ONE;
+        } else {  // no circle: the chord's own crossing
+          y = ay + (x0 * cy) / cx;
+          kind = D_FIT_LINE;
         }
-      }
-      double y;
-      const int kind = fit_crossing(ax, ay, bx, by, h1, p1x, p1y, h4, p4x, p4y, line_only != 0, &y);
-      C.y = y;
-      C.kind = (int8_t)kind;
-      if (C.fl & CF_OWNED) {  // static indices keep the counters in registers
-        cnt[D_FIT_ONLINE] += kind == D_FIT_ONLINE;
-        cnt[D_FIT_LINE] += kind == D_FIT_LINE;
-        cnt[D_FIT_ONE] += kind == D_FIT_ONE;
-        cnt[D_FIT_TWO] += kind == D_FIT_TWO;
+        C.y = y;
+        C.kind = (int8_t)kind;
+        if (C.fl & CF_OWNED) {  // static indices keep the counters in registers
+          cnt[D_FIT_ONLINE] += kind == D_FIT_ONLINE;
+          cnt[D_FIT_LINE] += kind == D_FIT_LINE;
+          cnt[D_FIT_ONE] += kind == D_FIT_ONE;
+          cnt[D_FIT_TWO] += kind == D_FIT_TWO;
+        }
       }
     }
     __syncthreads();
@@ -511,23 +713,13 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     // P6: one marker per unaligned edge (Sec. 2.4)
     const int ne = s_ne;
     for (int w = tid; w < ne; w += kTileThreads) {
-      const int e = M.le[w];
-      const int k = i0 + e % (kTI + 1), j = j0 + e / (kTI + 1);
-      const int ex = k - ri0, ey = j - rj0;
+      const int id = M.le[w], ex = id % kRX, ey = id / kRX;
       if (getb(M.ovf, ex, ey)) continue;
-      double cy[6];
-      int cvr[6], cvl[6], ord[6];
-      int n = 0;
-      for (int s = M.head[e]; s >= 0 && n < 6; s = M.next[s]) {
-        cy[n] = M.cand[s].y;
-        cvr[n] = M.cand[s].vr;
-        cvl[n] = M.cand[s].vl;
-        ord[n] = M.cand[s].ord;
-        ++n;
-      }
+      const int k = ri0 + ex, j = rj0 + ey;
+      const int e = (j - j0) * (kTI + 1) + (k - i0);
       const bool own = k < i0 + kTI;
       const int present = getb(M.kn, ex, ey) ^ getb(M.kn, ex, ey + 1);
-      const NewV<R> nv = select_candidates<R>(n, cy, cvr, cvl, ord, present);
+      const NewV<R> nv = select_linked<R>(M, M.head[e], present);
       if (own) {
         cnt[D_CANCELLED] += nv.cancelled;
         cnt[D_INVARIANT] += nv.invariant;
@@ -577,55 +769,60 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     __syncthreads();
   }
 
-  // P7: colour words (one warp per word, one lane per bit)
-  for (int w = warp; w < 64; w += kWarps) {
-    // sweep coordinates of this lane's vertex / cell, and the stored word
-    int i, j, row, word;
-    if (AX) {
-      i = i0 + w;
-      j = j0 + lane;
-      row = i;
-      word = j0 >> 5;
-    } else {
-      i = i0 + 32 * (w & 1) + lane;
-      j = j0 + (w >> 1);
-      row = j;
-      word = (i0 >> 5) + (w & 1);
-    }
-    const int lx = i - ri0, ly = j - rj0;
-    const bool vin = i <= tnx && j <= tny;
-    const unsigned kw = __ballot_sync(0xffffffffu, vin && getb(M.kn, lx, ly));
-    if (lane == 0 && row <= G.d.ny && word < G.d.kw) out.K[(long long)row * G.d.kw + word] = kw;
-    int zc = 0;
-    const bool cin = i < tnx && j < tny;
-    if (cin) {
-      zc = getb(M.zb, lx, ly);
-      if (busy) {
-        const int q = getb(M.kn, lx, ly) | (getb(M.kn, lx + 1, ly) << 1) |
-                      (getb(M.kn, lx + 1, ly + 1) << 2) | (getb(M.kn, lx, ly + 1) << 3);
-        if (q == 5 || q == 10) {
-          const int e = (j - j0) * (kTI + 1) + (i - i0);
-          const int a = (i >= 1) ? verdict_r(M.vrl[e]) : -1;
-          const int b = (i + 1 <= tnx - 1) ? verdict_l(M.vrl[e + 1]) : -1;
-          if (a >= 0) {
-            zc = a;
-            cnt[D_ZSET] += 1;
-            if (b >= 0 && b != a) cnt[D_ZCONFLICT] += 1;
-          } else if (b >= 0) {
-            zc = b;
-            cnt[D_ZSET] += 1;
-          }
+  // P7: colour words.  Lane L of warp ow (0 or 1) takes tile row j0 + L and
+  // the 32 vertices / cells i0 + 32 ow + b; the y sweep transposes them into
+  // stored rows.  Centre colours of new four-marker cells (all four edges
+  // with a marker) come from the verdicts of edges i (right) and i+1 (left);
+  // the right one wins.
+  if (warp < 2) {
+    const int ow = warp, ly = 2 + lane, cx0 = 4 + 32 * ow;
+    const int j = rj0 + ly;
+    uint32_t kw = bits32(M.kn, ly, cx0);
+    uint32_t zw = bits32(M.zb, ly, cx0);
+    const uint32_t vmask = ly <= vy1 ? upto32(cx0, vx1) : 0u;
+    const uint32_t cmask = ly <= ey1 ? upto32(cx0, ex1) : 0u;
+    if (busy && cmask) {
+      const uint32_t a1 = bits32(M.kn, ly, cx0 + 1);
+      const uint32_t b0 = bits32(M.kn, ly + 1, cx0), b1 = bits32(M.kn, ly + 1, cx0 + 1);
+      uint32_t fm = (kw ^ a1) & (b0 ^ b1) & (kw ^ b0) & cmask;
+      while (fm) {
+        const int b = __ffs(fm) - 1;
+        fm &= fm - 1;
+        const int i = i0 + 32 * ow + b;
+        const int e = (j - j0) * (kTI + 1) + (i - i0);
+        const int a = (i >= 1) ? verdict_r(M.vrl[e]) : -1;
+        const int bl = (i + 1 <= tnx - 1) ? verdict_l(M.vrl[e + 1]) : -1;
+        int zc = -1;
+        if (a >= 0) {
+          zc = a;
+          cnt[D_ZSET] += 1;
+          if (bl >= 0 && bl != a) cnt[D_ZCONFLICT] += 1;
+        } else if (bl >= 0) {
+          zc = bl;
+          cnt[D_ZSET] += 1;
         }
+        if (zc >= 0) zw = zc ? (zw | (1u << b)) : (zw & ~(1u << b));
       }
     }
-    const unsigned zw = __ballot_sync(0xffffffffu, cin && zc);
-    if (lane == 0 && row < G.d.ny && word < G.d.zw) out.Z[(long long)row * G.d.zw + word] = zw;
+    kw &= vmask;
+    zw &= cmask;
+    if (AX) {
+      kw = transpose32(kw, lane);
+      zw = transpose32(zw, lane);
+      const int row = i0 + 32 * ow + lane, word = j0 >> 5;
+      if (row <= G.d.ny && word < G.d.kw) out.K[(long long)row * G.d.kw + word] = kw;
+      if (row < G.d.ny && word < G.d.zw) out.Z[(long long)row * G.d.zw + word] = zw;
+    } else {
+      const int word = (i0 >> 5) + ow;
+      if (j <= G.d.ny && word < G.d.kw) out.K[(long long)j * G.d.kw + word] = kw;
+      if (j < G.d.ny && word < G.d.zw) out.Z[(long long)j * G.d.zw + word] = zw;
+    }
   }
 
   // block-level counters
 #pragma unroll
   for (int c = 0; c < D_NUSED; ++c) {
-    const int s = __reduce_add_sync(0xffffffffu, cnt[c]);
+    const int s = __reduce_add_sync(kFull, cnt[c]);
     if (s != 0 && lane == 0) atomicAdd(&s_cnt[c], s);
   }
   if (dmax > R(0)) atomicMax(&s_dmax, (unsigned long long)__double_as_longlong((double)dmax));
