@@ -91,6 +91,23 @@ struct Landing {
   R kept_fx;
 };
 
+// Bits [a, b] (inclusive, columns of a row of 32-bit words) within word wi;
+// empty if a > b.
+__device__ __forceinline__ uint32_t span_mask(int wi, int a, int b) {
+  const int lo = max(a - 32 * wi, 0), hi = min(b - 32 * wi, 31);
+  if (lo > hi) return 0u;
+  const uint32_t up = hi == 31 ? 0xffffffffu : ((1u << (hi + 1)) - 1u);
+  return up & ~((1u << lo) - 1u);
+}
+
+// Bits x0 .. x0+31 of a stored row of nw words (bits outside the row read 0).
+__device__ __forceinline__ uint32_t row_bits(const uint32_t* __restrict__ row, int nw, int x0) {
+  const int q = x0 >> 5, r = x0 & 31;
+  const uint32_t a = (q >= 0 && q < nw) ? __ldg(&row[q]) : 0u;
+  const uint32_t b = (q + 1 >= 0 && q + 1 < nw) ? __ldg(&row[q + 1]) : 0u;
+  return r ? ((a >> r) | (b << (32 - r))) : a;
+}
+
 // ---------------------------------------------------------------------------
 // Cell topology.  Corner c of cell (i,j) counter-clockwise from (i,j); edge e
 // joins corners e and e+1 (0 bottom, 1 right, 2 top, 3 left).

@@ -1,26 +1,25 @@
 // Fused fields kernel: volume fractions C, height-function curvature kappa,
 // the area partial sums and the marker counts of a state (Sec. 2.5), one
-// 64x32 tile of cells per block with a 3-cell halo of fractions in shared
-// memory for the 7x3 height stencils.
+// 64x32 tile of cells per block with a 3-cell halo for the 7x3 height
+// stencils.
 //
-// FP64 work is confined to interface cells: a full or empty cell has C equal
-// to its corner colour exactly, so full cells are counted as integers and only
-// interface fractions enter the double partial sums (in a fixed order per
-// thread, then fixed shuffle and block orders), which keeps the sums
-// deterministic.
+// Colours are read as bit rows; full, empty and interface cells are word
+// operations on them.  FP64 work is confined to interface cells: a full or
+// empty cell has C equal to its corner colour exactly, so full cells are
+// counted as integers and only interface fractions enter the double partial
+// sums.  The interface cells are listed in region order (a deterministic scan)
+// and each thread sums its list entries in order, then fixed shuffle and block
+// orders, which keeps the sums deterministic.
 #pragma once
 #include "ebit_device.cuh"
 
 namespace ebit {
 
 constexpr int kFX = 64, kFY = 32, kFH = 3;
-constexpr int kFRX = kFX + 2 * kFH, kFRY = kFY + 2 * kFH;  // region cells
-constexpr int kFVX = kFRX + 1, kFVY = kFRY + 1;            // region vertices
+constexpr int kFRX = kFX + 2 * kFH, kFRY = kFY + 2 * kFH;  // region cells (70 x 38)
+constexpr int kFVX = kFRX + 1, kFVY = kFRY + 1;            // region vertices (71 x 39)
+constexpr int kFW = 3;                                     // words per region bit row
 constexpr int kFieldThreads = 256;
-
-__device__ __forceinline__ int kbit_of(const uint32_t* K, const Dims& d, int x, int y) {
-  return (__ldg(&K[(long long)y * d.kw + (x >> 5)]) >> (x & 31)) & 1;
-}
 
 // Reference-phase area of cell (i,j) in cell units from its corner mask q,
 // centre colour and marker fractions; double arithmetic.
@@ -62,6 +61,24 @@ __device__ double fraction_of(int q, int zc, const R* __restrict__ sH, const R* 
   return zc == 0 ? Tsum : 1.0 - Tsum;
 }
 
+__device__ __forceinline__ int fgetb(const uint32_t* w, int lx, int ly) {
+  return (w[ly * kFW + (lx >> 5)] >> (lx & 31)) & 1;
+}
+__device__ __forceinline__ uint32_t fshr1(const uint32_t* w, int ly, int wi) {
+  uint32_t v = w[ly * kFW + wi] >> 1;
+  if (wi + 1 < kFW) v |= w[ly * kFW + wi + 1] << 31;
+  return v;
+}
+
+// Dense stores of four consecutive values of a row (16-byte aligned for float).
+__device__ __forceinline__ void store4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void store4(double* p, double a, double b, double c, double d) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+
 // The tile (bx, by) of one grid; its area partial goes to partial[slot].
 template <typename R>
 __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
@@ -69,149 +86,198 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
                                             const R* __restrict__ sH, const R* __restrict__ sV,
                                             const Dims& d, R dx, R* C, R* kappa, double* partial,
                                             long long slot, unsigned long long* ctr, int bx, int by) {
-  __shared__ uint8_t kb[kFVY * kFVX];
-  __shared__ uint8_t zb[kFRY * kFRX];
-  __shared__ R cs[kFRY * kFRX];
-  __shared__ uint16_t lst[kFRY * kFRX];  // interface cells of the region, in region order
+  __shared__ uint32_t kw[kFVY * kFW];  // vertex colours
+  __shared__ uint32_t zw[kFRY * kFW];  // centre colours
+  __shared__ uint32_t fw[kFRY * kFW];  // full cells
+  __shared__ uint32_t iw[kFRY * kFW];  // interface cells
+  __shared__ R cs[kFRY * kFRX];        // fractions of the region
+  __shared__ uint16_t lst[kFRY * kFRX];
+  __shared__ int s_woff[kFieldThreads / 32];
   __shared__ double s_wsum[kFieldThreads / 32];
-  __shared__ int s_wcnt[kFieldThreads / 32];
   __shared__ int s_cnt[D_NUSED];
-  __shared__ int s_nlist;
   __shared__ unsigned long long s_full;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i0 = bx * kFX, j0 = by * kFY;
   const int rx0 = i0 - kFH, ry0 = j0 - kFH;
   if (tid < D_NUSED) s_cnt[tid] = 0;
-  if (tid == 0) {
-    s_full = 0ull;
-    s_nlist = 0;
-  }
-  for (int t = tid; t < kFVX * kFVY; t += kFieldThreads) {
-    const int x = rx0 + t % kFVX, y = ry0 + t / kFVX;
-    kb[t] = (x >= 0 && x <= d.nx && y >= 0 && y <= d.ny) ? (uint8_t)kbit_of(K, d, x, y) : 0;
-  }
-  for (int t = tid; t < kFRX * kFRY; t += kFieldThreads) {
-    const int x = rx0 + t % kFRX, y = ry0 + t / kFRX;
-    zb[t] = (x >= 0 && x < d.nx && y >= 0 && y < d.ny)
-                ? (uint8_t)((__ldg(&Z[(long long)y * d.zw + (x >> 5)]) >> (x & 31)) & 1)
-                : 0;
+  if (tid == 0) s_full = 0ull;
+  // region columns / rows inside the grid
+  const int vx0 = max(0, -rx0), vx1 = min(kFVX - 1, d.nx - rx0);  // vertices
+  const int cx1 = min(kFRX - 1, d.nx - 1 - rx0);                  // cells
+  const int vy0 = max(0, -ry0), vy1 = min(kFVY - 1, d.ny - ry0);
+  const int cy1 = min(kFRY - 1, d.ny - 1 - ry0);
+  int cnt[D_NUSED];
+#pragma unroll
+  for (int c = 0; c < D_NUSED; ++c) cnt[c] = 0;
+
+  // colour bits
+  for (int t = tid; t < (kFVY + kFRY) * kFW; t += kFieldThreads) {
+    const bool zpl = t >= kFVY * kFW;
+    const int u = zpl ? t - kFVY * kFW : t;
+    const int ly = u / kFW, wi = u % kFW, y = ry0 + ly, x0 = rx0 + 32 * wi;
+    uint32_t v = 0u;
+    if (!zpl && ly >= vy0 && ly <= vy1)
+      v = row_bits(K + (long long)y * d.kw, d.kw, x0) & span_mask(wi, vx0, vx1);
+    if (zpl && ly >= vy0 && ly <= cy1)
+      v = row_bits(Z + (long long)y * d.zw, d.zw, x0) & span_mask(wi, vx0, cx1);
+    (zpl ? zw : kw)[u] = v;
   }
   __syncthreads();
-  auto qmask = [&](int lx, int ly) {
-    const int v = ly * kFVX + lx;
-    return kb[v] | (kb[v + 1] << 1) | (kb[v + kFVX + 1] << 2) | (kb[v + kFVX] << 3);
-  };
-  // fractions: full and empty cells directly; interface cells go to a list
-  // built in region order (ballot prefix sums), so that their FP64 work runs
-  // on full warps and the area sum has a fixed order
+
+  // full / interface cells; the tile's full cells and markers are counted
   int full = 0;
-  for (int base = 0; base < kFRX * kFRY; base += kFieldThreads) {
-    const int t = base + tid;
-    bool iface = false;
-    if (t < kFRX * kFRY) {
-      const int lx = t % kFRX, ly = t / kFRX;
-      const int x = rx0 + lx, y = ry0 + ly;
-      R c = R(0);
-      if (x >= 0 && x < d.nx && y >= 0 && y < d.ny) {
-        const int q = qmask(lx, ly);
-        if (q == 15) {
-          c = R(1);
-          full += lx >= kFH && lx < kFH + kFX && ly >= kFH && ly < kFH + kFY;
-        } else if (q != 0) {
-          iface = true;
-        }
+  for (int t = tid; t < kFRY * kFW; t += kFieldThreads) {
+    const int ly = t / kFW, wi = t % kFW;
+    uint32_t f = 0u, ic = 0u;
+    if (ly >= vy0 && ly <= cy1) {
+      const uint32_t a = kw[t], a1 = fshr1(kw, ly, wi), b = kw[t + kFW], b1 = fshr1(kw, ly + 1, wi);
+      const uint32_t cm = span_mask(wi, vx0, cx1);
+      f = a & a1 & b & b1 & cm;
+      ic = (a | a1 | b | b1) & ~f & cm;
+    }
+    fw[t] = f;
+    iw[t] = ic;
+    if (ly >= kFH && ly < kFH + kFY) {
+      const uint32_t tile = span_mask(wi, kFH, kFH + kFX - 1);
+      full += __popc(f & tile);
+      // markers on the tile's vertices' right and upper edges
+      if (ly <= vy1) {
+        const uint32_t a = kw[t];
+        cnt[D_NH] += __popc((a ^ fshr1(kw, ly, wi)) & tile & span_mask(wi, vx0, cx1));
+        if (ly + 1 <= vy1) cnt[D_NV] += __popc((a ^ kw[t + kFW]) & tile & span_mask(wi, vx0, vx1));
       }
-      cs[t] = c;
     }
-    const unsigned b = __ballot_sync(0xffffffffu, iface);
-    if (lane == 0) s_wcnt[warp] = __popc(b);
-    __syncthreads();
-    int off = s_nlist;
-    for (int w = 0; w < warp; ++w) off += s_wcnt[w];
-    if (iface) lst[off + __popc(b & ((1u << lane) - 1u))] = (uint16_t)t;
-    __syncthreads();
-    if (tid == 0) {
-      int tot = 0;
-      for (int w = 0; w < kFieldThreads / 32; ++w) tot += s_wcnt[w];
-      s_nlist += tot;
-    }
-    __syncthreads();
   }
-  const int nlist = s_nlist;
+  __syncthreads();
+
+  // interface list in region order: per-warp scans of the word counts
+  constexpr int kWords = kFRY * kFW;  // 114
+  int pos = 0, n = 0;
+  uint32_t mybits = 0u;
+  if (warp < (kWords + 31) / 32) {
+    const int t = warp * 32 + lane;
+    mybits = t < kWords ? iw[t] : 0u;
+    n = __popc(mybits);
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    pos = incl - n;
+    if (lane == 31) s_woff[warp] = incl;
+  }
+  // fractions of full and empty cells
+  for (int t = tid; t < kFRY * kFRX; t += kFieldThreads) {
+    const int lx = t % kFRX, ly = t / kFRX;
+    if (!fgetb(iw, lx, ly)) cs[t] = fgetb(fw, lx, ly) ? R(1) : R(0);
+  }
+  __syncthreads();
+  if (warp < (kWords + 31) / 32) {
+    for (int w = 0; w < warp; ++w) pos += s_woff[w];
+    const int t = warp * 32 + lane;
+    const int row0 = (t / kFW) * kFRX + 32 * (t % kFW);
+    while (mybits) {
+      const int b = __ffs(mybits) - 1;
+      mybits &= mybits - 1;
+      lst[pos++] = (uint16_t)(row0 + b);
+    }
+  }
+  int nlist = 0;
+#pragma unroll
+  for (int w = 0; w < (kWords + 31) / 32; ++w) nlist += s_woff[w];
+  __syncthreads();
+
+  // interface fractions (FP64 on full warps) and the tile's area
   double acc = 0.0;
   for (int e = tid; e < nlist; e += kFieldThreads) {
     const int t = lst[e];
     const int lx = t % kFRX, ly = t / kFRX;
-    const double f = fraction_of(qmask(lx, ly), zb[t], sH, sV, d, rx0 + lx, ry0 + ly);
+    const int q = fgetb(kw, lx, ly) | (fgetb(kw, lx + 1, ly) << 1) |
+                  (fgetb(kw, lx + 1, ly + 1) << 2) | (fgetb(kw, lx, ly + 1) << 3);
+    const double f = fraction_of(q, fgetb(zw, lx, ly), sH, sV, d, rx0 + lx, ry0 + ly);
     cs[t] = (R)f;
     if (lx >= kFH && lx < kFH + kFX && ly >= kFH && ly < kFH + kFY) acc = acc + f;
   }
   __syncthreads();
-  int cnt[D_NUSED];
-#pragma unroll
-  for (int c = 0; c < D_NUSED; ++c) cnt[c] = 0;
-  // dense pass: C, marker counts, kappa = NaN away from the interface
-  for (int t = tid; t < kFX * kFY; t += kFieldThreads) {
-    const int i = i0 + t % kFX, j = j0 + t / kFX;
-    if (i > d.nx || j > d.ny) continue;
-    const int lx = t % kFX + kFH, ly = t / kFX + kFH;
-    const int v = ly * kFVX + lx;
-    if (i < d.nx) cnt[D_NH] += kb[v] != kb[v + 1];
-    if (j < d.ny) cnt[D_NV] += kb[v] != kb[v + kFVX];
-    if (i >= d.nx || j >= d.ny) continue;
-    const int ci = ly * kFRX + lx;
-    C[(long long)j * d.P + i] = cs[ci];
-    const int q = qmask(lx, ly);
-    if (q == 0 || q == 15) kappa[(long long)j * d.P + i] = R(NAN);
-  }
-  // height-function curvature of the tile's interface cells, from the list
+
+  // height-function curvature of the tile's interface cells
   for (int e = tid; e < nlist; e += kFieldThreads) {
     const int ci = lst[e];
     const int lx = ci % kFRX, ly = ci / kFRX;
     if (lx < kFH || lx >= kFH + kFX || ly < kFH || ly >= kFH + kFY) continue;
     const int i = rx0 + lx, j = ry0 + ly;
-    const int q = qmask(lx, ly);
+    const int q = fgetb(kw, lx, ly) | (fgetb(kw, lx + 1, ly) << 1) |
+                  (fgetb(kw, lx + 1, ly + 1) << 2) | (fgetb(kw, lx, ly + 1) << 3);
     R out = R(NAN);
-    {
-      int seg[2][2];
-      const int ns = segments(q, edge_mask(q) == 15 ? zb[ci] : 0, seg);
-      const R px[4] = {__ldg(&sH[(long long)j * d.P + i]), R(1), __ldg(&sH[(long long)(j + 1) * d.P + i]), R(0)};
-      const R py[4] = {R(0), __ldg(&sV[(long long)j * d.P + i + 1]), R(1), __ldg(&sV[(long long)j * d.P + i])};
-      R ax = R(0), ay = R(0);
-      for (int s = 0; s < ns; ++s) {
-        const int a = seg[s][0], b = seg[s][1];
-        ax = ax + fabs(px[b] - px[a]);
-        ay = ay + fabs(py[b] - py[a]);
+    int seg[2][2];
+    const int ns = segments(q, edge_mask(q) == 15 ? fgetb(zw, lx, ly) : 0, seg);
+    const R px[4] = {__ldg(&sH[(long long)j * d.P + i]), R(1), __ldg(&sH[(long long)(j + 1) * d.P + i]), R(0)};
+    const R py[4] = {R(0), __ldg(&sV[(long long)j * d.P + i + 1]), R(1), __ldg(&sV[(long long)j * d.P + i])};
+    R ax = R(0), ay = R(0);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      if (s >= ns) break;
+      const int a = seg[s][0], b = seg[s][1];
+      ax = ax + fabs(px[b] - px[a]);
+      ay = ay + fabs(py[b] - py[a]);
+    }
+    const bool ycol = ax >= ay;
+    const bool inside = ycol ? (i - 1 >= 0 && i + 1 <= d.nx - 1 && j - 3 >= 0 && j + 3 <= d.ny - 1)
+                             : (j - 1 >= 0 && j + 1 <= d.ny - 1 && i - 3 >= 0 && i + 3 <= d.nx - 1);
+    bool valid = inside;
+    R h[3];
+    if (inside) {
+      int orient[3];
+#pragma unroll
+      for (int m = -1; m <= 1; ++m) {
+        R a = R(0);
+#pragma unroll
+        for (int s = -3; s <= 3; ++s)
+          a = a + (ycol ? cs[(ly + s) * kFRX + lx + m] : cs[(ly + m) * kFRX + lx + s]);
+        h[m + 1] = a;
+        const R lo = ycol ? cs[(ly - 3) * kFRX + lx + m] : cs[(ly + m) * kFRX + lx - 3];
+        const R hi = ycol ? cs[(ly + 3) * kFRX + lx + m] : cs[(ly + m) * kFRX + lx + 3];
+        orient[m + 1] = (lo == R(1) && hi == R(0)) ? 1 : (lo == R(0) && hi == R(1)) ? -1 : 0;
       }
-      const bool ycol = ax >= ay;
-      const bool inside = ycol ? (i - 1 >= 0 && i + 1 <= d.nx - 1 && j - 3 >= 0 && j + 3 <= d.ny - 1)
-                               : (j - 1 >= 0 && j + 1 <= d.ny - 1 && i - 3 >= 0 && i + 3 <= d.nx - 1);
-      bool valid = inside;
-      R h[3];
-      if (inside) {
-        int orient[3];
-        for (int m = -1; m <= 1; ++m) {
-          R a = R(0);
-          for (int s = -3; s <= 3; ++s)
-            a = a + (ycol ? cs[(ly + s) * kFRX + lx + m] : cs[(ly + m) * kFRX + lx + s]);
-          h[m + 1] = a;
-          const R lo = ycol ? cs[(ly - 3) * kFRX + lx + m] : cs[(ly + m) * kFRX + lx - 3];
-          const R hi = ycol ? cs[(ly + 3) * kFRX + lx + m] : cs[(ly + m) * kFRX + lx + 3];
-          orient[m + 1] = (lo == R(1) && hi == R(0)) ? 1 : (lo == R(0) && hi == R(1)) ? -1 : 0;
-        }
-        valid = orient[0] != 0 && orient[0] == orient[1] && orient[1] == orient[2];
-      }
-      if (valid) {
-        const R hp = (h[2] - h[0]) * R(0.5);
-        const R hpp = (h[2] - h[1]) - (h[1] - h[0]);
-        const R qv = R(1) + hp * hp;
-        const R den = dx * (qv * sqrt(qv));
-        out = -hpp / den;
-      } else {
-        cnt[D_HF_INVALID] += 1;
-      }
+      valid = orient[0] != 0 && orient[0] == orient[1] && orient[1] == orient[2];
+    }
+    if (valid) {
+      const R hp = (h[2] - h[0]) * R(0.5);
+      const R hpp = (h[2] - h[1]) - (h[1] - h[0]);
+      const R qv = R(1) + hp * hp;
+      const R den = dx * (qv * sqrt(qv));
+      out = -hpp / den;
+    } else {
+      cnt[D_HF_INVALID] += 1;
     }
     kappa[(long long)j * d.P + i] = out;
+  }
+  // dense outputs: C everywhere, kappa = NaN away from the interface (the
+  // interface cells' kappa is written above)
+  const bool vec = ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(kappa)) & 15) == 0;
+  for (int g = tid; g < kFX * kFY / 4; g += kFieldThreads) {
+    const int lx0 = (g % (kFX / 4)) * 4, ly0 = g / (kFX / 4);
+    const int i = i0 + lx0, j = j0 + ly0;
+    if (j >= d.ny || i >= d.nx) continue;
+    const int lx = lx0 + kFH, ly = ly0 + kFH;
+    const R* c = &cs[ly * kFRX + lx];
+    const uint32_t ib = (iw[ly * kFW + (lx >> 5)] >> (lx & 31)) |
+                        ((lx & 31) > 28 ? iw[ly * kFW + (lx >> 5) + 1] << (32 - (lx & 31)) : 0u);
+    R* Cp = C + (long long)j * d.P + i;
+    R* Kp = kappa + (long long)j * d.P + i;
+    if (vec && i + 3 < d.nx) {
+      store4(Cp, c[0], c[1], c[2], c[3]);
+      if (!(ib & 15u)) store4(Kp, R(NAN), R(NAN), R(NAN), R(NAN));
+      else
+        for (int m = 0; m < 4; ++m)
+          if (!((ib >> m) & 1u)) Kp[m] = R(NAN);
+    } else {
+      for (int m = 0; m < 4 && i + m < d.nx; ++m) {
+        Cp[m] = c[m];
+        if (!((ib >> m) & 1u)) Kp[m] = R(NAN);
+      }
+    }
   }
   // area partial: warps holding interface cells reduce in a fixed shuffle
   // order (adding 0.0 from the other lanes changes nothing)
@@ -221,8 +287,8 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
     acc = 0.0;
   }
   if (lane == 0) s_wsum[warp] = acc;
-  const int fw = __reduce_add_sync(0xffffffffu, full);
-  if (lane == 0 && fw) atomicAdd(&s_full, (unsigned long long)fw);
+  const int fsum = __reduce_add_sync(0xffffffffu, full);
+  if (lane == 0 && fsum) atomicAdd(&s_full, (unsigned long long)fsum);
 #pragma unroll
   for (int c = 0; c < D_NUSED; ++c) {
     const int s = __reduce_add_sync(0xffffffffu, cnt[c]);

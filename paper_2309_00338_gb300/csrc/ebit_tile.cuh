@@ -97,27 +97,11 @@ __device__ __forceinline__ int getb(const uint32_t* w, int lx, int ly) {
   return (w[ly * kRW + (lx >> 5)] >> (lx & 31)) & 1;
 }
 
-// Bits [a, b] (inclusive, region columns) within word wi; empty if a > b.
-__device__ __forceinline__ uint32_t span_mask(int wi, int a, int b) {
-  const int lo = max(a - 32 * wi, 0), hi = min(b - 32 * wi, 31);
-  if (lo > hi) return 0u;
-  const uint32_t up = hi == 31 ? 0xffffffffu : ((1u << (hi + 1)) - 1u);
-  return up & ~((1u << lo) - 1u);
-}
-
 // Word wi of row ly shifted right by one column (bit b = column 32 wi + b + 1).
 __device__ __forceinline__ uint32_t shr1(const uint32_t* w, int ly, int wi) {
   uint32_t v = w[ly * kRW + wi] >> 1;
   if (wi + 1 < kRW) v |= w[ly * kRW + wi + 1] << 31;
   return v;
-}
-
-// Bits x0 .. x0+31 of a stored row of nw words (bits outside the row read 0).
-__device__ __forceinline__ uint32_t row_bits(const uint32_t* __restrict__ row, int nw, int x0) {
-  const int q = x0 >> 5, r = x0 & 31;
-  const uint32_t a = (q >= 0 && q < nw) ? __ldg(&row[q]) : 0u;
-  const uint32_t b = (q + 1 >= 0 && q + 1 < nw) ? __ldg(&row[q + 1]) : 0u;
-  return r ? ((a >> r) | (b << (32 - r))) : a;
 }
 
 // Appends the set bits of plane word t as region indices.
