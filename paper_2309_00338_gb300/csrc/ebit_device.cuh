@@ -668,6 +668,24 @@ struct GView {
     Flags f;
     return advect(m, f);
   }
+  // L2 prefetch of what advect(m) reads.
+  __device__ __forceinline__ void prefetch(Mk m) const {
+    const R* s;
+    const R* w0;
+    const R* w1;
+    if (m.kind == 0) {
+      s = AX ? &sV[(long long)m.i * d.P + m.j] : &sH[(long long)m.j * d.P + m.i];
+      w0 = AX ? &w[(long long)m.i * (d.nx + 1) + m.j] : &w[(long long)m.j * (d.nx + 1) + m.i];
+      w1 = AX ? w0 + (d.nx + 1) : w0 + 1;
+    } else {
+      s = AX ? &sH[(long long)m.i * d.P + m.j] : &sV[(long long)m.j * d.P + m.i];
+      w0 = AX ? &w[(long long)m.i * (d.nx + 1) + m.j] : &w[(long long)m.j * (d.nx + 1) + m.i];
+      w1 = AX ? w0 + 1 : w0 + (d.nx + 1);
+    }
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(s));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(w0));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(w1));
+  }
   // New corner colour (Sec. 2.3, Fig. 5): vertex i of line j flips once for
   // each aligned marker that passes it; only markers of edges i-1 and i can.
   __device__ int knew(int i, int j) const {

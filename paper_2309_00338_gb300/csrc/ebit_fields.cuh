@@ -22,42 +22,41 @@ constexpr int kFW = 3;                                     // words per region b
 constexpr int kFieldThreads = 256;
 
 // Reference-phase area of cell (i,j) in cell units from its corner mask q,
-// centre colour and marker fractions; double arithmetic.
+// centre colour and marker fractions; double arithmetic.  The one-minus
+// terms are formed once and each case then takes a few operations, so that a
+// warp whose cells fall in different cases repeats little FP64 work.
 template <typename R>
 __device__ double fraction_of(int q, int zc, const R* __restrict__ sH, const R* __restrict__ sV,
                               const Dims& d, int i, int j) {
   const int em = edge_mask(q);
-  const double s0 = (double)__ldg(&sH[(long long)j * d.P + i]);
-  const double s1 = (double)__ldg(&sV[(long long)j * d.P + i + 1]);
-  const double s2 = (double)__ldg(&sH[(long long)(j + 1) * d.P + i]);
-  const double s3 = (double)__ldg(&sV[(long long)j * d.P + i]);
+  // exact conversions on the integer pipe
+  const double s0 = to_d<R>(__ldg(&sH[(long long)j * d.P + i]));
+  const double s1 = to_d<R>(__ldg(&sV[(long long)j * d.P + i + 1]));
+  const double s2 = to_d<R>(__ldg(&sH[(long long)(j + 1) * d.P + i]));
+  const double s3 = to_d<R>(__ldg(&sV[(long long)j * d.P + i]));
+  const double w0 = 1.0 - s0, w1 = 1.0 - s1, w2 = 1.0 - s2, w3 = 1.0 - s3;
+  // legs of the triangle cut off at corner c: (s3, s0) (w0, s1) (w1, w2) (s2, w3)
   auto tri = [&](int c) {
-    double a, b;
-    switch (c) {
-      case 0: a = s3; b = s0; break;
-      case 1: a = 1.0 - s0; b = s1; break;
-      case 2: a = 1.0 - s1; b = 1.0 - s2; break;
-      default: a = s2; b = 1.0 - s3; break;
-    }
+    const double a = c == 0 ? s3 : c == 1 ? w0 : c == 2 ? w1 : s2;
+    const double b = c == 0 ? s0 : c == 1 ? s1 : c == 2 ? w2 : w3;
     return 0.5 * (a * b);
   };
   if (em != 15) {
     const int e1 = __ffs(em) - 1, e2 = 31 - __clz(em);
     const int c0 = q & 1;
-    if (e2 - e1 == 2) {
-      if (e1 == 0) return c0 ? 0.5 * (s0 + s2) : 0.5 * ((1.0 - s0) + (1.0 - s2));
-      return c0 ? 0.5 * (s3 + s1) : 0.5 * ((1.0 - s3) + (1.0 - s1));
+    if (e2 - e1 == 2) {  // opposite edges: a trapezoid
+      const double a = e1 == 0 ? (c0 ? s0 : w0) : (c0 ? s3 : w3);
+      const double b = e1 == 0 ? (c0 ? s2 : w2) : (c0 ? s1 : w1);
+      return 0.5 * (a + b);
     }
     const int c = (e1 == 0 && e2 == 3) ? 0 : e2;
     const double T = tri(c);
     return ((q >> c) & 1) ? T : 1.0 - T;
   }
-  double Tsum = 0.0;
-  bool first = true;
-  for (int c = 0; c < 4; ++c)
-    if (((q >> c) & 1) != zc) {
-      if (first) { Tsum = tri(c); first = false; } else { Tsum = Tsum + tri(c); }
-    }
+  // four markers: the two corners of the other colour than the centre are cut
+  // off (corners 1 and 3 when corner 0 has the centre's colour, else 0 and 2)
+  const int ca = ((q & 1) == zc) ? 1 : 0;
+  const double Tsum = tri(ca) + tri(ca + 2);
   return zc == 0 ? Tsum : 1.0 - Tsum;
 }
 
@@ -281,7 +280,7 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
   }
   // area partial: warps holding interface cells reduce in a fixed shuffle
   // order (adding 0.0 from the other lanes changes nothing)
-  if (__any_sync(0xffffffffu, acc != 0.0)) {
+  if (__any_sync(0xffffffffu, !d_eq0(acc))) {
     for (int o = 16; o > 0; o >>= 1) acc = acc + __shfl_down_sync(0xffffffffu, acc, o);
   } else {
     acc = 0.0;

@@ -53,6 +53,7 @@ template <> constexpr int tile_min_blocks<double>() { return 2; }
 enum { CF_P1 = 1, CF_Q1 = 2, CF_P4 = 4, CF_Q4 = 8, CF_OWNED = 16 };
 struct Cand {
   double y;
+  float sf;  // the crossing as an FP32 marker fraction (FP32 state only)
   uint16_t a, b, p1, q1, p4, q4;
   uint16_t edge;  // (j - j0) * (kTI + 1) + (k - i0)
   uint8_t fl, ord;
@@ -69,7 +70,7 @@ struct TileMem {
   R hfx[kRN];              // moved aligned marker: fraction
   R vfx[kRN];              // moved unaligned marker: fraction along the sweep
   R vfy[kRN];              // ... and across it (the marker's own fraction)
-  int head[kNVE];          // first linked candidate of an unaligned edge, -1: none
+  alignas(16) int head[kNVE];  // first linked candidate of an unaligned edge, -1: none
   uint32_t kb[kRB];        // old corner colours
   uint32_t kn[kRB];        // new corner colours
   uint32_t zb[kRB];        // old centre colours (bit lx of row ly: cell (lx, ly))
@@ -85,7 +86,7 @@ struct TileMem {
   int8_t hix[kRN];         // moved aligned marker: ix - ri0
   int8_t vix[kRN];         // moved unaligned marker: ix - ri0
   int8_t lsrc[kRN];        // landing: kept source - i (kNoSrc: none)
-  uint8_t vrl[kNVE];       // centre verdicts of an edge: bits 0-1 right + 1, bits 2-3 left + 1
+  alignas(16) uint8_t vrl[kNVE];  // centre verdicts of an edge: bits 0-1 right + 1, bits 2-3 left + 1
 };
 
 template <typename R>
@@ -137,6 +138,14 @@ __device__ __forceinline__ int warp_alloc(int n, int* count, int lane) {
   int base = 0;
   if (lane == 31 && total) base = atomicAdd(count, total);
   return __shfl_sync(kFull, base, 31) + incl - n;
+}
+
+// Adds the lanes' v to the block's counter c, one shared atomic per warp (all
+// 32 lanes call it).  Counts are kept per phase so that no counter stays live
+// in registers across the kernel.
+__device__ __forceinline__ void flush_count(int* s_cnt, int c, int v, int lane) {
+  const int s = __reduce_add_sync(kFull, v);
+  if (s != 0 && lane == 0) atomicAdd(&s_cnt[c], s);
 }
 
 // push_bits for a whole warp (all 32 lanes call it).
@@ -246,6 +255,7 @@ struct TViewB {
 template <typename R>
 __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int present) {
   double cy[6];
+  float sf[6];
   long long key[6];
   int ord[6], cvr[6], cvl[6];
   int n = 0;
@@ -254,6 +264,7 @@ __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int
     if (s >= 0) {
       const Cand& C = M.cand[s];
       cy[q] = C.y;
+      sf[q] = C.sf;
       key[q] = okey(C.y);
       ord[q] = C.ord;
       cvr[q] = C.vr;
@@ -262,6 +273,7 @@ __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int
       s = M.next[s];
     } else {
       cy[q] = 0.0;
+      sf[q] = 0.0f;
       key[q] = 0;
       ord[q] = 0;
       cvr[q] = -1;
@@ -306,14 +318,17 @@ __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int
   }
   if (want >= 0) {
     double ysel = 0.0;
+    float fsel = 0.0f;
 #pragma unroll
     for (int t = 0; t < 6; ++t)
       if (t < n && rank[t] == want) {
         ysel = cy[t];
+        fsel = sf[t];
         out.vr = cvr[t];
         out.vl = cvl[t];
       }
-    out.s = to_fraction<R>(ysel);
+    if constexpr (sizeof(R) == 4) out.s = fsel;  // to_fraction<float>, taken in the fit phase
+    else out.s = to_fraction<R>(ysel);
   }
   return out;
 }
@@ -339,10 +354,6 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     s_nh = s_nv = s_nd = s_nc = s_ncand = s_ne = 0;
     s_dmax = 0ull;
   }
-  int cnt[D_NUSED];
-#pragma unroll
-  for (int c = 0; c < D_NUSED; ++c) cnt[c] = 0;
-  R dmax = R(0);
   auto owned = [&](int x, int y) { return x >= i0 && x < i0 + kTI && y >= j0 && y < j0 + kTJ; };
   // region columns / rows inside the grid
   const int vx0 = max(0, -ri0), vx1 = min(kRX - 1, tnx - ri0);  // vertices
@@ -406,6 +417,9 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     M.hc[t] = 0u;
     M.ovf[t] = 0u;
     mine |= (h | v) != 0u;
+    // start the reads of P2 now
+    for (uint32_t b = h; b; b &= b - 1) G.prefetch(Mk{0, ri0 + 32 * wi + __ffs(b) - 1, rj0 + ly});
+    for (uint32_t b = v; b; b &= b - 1) G.prefetch(Mk{1, ri0 + 32 * wi + __ffs(b) - 1, rj0 + ly});
   }
   const bool busy = __syncthreads_or(mine) != 0;
   const TViewB<R> TV{&M, ri0, rj0, tnx, tny};
@@ -416,15 +430,18 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       push_bits_warp(t < kRB ? M.hm[t] : 0u, t, M.lh, &s_nh, lane);
       push_bits_warp(t < kRB ? M.vm[t] : 0u, t, M.lv, &s_nv, lane);
     }
-    for (int e = tid; e < kNVE; e += kTileThreads) {
-      M.head[e] = -1;
-      M.vrl[e] = 0;
-    }
+    static_assert(kNVE % 16 == 0, "vector initialisation");
+    for (int e = tid; e < kNVE / 4; e += kTileThreads)
+      reinterpret_cast<int4*>(M.head)[e] = make_int4(-1, -1, -1, -1);
+    for (int e = tid; e < kNVE / 16; e += kTileThreads)
+      reinterpret_cast<uint4*>(M.vrl)[e] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
 
     // P2: moved points (aligned and unaligned markers in one pass), corner
     // flips, landing claims
     const int nh = s_nh, nm = s_nh + s_nv;
+    int n_cfl = 0, n_clamp = 0;
+    R dmax = R(0);
     for (int w0 = warp * 32; w0 < nm; w0 += kTileThreads) {
       const int w = w0 + lane;
       int claimed = -1;
@@ -436,8 +453,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         M.hix[id] = (int8_t)(p.ix - ri0);
         M.hfx[id] = p.fx;
         if (owned(x, y)) {
-          cnt[D_CFL] += f.cfl;
-          cnt[D_WALL_CLAMP] += f.clamp;
+          n_cfl += f.cfl;
+          n_clamp += f.clamp;
           dmax = fmax(dmax, dabs_of<R>(f));
         }
         // a marker moving right passes vertex x+1, one moving left vertex x
@@ -458,7 +475,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         M.vfy[id] = p.fy;
         if (owned(x, y)) {
           if (x >= 1 && x <= tnx - 1) {
-            cnt[D_CFL] += f.cfl;
+            n_cfl += f.cfl;
             dmax = fmax(dmax, dabs_of<R>(f));
           } else {  // a wall marker normal to the sweep stays
             if (AX) out.sH[(long long)x * P + y] = p.fy;
@@ -475,10 +492,17 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         if (claimed >= 0) M.ld[base + __popc(cm & ((1u << lane) - 1u))] = (uint16_t)claimed;
       }
     }
+    flush_count(s_cnt, D_CFL, n_cfl, lane);
+    flush_count(s_cnt, D_WALL_CLAMP, n_clamp, lane);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, o));
+    if (lane == 0 && dmax > R(0))
+      atomicMax(&s_dmax, (unsigned long long)__double_as_longlong((double)dmax));
     __syncthreads();
 
     // P3: landings on the claimed aligned edges
     const int nd = s_nd;
+    int n_canc = 0, n_inv = 0;
     for (int w = tid; w < nd; w += kTileThreads) {
       const int id = M.ld[w], dl = id % kRX, ly = id / kRX;
       const int x = ri0 + dl, y = rj0 + ly;
@@ -494,8 +518,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
           choose_landing3<R>(valid, fx, x, getb(M.kn, dl, ly) ^ getb(M.kn, dl + 1, ly));
       M.lsrc[id] = L.kept_src < 0 ? kNoSrc : (int8_t)(L.kept_src - x);
       if (owned(x, y)) {
-        cnt[D_CANCELLED] += L.cancelled;
-        cnt[D_INVARIANT] += L.invariant;
+        n_canc += L.cancelled;
+        n_inv += L.invariant;
         if (L.present) {
           if (AX) out.sV[(long long)x * P + y] = L.kept_fx;
           else out.sH[(long long)y * P + x] = L.kept_fx;
@@ -514,7 +538,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
           const int b = __ffs(bad) - 1;
           bad &= bad - 1;
           const int x = ri0 + 32 * wi + b, y = rj0 + ly;
-          cnt[D_INVARIANT] += 1;
+          n_inv += 1;
           if (AX) out.sV[(long long)x * P + y] = R(0.5);
           else out.sH[(long long)y * P + x] = R(0.5);
         }
@@ -529,6 +553,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       }
       push_bits_warp(ic, u, M.lh, &s_nc, lane);
     }
+    flush_count(s_cnt, D_CANCELLED, n_canc, lane);
+    flush_count(s_cnt, D_INVARIANT, n_inv, lane);
     __syncthreads();
 
     // P4: candidates.  A thread takes one interface cell: counts the grid
@@ -624,6 +650,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       push_bits_warp(M.hc[u], u, M.le, &s_ne, lane);
     }
     const int rot = (int)((blockIdx.x + blockIdx.y) & 3u);
+    int n_fit[4] = {0, 0, 0, 0};  // D_FIT_ONLINE .. D_FIT_TWO
     const int vt = (((warp + rot) & (kWarps - 1)) << 5) | lane;
     for (int b0 = 0; b0 < 2 * ncand; b0 += kTileThreads) {
       const int item = b0 + vt, side = item & 1;
@@ -635,33 +662,38 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         j = j0 + C.edge / (kTI + 1);
         act = !getb(M.ovf, k - ri0, j - rj0);  // else the edge is done in place
       }
-      double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0, cx = 1.0, cy = 0.0, x0 = 0.0, ys = 0.0;
-      bool online = false, ok = false;
-      if (act) {
-        TV.xy(C.a, k, j, &ax, &ay);
-        TV.xy(C.b, k, j, &bx, &by);
-        online = d_eq0(bx);
-        if (!online) {
-          cx = bx - ax;
-          cy = by - ay;
-          x0 = -ax;
-          const double c2 = cx * cx + cy * cy;
-          const uint8_t fl = C.fl;
-          if (!line_only && !d_below_sep(c2) && (fl & (side ? CF_P4 : CF_P1))) {
-            double X, Y;
-            TV.xy(side ? C.p4 : C.p1, k, j, &X, &Y);
-            FitPt T = fit_pt(X, Y, ax, ay, bx, by);
-            bool use = true;
-            if (d_below_sep(side ? T.t2 : T.r2)) {  // too close to A (B): the next marker
-              if (fl & (side ? CF_Q4 : CF_Q1)) {
-                TV.xy(side ? C.q4 : C.q1, k, j, &X, &Y);
-                T = fit_pt(X, Y, ax, ay, bx, by);
-              } else {
-                use = false;
-              }
+      // the pair shares the chord: the even lane converts A and forms cx,
+      // the odd lane B and cy, and they swap (shuffles instead of FP64 work)
+      double px = 0.0, py = 0.0;
+      if (act) TV.xy(side ? C.b : C.a, k, j, &px, &py);
+      const double ox = __shfl_xor_sync(kFull, px, 1), oy = __shfl_xor_sync(kFull, py, 1);
+      const double ax = side ? ox : px, ay = side ? oy : py;
+      const double bx = side ? px : ox, by = side ? py : oy;
+      const double dd = side ? by - ay : bx - ax;
+      const double od = __shfl_xor_sync(kFull, dd, 1);
+      const double cx = side ? od : dd, cy = side ? dd : od;
+      const double sq = dd * dd, osq = __shfl_xor_sync(kFull, sq, 1);
+      const double c2 = side ? osq + sq : sq + osq;  // cx*cx + cy*cy
+      const double x0 = -ax;
+      const bool online = d_eq0(bx);
+      double ys = 0.0;
+      bool ok = false;
+      if (act && !online) {
+        const uint8_t fl = C.fl;
+        if (!line_only && !d_below_sep(c2) && (fl & (side ? CF_P4 : CF_P1))) {
+          double X, Y;
+          TV.xy(side ? C.p4 : C.p1, k, j, &X, &Y);
+          FitPt T = fit_pt(X, Y, ax, ay, bx, by);
+          bool use = true;
+          if (d_below_sep(side ? T.t2 : T.r2)) {  // too close to A (B): the next marker
+            if (fl & (side ? CF_Q4 : CF_Q1)) {
+              TV.xy(side ? C.q4 : C.q1, k, j, &X, &Y);
+              T = fit_pt(X, Y, ax, ay, bx, by);
+            } else {
+              use = false;
             }
-            if (use) ok = circle_cross(ay, x0, cx, cy, c2, T, &ys);
           }
+          if (use) ok = circle_cross(ay, x0, cx, cy, c2, T, &ys);
         }
       }
       const double yo = __shfl_xor_sync(kFull, ys, 1);
@@ -683,19 +715,22 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
           kind = D_FIT_LINE;
         }
         C.y = y;
+        if (sizeof(R) == 4) C.sf = to_fraction<float>(y);  // here, where the FP64 pipe is busy anyway
         C.kind = (int8_t)kind;
         if (C.fl & CF_OWNED) {  // static indices keep the counters in registers
-          cnt[D_FIT_ONLINE] += kind == D_FIT_ONLINE;
-          cnt[D_FIT_LINE] += kind == D_FIT_LINE;
-          cnt[D_FIT_ONE] += kind == D_FIT_ONE;
-          cnt[D_FIT_TWO] += kind == D_FIT_TWO;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) n_fit[q] += kind == D_FIT_ONLINE + q;
         }
       }
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) flush_count(s_cnt, D_FIT_ONLINE + q, n_fit[q], lane);
     __syncthreads();
 
     // P6: one marker per unaligned edge (Sec. 2.4)
     const int ne = s_ne;
+    n_canc = 0;
+    n_inv = 0;
     for (int w = tid; w < ne; w += kTileThreads) {
       const int id = M.le[w], ex = id % kRX, ey = id / kRX;
       if (getb(M.ovf, ex, ey)) continue;
@@ -705,8 +740,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       const int present = getb(M.kn, ex, ey) ^ getb(M.kn, ex, ey + 1);
       const NewV<R> nv = select_linked<R>(M, M.head[e], present);
       if (own) {
-        cnt[D_CANCELLED] += nv.cancelled;
-        cnt[D_INVARIANT] += nv.invariant;
+        n_canc += nv.cancelled;
+        n_inv += nv.invariant;
       }
       M.vrl[e] = verdicts(nv.vr, nv.vl);
       if (own && nv.present) {
@@ -729,8 +764,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
 #pragma unroll
         for (int c = 0; c < D_NUSED; ++c) oc[c] = 0;
         const NewV<R> nv = new_unaligned<R>(TV, line_only != 0, k, j, own ? oc : nullptr);
-#pragma unroll
-        for (int c = 0; c < D_NUSED; ++c) cnt[c] += oc[c];
+        for (int c = 0; c < D_NUSED; ++c)
+          if (oc[c]) atomicAdd(&s_cnt[c], oc[c]);
         M.vrl[e] = verdicts(nv.vr, nv.vl);
         if (own && nv.present) {
           if (AX) out.sH[(long long)k * P + j] = nv.s;
@@ -745,11 +780,13 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         const int b = __ffs(miss) - 1;
         miss &= miss - 1;
         const int k = ri0 + 32 * wi + b, j = rj0 + ly;
-        cnt[D_INVARIANT] += 1;
+        n_inv += 1;
         if (AX) out.sH[(long long)k * P + j] = R(0.5);
         else out.sV[(long long)j * P + k] = R(0.5);
       }
     }
+    flush_count(s_cnt, D_CANCELLED, n_canc, lane);
+    flush_count(s_cnt, D_INVARIANT, n_inv, lane);
     __syncthreads();
   }
 
@@ -758,6 +795,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
   // stored rows.  Centre colours of new four-marker cells (all four edges
   // with a marker) come from the verdicts of edges i (right) and i+1 (left);
   // the right one wins.
+  int n_zset = 0, n_zconf = 0;
   if (warp < 2) {
     const int ow = warp, ly = 2 + lane, cx0 = 4 + 32 * ow;
     const int j = rj0 + ly;
@@ -779,11 +817,11 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         int zc = -1;
         if (a >= 0) {
           zc = a;
-          cnt[D_ZSET] += 1;
-          if (bl >= 0 && bl != a) cnt[D_ZCONFLICT] += 1;
+          n_zset += 1;
+          if (bl >= 0 && bl != a) n_zconf += 1;
         } else if (bl >= 0) {
           zc = bl;
-          cnt[D_ZSET] += 1;
+          n_zset += 1;
         }
         if (zc >= 0) zw = zc ? (zw | (1u << b)) : (zw & ~(1u << b));
       }
@@ -803,13 +841,10 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     }
   }
 
-  // block-level counters
-#pragma unroll
-  for (int c = 0; c < D_NUSED; ++c) {
-    const int s = __reduce_add_sync(kFull, cnt[c]);
-    if (s != 0 && lane == 0) atomicAdd(&s_cnt[c], s);
-  }
-  if (dmax > R(0)) atomicMax(&s_dmax, (unsigned long long)__double_as_longlong((double)dmax));
+  flush_count(s_cnt, D_ZSET, n_zset, lane);
+  flush_count(s_cnt, D_ZCONFLICT, n_zconf, lane);
+
+  // block counters to the grid's
   __syncthreads();
   if (tid < D_NUSED && s_cnt[tid] != 0) atomicAdd(&ctr[tid], (unsigned long long)s_cnt[tid]);
   if (tid == 0) {
