@@ -156,7 +156,7 @@ ebit_status launch_sweep(ebit_ctx* c, const void* vel, double lam) {
     const int tnx = AX ? L.d.ny : L.d.nx, tny = AX ? L.d.nx : L.d.ny;
     const dim3 grid((tnx + 1 + ebit::kTI - 1) / ebit::kTI, (tny + 1 + ebit::kTJ - 1) / ebit::kTJ);
     Timed t(c, EBIT_K_SWEEP);
-    ebit::k_sweep_tile<R, AX><<<grid, ebit::kTileThreads, smem, c->stream>>>(
+    ebit::k_sweep_tile<R, AX><<<grid, ebit::tile_threads<R>(), smem, c->stream>>>(
         S, out, line_only, c->ctr, c->cfl_bits, c->status);
   }
   EBIT_CK(cudaGetLastError());

@@ -714,6 +714,5 @@ struct GView {
   }
 };
 
-constexpr int8_t kNoSrc = -128;  // no landing source kept
 
 }  // namespace ebit

@@ -241,10 +241,10 @@ struct Group {
     constexpr size_t smem = ebit::tile_smem_bytes<R>();
     cudaMemcpyAsync(d_s0, h_s0, 2 * n * sizeof(ebit::SweepDesc<R, 0>), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_s1, h_s1, 2 * n * sizeof(ebit::SweepDesc<R, 1>), cudaMemcpyHostToDevice, st);
-    ebit::k_sweep_tile_batch<R, 0><<<n_items0, ebit::kTileThreads, smem, st>>>(d_s0, d_items0);
-    ebit::k_sweep_tile_batch<R, 1><<<n_items1, ebit::kTileThreads, smem, st>>>(d_s1, d_items1);
-    ebit::k_sweep_tile_batch<R, 1><<<n_items1, ebit::kTileThreads, smem, st>>>(d_s1 + n, d_items1);
-    ebit::k_sweep_tile_batch<R, 0><<<n_items0, ebit::kTileThreads, smem, st>>>(d_s0 + n, d_items0);
+    ebit::k_sweep_tile_batch<R, 0><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0, d_items0);
+    ebit::k_sweep_tile_batch<R, 1><<<n_items1, ebit::tile_threads<R>(), smem, st>>>(d_s1, d_items1);
+    ebit::k_sweep_tile_batch<R, 1><<<n_items1, ebit::tile_threads<R>(), smem, st>>>(d_s1 + n, d_items1);
+    ebit::k_sweep_tile_batch<R, 0><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0 + n, d_items0);
     ebit::k_fields_tile_batch<R><<<n_fitems, ebit::kFieldThreads, 0, st>>>(d_fd, d_fitems);
     k_area_batch<<<(unsigned)n, 256, 0, st>>>(d_ad);
     const cudaError_t e = cudaGetLastError();

@@ -39,13 +39,15 @@ constexpr int kRX = kTI + 8, kRY = kTJ + 5, kRN = kRX * kRY;
 constexpr int kRW = 3;                 // words per region bit row (72 columns used)
 constexpr int kRB = kRY * kRW;         // words per region bit plane
 constexpr int kNVE = (kTI + 1) * kTJ;  // unaligned edges k in [i0, i0+64], rows j0..j0+31
-constexpr int kTileThreads = 256;
 constexpr int kCandCap = 256;          // candidates per tile; an edge beyond it is done in place
 constexpr uint16_t kKindV = 0x8000;    // marker reference: region index | kKindV if unaligned
 
-template <typename R> constexpr int tile_min_blocks();
-template <> constexpr int tile_min_blocks<float>() { return 3; }
-template <> constexpr int tile_min_blocks<double>() { return 2; }
+// Block shape: 6 warps per tile; tiles resident per SM as shared memory and
+// registers allow (4 in the FP32 form, 3 in the FP64 form).
+template <typename R> __host__ __device__ constexpr int tile_threads() { return 192; }
+template <typename R> __host__ __device__ constexpr int tile_min_blocks();
+template <> __host__ __device__ constexpr int tile_min_blocks<float>() { return 4; }
+template <> __host__ __device__ constexpr int tile_min_blocks<double>() { return 3; }
 
 // Candidate of one unaligned edge: chord ends A (left of the line) and B,
 // point 1 (p1) with the next marker beyond it (q1) in case p1 is too close to
@@ -68,9 +70,10 @@ struct TileMem {
     uint16_t ld[kRN];      // P2-P3: claimed landing edges
   };
   R hfx[kRN];              // moved aligned marker: fraction
-  R vfx[kRN];              // moved unaligned marker: fraction along the sweep
-  R vfy[kRN];              // ... and across it (the marker's own fraction)
-  alignas(16) int head[kNVE];  // first linked candidate of an unaligned edge, -1: none
+  R vfx[kRN];              // moved unaligned marker: fraction along the sweep (the one
+                           // across it is the marker's own, read from the state)
+  alignas(16) uint32_t head[kNVE / 2];  // first linked candidate of unaligned edges
+                                        // 2m, 2m+1 (16 bits each, 0xffff: none)
   uint32_t kb[kRB];        // old corner colours
   uint32_t kn[kRB];        // new corner colours
   uint32_t zb[kRB];        // old centre colours (bit lx of row ly: cell (lx, ly))
@@ -79,13 +82,15 @@ struct TileMem {
   uint32_t claim[kRB];     // aligned edges some marker lands on
   uint32_t hc[kRB];        // unaligned edges with a linked candidate
   uint32_t ovf[kRB];       // unaligned edges done in place
+  // 2-bit codes (planes 0 and 1): moved aligned / unaligned marker ix - x + 1,
+  // landing kept source - i + 2 (0: none)
+  uint32_t hq[2][kRB];
+  uint32_t vq[2][kRB];
+  uint32_t lq[2][kRB];
   uint16_t lh[kRN];        // aligned marker list; in P3-P4 the interface-cell list
   uint16_t lv[kRN];        // unaligned marker list
   uint16_t le[kCandCap];   // unaligned edges with a linked candidate
   int16_t next[kCandCap];  // candidate links
-  int8_t hix[kRN];         // moved aligned marker: ix - ri0
-  int8_t vix[kRN];         // moved unaligned marker: ix - ri0
-  int8_t lsrc[kRN];        // landing: kept source - i (kNoSrc: none)
   alignas(16) uint8_t vrl[kNVE];  // centre verdicts of an edge: bits 0-1 right + 1, bits 2-3 left + 1
 };
 
@@ -96,6 +101,18 @@ constexpr size_t tile_smem_bytes() {
 
 __device__ __forceinline__ int getb(const uint32_t* w, int lx, int ly) {
   return (w[ly * kRW + (lx >> 5)] >> (lx & 31)) & 1;
+}
+
+// 2-bit code of region entry (lx, ly) held in two bit planes.
+__device__ __forceinline__ int get2(const uint32_t (&q)[2][kRB], int lx, int ly) {
+  const int w = ly * kRW + (lx >> 5), b = lx & 31;
+  return ((q[0][w] >> b) & 1) | (((q[1][w] >> b) & 1) << 1);
+}
+__device__ __forceinline__ void put2(uint32_t (&q)[2][kRB], int lx, int ly, int code) {
+  const int w = ly * kRW + (lx >> 5);
+  const uint32_t bit = 1u << (lx & 31);
+  if (code & 1) atomicOr(&q[0][w], bit);
+  if (code & 2) atomicOr(&q[1][w], bit);
 }
 
 // Word wi of row ly shifted right by one column (bit b = column 32 wi + b + 1).
@@ -191,9 +208,10 @@ __device__ __forceinline__ uint32_t upto32(int c0, int last) {
 // Accessor of the tile for the shared sweep logic (beyond, walk,
 // new_unaligned).  Indices are clamped into the region; the kernel only asks
 // inside it.
-template <typename R>
+template <typename R, int AX>
 struct TViewB {
   const TileMem<R>* m;
+  const GView<R, AX>* g;  // an unaligned marker's own fraction is read from the state
   int ri0, rj0, nx_, ny_;
   __device__ __forceinline__ int tnx() const { return nx_; }
   __device__ __forceinline__ int tny() const { return ny_; }
@@ -210,25 +228,25 @@ struct TViewB {
     return (uint16_t)((cy(mk.j) * kRX + cx(mk.i)) | (mk.kind ? kKindV : 0));
   }
   __device__ __forceinline__ AP<R> moved(Mk mk) const {
-    const int t = cy(mk.j) * kRX + cx(mk.i);
+    const int lx = cx(mk.i), ly = cy(mk.j), t = ly * kRX + lx;
     AP<R> p;
     p.jy = mk.j;
     if (mk.kind == 0) {
-      p.ix = m->hix[t] + ri0;
+      p.ix = mk.i + get2(m->hq, lx, ly) - 1;
       p.fx = m->hfx[t];
       p.fy = R(0);
     } else {
-      p.ix = m->vix[t] + ri0;
+      p.ix = mk.i + get2(m->vq, lx, ly) - 1;
       p.fx = m->vfx[t];
-      p.fy = m->vfy[t];
+      p.fy = g->v(mk.i, mk.j);
     }
     return p;
   }
   __device__ __forceinline__ Landing<R> landing(int i, int j) const {
-    const int s = m->lsrc[cy(j) * kRX + cx(i)];
+    const int c = get2(m->lq, cx(i), cy(j));
     Landing<R> L;
     L.present = knew(i, j) ^ knew(i + 1, j);
-    L.kept_src = s == kNoSrc ? -1 : i + s;
+    L.kept_src = c == 0 ? -1 : i + c - 2;
     L.kept_fx = R(0);
     L.cancelled = 0;
     L.invariant = 0;
@@ -236,14 +254,14 @@ struct TViewB {
   }
   // Moved point of a referenced marker relative to vertex (k, j).
   __device__ __forceinline__ void xy(uint16_t r, int k, int j, double* X, double* Y) const {
-    const int t = r & (kKindV - 1), ly = t / kRX;
+    const int t = r & (kKindV - 1), ly = t / kRX, lx = t - ly * kRX;
     // the same values as (double)n + (double)f; the conversions run on the
     // integer pipe and an aligned marker's y needs no addition
     if (r & kKindV) {
-      *X = i2d(m->vix[t] + ri0 - k) + to_d<R>(m->vfx[t]);
-      *Y = i2d(rj0 + ly - j) + to_d<R>(m->vfy[t]);
+      *X = i2d(ri0 + lx + get2(m->vq, lx, ly) - 1 - k) + to_d<R>(m->vfx[t]);
+      *Y = i2d(rj0 + ly - j) + to_d<R>(g->v(ri0 + lx, rj0 + ly));
     } else {
-      *X = i2d(m->hix[t] + ri0 - k) + to_d<R>(m->hfx[t]);
+      *X = i2d(ri0 + lx + get2(m->hq, lx, ly) - 1 - k) + to_d<R>(m->hfx[t]);
       *Y = i2d(rj0 + ly - j);
     }
   }
@@ -345,6 +363,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
   __shared__ unsigned long long s_dmax;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kTileThreads = tile_threads<R>();
   constexpr int kWarps = kTileThreads / 32;
   const int tnx = G.tnx(), tny = G.tny();
   const int ri0 = i0 - 4, rj0 = j0 - 2;
@@ -416,13 +435,16 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     M.claim[t] = 0u;
     M.hc[t] = 0u;
     M.ovf[t] = 0u;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      M.hq[q][t] = 0u;
+      M.vq[q][t] = 0u;
+      M.lq[q][t] = 0u;
+    }
     mine |= (h | v) != 0u;
-    // start the reads of P2 now
-    for (uint32_t b = h; b; b &= b - 1) G.prefetch(Mk{0, ri0 + 32 * wi + __ffs(b) - 1, rj0 + ly});
-    for (uint32_t b = v; b; b &= b - 1) G.prefetch(Mk{1, ri0 + 32 * wi + __ffs(b) - 1, rj0 + ly});
   }
   const bool busy = __syncthreads_or(mine) != 0;
-  const TViewB<R> TV{&M, ri0, rj0, tnx, tny};
+  const TViewB<R, AX> TV{&M, &G, ri0, rj0, tnx, tny};
 
   if (busy) {
     for (int t0 = warp * 32; t0 < kRB; t0 += kTileThreads) {
@@ -431,8 +453,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       push_bits_warp(t < kRB ? M.vm[t] : 0u, t, M.lv, &s_nv, lane);
     }
     static_assert(kNVE % 16 == 0, "vector initialisation");
-    for (int e = tid; e < kNVE / 4; e += kTileThreads)
-      reinterpret_cast<int4*>(M.head)[e] = make_int4(-1, -1, -1, -1);
+    for (int e = tid; e < kNVE / 8; e += kTileThreads)
+      reinterpret_cast<uint4*>(M.head)[e] = make_uint4(~0u, ~0u, ~0u, ~0u);
     for (int e = tid; e < kNVE / 16; e += kTileThreads)
       reinterpret_cast<uint4*>(M.vrl)[e] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
@@ -450,7 +472,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         const int x = ri0 + lx, y = rj0 + ly;
         Flags f;
         const AP<R> p = G.advect(Mk{0, x, y}, f);
-        M.hix[id] = (int8_t)(p.ix - ri0);
+        put2(M.hq, lx, ly, p.ix - x + 1);
         M.hfx[id] = p.fx;
         if (owned(x, y)) {
           n_cfl += f.cfl;
@@ -470,9 +492,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         const int x = ri0 + lx, y = rj0 + ly;
         Flags f;
         const AP<R> p = G.advect(Mk{1, x, y}, f);
-        M.vix[id] = (int8_t)(p.ix - ri0);
+        put2(M.vq, lx, ly, p.ix - x + 1);
         M.vfx[id] = p.fx;
-        M.vfy[id] = p.fy;
         if (owned(x, y)) {
           if (x >= 1 && x <= tnx - 1) {
             n_cfl += f.cfl;
@@ -501,9 +522,13 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     __syncthreads();
 
     // P3: landings on the claimed aligned edges
+    // landings on warps 0-4, the word pass (owned edges without a landing,
+    // interface cells) on warps 5-7 at the same time
     const int nd = s_nd;
     int n_canc = 0, n_inv = 0;
-    for (int w = tid; w < nd; w += kTileThreads) {
+    constexpr int kSplit = kTileThreads - kTJ * kRW;  // 96 words on the last three warps
+    static_assert(kSplit > 0 && kSplit % 32 == 0, "warp split");
+    for (int w = tid; w < nd && tid < kSplit; w += kSplit) {
       const int id = M.ld[w], dl = id % kRX, ly = id / kRX;
       const int x = ri0 + dl, y = rj0 + ly;
       bool valid[3];
@@ -511,12 +536,12 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const int e = dl - 1 + q, ie = ly * kRX + e;
-        valid[q] = getb(M.hm, e, ly) && M.hix[ie] == dl;
+        valid[q] = getb(M.hm, e, ly) && e + get2(M.hq, e, ly) - 1 == dl;
         fx[q] = valid[q] ? M.hfx[ie] : R(0);
       }
       const Landing<R> L =
           choose_landing3<R>(valid, fx, x, getb(M.kn, dl, ly) ^ getb(M.kn, dl + 1, ly));
-      M.lsrc[id] = L.kept_src < 0 ? kNoSrc : (int8_t)(L.kept_src - x);
+      if (L.kept_src >= 0) put2(M.lq, dl, ly, L.kept_src - x + 2);
       if (owned(x, y)) {
         n_canc += L.cancelled;
         n_inv += L.invariant;
@@ -526,8 +551,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         }
       }
     }
-    for (int t0 = warp * 32; t0 < kTJ * kRW; t0 += kTileThreads) {
-      const int t = t0 + lane;  // kTJ * kRW is a multiple of 32
+    if (tid >= kSplit) {
+      const int t = tid - kSplit;  // one word each
       const int ly = 2 + t / kRW, wi = t % kRW, u = ly * kRW + wi;
       // owned aligned edges that gain a marker none landed on (the colour
       // bookkeeping excludes it): counted, fraction 0.5
@@ -631,7 +656,17 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
           const int ll = walk(TV, mA, n1, k - 1);
           C.vr = (int8_t)(lr < 0 ? -1 : !TV.knew(k, lr));
           C.vl = (int8_t)(ll < 0 ? -1 : !TV.knew(k, ll));
-          M.next[slot] = (int16_t)atomicExch(&M.head[e], slot);
+          {  // push the slot on the edge's list: 16-bit head in a shared word
+            uint32_t* hw = &M.head[e >> 1];
+            const int sh = (e & 1) * 16;
+            uint32_t old = *hw, seen;
+            do {  // each retry follows another thread's successful update
+              seen = old;
+              old = atomicCAS(hw, seen, (seen & ~(0xffffu << sh)) | ((uint32_t)slot << sh));
+            } while (old != seen);
+            const uint32_t prev = (seen >> sh) & 0xffffu;
+            M.next[slot] = prev == 0xffffu ? (int16_t)-1 : (int16_t)prev;
+          }
           atomicOr(&M.hc[eu], ebit);
         }
       }
@@ -651,7 +686,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     }
     const int rot = (int)((blockIdx.x + blockIdx.y) & 3u);
     int n_fit[4] = {0, 0, 0, 0};  // D_FIT_ONLINE .. D_FIT_TWO
-    const int vt = (((warp + rot) & (kWarps - 1)) << 5) | lane;
+    const int vt = (((warp + rot) % kWarps) << 5) | lane;
     for (int b0 = 0; b0 < 2 * ncand; b0 += kTileThreads) {
       const int item = b0 + vt, side = item & 1;
       Cand& C = M.cand[min(item >> 1, kCandCap - 1)];
@@ -731,14 +766,15 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     const int ne = s_ne;
     n_canc = 0;
     n_inv = 0;
-    for (int w = tid; w < ne; w += kTileThreads) {
+    for (int w = tid; w < ne && tid < kSplit; w += kSplit) {
       const int id = M.le[w], ex = id % kRX, ey = id / kRX;
       if (getb(M.ovf, ex, ey)) continue;
       const int k = ri0 + ex, j = rj0 + ey;
       const int e = (j - j0) * (kTI + 1) + (k - i0);
       const bool own = k < i0 + kTI;
       const int present = getb(M.kn, ex, ey) ^ getb(M.kn, ex, ey + 1);
-      const NewV<R> nv = select_linked<R>(M, M.head[e], present);
+      const uint32_t hd = (M.head[e >> 1] >> ((e & 1) * 16)) & 0xffffu;
+      const NewV<R> nv = select_linked<R>(M, hd == 0xffffu ? -1 : (int)hd, present);
       if (own) {
         n_canc += nv.cancelled;
         n_inv += nv.invariant;
@@ -749,9 +785,9 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         else out.sV[(long long)j * P + k] = nv.s;
       }
     }
-    for (int t = tid; t < kTJ * kRW; t += kTileThreads) {
+    if (tid >= kSplit && 2 + (tid - kSplit) / kRW <= ty1) {  // rows of unaligned edges only
+      const int t = tid - kSplit;
       const int ly = 2 + t / kRW, wi = t % kRW, u = ly * kRW + wi;
-      if (ly > ty1) continue;
       // edges whose candidates did not fit in the tile's list: in place
       uint32_t o = M.ovf[u];
       while (o) {
@@ -856,7 +892,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
 
 // One grid: block (bx, by) runs the tile at (64 bx, 32 by).
 template <typename R, int AX>
-__global__ void __launch_bounds__(kTileThreads, tile_min_blocks<R>())
+__global__ void __launch_bounds__(tile_threads<R>(), tile_min_blocks<R>())
 k_sweep_tile(GView<R, AX> G, Buf<R> out, int line_only, unsigned long long* ctr,
              unsigned long long* cfl_bits, int* status) {
   sweep_tile<R, AX>(G, out, line_only, ctr, cfl_bits, status, blockIdx.x * kTI, blockIdx.y * kTJ);
@@ -881,7 +917,7 @@ struct WorkItem {
 };
 
 template <typename R, int AX>
-__global__ void __launch_bounds__(kTileThreads, tile_min_blocks<R>())
+__global__ void __launch_bounds__(tile_threads<R>(), tile_min_blocks<R>())
 k_sweep_tile_batch(const SweepDesc<R, AX>* __restrict__ descs, const WorkItem* __restrict__ items) {
   const WorkItem it = items[blockIdx.x];
   const SweepDesc<R, AX>& D = descs[it.grid];
