@@ -205,6 +205,22 @@ def run_reference(args, wl, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over the ranks of the default process group."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, cells, steps, max_ms):
+    """Whole-job throughput: every rank's cell-updates over the slowest rank's time."""
+    return world * cells * steps / (max_ms / 1e3)
+
+
 def timed_steps(torch, ebit, ctx, u, v, dt, K, stream):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
     ev[0].record(stream)
@@ -230,13 +246,6 @@ def run_ours(args, wl, world, rank, local):
         if world > 1:
             tdist.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        return float(t.item())
-
     stream = torch.cuda.current_stream()
     n = wl.n
     cells = n * n
@@ -256,9 +265,9 @@ def run_ours(args, wl, world, rank, local):
     barrier()
     clk = clocks.stop()
     ebit.ebit_sync(ctx)
-    total_ms = max_over_ranks(total_ms)
+    total_ms = max_over_ranks(total_ms, world, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * cells * args.steps / (total_ms / 1e3)
+    value = job_value(world, cells, args.steps, total_ms)
     diag = ebit.ebit_diagnostics(ctx)
 
     # per-kernel durations over a second timed region (events around each of
@@ -309,8 +318,8 @@ def run_ours(args, wl, world, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    e2e_ms = max_over_ranks(max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0)))
-    e2e = {"value": world * cells * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+    e2e_ms = max_over_ranks(max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0)), world, "cuda")
+    e2e = {"value": job_value(world, cells, args.steps, e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": int(hu.numel() * 4 + hv.numel() * 4), "d2h_bytes_per_step": 8}
     ebit.ebit_destroy(ctx)
 
@@ -326,9 +335,9 @@ def run_ours(args, wl, world, rank, local):
         t64, lat64 = timed_steps(torch, ebit, ctx64, u64, v64, wl.dt, args.steps, stream)
         barrier()
         ebit.ebit_sync(ctx64)
-        t64 = max_over_ranks(t64)
+        t64 = max_over_ranks(t64, world, "cuda")
         sb = step_bytes_per_cell(8) * cells
-        fp64 = {"value": world * cells * args.steps / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / args.steps,
+        fp64 = {"value": job_value(world, cells, args.steps, t64), "unit": UNIT, "ms_per_step": t64 / args.steps,
                 "p50_ms": float(np.percentile(lat64, 50)), "p99_ms": float(np.percentile(lat64, 99)),
                 "step_roofline_frac": sb / (t64 / args.steps / 1e3) / 1e9 / hbm}
         ebit.ebit_destroy(ctx64)

@@ -342,3 +342,73 @@ def test_fp32_form_mass_error_on_translation():
     assert out[0] < 1e-12
     bound = wl.steps * 2 * math.pi * 0.15 * 2.0 ** -24 * wl.dx / (math.pi * 0.15 ** 2)
     assert out[1] <= bound
+
+
+# ---------------------------------------------------------------------------
+# EBIT-SL mode (EBIT_FIT_LINE): the straight chord instead of the circle fit
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [oracle.FP64, oracle.FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("name", list(SCENES))
+def test_step_parity_line_only(name, prec):
+    S, f, dt = SCENES[name](prec)
+    ctx = ebit.ebit_create(S.nx, S.ny, S.dx, S.prec, flags=ebit.EBIT_FIT_LINE)
+    ebit.ebit_load_state(ctx, S.K, S.Z, S.sH, S.sV, S.step_index)
+    try:
+        u, v = dev(f.u, prec), dev(f.v, prec)
+        for k in range(2):
+            ebit.ebit_step(ctx, u, v, dt)
+            r = oracle.step(S, f.u, f.v, dt, line_only=True)
+            d = ebit.ebit_diagnostics(ctx)
+            assert np.array_equal(d["counters"][:13], r["counters"][:13]), (d["counters"][:13], r["counters"][:13])
+            assert d["counters"][oracle.FIT_ONE] == 0 and d["counters"][oracle.FIT_TWO] == 0
+            assert_same_state(ebit.ebit_get_state(ctx, S.nx, S.ny), S, prec)
+            assert_same_fields(ctx, S, r, prec)
+    finally:
+        ebit.ebit_destroy(ctx)
+
+
+def test_line_only_translation_matches_table1_sl_row():
+    """The whole EBIT-SL translation at 64^2 on the GPU: the area loss the
+    paper prints for EBIT-SL (Table 1), and the oracle's value to 1e-12."""
+    wl = W.translation_workload(64)
+    ctx = ebit.ebit_init(wl.n, wl.n, wl.dx, wl.scene, flags=ebit.EBIT_FIT_LINE)
+    S = oracle.init(wl.n, wl.n, wl.dx, wl.scene)
+    try:
+        a0 = ebit.ebit_fraction(ctx)
+        u, v = dev(wl.field.u, 0), dev(wl.field.v, 0)
+        for k in range(wl.steps):
+            dt = wl.field.dt_eff(k, wl.dt)
+            ebit.ebit_step(ctx, u, v, dt)
+            oracle.step(S, wl.field.u, wl.field.v, dt, line_only=True)
+        e_gpu = abs(ebit.ebit_fraction(ctx) - a0) / a0
+        _, a1 = oracle.fraction(S)
+        _, a0o = oracle.fraction(oracle.init(wl.n, wl.n, wl.dx, wl.scene))
+        e_orc = abs(a1 - a0o) / a0o
+        assert abs(e_gpu - e_orc) <= 1e-12
+        assert abs(e_gpu / 6.83e-1 - 1) < 0.05  # Table 1, EBIT-SL, N=64
+        assert_same_state(ebit.ebit_get_state(ctx, wl.n, wl.n), S, 0)
+    finally:
+        ebit.ebit_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# the thread-per-vertex gather kernels (EBIT_SWEEP=gather), kept as a
+# differential check of the tiled sweep
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [oracle.FP64, oracle.FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["disks", "vortex", "saddle"])
+def test_gather_kernels_parity(name, prec, monkeypatch):
+    monkeypatch.setenv("EBIT_SWEEP", "gather")
+    S, f, dt = SCENES[name](prec)
+    ctx = gpu_from(S)  # the kernels are chosen when the context is created
+    monkeypatch.delenv("EBIT_SWEEP")
+    try:
+        u, v = dev(f.u, prec), dev(f.v, prec)
+        for k in range(2):
+            ebit.ebit_step(ctx, u, v, dt)
+            r = oracle.step(S, f.u, f.v, dt)
+            d = ebit.ebit_diagnostics(ctx)
+            assert np.array_equal(d["counters"][:13], r["counters"][:13])
+            assert_same_state(ebit.ebit_get_state(ctx, S.nx, S.ny), S, prec)
+    finally:
+        ebit.ebit_destroy(ctx)

@@ -175,6 +175,63 @@ def test_vortex_T8_table4_topology_loss():
     assert out[1] < out[0]
 
 
+# ---------------------------------------------------------------------------
+# EBIT-SL: the straight chord instead of the circle fit (the first version of
+# the method, which the paper's tables report beside the new one)
+# ---------------------------------------------------------------------------
+def _total_loss(S, e_area):
+    return e_area == 1.0 and oracle.loops(S)[:2] == (0, 0)
+
+
+@pytest.mark.parametrize("n", [32, 64, 128])
+def test_sl_translation_table1(n):
+    """Table 1, EBIT-SL rows: all of the reference phase is lost at N=32
+    ("NA"); above it the area and shape errors match the printed values."""
+    row = read_golden("table1_translation_sl.txt")
+    row = row[row[:, 0] == n][0]
+    wl = W.translation_workload(n)
+    S, e_area, tot = run(wl, line_only=True)
+    assert tot[oracle.INVARIANT] == 0
+    if math.isnan(row[1]):
+        assert _total_loss(S, e_area)
+        return
+    assert abs(e_area / row[1] - 1) < 0.05
+    assert abs(oracle.shape_error(S, 0.25, 0.75, 0.15) / row[2] - 1) < 0.08
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_sl_vortex_T2_table3(n):
+    """Table 3, EBIT-SL rows (paper's vortex sign, CFL 0.125)."""
+    row = read_golden("table3_vortex_T2_sl.txt")
+    row = row[row[:, 0] == n][0]
+    wl = W.vortex_workload(n, period=2.0, cfl=0.125, paper_sign=True)
+    S, e_area, tot = run(wl, line_only=True)
+    assert tot[oracle.INVARIANT] == 0
+    assert abs(e_area / row[1] - 1) < 0.05
+    assert abs(oracle.shape_error(S, 0.5, 0.75, 0.15) / row[2] - 1) < 0.08
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_sl_vortex_T8_table4_total_loss(n):
+    """Table 4, EBIT-SL rows: at N=32 and 64 the ligament case loses all of
+    the reference phase ("NA"), where the circle fit keeps most of it."""
+    row = read_golden("table4_vortex_T8_sl.txt")
+    assert math.isnan(row[row[:, 0] == n][0][1])
+    wl = W.vortex_workload(n, period=8.0, cfl=0.125, paper_sign=True)
+    S, e_area, tot = run(wl, line_only=True)
+    assert tot[oracle.INVARIANT] == 0
+    assert _total_loss(S, e_area)
+
+
+def test_sl_loses_more_than_circle_fit():
+    """The circle fit is what makes the difference (Sec. 2.2): the same
+    translation with the straight chord loses orders of magnitude more area."""
+    wl = W.translation_workload(64)
+    _, e_circle, _ = run(wl)
+    _, e_line, _ = run(wl, line_only=True)
+    assert e_line > 1e6 * max(e_circle, 1e-16)
+
+
 def test_vortex_baseline_config_runs_clean():
     """The 64x64 plain FP64 workload (mirrored vortex, CFL 0.5, 256 steps):
     invariants hold every step and the shape comes back (time reversal)."""
