@@ -39,7 +39,7 @@ UNIT = "cell-updates/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-fp64", action="store_true")
@@ -78,6 +78,18 @@ def kernel_bytes_per_cell(kind: str, esz: int) -> float:
     }[kind]
 
 
+# FP64 operations of one crossing candidate of the sweep (two circle fits and
+# their mean), counting add, sub, mul, div and sqrt as one each: the chord's
+# end points and offsets (8), per circle the third point (1.5), its offsets
+# from both ends (10), the implicit-circle coefficients (9), c0 (3), the
+# discriminant (4), sqrt (1), h (2), the near root (1), its side test (3) and
+# the shift back to the edge (1), and the mean (2).
+FIT_OPS = 8 + 2 * (1.5 + 10 + 9 + 3 + 4 + 1 + 2 + 1 + 3 + 1) + 2
+# FP64 rate of a GB300 SM: one warp instruction per 16 cycles (2 lanes/clock,
+# 1/64 of the FP32 rate), over 152 SMs.
+FP64_OPS_PER_CLOCK = 2 * 152
+
+
 def step_bytes_per_cell(esz: int) -> float:
     """The fused-step model: state read and written once, u and v read once,
     C and kappa written once (32.5 B/cell FP32, 64.5 B/cell FP64)."""
@@ -101,7 +113,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -284,12 +296,26 @@ def run_ours(args, wl, world, rank, local):
     dom = max(kt, key=lambda k: kt[k][0])
     dom_ms = kt[dom][0] / max(1, kt[dom][1])
     dom_bytes = kernel_bytes_per_cell(dom, esz) * cells
-    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    dom_gbps = dom_bytes / (dom_ms / 1e3) / 1e9
     traffic_cell, _ = traffic_record(dom)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_source": f"{peak_kind} hbm_gbs (copy)",
+    # the sweep is bound by the FP64 pipe (the circle fits), not by HBM: its
+    # roofline is the algorithmic FP64 work of its fits against the SMs'
+    # FP64 rate at the clock sampled during the timed region
+    c = diag["counters"]
+    fits_per_launch = float(c[ebit.D_FIT_ONLINE] + c[ebit.D_FIT_LINE] + c[ebit.D_FIT_ONE]
+                            + c[ebit.D_FIT_TWO]) / 2.0
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    fp64_peak = FP64_OPS_PER_CLOCK * sm_mhz * 1e6 / 1e9  # Gop/s
+    fit_ops = fits_per_launch * FIT_OPS
+    roofline = {"bound": "alu", "pipe": "fp64", "kernel": dom, "achieved": fit_ops / (dom_ms / 1e3) / 1e9,
+                "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
+                "frac": fit_ops / (dom_ms / 1e3) / 1e9 / fp64_peak,
+                "peak_source": f"derived: {FP64_OPS_PER_CLOCK} FP64 ops/clock (152 SMs x 2) x {sm_mhz:.0f} MHz",
+                "algorithmic_flops": fit_ops, "fits_per_launch": fits_per_launch, "flops_per_fit": FIT_OPS,
                 "traffic": None if traffic_cell is None else traffic_cell * cells,
-                "algorithmic_bytes": dom_bytes, "avg_launch_ms": dom_ms,
+                "avg_launch_ms": dom_ms,
+                "hbm": {"achieved": dom_gbps, "peak": hbm, "unit": "GB/s", "frac": dom_gbps / hbm,
+                        "algorithmic_bytes": dom_bytes, "peak_source": f"{peak_kind} hbm_gbs (copy)"},
                 "kernels": {k: {"ms_per_launch": (t / max(1, nl)), "launches": nl,
                                 "share": t / max(1e-12, sum(tt for tt, _ in kt.values())),
                                 "GBps": kernel_bytes_per_cell(k, esz) * cells / (t / max(1, nl) / 1e3) / 1e9
@@ -431,7 +457,9 @@ def run_batched(args):
                      "batch_steps": st["batch_steps"],
                      "step_p50_ms": float(np.percentile(lat, 50)), "step_p99_ms": float(np.percentile(lat, 99)),
                      "e_area_reversed_median": float(np.median(ea)) if ea else None,
-                     "e_area_reversed_max": float(np.max(ea)) if ea else None}
+                     "e_area_reversed_max": float(np.max(ea)) if ea else None,
+                     "autotune": {"schedule": st["schedule"], "tuned_sets": st["tuned_sets"],
+                                  "tune_ms": st["tune_ms"]}}
     sub = specs[:16]
     res, st, wall = _serve(ebit, sub, 0, budget, max_instances=1)
     out["fp64_one_at_a_time"] = {"instances": len(sub), "cell_updates": st["cell_updates"],
@@ -488,7 +516,8 @@ def run_serving(args):
             "step_p50_ms": float(np.median(lat50)) if lat50 else None,
             "step_p99_ms": float(np.percentile(lat99, 99)) if lat99 else None,
             "queue_ms_p50": float(np.median(qw)) if qw else None,
-            "queue_ms_p99": float(np.percentile(qw, 99)) if qw else None}
+            "queue_ms_p99": float(np.percentile(qw, 99)) if qw else None,
+            "autotune": {"schedule": st["schedule"], "tuned_sets": st["tuned_sets"], "tune_ms": st["tune_ms"]}}
     print(json.dumps(line), flush=True)
 
 

@@ -233,23 +233,39 @@ typedef struct {
   int64_t cell_updates;        /* n*n*steps */
 } ebit_result;
 
+/* CTA schedules of the batched launches: the order of the (grid, tile) work
+ * items. */
+typedef enum {
+  EBIT_SCHED_LARGEST_FIRST = 0,  /* grid by grid, largest grids first */
+  EBIT_SCHED_INTERLEAVED = 1,    /* tile t of every grid, then tile t+1, largest first */
+  EBIT_SCHED_SMALLEST_FIRST = 2, /* grid by grid, smallest grids first */
+  EBIT_SCHED_COUNT = 3
+} ebit_schedule;
+
 typedef struct {
   int32_t max_instances;       /* 0: no limit besides the budget */
   int32_t use_graphs;          /* replay each batch step as a CUDA graph */
   int32_t device;              /* CUDA device ordinal */
+  int32_t autotune;            /* 1: time every schedule on the first steps of a new set of
+                                  grids and keep the fastest (cached per set signature);
+                                  0: use `schedule` */
+  int32_t schedule;            /* ebit_schedule when autotune is 0 */
 } ebit_server_opts;
 
 typedef struct {
   int64_t queued, running, batch_steps, cell_updates;
   double busy_ms;              /* GPU time of the batch steps */
   size_t bytes_in_use;
+  int32_t schedule;            /* ebit_schedule of the current set of grids */
+  int32_t tuned_sets;          /* set signatures whose schedule the autotuner has chosen */
+  double tune_ms[EBIT_SCHED_COUNT];  /* step time of each schedule, last tuning (0: not timed) */
 } ebit_server_stats;
 
 typedef struct ebit_server ebit_server;
 
 /* hbm_budget: device bytes the admitted requests may use together.  opts may
- * be NULL (graphs on, device 0).  No CUDA call happens before the first
- * admissible submission. */
+ * be NULL (graphs on, autotuned schedules, device 0).  No CUDA call happens
+ * before the first admissible submission. */
 ebit_status ebit_server_create(ebit_server** out, size_t hbm_budget, const ebit_server_opts* opts);
 /* EBIT_EINVAL for a malformed request; EBIT_EFULL if it can never fit the
  * budget.  Otherwise queues it and returns its ticket. */

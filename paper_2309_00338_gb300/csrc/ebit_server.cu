@@ -6,9 +6,10 @@
 // from pinned host memory, four sweep launches (x-first grids' first sweep,
 // y-first grids' first sweep, then the two second sweeps; a grid that is not
 // due in a launch is skipped by its blocks), the fields launch and the area
-// launch.  Work items are (grid, tile) pairs, largest grids first.  The
-// sequence is captured once per set of admitted grids as a CUDA graph and
-// replayed every step.  Grids keep their state in the same buffer across a
+// launch.  Work items are (grid, tile) pairs in the order of a CTA schedule
+// that an online autotuner picks per set of grids (ebit_schedule).  The
+// sequence is captured once per set of admitted grids (and schedule) as a
+// CUDA graph and replayed every step.  Grids keep their state in the same buffer across a
 // step (first sweep A->B, second B->A).
 //
 // Serving: one worker thread owns the GPU.  Between batch steps it retires
@@ -154,34 +155,40 @@ struct Group {
     *this = Group<R>();
   }
 
-  ebit_status build(const std::vector<Instance*>& all, int prec, cudaStream_t st) {
+  ebit_status build(const std::vector<Instance*>& all, int prec, int schedule, cudaStream_t st) {
     release();
     for (Instance* in : all)
       if (in->req.prec == prec) inst.push_back(in);
     if (inst.empty()) return EBIT_OK;
-    // largest grids first so their many tiles start early
-    std::stable_sort(inst.begin(), inst.end(),
-                     [](const Instance* a, const Instance* b) { return a->req.n > b->req.n; });
+    if (schedule == EBIT_SCHED_SMALLEST_FIRST)
+      std::stable_sort(inst.begin(), inst.end(),
+                       [](const Instance* a, const Instance* b) { return a->req.n < b->req.n; });
+    else
+      std::stable_sort(inst.begin(), inst.end(),
+                       [](const Instance* a, const Instance* b) { return a->req.n > b->req.n; });
     const size_t n = inst.size();
-    std::vector<ebit::WorkItem> it0, it1;
-    std::vector<ebit::FieldItem> fit;
+    // per grid, its tiles in row order; then the CTA schedule orders them
+    std::vector<std::vector<ebit::WorkItem>> g0(n), g1(n);
+    std::vector<std::vector<ebit::FieldItem>> gf(n);
     std::vector<ebit::FieldDesc<R>> fd(n);
     std::vector<AreaDesc> ad(n);
     for (size_t g = 0; g < n; ++g) {
       const ebit_ctx* c = inst[g]->ctx;
       const ebit::Dims& d = c->L.d;
       for (int ty = 0; ty < (d.ny + 1 + ebit::kTJ - 1) / ebit::kTJ; ++ty)
-        for (int tx = 0; tx < (d.nx + 1 + ebit::kTI - 1) / ebit::kTI; ++tx) it0.push_back({(int)g, tx, ty});
+        for (int tx = 0; tx < (d.nx + 1 + ebit::kTI - 1) / ebit::kTI; ++tx) g0[g].push_back({(int)g, tx, ty});
       for (int ty = 0; ty < (d.nx + 1 + ebit::kTJ - 1) / ebit::kTJ; ++ty)
-        for (int tx = 0; tx < (d.ny + 1 + ebit::kTI - 1) / ebit::kTI; ++tx) it1.push_back({(int)g, tx, ty});
+        for (int tx = 0; tx < (d.ny + 1 + ebit::kTI - 1) / ebit::kTI; ++tx) g1[g].push_back({(int)g, tx, ty});
       const int fx = (d.nx + 1 + ebit::kFX - 1) / ebit::kFX, fy = (d.ny + 1 + ebit::kFY - 1) / ebit::kFY;
       for (int ty = 0; ty < fy; ++ty)
-        for (int tx = 0; tx < fx; ++tx) fit.push_back({(int)g, tx, ty});
+        for (int tx = 0; tx < fx; ++tx) gf[g].push_back({(int)g, tx, ty});
       const int b = c->cur;
       fd[g] = ebit::FieldDesc<R>{c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], d,
                                  (R)c->grid.dx, (R*)c->C, (R*)c->kappa, c->partial, c->ctr, fx};
       ad[g] = AreaDesc{c->partial, (long long)fx * fy, c->grid.dx * c->grid.dx, c->area};
     }
+    const std::vector<ebit::WorkItem> it0 = order(g0, schedule), it1 = order(g1, schedule);
+    const std::vector<ebit::FieldItem> fit = order(gf, schedule);
     n_items0 = (int)it0.size();
     n_items1 = (int)it1.size();
     n_fitems = (int)fit.size();
@@ -205,6 +212,23 @@ struct Group {
       return fail_s(EBIT_ENOMEM, "cudaMallocHost (batch plan)");
     }
     return cudaStreamSynchronize(st) == cudaSuccess ? EBIT_OK : fail_s(EBIT_ECUDA, "plan upload");
+  }
+
+  // The work items of all grids in the order of the CTA schedule: grid by
+  // grid, or round robin (tile t of every grid before tile t+1).
+  template <typename Item>
+  static std::vector<Item> order(const std::vector<std::vector<Item>>& per_grid, int schedule) {
+    std::vector<Item> out;
+    if (schedule != EBIT_SCHED_INTERLEAVED) {
+      for (const auto& v : per_grid) out.insert(out.end(), v.begin(), v.end());
+      return out;
+    }
+    size_t longest = 0;
+    for (const auto& v : per_grid) longest = std::max(longest, v.size());
+    for (size_t t = 0; t < longest; ++t)
+      for (const auto& v : per_grid)
+        if (t < v.size()) out.push_back(v[t]);
+    return out;
   }
 
   // Descriptors of the coming step: lam and the split order of every grid.
@@ -285,8 +309,24 @@ struct ebit_server {
   cudaStream_t stream = nullptr;
   Group<float> g32;
   Group<double> g64;
-  bool dirty = true;
+  bool dirty = true;   // the set of grids changed: new plans, new schedule choice
+  bool replan = false; // same set, another schedule (autotuning)
   cudaGraphExec_t graph = nullptr;
+  // CTA-schedule autotuner: the first kTuneSteps steps of a new set of grids
+  // run under each schedule in turn (the work and its results do not depend
+  // on the order, so no step is wasted); the fastest is kept for the set and
+  // for later sets with the same signature
+  static constexpr int kTuneSteps = 2;
+  int sched = EBIT_SCHED_LARGEST_FIRST;
+  bool tuning = false;
+  uint64_t sig = 0;
+  double tune_acc[EBIT_SCHED_COUNT] = {0.0, 0.0, 0.0};
+  int tune_cnt[EBIT_SCHED_COUNT] = {0, 0, 0};
+  double last_tune_ms[EBIT_SCHED_COUNT] = {0.0, 0.0, 0.0};
+  std::map<uint64_t, int> tuned;
+
+  uint64_t signature(const std::vector<Instance*>& all) const;
+  void tune_after(float ms);
 
   void run();
   ebit_status admit(Instance* in);
@@ -366,12 +406,31 @@ ebit_status ebit_server::step() {
   for (auto& p : active) all.push_back(p.get());
   ebit_status s;
   if (dirty) {
+    sig = signature(all);
+    tuning = false;
+    if (!opts.autotune) {
+      sched = (opts.schedule >= 0 && opts.schedule < EBIT_SCHED_COUNT) ? opts.schedule : 0;
+    } else {
+      const auto it = tuned.find(sig);
+      if (it != tuned.end()) {
+        sched = it->second;
+      } else {
+        tuning = true;
+        sched = 0;
+        for (int q = 0; q < EBIT_SCHED_COUNT; ++q) {
+          tune_acc[q] = 0.0;
+          tune_cnt[q] = 0;
+        }
+      }
+    }
+  }
+  if (dirty || replan) {
     if (graph) {
       cudaGraphExecDestroy(graph);
       graph = nullptr;
     }
-    if ((s = g32.build(all, EBIT_FP32, stream)) != EBIT_OK) return s;
-    if ((s = g64.build(all, EBIT_FP64, stream)) != EBIT_OK) return s;
+    if ((s = g32.build(all, EBIT_FP32, sched, stream)) != EBIT_OK) return s;
+    if ((s = g64.build(all, EBIT_FP64, sched, stream)) != EBIT_OK) return s;
     if (opts.use_graphs) {
       cudaGraph_t gr = nullptr;
       if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
@@ -384,6 +443,7 @@ ebit_status ebit_server::step() {
       if (e != cudaSuccess) return fail_s(EBIT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     }
     dirty = false;
+    replan = false;
   }
   g32.fill();
   g64.fill();
@@ -403,6 +463,7 @@ ebit_status ebit_server::step() {
   cudaEventElapsedTime(&ms, a, b);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  if (tuning) tune_after(ms);
   int64_t cells = 0;
   for (Instance* in : all) {
     in->lat_ms.push_back(ms);
@@ -415,6 +476,41 @@ ebit_status ebit_server::step() {
   cell_updates += cells;
   busy_ms += ms;
   return EBIT_OK;
+}
+
+// Coarse signature of a set of grids: the number of grids and the total cell
+// count per precision, on a logarithmic scale.
+uint64_t ebit_server::signature(const std::vector<Instance*>& all) const {
+  uint64_t cnt[2] = {0, 0}, cells[2] = {0, 0};
+  for (const Instance* in : all) {
+    const int p = in->req.prec == EBIT_FP32 ? 1 : 0;
+    cnt[p] += 1;
+    cells[p] += (uint64_t)in->req.n * in->req.n;
+  }
+  auto lg = [](uint64_t v) { return v ? (uint64_t)(64 - __builtin_clzll(v)) : 0ull; };
+  return lg(cnt[0]) | (lg(cnt[1]) << 8) | (lg(cells[0]) << 16) | (lg(cells[1]) << 24);
+}
+
+void ebit_server::tune_after(float ms) {
+  tune_acc[sched] += ms;
+  tune_cnt[sched] += 1;
+  if (tune_cnt[sched] < kTuneSteps) return;
+  if (sched + 1 < EBIT_SCHED_COUNT) {
+    sched += 1;
+    replan = true;
+    return;
+  }
+  int best = 0;
+  for (int q = 0; q < EBIT_SCHED_COUNT; ++q) {
+    last_tune_ms[q] = tune_acc[q] / tune_cnt[q];
+    if (last_tune_ms[q] < last_tune_ms[best]) best = q;
+  }
+  tuned[sig] = best;
+  tuning = false;
+  if (best != sched) {
+    sched = best;
+    replan = true;
+  }
 }
 
 void ebit_server::run() {
@@ -513,8 +609,12 @@ ebit_status ebit_server_create(ebit_server** out, size_t hbm_budget, const ebit_
   ebit_server* s = new (std::nothrow) ebit_server;
   if (!s) return fail_s(EBIT_ENOMEM, "host allocation failed");
   s->budget = hbm_budget;
-  if (opts) s->opts = *opts;
-  else s->opts.use_graphs = 1;
+  if (opts) {
+    s->opts = *opts;
+  } else {
+    s->opts.use_graphs = 1;
+    s->opts.autotune = 1;
+  }
   *out = s;
   return EBIT_OK;
 }
@@ -571,6 +671,9 @@ ebit_status ebit_server_stats_get(ebit_server* s, ebit_server_stats* out) {
   out->cell_updates = s->cell_updates;
   out->busy_ms = s->busy_ms;
   out->bytes_in_use = s->in_use;
+  out->schedule = s->sched;
+  out->tuned_sets = (int32_t)s->tuned.size();
+  for (int q = 0; q < EBIT_SCHED_COUNT; ++q) out->tune_ms[q] = s->last_tune_ms[q];
   return EBIT_OK;
 }
 

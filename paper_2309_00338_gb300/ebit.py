@@ -293,15 +293,21 @@ class ebit_result(ctypes.Structure):
                 ("counters", ctypes.c_int64 * D_COUNT), ("cell_updates", ctypes.c_int64)]
 
 
+EBIT_SCHED_LARGEST_FIRST, EBIT_SCHED_INTERLEAVED, EBIT_SCHED_SMALLEST_FIRST, EBIT_SCHED_COUNT = range(4)
+
+
 class ebit_server_opts(ctypes.Structure):
     _fields_ = [("max_instances", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-                ("device", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("schedule", ctypes.c_int32)]
 
 
 class ebit_server_stats(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int64), ("running", ctypes.c_int64),
                 ("batch_steps", ctypes.c_int64), ("cell_updates", ctypes.c_int64),
-                ("busy_ms", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t)]
+                ("busy_ms", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t),
+                ("schedule", ctypes.c_int32), ("tuned_sets", ctypes.c_int32),
+                ("tune_ms", ctypes.c_double * EBIT_SCHED_COUNT)]
 
 
 SIGNATURES.update({
@@ -317,8 +323,10 @@ if _lib is not None:  # signatures added after an earlier load
         _f.restype, _f.argtypes = SIGNATURES[_n]
 
 
-def ebit_server_create(hbm_budget, max_instances=0, use_graphs=True, device=0):
-    o = ebit_server_opts(int(max_instances), int(bool(use_graphs)), int(device))
+def ebit_server_create(hbm_budget, max_instances=0, use_graphs=True, device=0, autotune=True,
+                       schedule=EBIT_SCHED_LARGEST_FIRST):
+    o = ebit_server_opts(int(max_instances), int(bool(use_graphs)), int(device), int(bool(autotune)),
+                         int(schedule))
     h = ctypes.c_void_p()
     _check(lib().ebit_server_create(ctypes.byref(h), int(hbm_budget), ctypes.byref(o)), "ebit_server_create")
     return h
@@ -368,7 +376,8 @@ def ebit_server_stats_get(server):
     s = ebit_server_stats()
     _check(lib().ebit_server_stats_get(server, ctypes.byref(s)), "ebit_server_stats_get")
     return {"queued": s.queued, "running": s.running, "batch_steps": s.batch_steps,
-            "cell_updates": s.cell_updates, "busy_ms": s.busy_ms, "bytes_in_use": s.bytes_in_use}
+            "cell_updates": s.cell_updates, "busy_ms": s.busy_ms, "bytes_in_use": s.bytes_in_use,
+            "schedule": s.schedule, "tuned_sets": s.tuned_sets, "tune_ms": list(s.tune_ms)}
 
 
 def ebit_server_destroy(server):

@@ -36,8 +36,8 @@ def _mix():
     return reqs
 
 
-def _run(specs, budget, use_graphs=True):
-    s = ebit.ebit_server_create(budget, use_graphs=use_graphs)
+def _run(specs, budget, use_graphs=True, autotune=True, schedule=0):
+    s = ebit.ebit_server_create(budget, use_graphs=use_graphs, autotune=autotune, schedule=schedule)
     keep, outs, tickets = [], [], []
     try:
         for sp in specs:
@@ -76,6 +76,24 @@ def test_graphs_and_plain_launches_agree():
     b, Cb, _ = _run(specs, 8 << 30, use_graphs=False)
     for ra, rb, ca, cb in zip(a, b, Ca, Cb):
         assert ra["area"] == rb["area"] and np.array_equal(ca, cb)
+
+
+def test_results_do_not_depend_on_the_cta_schedule():
+    """Every fixed CTA schedule and the autotuned one give identical results;
+    with all grids admitted at once the autotuner times every schedule."""
+    specs = _mix()
+    for sp in specs:
+        sp["steps"] = max(sp["steps"], 3 * ebit.EBIT_SCHED_COUNT)
+    tuned, Ct, stats = _run(specs, 8 << 30, autotune=True)
+    assert stats["tuned_sets"] >= 1
+    assert all(t > 0.0 for t in stats["tune_ms"])
+    assert 0 <= stats["schedule"] < ebit.EBIT_SCHED_COUNT
+    for sched in range(ebit.EBIT_SCHED_COUNT):
+        fixed, Cf, st = _run(specs, 8 << 30, autotune=False, schedule=sched)
+        assert st["schedule"] == sched and st["tuned_sets"] == 0
+        for rt, rf, ct, cf in zip(tuned, fixed, Ct, Cf):
+            assert rt["area"] == rf["area"] and np.array_equal(ct, cf)
+            assert np.array_equal(rt["counters"], rf["counters"])
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
