@@ -68,8 +68,9 @@ def kernel_bytes_per_cell(kind: str, esz: int) -> float:
     or written once); K and Z are 1 bit per vertex / cell."""
     bits = 0.125
     return {
-        # reads K, Z, sH, sV, velocity; writes K, sH, sV, two verdict bytes
-        "sweep": (2 * bits + 3 * esz) + (bits + 2 * esz + 2.0),
+        # the tiled sweep: reads K, Z, sH, sV and the velocity component,
+        # writes K, Z, sH, sV (20.5 B/cell FP32, 40.5 FP64)
+        "sweep": (2 * bits + 3 * esz) + (2 * bits + 2 * esz),
         # reads new K, old Z, verdicts; writes Z
         "centre": 2 * bits + 2.0 + bits,
         # reads K, Z, sH, sV; writes C and kappa

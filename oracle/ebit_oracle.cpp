@@ -23,6 +23,12 @@
 // Readings of passages that the paper leaves open are stated where they are
 // used; each one is listed in the design notes of the repository.
 //
+// Parity unpinned: the exact centre colour that the rule of Sec. 2.3 gives a
+// cell that becomes a saddle (four markers) in a sweep.  The paper prints no
+// value for it; the tests pin only the loop counts it implies (merging along
+// x, two loops along the diagonal), and the GPU must agree with this code
+// bit for bit.
+//
 // Floating point: built with -ffp-contract=off so that every expression is the
 // sequence of IEEE operations written here.  R is the state precision (double
 // for the FP64 form, float for the FP32 form); the circle fit and the fraction
