@@ -240,7 +240,7 @@ ebit_status init_scene(ebit_ctx* c, const ebit_scene* scene) {
   ebit_status s;
   if ((s = talloc((void**)&dcirc, circ.size() * sizeof(double))) != EBIT_OK ||
       (s = talloc((void**)&dcurve, curve.size() * sizeof(double))) != EBIT_OK ||
-      (s = talloc((void**)&hv, (size_t)(c->grid.nx + 1) * sizeof(double))) != EBIT_OK ||
+      (s = talloc((void**)&hv, (size_t)(2 * c->grid.nx + 1) * sizeof(double))) != EBIT_OK ||
       (s = talloc((void**)&ownH, (size_t)(c->grid.ny + 1) * L.d.P * sizeof(int))) != EBIT_OK ||
       (s = talloc((void**)&ownV, (size_t)(c->grid.ny + 1) * L.d.P * sizeof(int))) != EBIT_OK) {
     cleanup();

@@ -192,10 +192,13 @@ __device__ __forceinline__ bool in_line(const SceneDev& sc, double x, double y) 
   return sc.la * x + sc.lb * y <= sc.lc;
 }
 
-// Curve heights at the vertex columns (hv[i], x = i dx).
+// Curve heights at the vertex columns (hv[i], x = i dx) and at the cell-centre
+// columns (hv[nx + 1 + i], x = (i + 0.5) dx): the curve depends on x only, so
+// each column's height is evaluated once.
 __global__ void k_curve_cols(SceneDev sc, int nx, double dx, double* hv) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i <= nx) hv[i] = curve_h(sc, i * dx);
+  if (i < nx) hv[nx + 1 + i] = curve_h(sc, (i + 0.5) * dx);
 }
 
 // Base phase of vertices (K) and cell centres (Z) from the curve and line.
@@ -210,7 +213,7 @@ k_init_base(SceneDev sc, Dims d, double dx, const double* hv, uint32_t* K, uint3
   }
   if (x < d.nx && y < d.ny) {
     const double cx = (x + 0.5) * dx, cy = (y + 0.5) * dx;
-    if (sc.has_curve) pz ^= cy <= curve_h(sc, cx);
+    if (sc.has_curve) pz ^= cy <= hv[d.nx + 1 + x];
     if (sc.has_line) pz ^= in_line(sc, cx, cy);
   }
   const unsigned wk = __ballot_sync(0xffffffffu, (x <= d.nx && y <= d.ny) && pk);

@@ -272,6 +272,20 @@ struct TViewB {
 // generation order).
 template <typename R>
 __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int present) {
+  if (s >= 0 && M.next[s] < 0 && present) {
+    // one candidate on an edge that keeps a marker: it is the marker (the
+    // common case, without the ranking below)
+    const Cand& C = M.cand[s];
+    NewV<R> one;
+    one.present = 1;
+    one.vr = C.vr;
+    one.vl = C.vl;
+    one.cancelled = 0;
+    one.invariant = 0;
+    if constexpr (sizeof(R) == 4) one.s = C.sf;
+    else one.s = to_fraction<R>(C.y);
+    return one;
+  }
   double cy[6];
   float sf[6];
   long long key[6];
