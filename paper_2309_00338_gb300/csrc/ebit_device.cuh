@@ -379,6 +379,24 @@ template <typename R> __device__ __forceinline__ double to_d(R x);
 template <> __device__ __forceinline__ double to_d<float>(float x) { return f2d(x); }
 template <> __device__ __forceinline__ double to_d<double>(double x) { return x; }
 
+// (double)n + (double)f for an integer |n| <= 7 and a float 0 <= f < 1, the
+// value the FP64 addition gives.  When f >= 2^-26 the sum has at most 53
+// significant bits, so it is exact and is formed by integer operations;
+// smaller f take the FP64 addition.
+__device__ __forceinline__ double add_nf(int n, float f) {
+  const unsigned u = __float_as_uint(f);
+  if (u == 0u) return i2d(n);
+  const int e = (int)(u >> 23);
+  if (e < 101 || n < -7 || n > 7) return i2d(n) + f2d(f);
+  const int sh = 150 - e;  // f = m 2^-sh with 24 <= sh <= 49
+  const long long S = (long long)n * (1ll << sh) + (long long)((u & 0x7fffffu) | 0x800000u);
+  const unsigned long long sign = S < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long a = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+  const int p = 63 - __clzll((long long)a);  // leading bit; p <= sh + 3 <= 52
+  const unsigned long long mant = (a << (52 - p)) & 0xfffffffffffffull;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(1023 + p - sh) << 52) | mant));
+}
+
 // ---------------------------------------------------------------------------
 // Circle fit (Sec. 2.2, Fig. 3).  Coordinates in cells relative to vertex
 // (k,j): the grid line is x = 0, the edge's band 0 <= y <= 1.  Circle through
@@ -405,11 +423,12 @@ __device__ __forceinline__ FitPt fit_pt(double X, double Y, double Ax, double Ay
   return p;
 }
 
-// q = B - A, q2 = |q|^2.
-__device__ __forceinline__ bool circle_cross(double Ay, double x0, double qx, double qy, double q2,
-                                             const FitPt& T, double* y) {
-  if (d_below_sep(T.r2) || d_below_sep(T.t2)) return false;
-  const double rx = T.rx, ry = T.ry, r2 = T.r2;
+// q = B - A, q2 = |q|^2; (rx, ry) = T - A with r2 = |T - A|^2; t_far: T is
+// at least the minimum separation away from B.
+__device__ __forceinline__ bool circle_cross_r(double Ay, double x0, double qx, double qy,
+                                               double q2, double rx, double ry, double r2,
+                                               bool t_far, double* y) {
+  if (d_below_sep(r2) || !t_far) return false;
   const double kap = qx * ry - qy * rx;
   const double al = r2 * qy - q2 * ry;
   const double be = q2 * rx - r2 * qx;
@@ -435,6 +454,11 @@ __device__ __forceinline__ bool circle_cross(double Ay, double x0, double qx, do
   if (!d_in01(best)) return false;
   *y = best;
   return true;
+}
+
+__device__ __forceinline__ bool circle_cross(double Ay, double x0, double qx, double qy, double q2,
+                                             const FitPt& T, double* y) {
+  return circle_cross_r(Ay, x0, qx, qy, q2, T.rx, T.ry, T.r2, !d_below_sep(T.t2), y);
 }
 
 // Returns the fit kind (D_FIT_*) and the crossing ordinate; T1 (point 1) is

@@ -265,6 +265,36 @@ struct TViewB {
       *Y = i2d(rj0 + ly - j);
     }
   }
+  // An unaligned marker's own fraction (its y in the sweep), read from the
+  // state; 0 for an aligned marker.
+  __device__ __forceinline__ R own_fraction(uint16_t r) const {
+    if (!(r & kKindV)) return R(0);
+    const int t = r & (kKindV - 1), ly = t / kRX, lx = t - ly * kRX;
+    return g->v(ri0 + lx, rj0 + ly);
+  }
+  // The point in the FP32 form, given its own fraction fy: the exact sums by
+  // integer operations where they are exact (add_nf), and a float estimate
+  // (Xf, Yf) within 2^-22 of each coordinate.
+  __device__ __forceinline__ void xyf(uint16_t r, int k, int j, float fy, double* X, double* Y,
+                                      float* Xf, float* Yf) const {
+    const int t = r & (kKindV - 1), ly = t / kRX, lx = t - ly * kRX;
+    const int ny = rj0 + ly - j;
+    int nx;
+    float fx;
+    if (r & kKindV) {
+      nx = ri0 + lx + get2(m->vq, lx, ly) - 1 - k;
+      fx = (float)m->vfx[t];
+      *Y = add_nf(ny, fy);
+    } else {
+      nx = ri0 + lx + get2(m->hq, lx, ly) - 1 - k;
+      fx = (float)m->hfx[t];
+      fy = 0.0f;
+      *Y = i2d(ny);
+    }
+    *X = add_nf(nx, fx);
+    *Xf = (float)nx + fx;
+    *Yf = (float)ny + fy;
+  }
 };
 
 // One marker per edge from its linked candidates (the rule of
@@ -714,8 +744,22 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       // the pair shares the chord: the even lane converts A and forms cx,
       // the odd lane B and cy, and they swap (shuffles instead of FP64 work)
       double px = 0.0, py = 0.0;
-      if (act) TV.xy(side ? C.b : C.a, k, j, &px, &py);
+      float pxf = 0.0f, pyf = 0.0f, fy_t = 0.0f, fy_q = 0.0f;
+      if (act) {
+        if constexpr (sizeof(R) == 4) {
+          // the state reads this lane needs, issued together
+          const uint8_t fl = C.fl;
+          const float fy_ab = TV.own_fraction(side ? C.b : C.a);
+          if (fl & (side ? CF_P4 : CF_P1)) fy_t = TV.own_fraction(side ? C.p4 : C.p1);
+          if (fl & (side ? CF_Q4 : CF_Q1)) fy_q = TV.own_fraction(side ? C.q4 : C.q1);
+          TV.xyf(side ? C.b : C.a, k, j, fy_ab, &px, &py, &pxf, &pyf);
+        } else {
+          TV.xy(side ? C.b : C.a, k, j, &px, &py);
+        }
+      }
       const double ox = __shfl_xor_sync(kFull, px, 1), oy = __shfl_xor_sync(kFull, py, 1);
+      const float oxf = __shfl_xor_sync(kFull, pxf, 1), oyf = __shfl_xor_sync(kFull, pyf, 1);
+      const float bxf = side ? pxf : oxf, byf = side ? pyf : oyf;  // B, estimated in float
       const double ax = side ? ox : px, ay = side ? oy : py;
       const double bx = side ? px : ox, by = side ? py : oy;
       const double dd = side ? by - ay : bx - ax;
@@ -730,19 +774,49 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       if (act && !online) {
         const uint8_t fl = C.fl;
         if (!line_only && !d_below_sep(c2) && (fl & (side ? CF_P4 : CF_P1))) {
-          double X, Y;
-          TV.xy(side ? C.p4 : C.p1, k, j, &X, &Y);
-          FitPt T = fit_pt(X, Y, ax, ay, bx, by);
-          bool use = true;
-          if (d_below_sep(side ? T.t2 : T.r2)) {  // too close to A (B): the next marker
-            if (fl & (side ? CF_Q4 : CF_Q1)) {
-              TV.xy(side ? C.q4 : C.q1, k, j, &X, &Y);
-              T = fit_pt(X, Y, ax, ay, bx, by);
-            } else {
-              use = false;
+          if constexpr (sizeof(R) == 4) {
+            // the third point's offsets from A exactly; its distance from B
+            // only where a float estimate (error below 2e-6 per component)
+            // does not already put it clearly past the minimum separation
+            double rx, ry, r2;
+            bool tfar;
+            auto third = [&](uint16_t ref, float fy) {
+              double X, Y;
+              float Xf, Yf;
+              TV.xyf(ref, k, j, fy, &X, &Y, &Xf, &Yf);
+              rx = X - ax;
+              ry = Y - ay;
+              r2 = rx * rx + ry * ry;
+              const float txf = Xf - bxf, tyf = Yf - byf;
+              if (txf * txf + tyf * tyf >= 1.5e-4f) {
+                tfar = true;
+              } else {
+                const double tx = X - bx, ty = Y - by;
+                tfar = !d_below_sep(tx * tx + ty * ty);
+              }
+            };
+            third(side ? C.p4 : C.p1, fy_t);
+            bool use = true;
+            if (side ? !tfar : d_below_sep(r2)) {  // too close to B (A): the next marker
+              if (fl & (side ? CF_Q4 : CF_Q1)) third(side ? C.q4 : C.q1, fy_q);
+              else use = false;
             }
+            if (use) ok = circle_cross_r(ay, x0, cx, cy, c2, rx, ry, r2, tfar, &ys);
+          } else {
+            double X, Y;
+            TV.xy(side ? C.p4 : C.p1, k, j, &X, &Y);
+            FitPt T = fit_pt(X, Y, ax, ay, bx, by);
+            bool use = true;
+            if (d_below_sep(side ? T.t2 : T.r2)) {  // too close to A (B): the next marker
+              if (fl & (side ? CF_Q4 : CF_Q1)) {
+                TV.xy(side ? C.q4 : C.q1, k, j, &X, &Y);
+                T = fit_pt(X, Y, ax, ay, bx, by);
+              } else {
+                use = false;
+              }
+            }
+            if (use) ok = circle_cross(ay, x0, cx, cy, c2, T, &ys);
           }
-          if (use) ok = circle_cross(ay, x0, cx, cy, c2, T, &ys);
         }
       }
       const double yo = __shfl_xor_sync(kFull, ys, 1);
