@@ -166,10 +166,14 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
     pos = incl - n;
     if (lane == 31) s_woff[warp] = incl;
   }
-  // fractions of full and empty cells
-  for (int t = tid; t < kFRY * kFRX; t += kFieldThreads) {
-    const int lx = t % kFRX, ly = t / kFRX;
-    if (!fgetb(iw, lx, ly)) cs[t] = fgetb(fw, lx, ly) ? R(1) : R(0);
+  // fractions of full and empty cells, a warp per region row
+  for (int ly = warp; ly < kFRY; ly += kFieldThreads / 32) {
+#pragma unroll
+    for (int w = 0; w < kFW; ++w) {
+      const int lx = 32 * w + lane;
+      const uint32_t f = fw[ly * kFW + w], ic = iw[ly * kFW + w];
+      if (lx < kFRX && !((ic >> lane) & 1u)) cs[ly * kFRX + lx] = ((f >> lane) & 1u) ? R(1) : R(0);
+    }
   }
   __syncthreads();
   if (warp < (kWords + 31) / 32) {
