@@ -56,6 +56,7 @@ class _Scene(ctypes.Structure):
         ("amp", ctypes.c_void_p), ("phase", ctypes.c_void_p),
         ("has_line", ctypes.c_int32), ("la", ctypes.c_double), ("lb", ctypes.c_double),
         ("lc", ctypes.c_double),
+        ("nnotches", ctypes.c_int32), ("notch", ctypes.c_void_p),
     ]
 
 
@@ -188,6 +189,11 @@ def _scene_struct(scene, keep):
     if line is not None:
         sc.has_line = 1
         sc.la, sc.lb, sc.lc = (float(t) for t in line)
+    notches = scene.get("notches")
+    if notches:
+        nb = np.ascontiguousarray(np.asarray(notches, np.float64).reshape(-1, 4))
+        keep.append(nb)
+        sc.nnotches, sc.notch = nb.shape[0], nb.ctypes.data
     return sc
 
 

@@ -778,6 +778,31 @@ struct Scene {
     const double ddx = x - s->xc[c], ddy = y - s->yc[c];
     return ddx * ddx + ddy * ddy <= s->r[c] * s->r[c];
   }
+  bool in_notch(double x, double y) const {
+    for (int b = 0; b < s->nnotches; ++b) {
+      const double* q = s->notch + 4 * b;
+      if (x >= q[0] && x <= q[1] && y >= q[2] && y <= q[3]) return true;
+    }
+    return false;
+  }
+  // The scene's phase at a point: curve, line and circles toggle it, then
+  // the notches cut it out.
+  bool inside(double x, double y) const {
+    bool p = false;
+    if (s->has_curve) p ^= in_curve(x, y);
+    if (s->has_line) p ^= in_line(x, y);
+    for (int c = 0; c < s->ncircles; ++c) p ^= in_circle(c, x, y);
+    return p && !in_notch(x, y);
+  }
+  // Does the edge from (xa, ya) to (xb, yb) (axis-aligned, xa <= xb, ya <= yb)
+  // touch a notch box?
+  bool touches_notch(double xa, double ya, double xb, double yb) const {
+    for (int b = 0; b < s->nnotches; ++b) {
+      const double* q = s->notch + 4 * b;
+      if (xb >= q[0] && xa <= q[1] && yb >= q[2] && ya <= q[3]) return true;
+    }
+    return false;
+  }
 };
 
 template <typename R>
@@ -819,22 +844,32 @@ void init(State<R>& S, double dx, const orc_scene* sc) {
         if (i < nx && j < ny && P.in_circle(c, (i + 0.5) * dx, (j + 0.5) * dx)) S.z(i, j) ^= 1;
       }
   }
-  // Owner of each edge's marker: the curve, then the line, then the circle of
-  // lowest index whose own inside test differs at the two ends of the edge.
-  const int OWN_NONE = -3, OWN_CURVE = -2, OWN_LINE = -1;
+  // notches: vertices and cell centres inside a box leave the reference phase
+  if (sc->nnotches)
+    for (int j = 0; j <= ny; ++j)
+      for (int i = 0; i <= nx; ++i) {
+        if (P.in_notch(i * dx, j * dx)) S.k(i, j) = 0;
+        if (i < nx && j < ny && P.in_notch((i + 0.5) * dx, (j + 0.5) * dx)) S.z(i, j) = 0;
+      }
+  // Owner of each edge's marker: a notch when the edge touches one of the
+  // boxes, else the curve, then the line, then the circle of lowest index
+  // whose own inside test differs at the two ends of the edge.
+  const int OWN_NOTCH = -4, OWN_NONE = -3, OWN_CURVE = -2, OWN_LINE = -1;
   std::vector<int32_t> ownH((size_t)nx * (ny + 1), OWN_NONE), ownV((size_t)(nx + 1) * ny, OWN_NONE);
   for (int j = 0; j <= ny; ++j)
     for (int i = 0; i < nx; ++i) {
       if (!S.hasH(i, j)) continue;
       int32_t& o = ownH[(size_t)j * nx + i];
-      if (sc->has_curve && ((j * dx) <= hcol[i]) != ((j * dx) <= hcol[i + 1])) o = OWN_CURVE;
+      if (sc->nnotches && P.touches_notch(i * dx, j * dx, (i + 1) * dx, j * dx)) o = OWN_NOTCH;
+      else if (sc->has_curve && ((j * dx) <= hcol[i]) != ((j * dx) <= hcol[i + 1])) o = OWN_CURVE;
       else if (sc->has_line && P.in_line(i * dx, j * dx) != P.in_line((i + 1) * dx, j * dx)) o = OWN_LINE;
     }
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i <= nx; ++i) {
       if (!S.hasV(i, j)) continue;
       int32_t& o = ownV[(size_t)j * (nx + 1) + i];
-      if (sc->has_curve && ((j * dx) <= hcol[i]) != (((j + 1) * dx) <= hcol[i])) o = OWN_CURVE;
+      if (sc->nnotches && P.touches_notch(i * dx, j * dx, i * dx, (j + 1) * dx)) o = OWN_NOTCH;
+      else if (sc->has_curve && ((j * dx) <= hcol[i]) != (((j + 1) * dx) <= hcol[i])) o = OWN_CURVE;
       else if (sc->has_line && P.in_line(i * dx, j * dx) != P.in_line(i * dx, (j + 1) * dx)) o = OWN_LINE;
     }
   for (int c = 0; c < sc->ncircles; ++c) {
@@ -865,7 +900,16 @@ void init(State<R>& S, double dx, const orc_scene* sc) {
       const int32_t o = ownH[(size_t)j * nx + i];
       const double xi = i * dx, yj = j * dx;
       double s = 0.5;
-      if (o == OWN_CURVE) {
+      if (o == OWN_NOTCH) {
+        // bisection on the scene's phase along the edge
+        const bool side0 = P.inside(xi, yj);
+        double lo = 0.0, hi = 1.0;
+        for (int it = 0; it < 60; ++it) {
+          const double mid = 0.5 * (lo + hi);
+          if (P.inside(xi + mid * dx, yj) == side0) lo = mid; else hi = mid;
+        }
+        s = 0.5 * (lo + hi);
+      } else if (o == OWN_CURVE) {
         // bisection on the edge until the bracket is below 2^-52
         const bool side0 = yj <= hcol[i];
         double lo = 0.0, hi = 1.0;
@@ -892,7 +936,15 @@ void init(State<R>& S, double dx, const orc_scene* sc) {
       const int32_t o = ownV[(size_t)j * (nx + 1) + i];
       const double xi = i * dx, yj = j * dx;
       double s = 0.5;
-      if (o == OWN_CURVE) {
+      if (o == OWN_NOTCH) {
+        const bool side0 = P.inside(xi, yj);
+        double lo = 0.0, hi = 1.0;
+        for (int it = 0; it < 60; ++it) {
+          const double mid = 0.5 * (lo + hi);
+          if (P.inside(xi, yj + mid * dx) == side0) lo = mid; else hi = mid;
+        }
+        s = 0.5 * (lo + hi);
+      } else if (o == OWN_CURVE) {
         s = (hcol[i] - yj) / dx;
       } else if (o == OWN_LINE) {
         const double y = (sc->lc - sc->la * xi) / sc->lb;

@@ -37,6 +37,8 @@ typedef struct {
   const double *amp, *phase;
   int32_t has_line;          /* toggles the phase where la*x + lb*y <= lc  */
   double la, lb, lc;
+  int32_t nnotches;          /* boxes cut out of the reference phase after the */
+  const double* notch;       /* toggles: x0, x1, y0, y1 per box (closed)       */
 } orc_scene;
 
 /* Diagnostic counters written by orc_step / orc_sweep (summed over sweeps). */

@@ -267,6 +267,19 @@ def translation_workload(n=32, cfl=0.125):
                     {"circle": (0.25, 0.75, 0.15)})
 
 
+def zalesak_workload(n=64, cfl=math.pi / 16):
+    """Zalesak's disk (Sec. 3.4): a disk R=0.15 at (0.5,0.75) with a notch 0.05
+    wide reaching 0.25 up from its bottom, in solid rotation (u, v) =
+    (2 pi (0.5 - y), 2 pi (x - 0.5)) for one turn, T = 1; dt from the CFL with
+    the largest velocity component at t = 0 (pi)."""
+    dx = 1.0 / n
+    f = rotation_field(n, n, dx, 2.0 * math.pi, (0.5, 0.5))
+    dt = cfl * dx / f.umax
+    steps = int(round(1.0 / dt))
+    scene = {"circles": [(0.5, 0.75, 0.15)], "notches": [(0.475, 0.525, 0.55, 0.85)]}
+    return Workload(f"zalesak_n{n}", n, dx, scene, f, dt, steps, {"circle": (0.5, 0.75, 0.15)})
+
+
 ROT_CENTRE = (0.4841, 0.5477)
 
 

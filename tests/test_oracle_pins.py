@@ -232,6 +232,51 @@ def test_sl_loses_more_than_circle_fit():
     assert e_line > 1e6 * max(e_circle, 1e-16)
 
 
+# ---------------------------------------------------------------------------
+# Zalesak's disk (Sec. 3.4): a notched disk, corners and a thin slot
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [32, 64, 128])
+def test_zalesak_table5(n):
+    """Table 5: after one turn the circle fit keeps the area error within x3
+    of the printed EBIT values (which fluctuate with N, as the paper notes);
+    the straight-line variant loses everything at N=32 ("NA") and matches
+    the printed EBIT-SL area error within 5% above it."""
+    row = read_golden("table5_zalesak.txt")
+    row = row[row[:, 0] == n][0]
+    wl = W.zalesak_workload(n)
+    S, e_area, tot = run(wl)
+    assert tot[oracle.INVARIANT] == 0
+    assert row[1] / 3 <= e_area <= 3 * row[1]
+    assert oracle.loops(S)[:2] == (1, 0)
+    S, e_line, tot = run(wl, line_only=True)
+    assert tot[oracle.INVARIANT] == 0
+    if math.isnan(row[3]):
+        assert _total_loss(S, e_line)
+    else:
+        assert abs(e_line / row[3] - 1) < 0.05
+
+
+def test_init_notched_disk_markers_on_shape():
+    """Colours of the notched disk equal the direct inside test (disk minus
+    the closed box), and every marker lies on the disk's circle or on a side
+    of the notch to 1e-13."""
+    n = 96
+    dx = 1.0 / n
+    x0, x1, y0, y1 = 0.47, 0.53, 0.55, 0.85
+    scene = {"circles": [(0.5, 0.75, 0.15)], "notches": [(x0, x1, y0, y1)]}
+    S = oracle.init(n, n, dx, scene)
+    X, Y = np.meshgrid(np.arange(n + 1) * dx, np.arange(n + 1) * dx)
+    inside = ((X - 0.5) ** 2 + (Y - 0.75) ** 2 <= 0.15 ** 2) & ~((X >= x0) & (X <= x1) & (Y >= y0) & (Y <= y1))
+    assert np.array_equal(inside.astype(np.uint8), S.K)
+    P = oracle.markers(S)
+    d_circ = np.abs(np.hypot(P[:, 0] - 0.5, P[:, 1] - 0.75) - 0.15)
+    on_side = np.minimum(np.minimum(np.abs(P[:, 0] - x0), np.abs(P[:, 0] - x1)), np.abs(P[:, 1] - y1))
+    in_band = (P[:, 0] >= x0 - 1e-12) & (P[:, 0] <= x1 + 1e-12) & (P[:, 1] >= y0) & (P[:, 1] <= y1 + 1e-12)
+    d_notch = np.where(in_band, on_side, np.inf)
+    assert np.max(np.minimum(d_circ, d_notch)) < 1e-13
+    assert np.count_nonzero(d_notch < 1e-13) > 8   # the slot's sides carry markers
+
+
 def test_vortex_baseline_config_runs_clean():
     """The 64x64 plain FP64 workload (mirrored vortex, CFL 0.5, 256 steps):
     invariants hold every step and the shape comes back (time reversal)."""
