@@ -64,11 +64,17 @@ typedef struct {                                             /* reference phase 
   const double *amp, *phase;
 } ebit_curve;
 typedef struct { double a, b, c; } ebit_halfplane;          /* toggles phase where a x + b y <= c */
+typedef struct { double x0, x1, y0, y1; } ebit_notch;       /* cuts the closed box [x0,x1]x[y0,y1] out
+                                                               of the reference phase (Zalesak's
+                                                               slotted disk, Sec. 3.4) */
 typedef struct {
   const ebit_circle* circles;   /* host pointer, ncircles entries (may be NULL if 0) */
   int32_t ncircles;
   const ebit_curve* curve;      /* host pointer or NULL                     */
   const ebit_halfplane* line;   /* host pointer or NULL                     */
+  const ebit_notch* notches;    /* host pointer, nnotches entries (may be NULL if 0);
+                                   applied after the curve, line and circles */
+  int32_t nnotches;
 } ebit_scene;
 
 /* Host copy of a state.  K: (ny+1)*(nx+1) bytes, Z: ny*nx bytes (0/1),

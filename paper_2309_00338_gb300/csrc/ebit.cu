@@ -221,6 +221,13 @@ ebit_status init_scene(ebit_ctx* c, const ebit_scene* scene) {
     circ.push_back(scene->circles[t].yc);
     circ.push_back(scene->circles[t].r);
   }
+  std::vector<double> notch;
+  for (int b = 0; b < scene->nnotches; ++b) {
+    notch.push_back(scene->notches[b].x0);
+    notch.push_back(scene->notches[b].x1);
+    notch.push_back(scene->notches[b].y0);
+    notch.push_back(scene->notches[b].y1);
+  }
   std::vector<double> curve;
   if (scene->curve) {
     for (int k = 0; k < scene->curve->nmodes; ++k) curve.push_back(scene->curve->amp[k]);
@@ -235,11 +242,12 @@ ebit_status init_scene(ebit_ctx* c, const ebit_scene* scene) {
     return EBIT_OK;
   };
   auto cleanup = [&]() { cudaStreamSynchronize(c->stream); for (void* p : tmp) cudaFree(p); };
-  double *dcirc = nullptr, *dcurve = nullptr, *hv = nullptr;
+  double *dcirc = nullptr, *dcurve = nullptr, *hv = nullptr, *dnotch = nullptr;
   int *ownH = nullptr, *ownV = nullptr;
   ebit_status s;
   if ((s = talloc((void**)&dcirc, circ.size() * sizeof(double))) != EBIT_OK ||
       (s = talloc((void**)&dcurve, curve.size() * sizeof(double))) != EBIT_OK ||
+      (s = talloc((void**)&dnotch, notch.size() * sizeof(double))) != EBIT_OK ||
       (s = talloc((void**)&hv, (size_t)(2 * c->grid.nx + 1) * sizeof(double))) != EBIT_OK ||
       (s = talloc((void**)&ownH, (size_t)(c->grid.ny + 1) * L.d.P * sizeof(int))) != EBIT_OK ||
       (s = talloc((void**)&ownV, (size_t)(c->grid.ny + 1) * L.d.P * sizeof(int))) != EBIT_OK) {
@@ -251,6 +259,10 @@ ebit_status init_scene(ebit_ctx* c, const ebit_scene* scene) {
       EBIT_CK(cudaMemcpyAsync(dcirc, circ.data(), circ.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (!curve.empty())
       EBIT_CK(cudaMemcpyAsync(dcurve, curve.data(), curve.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (!notch.empty())
+      EBIT_CK(cudaMemcpyAsync(dnotch, notch.data(), notch.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    sc.notch = dnotch;
+    sc.nnotches = scene->nnotches;
     EBIT_CK(cudaMemsetAsync(ownH, 0x7f, (size_t)(c->grid.ny + 1) * L.d.P * sizeof(int), c->stream));
     EBIT_CK(cudaMemsetAsync(ownV, 0x7f, (size_t)(c->grid.ny + 1) * L.d.P * sizeof(int), c->stream));
     sc.circ = dcirc;
@@ -275,6 +287,7 @@ ebit_status init_scene(ebit_ctx* c, const ebit_scene* scene) {
       ebit::k_init_circles<<<sc.ncircles, 256, 0, c->stream>>>(sc, L.d, dx, c->K[b], c->Z[b]);
       ebit::k_init_owner<<<sc.ncircles, 256, 0, c->stream>>>(sc, L.d, dx, ownH, ownV);
     }
+    if (sc.nnotches > 0) ebit::k_init_notch<<<L.grid, L.block, 0, c->stream>>>(sc, L.d, dx, c->K[b], c->Z[b]);
     ebit::k_init_roots<R><<<L.grid, L.block, 0, c->stream>>>(sc, L.d, dx, c->K[b], hv, ownH, ownV,
                                                             (R*)c->sH[b], (R*)c->sV[b]);
     EBIT_CK(cudaGetLastError());
@@ -393,7 +406,8 @@ ebit_status ebit_init(ebit_ctx** out, const ebit_grid* grid, const ebit_scene* s
   if (!scene || scene->ncircles < 0 || (scene->ncircles > 0 && !scene->circles) ||
       (scene->curve && (scene->curve->nmodes < 0 || (scene->curve->nmodes > 0 &&
                                                      (!scene->curve->amp || !scene->curve->phase)))) ||
-      (scene->line && scene->line->a == 0.0 && scene->line->b == 0.0 && scene->line->c < 0.0))
+      (scene->line && scene->line->a == 0.0 && scene->line->b == 0.0 && scene->line->c < 0.0) ||
+      scene->nnotches < 0 || (scene->nnotches > 0 && !scene->notches))
     return fail(EBIT_EINVAL, "invalid scene");
   ebit_status s = new_ctx(out, grid, stream);
   if (s != EBIT_OK) return s;

@@ -172,6 +172,8 @@ struct SceneDev {
   const double* phase;
   int has_line;
   double la, lb, lc;
+  const double* notch;  // 4 per notch: x0, x1, y0, y1
+  int nnotches;
 };
 
 __device__ double curve_h(const SceneDev& sc, double x) {
@@ -190,6 +192,31 @@ __device__ __forceinline__ bool in_circle(const SceneDev& sc, int c, double x, d
 }
 __device__ __forceinline__ bool in_line(const SceneDev& sc, double x, double y) {
   return sc.la * x + sc.lb * y <= sc.lc;
+}
+__device__ __forceinline__ bool in_notch(const SceneDev& sc, double x, double y) {
+  for (int b = 0; b < sc.nnotches; ++b) {
+    const double* q = sc.notch + 4 * b;
+    if (x >= q[0] && x <= q[1] && y >= q[2] && y <= q[3]) return true;
+  }
+  return false;
+}
+// The scene's phase at a point: curve, line and circles toggle it, then the
+// notches cut it out.
+__device__ bool scene_inside(const SceneDev& sc, double x, double y) {
+  bool p = false;
+  if (sc.has_curve) p ^= y <= curve_h(sc, x);
+  if (sc.has_line) p ^= in_line(sc, x, y);
+  for (int c = 0; c < sc.ncircles; ++c) p ^= in_circle(sc, c, x, y);
+  return p && !in_notch(sc, x, y);
+}
+// Does the axis-aligned edge (xa, ya)-(xb, yb), xa <= xb, ya <= yb, touch a notch?
+__device__ __forceinline__ bool touches_notch(const SceneDev& sc, double xa, double ya, double xb,
+                                              double yb) {
+  for (int b = 0; b < sc.nnotches; ++b) {
+    const double* q = sc.notch + 4 * b;
+    if (xb >= q[0] && xa <= q[1] && yb >= q[2] && ya <= q[3]) return true;
+  }
+  return false;
 }
 
 // Curve heights at the vertex columns (hv[i], x = i dx) and at the cell-centre
@@ -220,6 +247,20 @@ k_init_base(SceneDev sc, Dims d, double dx, const double* hv, uint32_t* K, uint3
   const unsigned wz = __ballot_sync(0xffffffffu, (x < d.nx && y < d.ny) && pz);
   if (threadIdx.x == 0 && y <= d.ny && x <= d.nx) K[(long long)y * d.kw + (x >> 5)] = wk;
   if (threadIdx.x == 0 && y < d.ny && x < d.nx) Z[(long long)y * d.zw + (x >> 5)] = wz;
+}
+
+// Notches: vertices and cell centres inside a box leave the reference phase
+// (after the curve, line and circles have set it).
+__global__ void __launch_bounds__(32 * kBlockY)
+k_init_notch(SceneDev sc, Dims d, double dx, uint32_t* K, uint32_t* Z) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.y;
+  const bool vk = x <= d.nx && y <= d.ny && in_notch(sc, x * dx, y * dx);
+  const bool vz = x < d.nx && y < d.ny && in_notch(sc, (x + 0.5) * dx, (y + 0.5) * dx);
+  const unsigned mk = __ballot_sync(0xffffffffu, vk);
+  const unsigned mz = __ballot_sync(0xffffffffu, vz);
+  if (threadIdx.x == 0 && mk) K[(long long)y * d.kw + (x >> 5)] &= ~mk;
+  if (threadIdx.x == 0 && mz) Z[(long long)y * d.zw + (x >> 5)] &= ~mz;
 }
 
 __device__ __forceinline__ void circle_box(const SceneDev& sc, int c, const Dims& d, double dx,
@@ -285,7 +326,16 @@ k_init_roots(SceneDev sc, Dims d, double dx, const uint32_t* __restrict__ K,
   const double xi = x * dx, yj = y * dx;
   if (x < d.nx && kbit(K, d, x, y) != kbit(K, d, x + 1, y)) {
     double s = 0.5;
-    if (sc.has_curve && ((yj <= hv[x]) != (yj <= hv[x + 1]))) {
+    if (sc.nnotches && touches_notch(sc, xi, yj, (x + 1) * dx, yj)) {
+      // bisection on the scene's phase along the edge
+      const bool side0 = scene_inside(sc, xi, yj);
+      double lo = 0.0, hi = 1.0;
+      for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (scene_inside(sc, xi + mid * dx, yj) == side0) lo = mid; else hi = mid;
+      }
+      s = 0.5 * (lo + hi);
+    } else if (sc.has_curve && ((yj <= hv[x]) != (yj <= hv[x + 1]))) {
       const bool side0 = yj <= hv[x];
       double lo = 0.0, hi = 1.0;
       for (int it = 0; it < 60; ++it) {
@@ -311,7 +361,15 @@ k_init_roots(SceneDev sc, Dims d, double dx, const uint32_t* __restrict__ K,
   }
   if (y < d.ny && kbit(K, d, x, y) != kbit(K, d, x, y + 1)) {
     double s = 0.5;
-    if (sc.has_curve && ((yj <= hv[x]) != (((y + 1) * dx) <= hv[x]))) {
+    if (sc.nnotches && touches_notch(sc, xi, yj, xi, (y + 1) * dx)) {
+      const bool side0 = scene_inside(sc, xi, yj);
+      double lo = 0.0, hi = 1.0;
+      for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (scene_inside(sc, xi, yj + mid * dx) == side0) lo = mid; else hi = mid;
+      }
+      s = 0.5 * (lo + hi);
+    } else if (sc.has_curve && ((yj <= hv[x]) != (((y + 1) * dx) <= hv[x]))) {
       s = (hv[x] - yj) / dx;
     } else if (sc.has_line && in_line(sc, xi, yj) != in_line(sc, xi, (y + 1) * dx)) {
       const double yr = (sc.lc - sc.la * xi) / sc.lb;

@@ -54,9 +54,15 @@ class ebit_halfplane(ctypes.Structure):
     _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double)]
 
 
+class ebit_notch(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double),
+                ("y1", ctypes.c_double)]
+
+
 class ebit_scene(ctypes.Structure):
     _fields_ = [("circles", ctypes.POINTER(ebit_circle)), ("ncircles", ctypes.c_int32),
-                ("curve", ctypes.POINTER(ebit_curve)), ("line", ctypes.POINTER(ebit_halfplane))]
+                ("curve", ctypes.POINTER(ebit_curve)), ("line", ctypes.POINTER(ebit_halfplane)),
+                ("notches", ctypes.POINTER(ebit_notch)), ("nnotches", ctypes.c_int32)]
 
 
 class ebit_state_host(ctypes.Structure):
@@ -149,6 +155,11 @@ def _scene(scene: dict, keep: list):
         hp = ebit_halfplane(*(float(t) for t in scene["line"]))
         keep.append(hp)
         sc.line = ctypes.pointer(hp)
+    if scene.get("notches"):
+        nb = np.ascontiguousarray(np.asarray(scene["notches"], np.float64).reshape(-1, 4))
+        keep.append(nb)
+        sc.nnotches = nb.shape[0]
+        sc.notches = nb.ctypes.data_as(ctypes.POINTER(ebit_notch))
     return sc
 
 

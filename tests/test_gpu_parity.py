@@ -412,3 +412,47 @@ def test_gather_kernels_parity(name, prec, monkeypatch):
             assert_same_state(ebit.ebit_get_state(ctx, S.nx, S.ny), S, prec)
     finally:
         ebit.ebit_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# Zalesak's disk (Sec. 3.4): a scene with a notch cut out of a disk
+# ---------------------------------------------------------------------------
+def test_init_parity_notched_disk():
+    wl = W.zalesak_workload(96)
+    for prec in (0, 1):
+        S = oracle.init(wl.n, wl.n, wl.dx, wl.scene, prec)
+        ctx = ebit.ebit_init(wl.n, wl.n, wl.dx, wl.scene, prec)
+        try:
+            g = ebit.ebit_get_state(ctx, wl.n, wl.n)
+            assert np.array_equal(g["Z"], S.Z)
+            assert_same_state(g, S, 1)  # exact, in both forms
+        finally:
+            ebit.ebit_destroy(ctx)
+
+
+@pytest.mark.parametrize("line_only", [False, True], ids=["circle_fit", "straight_line"])
+def test_zalesak_64_turn(line_only):
+    """One turn of the notched disk at 64^2 (1024 steps, FP64): the GPU state
+    equals the oracle's along the way and the area error is the one Table 5
+    prints (EBIT within x3, EBIT-SL within 5%)."""
+    wl = W.zalesak_workload(64)
+    flags = ebit.EBIT_FIT_LINE if line_only else 0
+    S = oracle.init(wl.n, wl.n, wl.dx, wl.scene)
+    ctx = ebit.ebit_init(wl.n, wl.n, wl.dx, wl.scene, flags=flags)
+    try:
+        u, v = dev(wl.field.u, 0), dev(wl.field.v, 0)
+        a0 = ebit.ebit_fraction(ctx)
+        for k in range(wl.steps):
+            ebit.ebit_step(ctx, u, v, wl.dt)
+            r = oracle.step(S, wl.field.u, wl.field.v, wl.dt, line_only=line_only)
+            if k % 256 == 255:
+                assert_same_state(ebit.ebit_get_state(ctx, wl.n, wl.n), S, 0)
+        ebit.ebit_sync(ctx)
+        e_area = abs(ebit.ebit_fraction(ctx) - a0) / a0
+        assert abs(ebit.ebit_fraction(ctx) - r["area"]) <= 1e-12
+        if line_only:
+            assert abs(e_area / 7.33e-1 - 1) < 0.05   # Table 5, EBIT-SL, N=64
+        else:
+            assert 1.22e-3 / 3 <= e_area <= 3 * 1.22e-3  # Table 5, EBIT, N=64
+    finally:
+        ebit.ebit_destroy(ctx)
