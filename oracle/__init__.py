@@ -111,6 +111,7 @@ def _set_signatures(L):
     L.orc_fraction.argtypes = [i32, i32, f64, i32, P, P, P, P, P, P]
     L.orc_curvature.argtypes = [i32, i32, f64, i32, P, P, P, P, P, P, P]
     L.orc_fit.argtypes = [P, P, P, i32, P, i32, P]
+    L.orc_coupling.argtypes = [i32, i32, f64, i32, P, P, f64, f64, f64, f64, f64, P, P, P, P]
     L.orc_loops.argtypes = [i32, i32, f64, i32, P, P, P, P, P, P, P, i64, P]
     L.orc_loops.restype = i64
     L.orc_shape_error.argtypes = [i32, i32, f64, P, P, P, f64, f64, f64]
@@ -258,6 +259,18 @@ def curvature(S: State, C):
     lib().orc_curvature(S.nx, S.ny, S.dx, S.prec, _p(S.K), _p(S.Z), _p(S.sH), _p(S.sV), _p(C),
                         _p(kap), _p(n))
     return kap, int(n[0])
+
+
+def coupling(S: State, C, kappa, rho1, rho2, mu1, mu2, sigma):
+    """Properties and face surface-tension source from C and kappa; returns
+    (rho, mu, fx, fy) with shapes (ny, nx), (ny, nx), (ny, nx+1), (ny+1, nx)."""
+    C = np.ascontiguousarray(C, np.float64)
+    kappa = np.ascontiguousarray(kappa, np.float64)
+    rho = np.zeros((S.ny, S.nx)); mu = np.zeros((S.ny, S.nx))
+    fx = np.zeros((S.ny, S.nx + 1)); fy = np.zeros((S.ny + 1, S.nx))
+    lib().orc_coupling(S.nx, S.ny, S.dx, S.prec, _p(C), _p(kappa), rho1, rho2, mu1, mu2, sigma,
+                       _p(rho), _p(mu), _p(fx), _p(fy))
+    return rho, mu, fx, fy
 
 
 def fit(A, B, P1=None, P4=None):

@@ -1204,6 +1204,57 @@ int orc_curvature(int nx, int ny, double dx, int prec, const uint8_t* K, const u
   return 0;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Properties and surface-tension source (the coupling of Sec. 2.5): the
+// fraction C stands in for the Heaviside function of Eq. 8, and the surface
+// term sigma kappa n delta_S of Eq. 6 becomes sigma kappa grad(C)
+// at the faces, with the face curvature the mean of the two cells' valid
+// heights-based curvatures (one valid: that one; none: 0).
+template <typename R>
+void coupling(int nx, int ny, double dx, const double* C, const double* kappa, double rho1,
+              double rho2, double mu1, double mu2, double sigma, double* rho, double* mu,
+              double* fx, double* fy) {
+  const R r1 = (R)rho1, r2 = (R)rho2, m1 = (R)mu1, m2 = (R)mu2, sg = (R)sigma, h = (R)dx;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const R c = (R)C[(size_t)j * nx + i];
+      rho[(size_t)j * nx + i] = (double)(c * r1 + (R(1) - c) * r2);
+      mu[(size_t)j * nx + i] = (double)(c * m1 + (R(1) - c) * m2);
+    }
+  auto face = [&](size_t a, size_t b) -> double {  // cells a (low side), b (high side)
+    const R ka = (R)kappa[a], kb = (R)kappa[b];
+    const bool va = !std::isnan(ka), vb = !std::isnan(kb);
+    R kf = R(0);
+    if (va && vb) kf = (ka + kb) * R(0.5);
+    else if (va) kf = ka;
+    else if (vb) kf = kb;
+    return (double)(sg * kf * ((R)C[b] - (R)C[a]) / h);
+  };
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i <= nx; ++i)
+      fx[(size_t)j * (nx + 1) + i] =
+          (i == 0 || i == nx) ? 0.0 : face((size_t)j * nx + i - 1, (size_t)j * nx + i);
+  for (int j = 0; j <= ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      fy[(size_t)j * nx + i] =
+          (j == 0 || j == ny) ? 0.0 : face((size_t)(j - 1) * nx + i, (size_t)j * nx + i);
+}
+
+}  // namespace
+
+extern "C" {
+
+int orc_coupling(int nx, int ny, double dx, int prec, const double* C, const double* kappa,
+                 double rho1, double rho2, double mu1, double mu2, double sigma,
+                 double* rho, double* mu, double* fx, double* fy) {
+  if ((prec & 1) == 0) coupling<double>(nx, ny, dx, C, kappa, rho1, rho2, mu1, mu2, sigma, rho, mu, fx, fy);
+  else coupling<float>(nx, ny, dx, C, kappa, rho1, rho2, mu1, mu2, sigma, rho, mu, fx, fy);
+  return 0;
+}
+
 int orc_fit(const double* A, const double* B, const double* P1, int has_p1, const double* P4,
             int has_p4, double* y_out) {
   const P2 a{A[0], A[1]}, b{B[0], B[1]};

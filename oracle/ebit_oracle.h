@@ -83,6 +83,17 @@ int orc_curvature(int nx, int ny, double dx, int prec, const uint8_t* K,
                   const uint8_t* Z, const double* sH, const double* sV,
                   const double* C, double* kappa, int64_t* n_invalid);
 
+/* Hand-off to a one-fluid Navier-Stokes solver (Sec. 2.5: the surface term
+ * of Eq. 6 and the property law of Eq. 8, with the fractions standing in for
+ * the Heaviside function):
+ * rho = C rho1 + (1 - C) rho2 and mu likewise per cell (ny*nx), and the
+ * surface-tension source sigma kappa grad(C) on the faces: fx on the
+ * (nx+1)*ny vertical faces, fy on the nx*(ny+1) horizontal ones, zero on the
+ * walls.  Arithmetic in the state precision. */
+int orc_coupling(int nx, int ny, double dx, int prec, const double* C, const double* kappa,
+                 double rho1, double rho2, double mu1, double mu2, double sigma,
+                 double* rho, double* mu, double* fx, double* fy);
+
 /* Vertex-local circle fit of one crossing (test hook).  Points are (x,y)
  * pairs in cell units relative to the vertex on the grid line x = 0; A has
  * x < 0, B has x >= 0; has_p1 / has_p4 select the optional neighbours.

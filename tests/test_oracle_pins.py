@@ -630,6 +630,118 @@ def test_hf_circle_curvature_converges():
 
 
 # ---------------------------------------------------------------------------
+# coupling to a one-fluid flow solver (Sec. 2.5, Eqs. 6 and 8)
+# ---------------------------------------------------------------------------
+FLUIDS = dict(rho1=1000.0, rho2=1.2, mu1=1.0e-3, mu2=1.8e-5, sigma=0.0728)
+
+
+def _drop_coupling(n, R_cells, prec=oracle.FP64, drop=True):
+    dx = 1.0 / n
+    c = (0.5 + 0.123 * dx, 0.5 - 0.271 * dx, R_cells * dx)
+    scene = W.circle_scene([c])
+    if not drop:
+        scene["line"] = (0.0, 0.0, 1.0)
+    S = oracle.init(n, n, dx, scene, prec)
+    C, _ = oracle.fraction(S)
+    kap, _ = oracle.curvature(S, C)
+    return S, c, C, kap, oracle.coupling(S, C, kap, **FLUIDS)
+
+
+@pytest.mark.parametrize("prec", [oracle.FP64, oracle.FP32])
+def test_coupling_properties_pure_phases_and_mass(prec):
+    """rho and mu equal the pure-phase values where C is 0 or 1, lie between
+    them elsewhere, and the total mass of a drop is rho1 pi R^2 + rho2 (1 -
+    pi R^2) to within the area error of the polygonal interface."""
+    S, c, C, kap, (rho, mu, fx, fy) = _drop_coupling(128, 12, prec)
+    f = FLUIDS
+    cast = np.float32 if prec == oracle.FP32 else np.float64
+    assert np.all(rho[C == 1] == cast(f["rho1"])) and np.all(mu[C == 1] == cast(f["mu1"]))
+    assert np.all(rho[C == 0] == cast(f["rho2"])) and np.all(mu[C == 0] == cast(f["mu2"]))
+    part = (C > 0) & (C < 1)
+    assert part.sum() > 0
+    assert np.all((rho[part] > f["rho2"]) & (rho[part] < f["rho1"]))
+    assert np.all((mu[part] > f["mu2"]) & (mu[part] < f["mu1"]))
+    A = math.pi * c[2] ** 2
+    mass = rho.sum() * S.dx ** 2
+    exact = f["rho1"] * A + f["rho2"] * (1 - A)
+    assert abs(mass - exact) / (f["rho1"] * A) < 2e-3
+
+
+def test_coupling_flat_interface_has_no_force():
+    """A straight interface has zero curvature, so the surface-tension source
+    vanishes on every face (to roundoff), while grad C does not."""
+    n = 64
+    dx = 1.0 / n
+    for la, lb in ((0.3, 1.0), (1.0, 0.45), (0.0, 1.0)):
+        S = oracle.init(n, n, dx, {"line": (la, lb, 0.5 * la + 0.5 * lb + 0.17 * dx)})
+        C, _ = oracle.fraction(S)
+        kap, _ = oracle.curvature(S, C)
+        rho, mu, fx, fy = oracle.coupling(S, C, kap, **FLUIDS)
+        assert max(np.abs(np.diff(C, axis=0)).max(), np.abs(np.diff(C, axis=1)).max()) > 0.3
+        assert np.abs(fx).max() < 1e-9 and np.abs(fy).max() < 1e-9
+
+
+def test_coupling_constant_curvature_telescopes():
+    """With a uniform curvature field the face sources along a row are
+    sigma kappa times a difference of C, so their sum times dx telescopes to
+    sigma kappa (C_last - C_first); walls carry no force."""
+    rng = np.random.default_rng(5)
+    n = 24
+    S = oracle.init(n, n + 3, 1.0 / n, {"line": (1.0, 0.2, 0.6)})
+    C = rng.uniform(0, 1, (S.ny, S.nx))
+    k = 3.5
+    _, _, fx, fy = oracle.coupling(S, C, np.full_like(C, k), **FLUIDS)
+    sg = FLUIDS["sigma"]
+    assert np.all(fx[:, 0] == 0) and np.all(fx[:, -1] == 0)
+    assert np.all(fy[0, :] == 0) and np.all(fy[-1, :] == 0)
+    np.testing.assert_allclose(fx.sum(axis=1) * S.dx, sg * k * (C[:, -1] - C[:, 0]), atol=1e-13)
+    np.testing.assert_allclose(fy.sum(axis=0) * S.dx, sg * k * (C[-1, :] - C[0, :]), atol=1e-13)
+    # the face between a low and a high cell points from low C to high C
+    assert np.all(np.sign(fx[:, 1:-1]) == np.sign(np.diff(C, axis=1)))
+
+
+def test_coupling_face_curvature_reading():
+    """Face curvature: mean of the two cells' values where both are valid,
+    the valid one where only one is, and no force where neither is."""
+    n = 8
+    S = oracle.init(n, n, 1.0 / n, {"line": (1.0, 0.2, 0.6)})
+    C = np.zeros((n, n))
+    C[:, 4:] = 1.0
+    kap = np.full((n, n), np.nan)
+    kap[1, 3], kap[1, 4] = 2.0, 6.0     # both valid: 4
+    kap[2, 3] = 5.0                      # left only
+    kap[3, 4] = 7.0                      # right only
+    _, _, fx, fy = oracle.coupling(S, C, kap, **FLUIDS)
+    sg = FLUIDS["sigma"]
+    assert fx[1, 4] == pytest.approx(sg * 4.0 * n)
+    assert fx[2, 4] == pytest.approx(sg * 5.0 * n)
+    assert fx[3, 4] == pytest.approx(sg * 7.0 * n)
+    assert fx[0, 4] == 0 and fx[4, 4] == 0
+    assert np.all(fy == 0)
+
+
+@pytest.mark.parametrize("drop", [True, False])
+def test_coupling_laplace_pressure_jump(drop):
+    """Balanced by a pressure gradient, the source integrates along a ray
+    from the wall to the centre of a drop (or bubble) of radius R to the
+    Laplace jump p_in - p_out = sigma / R (positive for both), within the
+    curvature error (1% at R = 16 cells); the net force on the drop is ~0."""
+    n = 128
+    S, c, C, kap, (rho, mu, fx, fy) = _drop_coupling(n, 16, drop=drop)
+    sg = FLUIDS["sigma"]
+    ic = int(c[0] / S.dx)
+    jc = int(c[1] / S.dx)
+    jump_x = fx[jc, : ic + 1].sum() * S.dx
+    jump_y = fy[: jc + 1, ic].sum() * S.dx
+    for jump in (jump_x, jump_y):
+        assert jump == pytest.approx(sg / c[2], rel=1e-2)
+    # the opposite side gives the same jump with the other sign
+    assert -fx[jc, ic + 1:].sum() * S.dx == pytest.approx(sg / c[2], rel=1e-2)
+    scale = np.abs(fx).sum()
+    assert abs(fx.sum()) < 1e-2 * scale and abs(fy.sum()) < 1e-2 * scale
+
+
+# ---------------------------------------------------------------------------
 # initialisation (Sec. 3.2)
 # ---------------------------------------------------------------------------
 def test_init_markers_on_shapes():
