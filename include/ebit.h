@@ -151,6 +151,29 @@ ebit_status ebit_curvature(ebit_ctx* ctx, void* kappa_dev, int32_t* n_invalid_ho
  * pointers, row pitch in elements); valid until the next step or destroy. */
 ebit_status ebit_fields(ebit_ctx* ctx, const void** C, const void** kappa, int64_t* pitch);
 
+/* Material properties and surface tension of the two phases; phase 1 is the
+ * reference phase (colour 1). */
+typedef struct { double rho1, rho2, mu1, mu2, sigma; } ebit_fluids;
+
+/* Hand-off to a one-fluid Navier-Stokes solver (Sec. 2.5), from the
+ * context's current fractions C and curvature kappa:
+ *   rho = C rho1 + (1 - C) rho2,  mu = C mu1 + (1 - C) mu2        (Eq. 8,
+ *   with C in place of the Heaviside function), per cell, ny*nx;
+ *   fx = sigma kappa_f (C(i,j) - C(i-1,j)) / dx on the vertical faces,
+ *   ny*(nx+1), face (i,j) between cells (i-1,j) and (i,j);
+ *   fy = sigma kappa_f (C(i,j) - C(i,j-1)) / dx on the horizontal faces,
+ *   (ny+1)*nx, face (i,j) between cells (i,j-1) and (i,j)
+ * (the surface term sigma kappa n delta_S of Eq. 6 as a face force density
+ * sigma kappa grad C, the form whose pressure balance is exact).  kappa_f is
+ * the mean of the two cells' curvatures when both are valid, the valid one
+ * when one is, and 0 when neither is; wall faces carry 0.
+ * Outputs: caller-owned DEVICE buffers, contiguous row-major, element type of
+ * the context precision; any may be NULL (not written).  Arithmetic in the
+ * context precision.  Asynchronous on the context's stream; EBIT_EINVAL for a
+ * NULL ctx or fluids. */
+ebit_status ebit_coupling(ebit_ctx* ctx, const ebit_fluids* fluids, void* rho_dev, void* mu_dev,
+                          void* fx_dev, void* fy_dev);
+
 /* Counters of the last step (synchronous). */
 ebit_status ebit_diagnostics(ebit_ctx* ctx, ebit_diag* out);
 
@@ -168,8 +191,8 @@ const char* ebit_last_error(void);
  * milliseconds and the number of launches since the last call, then resets.
  * Kinds: EBIT_K_SWEEP (a split sweep), EBIT_K_CENTRE (second pass of the
  * gather sweep, when selected), EBIT_K_FIELDS (fractions, curvature and area
- * partials), EBIT_K_AREA (area sum). */
-enum { EBIT_K_SWEEP = 0, EBIT_K_CENTRE, EBIT_K_FIELDS, EBIT_K_AREA, EBIT_K_COUNT = 8 };
+ * partials), EBIT_K_AREA (area sum), EBIT_K_COUPLING (ebit_coupling). */
+enum { EBIT_K_SWEEP = 0, EBIT_K_CENTRE, EBIT_K_FIELDS, EBIT_K_AREA, EBIT_K_COUPLING, EBIT_K_COUNT = 8 };
 ebit_status ebit_set_timing(ebit_ctx* ctx, int on);
 ebit_status ebit_timings(ebit_ctx* ctx, double* ms, int64_t* launches);
 

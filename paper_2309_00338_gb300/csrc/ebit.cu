@@ -12,6 +12,7 @@
 #include "ebit_kernels.cuh"
 #include "ebit_tile.cuh"
 #include "ebit_fields.cuh"
+#include "ebit_coupling.cuh"
 
 namespace {
 
@@ -122,6 +123,22 @@ ebit_status launch_fields(ebit_ctx* c) {
 
 ebit_status fields(ebit_ctx* c) {
   return c->grid.prec == EBIT_FP32 ? launch_fields<float>(c) : launch_fields<double>(c);
+}
+
+template <typename R>
+ebit_status launch_coupling(ebit_ctx* c, const ebit_fluids* fl, void* rho, void* mu, void* fx,
+                            void* fy) {
+  const Layout& L = c->L;
+  const ebit::Fluids<R> f{(R)fl->rho1, (R)fl->rho2, (R)fl->mu1, (R)fl->mu2, (R)fl->sigma,
+                          (R)c->grid.dx};
+  const dim3 grid((L.d.nx + 1 + ebit::kCT - 1) / ebit::kCT, (L.d.ny + 1 + ebit::kCR - 1) / ebit::kCR);
+  {
+    Timed t(c, EBIT_K_COUPLING);
+    ebit::k_coupling<R><<<grid, ebit::kCT, 0, c->stream>>>((const R*)c->C, (const R*)c->kappa, L.d, f,
+                                                           (R*)rho, (R*)mu, (R*)fx, (R*)fy);
+  }
+  EBIT_CK(cudaGetLastError());
+  return EBIT_OK;
 }
 
 template <typename R, int AX>
@@ -484,6 +501,13 @@ ebit_status ebit_curvature(ebit_ctx* c, void* kappa_dev, int32_t* n_invalid_host
     return s;
   }
   return EBIT_OK;
+}
+
+ebit_status ebit_coupling(ebit_ctx* c, const ebit_fluids* fl, void* rho, void* mu, void* fx,
+                          void* fy) {
+  if (!c || !fl) return fail(EBIT_EINVAL, "NULL argument");
+  return c->grid.prec == EBIT_FP32 ? launch_coupling<float>(c, fl, rho, mu, fx, fy)
+                                   : launch_coupling<double>(c, fl, rho, mu, fx, fy);
 }
 
 ebit_status ebit_fields(ebit_ctx* c, const void** C, const void** kappa, int64_t* pitch) {

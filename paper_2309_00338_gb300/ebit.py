@@ -65,6 +65,11 @@ class ebit_scene(ctypes.Structure):
                 ("notches", ctypes.POINTER(ebit_notch)), ("nnotches", ctypes.c_int32)]
 
 
+class ebit_fluids(ctypes.Structure):
+    _fields_ = [("rho1", ctypes.c_double), ("rho2", ctypes.c_double), ("mu1", ctypes.c_double),
+                ("mu2", ctypes.c_double), ("sigma", ctypes.c_double)]
+
+
 class ebit_state_host(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("K", ctypes.c_void_p), ("Z", ctypes.c_void_p),
@@ -97,11 +102,12 @@ SIGNATURES = {
     "ebit_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "ebit_timings": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "ebit_fraction_noalloc": (ctypes.c_int, [ctypes.POINTER(ebit_grid), _P, _P, _P, _P, _P, _P, _P, _P]),
+    "ebit_coupling": (ctypes.c_int, [_P, ctypes.POINTER(ebit_fluids), _P, _P, _P, _P]),
 }
 
-K_SWEEP, K_CENTRE, K_FIELDS, K_AREA = range(4)
+K_SWEEP, K_CENTRE, K_FIELDS, K_AREA, K_COUPLING = range(5)
 K_COUNT = 8
-KERNEL_NAMES = ["sweep", "centre", "fields", "area"]
+KERNEL_NAMES = ["sweep", "centre", "fields", "area", "coupling"]
 
 
 def lib(path: str | None = None):
@@ -241,6 +247,16 @@ def ebit_fields(ctx):
     p = ctypes.c_int64()
     _check(lib().ebit_fields(ctx, ctypes.byref(c), ctypes.byref(k), ctypes.byref(p)), "ebit_fields")
     return c.value, k.value, p.value
+
+
+def ebit_coupling(ctx, rho1, rho2, mu1, mu2, sigma, rho=None, mu=None, fx=None, fy=None):
+    """Properties (rho, mu: (ny, nx)) and face surface-tension sources (fx:
+    (ny, nx+1), fy: (ny+1, nx)) from the context's current C and kappa, into
+    caller-owned contiguous CUDA tensors of the context precision (None:
+    skipped).  Asynchronous on the context's stream."""
+    fl = ebit_fluids(rho1, rho2, mu1, mu2, sigma)
+    _check(lib().ebit_coupling(ctx, ctypes.byref(fl), _dev_ptr(rho), _dev_ptr(mu), _dev_ptr(fx), _dev_ptr(fy)),
+           "ebit_coupling")
 
 
 def ebit_diagnostics(ctx):
