@@ -76,7 +76,16 @@ def kernel_bytes_per_cell(kind: str, esz: int) -> float:
         # reads K, Z, sH, sV; writes C and kappa
         "fields": 2 * bits + 2 * esz + 2 * esz,
         "area": 0.0,
+        # reads C and kappa; writes rho, mu, fx and fy (the face arrays carry
+        # one extra column / row, counted exactly in coupling_bytes)
+        "coupling": 6 * esz,
     }[kind]
+
+
+def coupling_bytes(nx: int, ny: int, esz: int) -> int:
+    """Algorithmic bytes of one ebit_coupling launch: C and kappa read,
+    rho and mu written (ny*nx each), fx ny*(nx+1) and fy (ny+1)*nx written."""
+    return esz * (4 * nx * ny + ny * (nx + 1) + (ny + 1) * nx)
 
 
 # FP64 operations of one crossing candidate of the sweep (two circle fits and
@@ -290,7 +299,21 @@ def run_ours(args, wl, world, rank, local):
     for _ in range(args.steps):
         ebit.ebit_step(ctx, u, v, wl.dt)
     kt = ebit.ebit_timings(ctx)
+    # the hand-off to a flow solver (properties and surface-tension source
+    # from the step's C and kappa), timed the same way over its own launches;
+    # not part of the step
+    outs = [torch.empty(sh, dtype=torch.float32, device="cuda")
+            for sh in ((n, n), (n, n), (n, n + 1), (n + 1, n))]
+    fl = dict(rho1=1000.0, rho2=1.2, mu1=1.0e-3, mu2=1.8e-5, sigma=0.0728)
+    for _ in range(3):
+        ebit.ebit_coupling(ctx, **fl, rho=outs[0], mu=outs[1], fx=outs[2], fy=outs[3])
+    ebit.ebit_timings(ctx)
+    for _ in range(args.steps):
+        ebit.ebit_coupling(ctx, **fl, rho=outs[0], mu=outs[1], fx=outs[2], fy=outs[3])
+    kc = ebit.ebit_timings(ctx)["coupling"]
     ebit.ebit_set_timing(ctx, False)
+    del outs
+    kt = {k: t for k, t in kt.items() if t[1] > 0 or k != "coupling"}
     launches_per_step = sum(nl for _, nl in kt.values()) / args.steps
     hbm, peak_kind = peaks()
     esz = 4
@@ -322,6 +345,14 @@ def run_ours(args, wl, world, rank, local):
                                 "GBps": kernel_bytes_per_cell(k, esz) * cells / (t / max(1, nl) / 1e3) / 1e9
                                 if t > 0 and k != "area" else None}
                             for k, (t, nl) in kt.items()}}
+    cb = coupling_bytes(n, n, esz)
+    c_ms = kc[0] / max(1, kc[1])
+    c_traffic, _ = traffic_record("coupling")
+    coupling = {"kernel": "k_coupling", "bound": "hbm", "launches": kc[1], "avg_launch_ms": c_ms,
+                "achieved": cb / (c_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": cb / (c_ms / 1e3) / 1e9 / hbm, "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                "algorithmic_bytes": cb, "traffic": None if c_traffic is None else c_traffic * cells,
+                "l2": "C, kappa and outputs (0.40 GB) larger than L2, no flush"}
     step_model = step_bytes_per_cell(esz) * cells
     step_roof = {"bytes_per_cell": step_bytes_per_cell(esz), "achieved_GBps": step_model / (ms_per_step / 1e3) / 1e9,
                  "frac": step_model / (ms_per_step / 1e3) / 1e9 / hbm}
@@ -406,7 +437,8 @@ def run_ours(args, wl, world, rank, local):
                            "l2": "working set (~0.45 GB) larger than L2, no flush"},
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(round(launches_per_step * args.steps)),
-                "roofline": roofline, "step_roofline": step_roof, "fp64": fp64, "cpu_baseline": cpu,
+                "roofline": roofline, "step_roofline": step_roof, "coupling": coupling, "fp64": fp64,
+                "cpu_baseline": cpu,
                 "markers": {"nH": int(diag["counters"][0]), "nV": int(diag["counters"][1])}}
         print(json.dumps(line), flush=True)
     if world > 1:
