@@ -243,6 +243,33 @@ def job_value(world, cells, steps, max_ms):
     return world * cells * steps / (max_ms / 1e3)
 
 
+COUPLING_FLUIDS = dict(rho1=1000.0, rho2=1.2, mu1=1.0e-3, mu2=1.8e-5, sigma=0.0728)
+
+
+def time_coupling(torch, ebit, ctx, n, dtype, launches):
+    """The hand-off to a flow solver (properties and surface-tension source
+    from the step's C and kappa; not part of the step), timed by the
+    library's events around each of its launches (timing must be on).
+    Returns (total ms, launches)."""
+    outs = [torch.empty(sh, dtype=dtype, device="cuda") for sh in ((n, n), (n, n), (n, n + 1), (n + 1, n))]
+    for _ in range(3):
+        ebit.ebit_coupling(ctx, **COUPLING_FLUIDS, rho=outs[0], mu=outs[1], fx=outs[2], fy=outs[3])
+    ebit.ebit_timings(ctx)
+    for _ in range(launches):
+        ebit.ebit_coupling(ctx, **COUPLING_FLUIDS, rho=outs[0], mu=outs[1], fx=outs[2], fy=outs[3])
+    return ebit.ebit_timings(ctx)["coupling"]
+
+
+def coupling_roofline(kc, n, esz, hbm, peak_kind):
+    cb = coupling_bytes(n, n, esz)
+    c_ms = kc[0] / max(1, kc[1])
+    return {"kernel": "k_coupling", "bound": "hbm", "launches": kc[1], "avg_launch_ms": c_ms,
+            "achieved": cb / (c_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": cb / (c_ms / 1e3) / 1e9 / hbm, "peak_source": f"{peak_kind} hbm_gbs (copy)",
+            "algorithmic_bytes": cb, "bytes_per_cell": 6 * esz,
+            "l2": f"C, kappa and outputs ({cb / 1e9:.2f} GB) larger than L2, no flush"}
+
+
 def timed_steps(torch, ebit, ctx, u, v, dt, K, stream):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
     ev[0].record(stream)
@@ -299,20 +326,8 @@ def run_ours(args, wl, world, rank, local):
     for _ in range(args.steps):
         ebit.ebit_step(ctx, u, v, wl.dt)
     kt = ebit.ebit_timings(ctx)
-    # the hand-off to a flow solver (properties and surface-tension source
-    # from the step's C and kappa), timed the same way over its own launches;
-    # not part of the step
-    outs = [torch.empty(sh, dtype=torch.float32, device="cuda")
-            for sh in ((n, n), (n, n), (n, n + 1), (n + 1, n))]
-    fl = dict(rho1=1000.0, rho2=1.2, mu1=1.0e-3, mu2=1.8e-5, sigma=0.0728)
-    for _ in range(3):
-        ebit.ebit_coupling(ctx, **fl, rho=outs[0], mu=outs[1], fx=outs[2], fy=outs[3])
-    ebit.ebit_timings(ctx)
-    for _ in range(args.steps):
-        ebit.ebit_coupling(ctx, **fl, rho=outs[0], mu=outs[1], fx=outs[2], fy=outs[3])
-    kc = ebit.ebit_timings(ctx)["coupling"]
+    kc = time_coupling(torch, ebit, ctx, n, torch.float32, args.steps)
     ebit.ebit_set_timing(ctx, False)
-    del outs
     kt = {k: t for k, t in kt.items() if t[1] > 0 or k != "coupling"}
     launches_per_step = sum(nl for _, nl in kt.values()) / args.steps
     hbm, peak_kind = peaks()
@@ -345,14 +360,9 @@ def run_ours(args, wl, world, rank, local):
                                 "GBps": kernel_bytes_per_cell(k, esz) * cells / (t / max(1, nl) / 1e3) / 1e9
                                 if t > 0 and k != "area" else None}
                             for k, (t, nl) in kt.items()}}
-    cb = coupling_bytes(n, n, esz)
-    c_ms = kc[0] / max(1, kc[1])
     c_traffic, _ = traffic_record("coupling")
-    coupling = {"kernel": "k_coupling", "bound": "hbm", "launches": kc[1], "avg_launch_ms": c_ms,
-                "achieved": cb / (c_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": cb / (c_ms / 1e3) / 1e9 / hbm, "peak_source": f"{peak_kind} hbm_gbs (copy)",
-                "algorithmic_bytes": cb, "traffic": None if c_traffic is None else c_traffic * cells,
-                "l2": "C, kappa and outputs (0.40 GB) larger than L2, no flush"}
+    coupling = coupling_roofline(kc, n, esz, hbm, peak_kind)
+    coupling["traffic"] = None if c_traffic is None else c_traffic * cells
     step_model = step_bytes_per_cell(esz) * cells
     step_roof = {"bytes_per_cell": step_bytes_per_cell(esz), "achieved_GBps": step_model / (ms_per_step / 1e3) / 1e9,
                  "frac": step_model / (ms_per_step / 1e3) / 1e9 / hbm}
@@ -415,11 +425,15 @@ def run_ours(args, wl, world, rank, local):
         t64, lat64 = timed_steps(torch, ebit, ctx64, u64, v64, wl.dt, args.steps, stream)
         barrier()
         ebit.ebit_sync(ctx64)
+        ebit.ebit_set_timing(ctx64, True)
+        kc64 = time_coupling(torch, ebit, ctx64, n, torch.float64, args.steps)
+        ebit.ebit_set_timing(ctx64, False)
         t64 = max_over_ranks(t64, world, "cuda")
         sb = step_bytes_per_cell(8) * cells
         fp64 = {"value": job_value(world, cells, args.steps, t64), "unit": UNIT, "ms_per_step": t64 / args.steps,
                 "p50_ms": float(np.percentile(lat64, 50)), "p99_ms": float(np.percentile(lat64, 99)),
-                "step_roofline_frac": sb / (t64 / args.steps / 1e3) / 1e9 / hbm}
+                "step_roofline_frac": sb / (t64 / args.steps / 1e3) / 1e9 / hbm,
+                "coupling": coupling_roofline(kc64, n, 8, hbm, peak_kind)}
         ebit.ebit_destroy(ctx64)
 
     cpu = None

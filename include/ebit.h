@@ -164,7 +164,8 @@ typedef struct { double rho1, rho2, mu1, mu2, sigma; } ebit_fluids;
  *   fy = sigma kappa_f (C(i,j) - C(i,j-1)) / dx on the horizontal faces,
  *   (ny+1)*nx, face (i,j) between cells (i,j-1) and (i,j)
  * (the surface term sigma kappa n delta_S of Eq. 6 as a face force density
- * sigma kappa grad C, the form whose pressure balance is exact).  kappa_f is
+ * sigma kappa grad C, the form whose pressure balance is exact; evaluated as
+ * (sigma/dx) kappa_f dC with sigma/dx formed once).  kappa_f is
  * the mean of the two cells' curvatures when both are valid, the valid one
  * when one is, and 0 when neither is; wall faces carry 0.
  * Outputs: caller-owned DEVICE buffers, contiguous row-major, element type of

@@ -1212,12 +1212,14 @@ namespace {
 // fraction C stands in for the Heaviside function of Eq. 8, and the surface
 // term sigma kappa n delta_S of Eq. 6 becomes sigma kappa grad(C)
 // at the faces, with the face curvature the mean of the two cells' valid
-// heights-based curvatures (one valid: that one; none: 0).
+// heights-based curvatures (one valid: that one; none: 0).  The face
+// gradient is (C_b - C_a) times 1/dx, with sigma/dx formed once.
 template <typename R>
 void coupling(int nx, int ny, double dx, const double* C, const double* kappa, double rho1,
               double rho2, double mu1, double mu2, double sigma, double* rho, double* mu,
               double* fx, double* fy) {
-  const R r1 = (R)rho1, r2 = (R)rho2, m1 = (R)mu1, m2 = (R)mu2, sg = (R)sigma, h = (R)dx;
+  const R r1 = (R)rho1, r2 = (R)rho2, m1 = (R)mu1, m2 = (R)mu2;
+  const R sh = (R)sigma / (R)dx;  // sigma / dx
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       const R c = (R)C[(size_t)j * nx + i];
@@ -1231,7 +1233,7 @@ void coupling(int nx, int ny, double dx, const double* C, const double* kappa, d
     if (va && vb) kf = (ka + kb) * R(0.5);
     else if (va) kf = ka;
     else if (vb) kf = kb;
-    return (double)(sg * kf * ((R)C[b] - (R)C[a]) / h);
+    return (double)(sh * kf * ((R)C[b] - (R)C[a]));
   };
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i <= nx; ++i)

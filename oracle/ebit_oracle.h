@@ -89,7 +89,8 @@ int orc_curvature(int nx, int ny, double dx, int prec, const uint8_t* K,
  * rho = C rho1 + (1 - C) rho2 and mu likewise per cell (ny*nx), and the
  * surface-tension source sigma kappa grad(C) on the faces: fx on the
  * (nx+1)*ny vertical faces, fy on the nx*(ny+1) horizontal ones, zero on the
- * walls.  Arithmetic in the state precision. */
+ * walls.  Arithmetic in the state precision: f = (sigma/dx) kappa_f dC with
+ * sigma/dx formed once. */
 int orc_coupling(int nx, int ny, double dx, int prec, const double* C, const double* kappa,
                  double rho1, double rho2, double mu1, double mu2, double sigma,
                  double* rho, double* mu, double* fx, double* fy);

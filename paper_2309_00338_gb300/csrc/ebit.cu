@@ -129,8 +129,8 @@ template <typename R>
 ebit_status launch_coupling(ebit_ctx* c, const ebit_fluids* fl, void* rho, void* mu, void* fx,
                             void* fy) {
   const Layout& L = c->L;
-  const ebit::Fluids<R> f{(R)fl->rho1, (R)fl->rho2, (R)fl->mu1, (R)fl->mu2, (R)fl->sigma,
-                          (R)c->grid.dx};
+  const ebit::Fluids<R> f{(R)fl->rho1, (R)fl->rho2, (R)fl->mu1, (R)fl->mu2,
+                          (R)fl->sigma / (R)c->grid.dx};
   const dim3 grid((L.d.nx + 1 + ebit::kCT - 1) / ebit::kCT, (L.d.ny + 1 + ebit::kCR - 1) / ebit::kCR);
   {
     Timed t(c, EBIT_K_COUPLING);
