@@ -134,8 +134,12 @@ ebit_status launch_coupling(ebit_ctx* c, const ebit_fluids* fl, void* rho, void*
   const dim3 grid((L.d.nx + 1 + ebit::kCT - 1) / ebit::kCT, (L.d.ny + 1 + ebit::kCR - 1) / ebit::kCR);
   {
     Timed t(c, EBIT_K_COUPLING);
-    ebit::k_coupling<R><<<grid, ebit::kCT, 0, c->stream>>>((const R*)c->C, (const R*)c->kappa, L.d, f,
-                                                           (R*)rho, (R*)mu, (R*)fx, (R*)fy);
+    if constexpr (sizeof(R) == 8)
+      ebit::k_coupling_q<<<grid, ebit::kCT, 0, c->stream>>>((const R*)c->C, (const R*)c->kappa, L.d, f,
+                                                            (R*)rho, (R*)mu, (R*)fx, (R*)fy);
+    else
+      ebit::k_coupling<R><<<grid, ebit::kCT, 0, c->stream>>>((const R*)c->C, (const R*)c->kappa, L.d,
+                                                             f, (R*)rho, (R*)mu, (R*)fx, (R*)fy);
   }
   EBIT_CK(cudaGetLastError());
   return EBIT_OK;

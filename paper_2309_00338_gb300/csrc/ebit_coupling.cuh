@@ -125,4 +125,159 @@ __global__ void __launch_bounds__(kCT) k_coupling(const R* __restrict__ C, const
   }
 }
 
+// The double form.  On this part the FP64 pipe retires a warp instruction
+// every 16 cycles, so FP64 work issued by a warp in which only a few lanes
+// hold a mixed cell or a face with a valid curvature would bound the kernel.
+// Instead every lane settles pure cells and force-free faces with integer
+// tests and stores them, and queues the rest in per-warp rings in shared
+// memory; whenever a ring holds 32 items the warp evaluates them with every
+// lane busy and stores the results.  The arithmetic is the one above: a face
+// with one valid curvature k queues (k, k), whose mean (k + k) / 2 is k.
+struct FaceRing {
+  static constexpr int kCap = 128;  // >= 31 left over + 64 queued per row
+  double ka[kCap], kb[kCap], ca[kCap], cb[kCap];
+  double* out[kCap];
+};
+struct MixRing {
+  static constexpr int kCap = 64;  // >= 31 left over + 32 queued per row
+  double c[kCap];
+  long long idx[kCap];
+};
+
+__device__ __forceinline__ void face_push(FaceRing& F, unsigned& tail, bool need, double ka, double kb,
+                                          double ca, double cb, double* out) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, need);
+  if (need) {
+    const unsigned s = (tail + __popc(m & ((1u << lane) - 1u))) & (FaceRing::kCap - 1);
+    F.ka[s] = ka;
+    F.kb[s] = kb;
+    F.ca[s] = ca;
+    F.cb[s] = cb;
+    F.out[s] = out;
+  }
+  tail += __popc(m);
+}
+
+__device__ __forceinline__ void face_run(const FaceRing& F, unsigned head, const Fluids<double>& f) {
+  const unsigned s = (head + (threadIdx.x & 31)) & (FaceRing::kCap - 1);
+  const double kf = (F.ka[s] + F.kb[s]) * 0.5;
+  *F.out[s] = f.sh * kf * (F.cb[s] - F.ca[s]);
+}
+
+__device__ __forceinline__ void mix_run(const MixRing& M, unsigned head, const Fluids<double>& f,
+                                        double* __restrict__ rho, double* __restrict__ mu) {
+  const unsigned s = (head + (threadIdx.x & 31)) & (MixRing::kCap - 1);
+  const double c = M.c[s];
+  const double o = 1.0 - c;
+  if (rho) rho[M.idx[s]] = c * f.r1 + o * f.r2;
+  if (mu) mu[M.idx[s]] = c * f.m1 + o * f.m2;
+}
+
+// Same grid, layouts and outputs as k_coupling.
+template <int CR = kCR, int NB = 2>
+__global__ void __launch_bounds__(kCT) k_coupling_q(const double* __restrict__ C,
+                                                    const double* __restrict__ kap, Dims d,
+                                                    Fluids<double> f, double* __restrict__ rho,
+                                                    double* __restrict__ mu, double* __restrict__ fx,
+                                                    double* __restrict__ fy) {
+  static_assert(CR % NB == 0, "strip of whole batches");
+  __shared__ FaceRing face_ring[kCT / 32];
+  __shared__ MixRing mix_ring[kCT / 32];
+  FaceRing& F = face_ring[threadIdx.x >> 5];
+  MixRing& M = mix_ring[threadIdx.x >> 5];
+  unsigned fh = 0, ft = 0, mh = 0, mt = 0;  // ring heads and tails, warp-uniform
+  const int i = blockIdx.x * kCT + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int j0 = blockIdx.y * CR;
+  const int jc = min(j0 + CR, d.ny);
+  const int j1 = min(j0 + CR, d.ny + 1);
+  const bool cell = i < d.nx;
+  const bool left = lane == 0 && cell && i > 0;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  const long long wx = (long long)d.nx + 1;
+  const bool props = rho || mu;
+  double cb = 0.0, kb = nan;
+  if (j0 > 0 && cell) {
+    cb = __ldg(&C[(long long)(j0 - 1) * d.P + i]);
+    kb = __ldg(&kap[(long long)(j0 - 1) * d.P + i]);
+  }
+  for (int jb = j0; jb < j1; jb += NB) {
+    double c[NB], k[NB], cl[NB], kl[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int j = jb + q;
+      c[q] = 0.0;
+      k[q] = nan;
+      cl[q] = 0.0;
+      kl[q] = nan;
+      if (j < jc && cell) {
+        c[q] = __ldg(&C[(long long)j * d.P + i]);
+        k[q] = __ldg(&kap[(long long)j * d.P + i]);
+      }
+      if (j < jc && left) {
+        cl[q] = __ldg(&C[(long long)j * d.P + i - 1]);
+        kl[q] = __ldg(&kap[(long long)j * d.P + i - 1]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int j = jb + q;
+      const double cs = __shfl_up_sync(0xffffffffu, c[q], 1);
+      const double ks = __shfl_up_sync(0xffffffffu, k[q], 1);
+      if (lane != 0) {
+        cl[q] = cs;
+        kl[q] = ks;
+      }
+      const bool vk = !nan_bits(k[q]);
+      // cell properties
+      const bool cell_row = cell && j < jc && props;
+      const bool pure1 = one_bits(c[q]), pure0 = zero_bits(c[q]);
+      if (cell_row && (pure1 || pure0)) {
+        const long long o = (long long)j * d.nx + i;
+        if (rho) rho[o] = pure1 ? f.r1 : f.r2;
+        if (mu) mu[o] = pure1 ? f.m1 : f.m2;
+      }
+      const bool mneed = cell_row && !pure1 && !pure0;
+      {
+        const unsigned m = __ballot_sync(0xffffffffu, mneed);
+        if (mneed) {
+          const unsigned s = (mt + __popc(m & ((1u << lane) - 1u))) & (MixRing::kCap - 1);
+          M.c[s] = c[q];
+          M.idx[s] = (long long)j * d.nx + i;
+        }
+        mt += __popc(m);
+      }
+      // vertical face (i, j) between cells (i-1, j) and (i, j)
+      const bool xrow = fx && j < jc && i <= d.nx;
+      const bool vl = !nan_bits(kl[q]);
+      const bool xneed = xrow && i > 0 && i < d.nx && (vl || vk);
+      if (xrow && !xneed) fx[(long long)j * wx + i] = 0.0;
+      face_push(F, ft, xneed, vl ? kl[q] : k[q], vk ? k[q] : kl[q], cl[q], c[q],
+                xneed ? fx + (long long)j * wx + i : nullptr);
+      // horizontal face (i, j) between cells (i, j-1) and (i, j)
+      const bool yrow = fy && cell && j < j1;
+      const bool vb = !nan_bits(kb);
+      const bool yneed = yrow && j > 0 && j < d.ny && (vb || vk);
+      if (yrow && !yneed) fy[(long long)j * d.nx + i] = 0.0;
+      face_push(F, ft, yneed, vb ? kb : k[q], vk ? k[q] : kb, cb, c[q],
+                yneed ? fy + (long long)j * d.nx + i : nullptr);
+      cb = c[q];
+      kb = k[q];
+      __syncwarp();
+      while (ft - fh >= 32) {
+        face_run(F, fh, f);
+        fh += 32;
+      }
+      if (mt - mh >= 32) {
+        mix_run(M, mh, f, rho, mu);
+        mh += 32;
+      }
+      __syncwarp();
+    }
+  }
+  if ((unsigned)lane < ft - fh) face_run(F, fh, f);
+  if ((unsigned)lane < mt - mh) mix_run(M, mh, f, rho, mu);
+}
+
 }  // namespace ebit
