@@ -159,22 +159,33 @@ def dist():
     return world, rank, local
 
 
+# the sources each kernel is compiled from (its own header and the device
+# code it shares); a traffic record is valid while these are unchanged
+KERNEL_SOURCES = {
+    "sweep": ["ebit_tile.cuh", "ebit_device.cuh"],
+    "fields": ["ebit_fields.cuh", "ebit_device.cuh"],
+    "coupling": ["ebit_coupling.cuh", "ebit_device.cuh"],
+}
+
+
+def kernel_source_hash(kernel):
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2309_00338_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def traffic_record(kernel):
-    """ncu DRAM bytes per launch for the kernel, if the committed record was
-    taken on the current kernel sources."""
+    """ncu DRAM bytes per cell and launch for the kernel, if the committed
+    record was taken on the kernel's current sources."""
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
             rec = json.load(f)
     except Exception:
         return None, None
-    h = hashlib.sha256()
-    for name in sorted(os.listdir(os.path.join(ROOT, "paper_2309_00338_gb300", "csrc"))):
-        with open(os.path.join(ROOT, "paper_2309_00338_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
-    if rec.get("csrc_sha256") != h.hexdigest():
-        return None, rec
     k = rec.get("kernels", {}).get(kernel)
-    if not k:
+    if not k or k.get("sources_sha256") != kernel_source_hash(kernel):
         return None, rec
     return k["dram_bytes_per_cell"], rec
 
