@@ -32,6 +32,7 @@ NCOUNTERS = 16
 
 FP64, FP32 = 0, 1
 LINE_ONLY = 2  # flag: straight-line fit (EBIT-SL)
+GHF = 4        # flag: generalised height-function fallbacks for curvature
 
 
 def build(force: bool = False) -> str:
@@ -112,6 +113,7 @@ def _set_signatures(L):
     L.orc_curvature.argtypes = [i32, i32, f64, i32, P, P, P, P, P, P, P]
     L.orc_fit.argtypes = [P, P, P, i32, P, i32, P]
     L.orc_coupling.argtypes = [i32, i32, f64, i32, P, P, f64, f64, f64, f64, f64, P, P, P, P]
+    L.orc_parabola_kappa.argtypes = [i32, P, P, P, f64, f64, f64, f64, f64, P]
     L.orc_loops.argtypes = [i32, i32, f64, i32, P, P, P, P, P, P, P, i64, P]
     L.orc_loops.restype = i64
     L.orc_shape_error.argtypes = [i32, i32, f64, P, P, P, f64, f64, f64]
@@ -229,7 +231,7 @@ def sweep(S: State, axis: int, vel, lam: float, line_only=False):
     return ctr, float(mc[0])
 
 
-def step(S: State, u, v, dt: float, line_only=False):
+def step(S: State, u, v, dt: float, line_only=False, ghf=False):
     """One full EBIT step in place.  Returns dict with C, kappa, counters,
     area and max_cfl; the state's step_index advances by one."""
     C = np.zeros((S.ny, S.nx), np.float64)
@@ -237,7 +239,8 @@ def step(S: State, u, v, dt: float, line_only=False):
     ctr = np.zeros(NCOUNTERS, np.int64)
     stats = np.zeros(2, np.float64)
     uu, vv = _vel(u, S), _vel(v, S)
-    rc = lib().orc_step(S.nx, S.ny, S.dx, S.prec | (LINE_ONLY if line_only else 0), S.step_index,
+    rc = lib().orc_step(S.nx, S.ny, S.dx, S.prec | (LINE_ONLY if line_only else 0) | (GHF if ghf else 0),
+                        S.step_index,
                         _p(S.K), _p(S.Z), _p(S.sH), _p(S.sV), _p(uu), _p(vv), float(dt),
                         _p(C), _p(kap), _p(ctr), _p(stats))
     S.step_index += 1
@@ -252,13 +255,29 @@ def fraction(S: State):
     return C, float(a[0])
 
 
-def curvature(S: State, C):
+def curvature(S: State, C, ghf=False):
+    """kappa (NaN where none) and the number of interface cells without a
+    valid 7x3 stencil; with ghf=True also the counts resolved by the other
+    direction, mixed heights and the markers of the 3x3 block."""
     C = np.ascontiguousarray(C, np.float64)
     kap = np.zeros((S.ny, S.nx), np.float64)
-    n = np.zeros(1, np.int64)
-    lib().orc_curvature(S.nx, S.ny, S.dx, S.prec, _p(S.K), _p(S.Z), _p(S.sH), _p(S.sV), _p(C),
-                        _p(kap), _p(n))
+    n = np.zeros(4, np.int64)
+    lib().orc_curvature(S.nx, S.ny, S.dx, S.prec | (GHF if ghf else 0), _p(S.K), _p(S.Z), _p(S.sH),
+                        _p(S.sV), _p(C), _p(kap), _p(n))
+    if ghf:
+        return kap, int(n[0]), {"other": int(n[1]), "mixed": int(n[2]), "markers": int(n[3])}
     return kap, int(n[0])
+
+
+def parabola_kappa(X, Y, W, origin, normal, dx=1.0):
+    """Test hook: the least-squares parabola fit of the generalised
+    fallbacks; returns kappa or None when the fit is singular."""
+    X = np.ascontiguousarray(X, np.float64); Y = np.ascontiguousarray(Y, np.float64)
+    W = np.ascontiguousarray(W, np.float64)
+    k = np.zeros(1, np.float64)
+    ok = lib().orc_parabola_kappa(len(X), _p(X), _p(Y), _p(W), float(origin[0]), float(origin[1]),
+                                  float(normal[0]), float(normal[1]), float(dx), _p(k))
+    return float(k[0]) if ok else None
 
 
 def coupling(S: State, C, kappa, rho1, rho2, mu1, mu2, sigma):

@@ -693,16 +693,95 @@ double fraction(const State<R>& S, double dx, double* C) {
 }
 
 // ---------------------------------------------------------------------------
-// Height-function curvature (Sec. 2.5; the standard 7x3 height functions).
+// Height-function curvature (Sec. 2.5): the standard 7x3 height functions,
+// and, when asked for, the generalised fallbacks of the height-function
+// method the paper cites (Popinet 2009): the stencil along the other
+// direction, then a parabola fitted to the heights of both directions
+// ("mixed heights"), then a parabola fitted to the markers of the 3x3 block
+// (where the volume-of-fluid form fits interface-fragment centroids, the
+// markers give points that lie on the interface).
 // ---------------------------------------------------------------------------
+
+// Curvature of the parabola z = a s^2 + b s + c fitted by weighted least
+// squares to the points (X, Y) (cell units), in the frame with origin (ox, oy)
+// and unit normal (nx, ny) pointing out of the reference phase (tangent
+// (ny, -nx)), evaluated at s = 0: kappa = -2a / (1 + b^2)^(3/2) / dx, which is
+// +1/R for a reference-phase drop of radius R.  The normal equations are
+// solved by Cramer's rule.  Returns false when the system is singular.
+bool parabola_kappa(int n, const double* X, const double* Y, const double* W, double ox, double oy,
+                    double nx, double ny, double dx, double* kappa) {
+  double S0 = 0.0, S1 = 0.0, S2 = 0.0, S3 = 0.0, S4 = 0.0, T0 = 0.0, T1 = 0.0, T2 = 0.0;
+  for (int p = 0; p < n; ++p) {
+    const double ddx = X[p] - ox, ddy = Y[p] - oy;
+    const double sv = ddx * ny - ddy * nx;  // along the tangent (ny, -nx)
+    const double zv = ddx * nx + ddy * ny;  // along the normal
+    const double w = W[p];
+    const double s2 = sv * sv;
+    S0 = S0 + w;
+    S1 = S1 + w * sv;
+    S2 = S2 + w * s2;
+    S3 = S3 + w * (s2 * sv);
+    S4 = S4 + w * (s2 * s2);
+    T0 = T0 + w * zv;
+    T1 = T1 + w * (zv * sv);
+    T2 = T2 + w * (zv * s2);
+  }
+  const double m00 = S2 * S0 - S1 * S1;
+  const double m01 = S3 * S0 - S1 * S2;
+  const double m02 = S3 * S1 - S2 * S2;
+  const double det = S4 * m00 - S3 * m01 + S2 * m02;
+  if (!(std::fabs(det) > 1e-10 * (S0 * S0 * S0))) return false;
+  const double u1 = T1 * S0 - S1 * T0;
+  const double da = T2 * m00 - S3 * u1 + S2 * (T1 * S1 - S2 * T0);
+  const double db = S4 * u1 - T2 * m01 + S2 * (S3 * T0 - T1 * S2);
+  const double a = da / det, b = db / det;
+  const double q = 1.0 + b * b;
+  *kappa = (-2.0 * a) / (q * std::sqrt(q)) / dx;
+  return std::isfinite(*kappa);
+}
+
 template <typename R>
-void curvature(const State<R>& S, const double* Cd, double dx, double* kappa, int64_t* ninv) {
+void curvature(const State<R>& S, const double* Cd, double dx, double* kappa, int64_t* ctr,
+               bool ghf) {
   const int nx = S.nx, ny = S.ny;
   std::vector<R> C((size_t)nx * ny);
   for (size_t t = 0; t < C.size(); ++t) C[t] = (R)Cd[t];
   auto cf = [&](int i, int j) { return C[(size_t)j * nx + i]; };
   const R dxR = (R)dx;
   const R nanv = std::numeric_limits<R>::quiet_NaN();
+  // The column of seven cells through (i+m, j-3..j+3) (ycol) or the row
+  // (i-3..i+3, j+m): its count h of reference-phase cells and its
+  // orientation: 1 when the low end is reference phase and the high end is
+  // not, -1 for the reverse, 0 when the column is not a valid height (an end
+  // cell is mixed, both ends agree, or it leaves the domain).
+  auto column = [&](int i, int j, int m, bool ycol, R* h) -> int {
+    const bool in = ycol ? (i + m >= 0 && i + m <= nx - 1 && j - 3 >= 0 && j + 3 <= ny - 1)
+                         : (j + m >= 0 && j + m <= ny - 1 && i - 3 >= 0 && i + 3 <= nx - 1);
+    if (!in) return 0;
+    R acc = R(0);
+    for (int t = -3; t <= 3; ++t) acc = acc + (ycol ? cf(i + m, j + t) : cf(i + t, j + m));
+    *h = acc;
+    const R lo = ycol ? cf(i + m, j - 3) : cf(i - 3, j + m);
+    const R hi = ycol ? cf(i + m, j + 3) : cf(i + 3, j + m);
+    return (lo == R(1) && hi == R(0)) ? 1 : (lo == R(0) && hi == R(1)) ? -1 : 0;
+  };
+  // The standard 7x3 stencil: three valid columns of one orientation.
+  auto stencil = [&](int i, int j, bool ycol, double* out) -> bool {
+    R h[3];
+    int orient[3];
+    for (int m = -1; m <= 1; ++m) orient[m + 1] = column(i, j, m, ycol, &h[m + 1]);
+    if (orient[0] == 0 || orient[0] != orient[1] || orient[1] != orient[2]) return false;
+    // h counts reference-phase cells in the column, so for either
+    // orientation kappa = -h'' / (dx (1 + h'^2)^(3/2)) is positive for a
+    // reference-phase drop.
+    const R hp = (h[2] - h[0]) * R(0.5);
+    const R hpp = (h[2] - h[1]) - (h[1] - h[0]);
+    const R q = R(1) + hp * hp;
+    const R den = dxR * (q * std::sqrt(q));
+    *out = (double)(-hpp / den);
+    return true;
+  };
+  const R one = R(1), zero = R(0);
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       double& out = kappa[(size_t)j * nx + i];
@@ -714,8 +793,8 @@ void curvature(const State<R>& S, const double* Cd, double dx, double* kappa, in
       }
       // Orientation from the cell's own segments: heights are taken along y
       // when the segments are at least as long in x as in y.
-      const R px[4] = {S.hc(i, j), R(1), S.hc(i, j + 1), R(0)};
-      const R py[4] = {R(0), S.vc(i + 1, j), R(1), S.vc(i, j)};
+      const R px[4] = {S.hc(i, j), one, S.hc(i, j + 1), zero};
+      const R py[4] = {zero, S.vc(i + 1, j), one, S.vc(i, j)};
       int seg[2][2];
       const int ns = cell_segments(S, i, j, seg);
       R ax = R(0), ay = R(0);
@@ -725,36 +804,92 @@ void curvature(const State<R>& S, const double* Cd, double dx, double* kappa, in
         ay = ay + std::fabs(py[b] - py[a]);
       }
       const bool ycol = ax >= ay;
-      R h[3];
-      int orient[3];
-      bool inside = ycol ? (i - 1 >= 0 && i + 1 <= nx - 1 && j - 3 >= 0 && j + 3 <= ny - 1)
-                         : (j - 1 >= 0 && j + 1 <= ny - 1 && i - 3 >= 0 && i + 3 <= nx - 1);
-      if (!inside) {
-        out = (double)nanv;
-        *ninv += 1;
+      if (stencil(i, j, ycol, &out)) continue;
+      ctr[ORC_HF_INVALID] += 1;
+      out = (double)nanv;
+      if (!ghf) continue;
+      // 1. the standard stencil along the other direction
+      if (stencil(i, j, !ycol, &out)) {
+        ctr[ORC_HF_OTHER] += 1;
         continue;
       }
-      for (int m = -1; m <= 1; ++m) {
-        R acc = R(0);
-        for (int t = -3; t <= 3; ++t) acc = acc + (ycol ? cf(i + m, j + t) : cf(i + t, j + m));
-        h[m + 1] = acc;
-        const R lo = ycol ? cf(i + m, j - 3) : cf(i - 3, j + m);
-        const R hi = ycol ? cf(i + m, j + 3) : cf(i + 3, j + m);
-        orient[m + 1] = (lo == R(1) && hi == R(0)) ? 1 : (lo == R(0) && hi == R(1)) ? -1 : 0;
+      out = (double)nanv;
+      // The fitting frame needs the cell's single segment A->B: origin at its
+      // midpoint, normal perpendicular to it, turned away from the
+      // reference-phase corners (their offsets from the cell centre, each
+      // signed by colour, sum to a vector into the reference phase).
+      if (ns != 1) continue;
+      const int ea = seg[0][0], eb = seg[0][1];
+      const double Ax = (double)i + (double)px[ea], Ay = (double)j + (double)py[ea];
+      const double Bx = (double)i + (double)px[eb], By = (double)j + (double)py[eb];
+      const double ox = (Ax + Bx) * 0.5, oy = (Ay + By) * 0.5;
+      double n0x = By - Ay, n0y = -(Bx - Ax);
+      static const int sxc[4] = {-1, 1, 1, -1}, syc[4] = {-1, -1, 1, 1};
+      int gx = 0, gy = 0;
+      for (int q = 0; q < 4; ++q) {
+        gx += (2 * c[q] - 1) * sxc[q];
+        gy += (2 * c[q] - 1) * syc[q];
       }
-      if (orient[0] == 0 || orient[0] != orient[1] || orient[1] != orient[2]) {
-        out = (double)nanv;
-        *ninv += 1;
+      const double dot = n0x * (double)gx + n0y * (double)gy;
+      if (dot == 0.0) continue;
+      if (dot > 0.0) {
+        n0x = -n0x;
+        n0y = -n0y;
+      }
+      const double len = std::sqrt(n0x * n0x + n0y * n0y);
+      if (!(len > 0.0)) continue;
+      const double unx = n0x / len, uny = n0y / len;
+      // Points kept only when at least half a cell from every point already
+      // kept (independent positions).
+      double X[16], Y[16], W[16];
+      int np = 0;
+      auto add = [&](double x, double y, double w) {
+        for (int p = 0; p < np; ++p) {
+          const double ex = x - X[p], ey = y - Y[p];
+          if (ex * ex + ey * ey < 0.25) return;
+        }
+        X[np] = x;
+        Y[np] = y;
+        W[np] = w;
+        ++np;
+      };
+      // 2. mixed heights: every valid column of the cell's stencils in both
+      // directions gives the interface point on its centre line
+      for (int dir = 0; dir < 2; ++dir) {
+        const bool yc = dir == 0;
+        for (int m = -1; m <= 1; ++m) {
+          R h = R(0);
+          const int o = column(i, j, m, yc, &h);
+          if (o == 0) continue;
+          const double hd = (double)h;
+          const double lo = (double)((yc ? j : i) - 3), hi = (double)((yc ? j : i) + 4);
+          const double pos = o == 1 ? lo + hd : hi - hd;
+          const double mid = (double)((yc ? i : j) + m) + 0.5;
+          if (yc) add(mid, pos, 1.0);
+          else add(pos, mid, 1.0);
+        }
+      }
+      double kv = 0.0;
+      if (np >= 3 && parabola_kappa(np, X, Y, W, ox, oy, unx, uny, dx, &kv)) {
+        out = (double)(R)kv;
+        ctr[ORC_HF_MIXED] += 1;
         continue;
       }
-      // h counts reference-phase cells in the column, so for either
-      // orientation kappa = -h'' / (dx (1 + h'^2)^(3/2)) is positive for a
-      // reference-phase drop.
-      const R hp = (h[2] - h[0]) * R(0.5);
-      const R hpp = (h[2] - h[1]) - (h[1] - h[0]);
-      const R q = R(1) + hp * hp;
-      const R den = dxR * (q * std::sqrt(q));
-      out = (double)(-hpp / den);
+      // 3. the markers on the edges of the 3x3 block of cells around the
+      // cell (interface points on the grid lines)
+      np = 0;
+      for (int b = j - 1; b <= j + 2; ++b)
+        for (int a = i - 1; a <= i + 1; ++a)
+          if (a >= 0 && a < nx && b >= 0 && b <= ny && S.hasH(a, b))
+            add((double)a + (double)S.hc(a, b), (double)b, 1.0);
+      for (int b = j - 1; b <= j + 1; ++b)
+        for (int a = i - 1; a <= i + 2; ++a)
+          if (a >= 0 && a <= nx && b >= 0 && b < ny && S.hasV(a, b))
+            add((double)a, (double)b + (double)S.vc(a, b), 1.0);
+      if (np >= 3 && parabola_kappa(np, X, Y, W, ox, oy, unx, uny, dx, &kv)) {
+        out = (double)(R)kv;
+        ctr[ORC_HF_MARKERS] += 1;
+      }
     }
 }
 
@@ -1102,7 +1237,7 @@ int64_t loops(const State<R>& S, double dx, int64_t* n_open, double* area, doubl
 }
 
 template <typename R>
-int do_step(int nx, int ny, double dx, int64_t step_index, bool line_only, uint8_t* K,
+int do_step(int nx, int ny, double dx, int64_t step_index, bool line_only, bool ghf, uint8_t* K,
             uint8_t* Z, double* sH, double* sV, const double* u, const double* v, double dt,
             double* C, double* kappa, int64_t* counters, double* stats) {
   State<R> S = load<R>(nx, ny, K, Z, sH, sV);
@@ -1122,7 +1257,7 @@ int do_step(int nx, int ny, double dx, int64_t step_index, bool line_only, uint8
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i <= nx; ++i) ctr[ORC_N_V] += S.hasV(i, j);
   const double area = fraction(S, dx, C);
-  curvature(S, C, dx, kappa, &ctr[ORC_HF_INVALID]);
+  curvature(S, C, dx, kappa, ctr, ghf);
   store(S, K, Z, sH, sV);
   if (counters)
     for (int t = 0; t < ORC_NCOUNTERS; ++t) counters[t] = ctr[t];
@@ -1177,11 +1312,11 @@ int orc_step(int nx, int ny, double dx, int prec, int64_t step_index, uint8_t* K
              double* sH, double* sV, const double* u, const double* v, double dt, double* C,
              double* kappa, int64_t* counters, double* stats) {
   if (nx < 1 || ny < 1 || !(dx > 0.0)) return -1;
-  const bool line_only = (prec & 2) != 0;
+  const bool line_only = (prec & 2) != 0, ghf = (prec & 4) != 0;
   if ((prec & 1) == 0)
-    return do_step<double>(nx, ny, dx, step_index, line_only, K, Z, sH, sV, u, v, dt, C, kappa,
-                           counters, stats);
-  return do_step<float>(nx, ny, dx, step_index, line_only, K, Z, sH, sV, u, v, dt, C, kappa,
+    return do_step<double>(nx, ny, dx, step_index, line_only, ghf, K, Z, sH, sV, u, v, dt, C,
+                           kappa, counters, stats);
+  return do_step<float>(nx, ny, dx, step_index, line_only, ghf, K, Z, sH, sV, u, v, dt, C, kappa,
                         counters, stats);
 }
 
@@ -1196,12 +1331,24 @@ int orc_fraction(int nx, int ny, double dx, int prec, const uint8_t* K, const ui
 
 int orc_curvature(int nx, int ny, double dx, int prec, const uint8_t* K, const uint8_t* Z,
                   const double* sH, const double* sV, const double* C, double* kappa,
-                  int64_t* n_invalid) {
-  int64_t n = 0;
-  if ((prec & 1) == 0) curvature(load<double>(nx, ny, K, Z, sH, sV), C, dx, kappa, &n);
-  else curvature(load<float>(nx, ny, K, Z, sH, sV), C, dx, kappa, &n);
-  if (n_invalid) *n_invalid = n;
+                  int64_t* counts) {
+  int64_t ctr[ORC_NCOUNTERS] = {0};
+  const bool ghf = (prec & 4) != 0;
+  if ((prec & 1) == 0) curvature(load<double>(nx, ny, K, Z, sH, sV), C, dx, kappa, ctr, ghf);
+  else curvature(load<float>(nx, ny, K, Z, sH, sV), C, dx, kappa, ctr, ghf);
+  if (counts) {
+    counts[0] = ctr[ORC_HF_INVALID];
+    counts[1] = ctr[ORC_HF_OTHER];
+    counts[2] = ctr[ORC_HF_MIXED];
+    counts[3] = ctr[ORC_HF_MARKERS];
+  }
   return 0;
+}
+
+int orc_parabola_kappa(int n, const double* X, const double* Y, const double* W, double ox,
+                       double oy, double nx, double ny, double dx, double* kappa) {
+  if (n < 3 || n > 64) return 0;
+  return parabola_kappa(n, X, Y, W, ox, oy, nx, ny, dx, kappa) ? 1 : 0;
 }
 
 }  // extern "C"

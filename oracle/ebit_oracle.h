@@ -20,6 +20,8 @@
  * prec: 0 = FP64 throughout; 1 = FP32 state, FP32 advection arithmetic,
  *       FP64 circle fit and FP64 fraction arithmetic (values exchanged here
  *       as doubles that are exactly representable in FP32).
+ *       Flags or-ed into prec: 2 = straight-line fit (EBIT-SL), 4 = the
+ *       generalised height-function fallbacks for curvature.
  */
 #ifndef EBIT_ORACLE_H
 #define EBIT_ORACLE_H
@@ -56,6 +58,9 @@ enum {
   ORC_INVARIANT,       /* colour/marker parity mismatches (must stay 0)    */
   ORC_HF_INVALID,      /* interface cells without a valid 7x3 height stencil */
   ORC_CFL,             /* markers whose displacement exceeded one cell     */
+  ORC_HF_OTHER,        /* of those without a 7x3 stencil (generalised mode): */
+  ORC_HF_MIXED,        /*   resolved by the other direction's stencil, by a  */
+  ORC_HF_MARKERS,      /*   mixed-heights fit, by a fit to nearby markers    */
   ORC_NCOUNTERS = 16
 };
 
@@ -79,9 +84,20 @@ int orc_fraction(int nx, int ny, double dx, int prec, const uint8_t* K,
                  const uint8_t* Z, const double* sH, const double* sV,
                  double* C, double* area);
 
+/* Curvature of the fractions C; counts[4] (or NULL) receives the interface
+ * cells without a valid 7x3 stencil and, with flag 4, how many of them the
+ * other direction, mixed heights and the markers of the 3x3 block resolved.  Fallback
+ * fits run in double in both precision forms. */
 int orc_curvature(int nx, int ny, double dx, int prec, const uint8_t* K,
                   const uint8_t* Z, const double* sH, const double* sV,
-                  const double* C, double* kappa, int64_t* n_invalid);
+                  const double* C, double* kappa, int64_t* counts);
+
+/* Weighted least-squares parabola through n points (X, Y in cell units) in
+ * the frame of origin (ox, oy) and unit normal (nx, ny) (out of the reference
+ * phase); kappa at the origin, divided by dx.  Returns 1 if the fit is
+ * regular (test hook of the generalised fallbacks). */
+int orc_parabola_kappa(int n, const double* X, const double* Y, const double* W, double ox,
+                       double oy, double nx, double ny, double dx, double* kappa);
 
 /* Hand-off to a one-fluid Navier-Stokes solver (Sec. 2.5: the surface term
  * of Eq. 6 and the property law of Eq. 8, with the fractions standing in for
