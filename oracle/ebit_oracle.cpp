@@ -841,7 +841,7 @@ void curvature(const State<R>& S, const double* Cd, double dx, double* kappa, in
       const double unx = n0x / len, uny = n0y / len;
       // Points kept only when at least half a cell from every point already
       // kept (independent positions).
-      double X[16], Y[16], W[16];
+      double X[32], Y[32], W[32];  // at most 24 markers on the 3x3 block
       int np = 0;
       auto add = [&](double x, double y, double w) {
         for (int p = 0; p < np; ++p) {
