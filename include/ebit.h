@@ -47,8 +47,16 @@ typedef enum {
 typedef enum { EBIT_FP64 = 0, EBIT_FP32 = 1 } ebit_precision;
 
 /* flags: EBIT_FIT_LINE places unaligned markers on the chord crossing only
- * (the straight-line fit of the first EBIT version, Sec. 2.2). */
+ * (the straight-line fit of the first EBIT version, Sec. 2.2).
+ * EBIT_CURV_GHF gives the interface cells without a valid 7x3 height stencil
+ * a curvature from the generalised height-function method Sec. 2.5 cites:
+ * the stencil along the other direction, else a least-squares parabola
+ * through the valid heights of both directions, else one through the markers
+ * on the edges of the 3x3 block of cells (fits in double in both precision
+ * forms).  It costs one more dense pass over kappa and the fits, and a list
+ * of nx*ny int32 in the context.  Contexts only (servers reject it). */
 #define EBIT_FIT_LINE 1u
+#define EBIT_CURV_GHF 2u
 
 typedef struct {
   int32_t nx, ny;   /* cells; 1 <= nx, ny <= 32768                           */
@@ -94,6 +102,9 @@ enum {
   EBIT_D_NH = 0, EBIT_D_NV, EBIT_D_CANCELLED, EBIT_D_ZSET, EBIT_D_ZCONFLICT,
   EBIT_D_FIT_ONLINE, EBIT_D_FIT_LINE, EBIT_D_FIT_ONE, EBIT_D_FIT_TWO,
   EBIT_D_WALL_CLAMP, EBIT_D_INVARIANT, EBIT_D_HF_INVALID, EBIT_D_CFL,
+  /* with EBIT_CURV_GHF: of the EBIT_D_HF_INVALID cells, those resolved by the
+   * other direction, by mixed heights, by the markers fit */
+  EBIT_D_HF_OTHER, EBIT_D_HF_MIXED, EBIT_D_HF_MARKERS,
   EBIT_D_COUNT = 16
 };
 typedef struct {
@@ -192,8 +203,10 @@ const char* ebit_last_error(void);
  * milliseconds and the number of launches since the last call, then resets.
  * Kinds: EBIT_K_SWEEP (a split sweep), EBIT_K_CENTRE (second pass of the
  * gather sweep, when selected), EBIT_K_FIELDS (fractions, curvature and area
- * partials), EBIT_K_AREA (area sum), EBIT_K_COUPLING (ebit_coupling). */
-enum { EBIT_K_SWEEP = 0, EBIT_K_CENTRE, EBIT_K_FIELDS, EBIT_K_AREA, EBIT_K_COUPLING, EBIT_K_COUNT = 8 };
+ * partials), EBIT_K_AREA (area sum), EBIT_K_COUPLING (ebit_coupling),
+ * EBIT_K_GHF (list and fits of the generalised fallbacks). */
+enum { EBIT_K_SWEEP = 0, EBIT_K_CENTRE, EBIT_K_FIELDS, EBIT_K_AREA, EBIT_K_COUPLING, EBIT_K_GHF,
+       EBIT_K_COUNT = 8 };
 ebit_status ebit_set_timing(ebit_ctx* ctx, int on);
 ebit_status ebit_timings(ebit_ctx* ctx, double* ms, int64_t* launches);
 

@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/ebit.h: context allocation, the
 // launch sequence of one EBIT step, state I/O and error reporting.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -13,6 +14,7 @@
 #include "ebit_tile.cuh"
 #include "ebit_fields.cuh"
 #include "ebit_coupling.cuh"
+#include "ebit_ghf.cuh"
 
 namespace {
 
@@ -92,6 +94,10 @@ ebit_status alloc_ctx(ebit_ctx* c) {
   EBIT_AL(c->ctr, ebit::kCounters * sizeof(unsigned long long));
   EBIT_AL(c->cfl_bits, sizeof(unsigned long long));
   EBIT_AL(c->status, sizeof(int));
+  if (c->grid.flags & EBIT_CURV_GHF) {
+    EBIT_AL(c->ghf_list, (size_t)c->grid.nx * c->grid.ny * sizeof(int));
+    EBIT_AL(c->ghf_count, sizeof(unsigned));
+  }
 #undef EBIT_AL
   return EBIT_OK;
 }
@@ -116,6 +122,21 @@ ebit_status launch_fields(ebit_ctx* c) {
     Timed t(c, EBIT_K_AREA);
     ebit::k_area<<<1, 256, 0, c->stream>>>(c->partial, (long long)fgrid.x * fgrid.y,
                                            c->grid.dx * c->grid.dx, c->area);
+  }
+  if (c->grid.flags & EBIT_CURV_GHF) {
+    Timed t(c, EBIT_K_GHF);
+    EBIT_CK(cudaMemsetAsync(c->ghf_count, 0, sizeof(unsigned), c->stream));
+    const dim3 lgrid((L.d.nx + ebit::kGhfListX - 1) / ebit::kGhfListX,
+                     (L.d.ny + ebit::kGhfListY - 1) / ebit::kGhfListY);
+    ebit::k_ghf_list<R><<<lgrid, dim3(ebit::kGhfListX, ebit::kGhfListY), 0, c->stream>>>(
+        c->K[b], (const R*)c->kappa, L.d, c->ghf_list, c->ghf_count);
+    const ebit::GhfView<R> S{c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b],
+                             (const R*)c->C, L.d};
+    const long long cells = (long long)L.d.nx * L.d.ny;
+    const int blocks = (int)std::min<long long>((cells + ebit::kGhfThreads - 1) / ebit::kGhfThreads,
+                                                152LL * 8);
+    ebit::k_ghf_fit<R><<<blocks, ebit::kGhfThreads, 0, c->stream>>>(
+        S, (R)c->grid.dx, c->grid.dx, c->ghf_list, c->ghf_count, (R*)c->kappa, c->ctr);
   }
   EBIT_CK(cudaGetLastError());
   return EBIT_OK;

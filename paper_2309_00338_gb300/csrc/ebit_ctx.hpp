@@ -18,17 +18,18 @@ constexpr int kBlockX = 32, kBlockY = 8;  // thread blocks of the per-vertex ker
 struct Layout {
   ebit::Dims d;
   size_t esz;
-  size_t k_bytes, z_bytes, h_bytes, v_bytes, field_bytes, verdict_bytes, partial_count;
+  size_t k_bytes, z_bytes, h_bytes, v_bytes, field_bytes, verdict_bytes, partial_count, ghf_bytes;
   dim3 grid, block;
   size_t total() const {
     return 2 * (k_bytes + z_bytes + h_bytes + v_bytes) + 2 * field_bytes + 2 * verdict_bytes +
-           partial_count * sizeof(double) + 4096;
+           partial_count * sizeof(double) + ghf_bytes + 4096;
   }
 };
 
 inline bool valid_grid(const ebit_grid* g) {
   return g && g->nx >= 1 && g->ny >= 1 && g->nx <= kMaxSide && g->ny <= kMaxSide && g->dx > 0.0 &&
-         (g->prec == EBIT_FP64 || g->prec == EBIT_FP32) && (g->flags & ~EBIT_FIT_LINE) == 0;
+         (g->prec == EBIT_FP64 || g->prec == EBIT_FP32) &&
+         (g->flags & ~(EBIT_FIT_LINE | EBIT_CURV_GHF)) == 0;
 }
 
 inline Layout layout_of(const ebit_grid* g) {
@@ -45,6 +46,7 @@ inline Layout layout_of(const ebit_grid* g) {
   L.v_bytes = (size_t)g->ny * L.d.P * L.esz;
   L.field_bytes = (size_t)g->ny * L.d.P * L.esz;
   L.verdict_bytes = (size_t)g->nx * g->ny;
+  L.ghf_bytes = (g->flags & EBIT_CURV_GHF) ? (size_t)g->nx * g->ny * sizeof(int) + 256 : 0;
   L.block = dim3(kBlockX, kBlockY);
   L.grid = dim3((g->nx + 1 + kBlockX - 1) / kBlockX, (g->ny + 1 + kBlockY - 1) / kBlockY);
   L.partial_count = (size_t)L.grid.x * L.grid.y;
@@ -71,6 +73,8 @@ struct ebit_ctx {
   unsigned long long* ctr = nullptr;
   unsigned long long* cfl_bits = nullptr;
   int* status = nullptr;
+  int* ghf_list = nullptr;          // EBIT_CURV_GHF: cells left without kappa
+  unsigned* ghf_count = nullptr;
   int64_t step_index = 0;
   std::vector<void*> allocs;
   // EBIT_SWEEP=gather in the environment selects the thread-per-vertex gather

@@ -1,0 +1,255 @@
+// Generalised height-function fallbacks (Sec. 2.5 takes its curvature from
+// the generalised height-function method, Popinet 2009).  The fused fields
+// kernel computes the standard 7x3 height-function curvature; interface
+// cells without a valid stencil are left NaN there.  When the context asks
+// for the generalised method, two more launches give those cells a value:
+//
+//   k_ghf_list  a dense pass over kappa and the corner bits that lists the
+//               interface cells whose kappa is NaN (warp-aggregated appends);
+//   k_ghf_fit   one thread per listed cell, in turn: the standard stencil
+//               along the other direction; a parabola fitted to the valid
+//               heights of both directions ("mixed heights"); a parabola
+//               fitted to the markers on the edges of the 3x3 block of cells
+//               (the markers lie on the interface, where the volume-of-fluid
+//               form would fit fragment centroids).
+//
+// The listed cells are a few per cent of the interface cells, so the fits
+// (double arithmetic in both precision forms) run on compacted work.
+#pragma once
+#include "ebit_device.cuh"
+
+namespace ebit {
+
+// counters of the fallbacks, after the ones the other kernels use
+constexpr int D_HF_OTHER = 13, D_HF_MIXED = 14, D_HF_MARKERS = 15;
+static_assert(D_NUSED <= D_HF_OTHER && D_HF_MARKERS < kCounters, "counter slots");
+
+constexpr int kGhfListX = 32, kGhfListY = 8;  // k_ghf_list block
+constexpr int kGhfThreads = 128;              // k_ghf_fit block
+
+__device__ __forceinline__ int kbit(const uint32_t* __restrict__ K, int kw, int i, int j) {
+  return (__ldg(&K[(long long)j * kw + (i >> 5)]) >> (i & 31)) & 1;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kGhfListX* kGhfListY)
+    k_ghf_list(const uint32_t* __restrict__ K, const R* __restrict__ kappa, Dims d,
+               int* __restrict__ list, unsigned* __restrict__ count) {
+  const int i = blockIdx.x * kGhfListX + threadIdx.x;
+  const int j = blockIdx.y * kGhfListY + threadIdx.y;
+  bool need = false;
+  if (i < d.nx && j < d.ny && isnan(__ldg(&kappa[(long long)j * d.P + i]))) {
+    const int c0 = kbit(K, d.kw, i, j), c1 = kbit(K, d.kw, i + 1, j);
+    const int c2 = kbit(K, d.kw, i + 1, j + 1), c3 = kbit(K, d.kw, i, j + 1);
+    need = !(c0 == c1 && c1 == c2 && c2 == c3);
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, need);
+  if (m == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (need) list[base + __popc(m & ((1u << lane) - 1u))] = j * d.nx + i;
+}
+
+// Read-only view of the state and fractions of one context.
+template <typename R>
+struct GhfView {
+  const uint32_t* K;
+  const uint32_t* Z;
+  const R* sH;
+  const R* sV;
+  const R* C;
+  Dims d;
+  __device__ int k(int i, int j) const { return kbit(K, d.kw, i, j); }
+  __device__ int z(int i, int j) const { return kbit(Z, d.zw, i, j); }
+  __device__ R c(int i, int j) const { return __ldg(&C[(long long)j * d.P + i]); }
+  __device__ R h(int i, int j) const { return __ldg(&sH[(long long)j * d.P + i]); }
+  __device__ R v(int i, int j) const { return __ldg(&sV[(long long)j * d.P + i]); }
+};
+
+// The column of seven cells through (i+m, j-3..j+3) (ycol) or the row
+// (i-3..i+3, j+m): its count h of reference-phase cells (summed in that
+// order) and orientation: 1 = reference phase at the low end only, -1 = at
+// the high end only, 0 = not a valid height (mixed end cell, equal ends, or
+// outside the domain).
+template <typename R>
+__device__ int ghf_column(const GhfView<R>& S, int i, int j, int m, bool ycol, R* h) {
+  const bool in = ycol ? (i + m >= 0 && i + m <= S.d.nx - 1 && j - 3 >= 0 && j + 3 <= S.d.ny - 1)
+                       : (j + m >= 0 && j + m <= S.d.ny - 1 && i - 3 >= 0 && i + 3 <= S.d.nx - 1);
+  if (!in) return 0;
+  R acc = R(0);
+#pragma unroll
+  for (int t = -3; t <= 3; ++t) acc = acc + (ycol ? S.c(i + m, j + t) : S.c(i + t, j + m));
+  *h = acc;
+  const R lo = ycol ? S.c(i + m, j - 3) : S.c(i - 3, j + m);
+  const R hi = ycol ? S.c(i + m, j + 3) : S.c(i + 3, j + m);
+  return (lo == R(1) && hi == R(0)) ? 1 : (lo == R(0) && hi == R(1)) ? -1 : 0;
+}
+
+// Points of a fit, kept only when at least half a cell from every point
+// already kept, with the least-squares sums accumulated in that order in the
+// frame of origin (ox, oy), unit normal (nx, ny) and tangent (ny, -nx).
+struct ParabolaFit {
+  double ox, oy, nx, ny;
+  double X[24], Y[24];
+  int np;
+  double S0, S1, S2, S3, S4, T0, T1, T2;
+  __device__ void reset() {
+    np = 0;
+    S0 = S1 = S2 = S3 = S4 = T0 = T1 = T2 = 0.0;
+  }
+  __device__ void add(double x, double y, double w) {
+    for (int p = 0; p < np; ++p) {
+      const double ex = x - X[p], ey = y - Y[p];
+      if (ex * ex + ey * ey < 0.25) return;
+    }
+    if (np >= 24) return;
+    X[np] = x;
+    Y[np] = y;
+    ++np;
+    const double ddx = x - ox, ddy = y - oy;
+    const double sv = ddx * ny - ddy * nx;
+    const double zv = ddx * nx + ddy * ny;
+    const double s2 = sv * sv;
+    S0 = S0 + w;
+    S1 = S1 + w * sv;
+    S2 = S2 + w * s2;
+    S3 = S3 + w * (s2 * sv);
+    S4 = S4 + w * (s2 * s2);
+    T0 = T0 + w * zv;
+    T1 = T1 + w * (zv * sv);
+    T2 = T2 + w * (zv * s2);
+  }
+  // z = a s^2 + b s + c by Cramer's rule; kappa = -2a / (1 + b^2)^(3/2) / dx
+  __device__ bool kappa(double dx, double* out) const {
+    if (np < 3) return false;
+    const double m00 = S2 * S0 - S1 * S1;
+    const double m01 = S3 * S0 - S1 * S2;
+    const double m02 = S3 * S1 - S2 * S2;
+    const double det = S4 * m00 - S3 * m01 + S2 * m02;
+    if (!(fabs(det) > 1e-10 * (S0 * S0 * S0))) return false;
+    const double u1 = T1 * S0 - S1 * T0;
+    const double da = T2 * m00 - S3 * u1 + S2 * (T1 * S1 - S2 * T0);
+    const double db = S4 * u1 - T2 * m01 + S2 * (S3 * T0 - T1 * S2);
+    const double a = da / det, b = db / det;
+    const double q = 1.0 + b * b;
+    *out = (-2.0 * a) / (q * sqrt(q)) / dx;
+    return isfinite(*out);
+  }
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kGhfThreads)
+    k_ghf_fit(GhfView<R> S, R dxR, double dx, const int* __restrict__ list,
+              const unsigned* __restrict__ count, R* __restrict__ kappa,
+              unsigned long long* __restrict__ ctr) {
+  __shared__ unsigned s_cnt[3];
+  if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const unsigned n = *count;
+  unsigned got[3] = {0, 0, 0};
+  for (unsigned e = blockIdx.x * kGhfThreads + threadIdx.x; e < n; e += gridDim.x * kGhfThreads) {
+    const int idx = __ldg(&list[e]);
+    const int i = idx % S.d.nx, j = idx / S.d.nx;
+    const int c[4] = {S.k(i, j), S.k(i + 1, j), S.k(i + 1, j + 1), S.k(i, j + 1)};
+    const int q = c[0] | (c[1] << 1) | (c[2] << 2) | (c[3] << 3);
+    int seg[2][2];
+    const int ns = segments(q, edge_mask(q) == 15 ? S.z(i, j) : 0, seg);
+    const R px[4] = {S.h(i, j), R(1), S.h(i, j + 1), R(0)};
+    const R py[4] = {R(0), S.v(i + 1, j), R(1), S.v(i, j)};
+    R ax = R(0), ay = R(0);
+    for (int t = 0; t < ns; ++t) {
+      ax = ax + fabs(px[seg[t][1]] - px[seg[t][0]]);
+      ay = ay + fabs(py[seg[t][1]] - py[seg[t][0]]);
+    }
+    // 1. the standard stencil along the other direction
+    const bool ycol = !(ax >= ay);
+    {
+      R h[3];
+      int o[3];
+#pragma unroll
+      for (int m = -1; m <= 1; ++m) o[m + 1] = ghf_column(S, i, j, m, ycol, &h[m + 1]);
+      if (o[0] != 0 && o[0] == o[1] && o[1] == o[2]) {
+        const R hp = (h[2] - h[0]) * R(0.5);
+        const R hpp = (h[2] - h[1]) - (h[1] - h[0]);
+        const R qv = R(1) + hp * hp;
+        const R den = dxR * (qv * sqrt(qv));
+        kappa[(long long)j * S.d.P + i] = -hpp / den;
+        ++got[0];
+        continue;
+      }
+    }
+    // the frame: the cell's single segment A->B, origin at its midpoint,
+    // normal perpendicular to it and turned away from the reference-phase
+    // corners (their colour-signed offsets from the centre sum into the
+    // reference phase)
+    if (ns != 1) continue;
+    const int ea = seg[0][0], eb = seg[0][1];
+    const double Ax = (double)i + (double)px[ea], Ay = (double)j + (double)py[ea];
+    const double Bx = (double)i + (double)px[eb], By = (double)j + (double)py[eb];
+    ParabolaFit F;
+    F.ox = (Ax + Bx) * 0.5;
+    F.oy = (Ay + By) * 0.5;
+    double n0x = By - Ay, n0y = -(Bx - Ax);
+    const int gx = (2 * c[1] - 1) + (2 * c[2] - 1) - (2 * c[0] - 1) - (2 * c[3] - 1);
+    const int gy = (2 * c[2] - 1) + (2 * c[3] - 1) - (2 * c[0] - 1) - (2 * c[1] - 1);
+    const double dot = n0x * (double)gx + n0y * (double)gy;
+    if (dot == 0.0) continue;
+    if (dot > 0.0) {
+      n0x = -n0x;
+      n0y = -n0y;
+    }
+    const double len = sqrt(n0x * n0x + n0y * n0y);
+    if (!(len > 0.0)) continue;
+    F.nx = n0x / len;
+    F.ny = n0y / len;
+    // 2. mixed heights: the valid columns of both directions' stencils
+    F.reset();
+    for (int dir = 0; dir < 2; ++dir) {
+      const bool yc = dir == 0;
+      for (int m = -1; m <= 1; ++m) {
+        R h = R(0);
+        const int o = ghf_column(S, i, j, m, yc, &h);
+        if (o == 0) continue;
+        const double hd = (double)h;
+        const double lo = (double)((yc ? j : i) - 3), hi = (double)((yc ? j : i) + 4);
+        const double pos = o == 1 ? lo + hd : hi - hd;
+        const double mid = (double)((yc ? i : j) + m) + 0.5;
+        if (yc) F.add(mid, pos, 1.0);
+        else F.add(pos, mid, 1.0);
+      }
+    }
+    double kv;
+    if (F.kappa(dx, &kv)) {
+      kappa[(long long)j * S.d.P + i] = (R)kv;
+      ++got[1];
+      continue;
+    }
+    // 3. the markers on the edges of the 3x3 block
+    F.reset();
+    for (int b = j - 1; b <= j + 2; ++b)
+      for (int a = i - 1; a <= i + 1; ++a)
+        if (a >= 0 && a < S.d.nx && b >= 0 && b <= S.d.ny && S.k(a, b) != S.k(a + 1, b))
+          F.add((double)a + (double)S.h(a, b), (double)b, 1.0);
+    for (int b = j - 1; b <= j + 1; ++b)
+      for (int a = i - 1; a <= i + 2; ++a)
+        if (a >= 0 && a <= S.d.nx && b >= 0 && b < S.d.ny && S.k(a, b) != S.k(a, b + 1))
+          F.add((double)a, (double)b + (double)S.v(a, b), 1.0);
+    if (F.kappa(dx, &kv)) {
+      kappa[(long long)j * S.d.P + i] = (R)kv;
+      ++got[2];
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const unsigned s = __reduce_add_sync(0xffffffffu, got[t]);
+    if (s && (threadIdx.x & 31) == 0) atomicAdd(&s_cnt[t], s);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3 && s_cnt[threadIdx.x])
+    atomicAdd(&ctr[D_HF_OTHER + threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
+}
+
+}  // namespace ebit

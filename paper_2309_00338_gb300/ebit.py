@@ -19,10 +19,11 @@ EBIT_EINVAL, EBIT_ENOMEM, EBIT_ECFL, EBIT_EINVARIANT, EBIT_ECUDA, EBIT_ETIMEOUT,
     -1, -2, -3, -4, -5, -6, -7
 EBIT_FP64, EBIT_FP32 = 0, 1
 EBIT_FIT_LINE = 1
+EBIT_CURV_GHF = 2
 
 # diagnostics indices (include/ebit.h)
 D_NH, D_NV, D_CANCELLED, D_ZSET, D_ZCONFLICT, D_FIT_ONLINE, D_FIT_LINE, D_FIT_ONE, D_FIT_TWO, \
-    D_WALL_CLAMP, D_INVARIANT, D_HF_INVALID, D_CFL = range(13)
+    D_WALL_CLAMP, D_INVARIANT, D_HF_INVALID, D_CFL, D_HF_OTHER, D_HF_MIXED, D_HF_MARKERS = range(16)
 D_COUNT = 16
 
 _STATUS_NAMES = {0: "EBIT_OK", 1: "EBIT_EAGAIN", -1: "EBIT_EINVAL", -2: "EBIT_ENOMEM",
@@ -105,9 +106,9 @@ SIGNATURES = {
     "ebit_coupling": (ctypes.c_int, [_P, ctypes.POINTER(ebit_fluids), _P, _P, _P, _P]),
 }
 
-K_SWEEP, K_CENTRE, K_FIELDS, K_AREA, K_COUPLING = range(5)
+K_SWEEP, K_CENTRE, K_FIELDS, K_AREA, K_COUPLING, K_GHF = range(6)
 K_COUNT = 8
-KERNEL_NAMES = ["sweep", "centre", "fields", "area", "coupling"]
+KERNEL_NAMES = ["sweep", "centre", "fields", "area", "coupling", "ghf"]
 
 
 def lib(path: str | None = None):
