@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-ghf", action="store_true", help="skip the generalised height-function leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default="cellular_curve_4096",
                    choices=["cellular_curve_4096", "batched", "serving"],
@@ -424,6 +425,32 @@ def run_ours(args, wl, world, rank, local):
            "overlap": "inputs of step k+1 copied on a second stream during step k"}
     ebit.ebit_destroy(ctx)
 
+    # the same FP32 steps with the generalised height-function fallbacks on
+    ghf = None
+    if not args.no_ghf:
+        ctxg = ebit.ebit_init(n, n, wl.dx, wl.scene, prec, flags=ebit.EBIT_CURV_GHF, stream=stream)
+        for _ in range(args.warmup):
+            ebit.ebit_step(ctxg, u, v, wl.dt)
+        torch.cuda.synchronize()
+        barrier()
+        tg, latg = timed_steps(torch, ebit, ctxg, u, v, wl.dt, args.steps, stream)
+        barrier()
+        ebit.ebit_sync(ctxg)
+        tg = max_over_ranks(tg, world, "cuda")
+        dg = ebit.ebit_diagnostics(ctxg)["counters"]
+        ebit.ebit_set_timing(ctxg, True)
+        ebit.ebit_timings(ctxg)
+        for _ in range(args.steps):
+            ebit.ebit_step(ctxg, u, v, wl.dt)
+        ktg = ebit.ebit_timings(ctxg)
+        ebit.ebit_set_timing(ctxg, False)
+        ebit.ebit_destroy(ctxg)
+        ghf = {"value": job_value(world, cells, args.steps, tg), "unit": UNIT, "ms_per_step": tg / args.steps,
+               "ghf_ms_per_step": ktg["ghf"][0] / args.steps,
+               "hf_invalid": int(dg[ebit.D_HF_INVALID]), "resolved_other": int(dg[ebit.D_HF_OTHER]),
+               "resolved_mixed": int(dg[ebit.D_HF_MIXED]), "resolved_markers": int(dg[ebit.D_HF_MARKERS]),
+               "note": "list pass over kappa plus compacted fits, per step (last step's counters)"}
+
     fp64 = None
     if not args.no_fp64:
         ctx64 = ebit.ebit_init(n, n, wl.dx, wl.scene, ebit.EBIT_FP64, stream=stream)
@@ -462,7 +489,8 @@ def run_ours(args, wl, world, rank, local):
                            "l2": "working set (~0.45 GB) larger than L2, no flush"},
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(round(launches_per_step * args.steps)),
-                "roofline": roofline, "step_roofline": step_roof, "coupling": coupling, "fp64": fp64,
+                "roofline": roofline, "step_roofline": step_roof, "coupling": coupling, "ghf": ghf,
+                "fp64": fp64,
                 "cpu_baseline": cpu,
                 "markers": {"nH": int(diag["counters"][0]), "nV": int(diag["counters"][1])}}
         print(json.dumps(line), flush=True)
