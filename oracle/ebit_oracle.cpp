@@ -707,16 +707,19 @@ double fraction(const State<R>& S, double dx, double* C) {
 // and unit normal (nx, ny) pointing out of the reference phase (tangent
 // (ny, -nx)), evaluated at s = 0: kappa = -2a / (1 + b^2)^(3/2) / dx, which is
 // +1/R for a reference-phase drop of radius R.  The normal equations are
-// solved by Cramer's rule.  Returns false when the system is singular.
-bool parabola_kappa(int n, const double* X, const double* Y, const double* W, double ox, double oy,
-                    double nx, double ny, double dx, double* kappa) {
-  double S0 = 0.0, S1 = 0.0, S2 = 0.0, S3 = 0.0, S4 = 0.0, T0 = 0.0, T1 = 0.0, T2 = 0.0;
+// solved by Cramer's rule, in the arithmetic R.  Returns false when the
+// system is singular (|det| <= eps S0^3, eps = 1e-10 in double, 1e-5 in
+// float).
+template <typename R>
+bool parabola_kappa(int n, const R* X, const R* Y, const R* W, R ox, R oy, R nx, R ny, R dx,
+                    R* kappa) {
+  R S0 = R(0), S1 = R(0), S2 = R(0), S3 = R(0), S4 = R(0), T0 = R(0), T1 = R(0), T2 = R(0);
   for (int p = 0; p < n; ++p) {
-    const double ddx = X[p] - ox, ddy = Y[p] - oy;
-    const double sv = ddx * ny - ddy * nx;  // along the tangent (ny, -nx)
-    const double zv = ddx * nx + ddy * ny;  // along the normal
-    const double w = W[p];
-    const double s2 = sv * sv;
+    const R ddx = X[p] - ox, ddy = Y[p] - oy;
+    const R sv = ddx * ny - ddy * nx;  // along the tangent (ny, -nx)
+    const R zv = ddx * nx + ddy * ny;  // along the normal
+    const R w = W[p];
+    const R s2 = sv * sv;
     S0 = S0 + w;
     S1 = S1 + w * sv;
     S2 = S2 + w * s2;
@@ -726,17 +729,18 @@ bool parabola_kappa(int n, const double* X, const double* Y, const double* W, do
     T1 = T1 + w * (zv * sv);
     T2 = T2 + w * (zv * s2);
   }
-  const double m00 = S2 * S0 - S1 * S1;
-  const double m01 = S3 * S0 - S1 * S2;
-  const double m02 = S3 * S1 - S2 * S2;
-  const double det = S4 * m00 - S3 * m01 + S2 * m02;
-  if (!(std::fabs(det) > 1e-10 * (S0 * S0 * S0))) return false;
-  const double u1 = T1 * S0 - S1 * T0;
-  const double da = T2 * m00 - S3 * u1 + S2 * (T1 * S1 - S2 * T0);
-  const double db = S4 * u1 - T2 * m01 + S2 * (S3 * T0 - T1 * S2);
-  const double a = da / det, b = db / det;
-  const double q = 1.0 + b * b;
-  *kappa = (-2.0 * a) / (q * std::sqrt(q)) / dx;
+  const R m00 = S2 * S0 - S1 * S1;
+  const R m01 = S3 * S0 - S1 * S2;
+  const R m02 = S3 * S1 - S2 * S2;
+  const R det = S4 * m00 - S3 * m01 + S2 * m02;
+  const R eps = sizeof(R) == 4 ? R(1e-5) : R(1e-10);
+  if (!(std::fabs(det) > eps * (S0 * S0 * S0))) return false;
+  const R u1 = T1 * S0 - S1 * T0;
+  const R da = T2 * m00 - S3 * u1 + S2 * (T1 * S1 - S2 * T0);
+  const R db = S4 * u1 - T2 * m01 + S2 * (S3 * T0 - T1 * S2);
+  const R a = da / det, b = db / det;
+  const R q = R(1) + b * b;
+  *kappa = (R(-2) * a) / (q * std::sqrt(q)) / dx;
   return std::isfinite(*kappa);
 }
 
@@ -814,43 +818,44 @@ void curvature(const State<R>& S, const double* Cd, double dx, double* kappa, in
         continue;
       }
       out = (double)nanv;
-      // The fitting frame needs the cell's single segment A->B: origin at its
-      // midpoint, normal perpendicular to it, turned away from the
-      // reference-phase corners (their offsets from the cell centre, each
-      // signed by colour, sum to a vector into the reference phase).
+      // The fits work in the state precision, in cell units relative to the
+      // cell's lower-left corner.  The frame needs the cell's single segment
+      // A->B: origin at its midpoint, normal perpendicular to it, turned
+      // away from the reference-phase corners (their offsets from the cell
+      // centre, each signed by colour, sum to a vector into the reference
+      // phase).
       if (ns != 1) continue;
       const int ea = seg[0][0], eb = seg[0][1];
-      const double Ax = (double)i + (double)px[ea], Ay = (double)j + (double)py[ea];
-      const double Bx = (double)i + (double)px[eb], By = (double)j + (double)py[eb];
-      const double ox = (Ax + Bx) * 0.5, oy = (Ay + By) * 0.5;
-      double n0x = By - Ay, n0y = -(Bx - Ax);
+      const R Ax = px[ea], Ay = py[ea], Bx = px[eb], By = py[eb];
+      const R ox = (Ax + Bx) * R(0.5), oy = (Ay + By) * R(0.5);
+      R n0x = By - Ay, n0y = -(Bx - Ax);
       static const int sxc[4] = {-1, 1, 1, -1}, syc[4] = {-1, -1, 1, 1};
       int gx = 0, gy = 0;
       for (int q = 0; q < 4; ++q) {
         gx += (2 * c[q] - 1) * sxc[q];
         gy += (2 * c[q] - 1) * syc[q];
       }
-      const double dot = n0x * (double)gx + n0y * (double)gy;
-      if (dot == 0.0) continue;
-      if (dot > 0.0) {
+      const R dot = n0x * (R)gx + n0y * (R)gy;
+      if (dot == R(0)) continue;
+      if (dot > R(0)) {
         n0x = -n0x;
         n0y = -n0y;
       }
-      const double len = std::sqrt(n0x * n0x + n0y * n0y);
-      if (!(len > 0.0)) continue;
-      const double unx = n0x / len, uny = n0y / len;
+      const R len = std::sqrt(n0x * n0x + n0y * n0y);
+      if (!(len > R(0))) continue;
+      const R unx = n0x / len, uny = n0y / len;
       // Points kept only when at least half a cell from every point already
       // kept (independent positions).
-      double X[32], Y[32], W[32];  // at most 24 markers on the 3x3 block
+      R X[32], Y[32], W[32];  // at most 24 markers on the 3x3 block
       int np = 0;
-      auto add = [&](double x, double y, double w) {
+      auto add = [&](R x, R y) {
         for (int p = 0; p < np; ++p) {
-          const double ex = x - X[p], ey = y - Y[p];
-          if (ex * ex + ey * ey < 0.25) return;
+          const R ex = x - X[p], ey = y - Y[p];
+          if (ex * ex + ey * ey < R(0.25)) return;
         }
         X[np] = x;
         Y[np] = y;
-        W[np] = w;
+        W[np] = R(1);
         ++np;
       };
       // 2. mixed heights: every valid column of the cell's stencils in both
@@ -861,17 +866,15 @@ void curvature(const State<R>& S, const double* Cd, double dx, double* kappa, in
           R h = R(0);
           const int o = column(i, j, m, yc, &h);
           if (o == 0) continue;
-          const double hd = (double)h;
-          const double lo = (double)((yc ? j : i) - 3), hi = (double)((yc ? j : i) + 4);
-          const double pos = o == 1 ? lo + hd : hi - hd;
-          const double mid = (double)((yc ? i : j) + m) + 0.5;
-          if (yc) add(mid, pos, 1.0);
-          else add(pos, mid, 1.0);
+          const R pos = o == 1 ? R(-3) + h : R(4) - h;
+          const R mid = (R)m + R(0.5);
+          if (yc) add(mid, pos);
+          else add(pos, mid);
         }
       }
-      double kv = 0.0;
-      if (np >= 3 && parabola_kappa(np, X, Y, W, ox, oy, unx, uny, dx, &kv)) {
-        out = (double)(R)kv;
+      R kv = R(0);
+      if (np >= 3 && parabola_kappa<R>(np, X, Y, W, ox, oy, unx, uny, dxR, &kv)) {
+        out = (double)kv;
         ctr[ORC_HF_MIXED] += 1;
         continue;
       }
@@ -881,13 +884,13 @@ void curvature(const State<R>& S, const double* Cd, double dx, double* kappa, in
       for (int b = j - 1; b <= j + 2; ++b)
         for (int a = i - 1; a <= i + 1; ++a)
           if (a >= 0 && a < nx && b >= 0 && b <= ny && S.hasH(a, b))
-            add((double)a + (double)S.hc(a, b), (double)b, 1.0);
+            add((R)(a - i) + S.hc(a, b), (R)(b - j));
       for (int b = j - 1; b <= j + 1; ++b)
         for (int a = i - 1; a <= i + 2; ++a)
           if (a >= 0 && a <= nx && b >= 0 && b < ny && S.hasV(a, b))
-            add((double)a, (double)b + (double)S.vc(a, b), 1.0);
-      if (np >= 3 && parabola_kappa(np, X, Y, W, ox, oy, unx, uny, dx, &kv)) {
-        out = (double)(R)kv;
+            add((R)(a - i), (R)(b - j) + S.vc(a, b));
+      if (np >= 3 && parabola_kappa<R>(np, X, Y, W, ox, oy, unx, uny, dxR, &kv)) {
+        out = (double)kv;
         ctr[ORC_HF_MARKERS] += 1;
       }
     }
@@ -1348,7 +1351,7 @@ int orc_curvature(int nx, int ny, double dx, int prec, const uint8_t* K, const u
 int orc_parabola_kappa(int n, const double* X, const double* Y, const double* W, double ox,
                        double oy, double nx, double ny, double dx, double* kappa) {
   if (n < 3 || n > 64) return 0;
-  return parabola_kappa(n, X, Y, W, ox, oy, nx, ny, dx, kappa) ? 1 : 0;
+  return parabola_kappa<double>(n, X, Y, W, ox, oy, nx, ny, dx, kappa) ? 1 : 0;
 }
 
 }  // extern "C"

@@ -47,20 +47,19 @@ MUTANTS = [
      [("for (int i = 0; i < S.nx; ++i) T.v(j, i) = S.hc(i, j);",
        "for (int i = 0; i < S.nx; ++i) T.v(j, i) = R(1) - S.hc(i, j);")]),
     ("parabola fit: tangent and normal coordinates swapped",
-     [("const double sv = ddx * ny - ddy * nx;  // along the tangent (ny, -nx)",
-       "const double sv = ddx * nx + ddy * ny;  // along the tangent (ny, -nx)"),
-      ("const double zv = ddx * nx + ddy * ny;  // along the normal",
-       "const double zv = ddx * ny - ddy * nx;  // along the normal")]),
+     [("const R sv = ddx * ny - ddy * nx;  // along the tangent (ny, -nx)",
+       "const R sv = ddx * nx + ddy * ny;  // along the tangent (ny, -nx)"),
+      ("const R zv = ddx * nx + ddy * ny;  // along the normal",
+       "const R zv = ddx * ny - ddy * nx;  // along the normal")]),
     ("parabola fit: Cramer numerator with a wrong column",
-     [("const double da = T2 * m00 - S3 * u1 + S2 * (T1 * S1 - S2 * T0);",
-       "const double da = T2 * m00 - S3 * u1 + S2 * (T1 * S1 - S1 * T0);")]),
+     [("const R da = T2 * m00 - S3 * u1 + S2 * (T1 * S1 - S2 * T0);",
+       "const R da = T2 * m00 - S3 * u1 + S2 * (T1 * S1 - S1 * T0);")]),
     ("fitting frame normal not turned away from the reference phase",
-     [("      if (dot > 0.0) {\n        n0x = -n0x;", "      if (dot < 0.0) {\n        n0x = -n0x;")]),
+     [("      if (dot > R(0)) {\n        n0x = -n0x;", "      if (dot < R(0)) {\n        n0x = -n0x;")]),
     ("mixed heights measured from the wrong end",
-     [("const double pos = o == 1 ? lo + hd : hi - hd;", "const double pos = o == 1 ? hi - hd : lo + hd;")]),
+     [("const R pos = o == 1 ? R(-3) + h : R(4) - h;", "const R pos = o == 1 ? R(4) - h : R(-3) + h;")]),
     ("markers fit takes vertical markers one edge off",
-     [("add((double)a, (double)b + (double)S.vc(a, b), 1.0);",
-       "add((double)a + 1.0, (double)b + (double)S.vc(a, b), 1.0);")]),
+     [("add((R)(a - i), (R)(b - j) + S.vc(a, b));", "add((R)(a - i) + R(1), (R)(b - j) + S.vc(a, b));")]),
 ]
 
 BATTERY = [
@@ -83,7 +82,7 @@ BATTERY = [
     (P.test_vortex_T2_table3, (32,)),
     (P.test_parabola_fit_exact_on_parabolas, ()),
     (P.test_parabola_fit_circle_and_singular, ()),
-    (P.test_ghf_keeps_standard_values_and_resolves_packed_disks, ()),
+    (P.test_ghf_keeps_standard_values_and_resolves_packed_disks, (0,)),
     (P.test_ghf_bubbles_negative_and_lines_flat, ()),
 ]
 

@@ -682,7 +682,8 @@ def _packed_disks(n=256, seed=5, rmin=3.0, rmax=8.0):
     return dx, circles
 
 
-def test_ghf_keeps_standard_values_and_resolves_packed_disks():
+@pytest.mark.parametrize("prec", [oracle.FP64, oracle.FP32], ids=["fp64", "fp32"])
+def test_ghf_keeps_standard_values_and_resolves_packed_disks(prec):
     """Disks 3-8 cells across with 2-cell gaps break many 7x3 stencils.  The
     generalised fallbacks leave every standard value as it was, give a
     curvature to (nearly) every other interface cell, and those values follow
@@ -690,7 +691,7 @@ def test_ghf_keeps_standard_values_and_resolves_packed_disks():
     values themselves: 0.05, 0.14)."""
     dx, circles = _packed_disks()
     n = int(round(1 / dx))
-    S = oracle.init(n, n, dx, W.circle_scene(circles))
+    S = oracle.init(n, n, dx, W.circle_scene(circles), prec)
     C, _ = oracle.fraction(S)
     k0, n0 = oracle.curvature(S, C)
     k1, n1, res = oracle.curvature(S, C, ghf=True)
