@@ -52,8 +52,8 @@ typedef enum { EBIT_FP64 = 0, EBIT_FP32 = 1 } ebit_precision;
  * a curvature from the generalised height-function method Sec. 2.5 cites:
  * the stencil along the other direction, else a least-squares parabola
  * through the valid heights of both directions, else one through the markers
- * on the edges of the 3x3 block of cells (fits in double in both precision
- * forms).  It costs one more dense pass over kappa and the fits, and a list
+ * on the edges of the 3x3 block of cells (fits in the context precision, in
+ * cell units relative to the cell).  It costs one more dense pass over kappa and the fits, and a list
  * of nx*ny int32 in the context.  Contexts only (servers reject it). */
 #define EBIT_FIT_LINE 1u
 #define EBIT_CURV_GHF 2u

@@ -136,7 +136,7 @@ ebit_status launch_fields(ebit_ctx* c) {
     const int blocks = (int)std::min<long long>((cells + ebit::kGhfThreads - 1) / ebit::kGhfThreads,
                                                 152LL * 8);
     ebit::k_ghf_fit<R><<<blocks, ebit::kGhfThreads, 0, c->stream>>>(
-        S, (R)c->grid.dx, c->grid.dx, c->ghf_list, c->ghf_count, (R*)c->kappa, c->ctr);
+        S, (R)c->grid.dx, c->ghf_list, c->ghf_count, (R*)c->kappa, c->ctr);
   }
   EBIT_CK(cudaGetLastError());
   return EBIT_OK;

@@ -14,7 +14,8 @@
 //               form would fit fragment centroids).
 //
 // The listed cells are a few per cent of the interface cells, so the fits
-// (double arithmetic in both precision forms) run on compacted work.
+// (in the context precision, in cell units relative to the cell) run on
+// compacted work.
 #pragma once
 #include "ebit_device.cuh"
 
@@ -89,62 +90,65 @@ __device__ int ghf_column(const GhfView<R>& S, int i, int j, int m, bool ycol, R
 }
 
 // Points of a fit, kept only when at least half a cell from every point
-// already kept, with the least-squares sums accumulated in that order in the
-// frame of origin (ox, oy), unit normal (nx, ny) and tangent (ny, -nx).
+// already kept, with the least-squares sums (unit weights) accumulated in that
+// order in the frame of origin (ox, oy), unit normal (nx, ny) and tangent
+// (ny, -nx).  Arithmetic in R, coordinates in cell units relative to the
+// cell's lower-left corner.
+template <typename R>
 struct ParabolaFit {
-  double ox, oy, nx, ny;
-  double X[24], Y[24];
+  R ox, oy, nx, ny;
+  R X[24], Y[24];
   int np;
-  double S0, S1, S2, S3, S4, T0, T1, T2;
+  R S0, S1, S2, S3, S4, T0, T1, T2;
   __device__ void reset() {
     np = 0;
-    S0 = S1 = S2 = S3 = S4 = T0 = T1 = T2 = 0.0;
+    S0 = S1 = S2 = S3 = S4 = T0 = T1 = T2 = R(0);
   }
-  __device__ void add(double x, double y, double w) {
+  __device__ void add(R x, R y) {
     for (int p = 0; p < np; ++p) {
-      const double ex = x - X[p], ey = y - Y[p];
-      if (ex * ex + ey * ey < 0.25) return;
+      const R ex = x - X[p], ey = y - Y[p];
+      if (ex * ex + ey * ey < R(0.25)) return;
     }
     if (np >= 24) return;
     X[np] = x;
     Y[np] = y;
     ++np;
-    const double ddx = x - ox, ddy = y - oy;
-    const double sv = ddx * ny - ddy * nx;
-    const double zv = ddx * nx + ddy * ny;
-    const double s2 = sv * sv;
-    S0 = S0 + w;
-    S1 = S1 + w * sv;
-    S2 = S2 + w * s2;
-    S3 = S3 + w * (s2 * sv);
-    S4 = S4 + w * (s2 * s2);
-    T0 = T0 + w * zv;
-    T1 = T1 + w * (zv * sv);
-    T2 = T2 + w * (zv * s2);
+    const R ddx = x - ox, ddy = y - oy;
+    const R sv = ddx * ny - ddy * nx;
+    const R zv = ddx * nx + ddy * ny;
+    const R s2 = sv * sv;
+    S0 = S0 + R(1);
+    S1 = S1 + sv;
+    S2 = S2 + s2;
+    S3 = S3 + s2 * sv;
+    S4 = S4 + s2 * s2;
+    T0 = T0 + zv;
+    T1 = T1 + zv * sv;
+    T2 = T2 + zv * s2;
   }
   // z = a s^2 + b s + c by Cramer's rule; kappa = -2a / (1 + b^2)^(3/2) / dx
-  __device__ bool kappa(double dx, double* out) const {
+  __device__ bool kappa(R dx, R* out) const {
     if (np < 3) return false;
-    const double m00 = S2 * S0 - S1 * S1;
-    const double m01 = S3 * S0 - S1 * S2;
-    const double m02 = S3 * S1 - S2 * S2;
-    const double det = S4 * m00 - S3 * m01 + S2 * m02;
-    if (!(fabs(det) > 1e-10 * (S0 * S0 * S0))) return false;
-    const double u1 = T1 * S0 - S1 * T0;
-    const double da = T2 * m00 - S3 * u1 + S2 * (T1 * S1 - S2 * T0);
-    const double db = S4 * u1 - T2 * m01 + S2 * (S3 * T0 - T1 * S2);
-    const double a = da / det, b = db / det;
-    const double q = 1.0 + b * b;
-    *out = (-2.0 * a) / (q * sqrt(q)) / dx;
+    const R m00 = S2 * S0 - S1 * S1;
+    const R m01 = S3 * S0 - S1 * S2;
+    const R m02 = S3 * S1 - S2 * S2;
+    const R det = S4 * m00 - S3 * m01 + S2 * m02;
+    const R eps = sizeof(R) == 4 ? R(1e-5) : R(1e-10);
+    if (!(fabs(det) > eps * (S0 * S0 * S0))) return false;
+    const R u1 = T1 * S0 - S1 * T0;
+    const R da = T2 * m00 - S3 * u1 + S2 * (T1 * S1 - S2 * T0);
+    const R db = S4 * u1 - T2 * m01 + S2 * (S3 * T0 - T1 * S2);
+    const R a = da / det, b = db / det;
+    const R q = R(1) + b * b;
+    *out = (R(-2) * a) / (q * sqrt(q)) / dx;
     return isfinite(*out);
   }
 };
 
 template <typename R>
 __global__ void __launch_bounds__(kGhfThreads)
-    k_ghf_fit(GhfView<R> S, R dxR, double dx, const int* __restrict__ list,
-              const unsigned* __restrict__ count, R* __restrict__ kappa,
-              unsigned long long* __restrict__ ctr) {
+    k_ghf_fit(GhfView<R> S, R dx, const int* __restrict__ list, const unsigned* __restrict__ count,
+              R* __restrict__ kappa, unsigned long long* __restrict__ ctr) {
   __shared__ unsigned s_cnt[3];
   if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(kGhfThreads)
         const R hp = (h[2] - h[0]) * R(0.5);
         const R hpp = (h[2] - h[1]) - (h[1] - h[0]);
         const R qv = R(1) + hp * hp;
-        const R den = dxR * (qv * sqrt(qv));
+        const R den = dx * (qv * sqrt(qv));
         kappa[(long long)j * S.d.P + i] = -hpp / den;
         ++got[0];
         continue;
@@ -187,22 +191,20 @@ __global__ void __launch_bounds__(kGhfThreads)
     // reference phase)
     if (ns != 1) continue;
     const int ea = seg[0][0], eb = seg[0][1];
-    const double Ax = (double)i + (double)px[ea], Ay = (double)j + (double)py[ea];
-    const double Bx = (double)i + (double)px[eb], By = (double)j + (double)py[eb];
-    ParabolaFit F;
-    F.ox = (Ax + Bx) * 0.5;
-    F.oy = (Ay + By) * 0.5;
-    double n0x = By - Ay, n0y = -(Bx - Ax);
+    ParabolaFit<R> F;
+    F.ox = (px[ea] + px[eb]) * R(0.5);
+    F.oy = (py[ea] + py[eb]) * R(0.5);
+    R n0x = py[eb] - py[ea], n0y = -(px[eb] - px[ea]);
     const int gx = (2 * c[1] - 1) + (2 * c[2] - 1) - (2 * c[0] - 1) - (2 * c[3] - 1);
     const int gy = (2 * c[2] - 1) + (2 * c[3] - 1) - (2 * c[0] - 1) - (2 * c[1] - 1);
-    const double dot = n0x * (double)gx + n0y * (double)gy;
-    if (dot == 0.0) continue;
-    if (dot > 0.0) {
+    const R dot = n0x * (R)gx + n0y * (R)gy;
+    if (dot == R(0)) continue;
+    if (dot > R(0)) {
       n0x = -n0x;
       n0y = -n0y;
     }
-    const double len = sqrt(n0x * n0x + n0y * n0y);
-    if (!(len > 0.0)) continue;
+    const R len = sqrt(n0x * n0x + n0y * n0y);
+    if (!(len > R(0))) continue;
     F.nx = n0x / len;
     F.ny = n0y / len;
     // 2. mixed heights: the valid columns of both directions' stencils
@@ -213,17 +215,15 @@ __global__ void __launch_bounds__(kGhfThreads)
         R h = R(0);
         const int o = ghf_column(S, i, j, m, yc, &h);
         if (o == 0) continue;
-        const double hd = (double)h;
-        const double lo = (double)((yc ? j : i) - 3), hi = (double)((yc ? j : i) + 4);
-        const double pos = o == 1 ? lo + hd : hi - hd;
-        const double mid = (double)((yc ? i : j) + m) + 0.5;
-        if (yc) F.add(mid, pos, 1.0);
-        else F.add(pos, mid, 1.0);
+        const R pos = o == 1 ? R(-3) + h : R(4) - h;
+        const R mid = (R)m + R(0.5);
+        if (yc) F.add(mid, pos);
+        else F.add(pos, mid);
       }
     }
-    double kv;
+    R kv;
     if (F.kappa(dx, &kv)) {
-      kappa[(long long)j * S.d.P + i] = (R)kv;
+      kappa[(long long)j * S.d.P + i] = kv;
       ++got[1];
       continue;
     }
@@ -232,13 +232,13 @@ __global__ void __launch_bounds__(kGhfThreads)
     for (int b = j - 1; b <= j + 2; ++b)
       for (int a = i - 1; a <= i + 1; ++a)
         if (a >= 0 && a < S.d.nx && b >= 0 && b <= S.d.ny && S.k(a, b) != S.k(a + 1, b))
-          F.add((double)a + (double)S.h(a, b), (double)b, 1.0);
+          F.add((R)(a - i) + S.h(a, b), (R)(b - j));
     for (int b = j - 1; b <= j + 1; ++b)
       for (int a = i - 1; a <= i + 2; ++a)
         if (a >= 0 && a <= S.d.nx && b >= 0 && b < S.d.ny && S.k(a, b) != S.k(a, b + 1))
-          F.add((double)a, (double)b + (double)S.v(a, b), 1.0);
+          F.add((R)(a - i), (R)(b - j) + S.v(a, b));
     if (F.kappa(dx, &kv)) {
-      kappa[(long long)j * S.d.P + i] = (R)kv;
+      kappa[(long long)j * S.d.P + i] = kv;
       ++got[2];
     }
   }
