@@ -55,8 +55,8 @@ class _Scene(ctypes.Structure):
         ("xc", ctypes.c_void_p), ("yc", ctypes.c_void_p), ("r", ctypes.c_void_p),
         ("has_curve", ctypes.c_int32), ("y0", ctypes.c_double), ("nmodes", ctypes.c_int32),
         ("amp", ctypes.c_void_p), ("phase", ctypes.c_void_p),
-        ("has_line", ctypes.c_int32), ("la", ctypes.c_double), ("lb", ctypes.c_double),
-        ("lc", ctypes.c_double),
+        ("nlines", ctypes.c_int32), ("la", ctypes.c_double * 4), ("lb", ctypes.c_double * 4),
+        ("lc", ctypes.c_double * 4),
         ("nnotches", ctypes.c_int32), ("notch", ctypes.c_void_p),
     ]
 
@@ -188,10 +188,14 @@ def _scene_struct(scene, keep):
         keep += [amp, ph]
         sc.has_curve, sc.y0, sc.nmodes = 1, float(curve["y0"]), int(amp.size)
         sc.amp, sc.phase = amp.ctypes.data, ph.ctypes.data
-    line = scene.get("line")
-    if line is not None:
-        sc.has_line = 1
-        sc.la, sc.lb, sc.lc = (float(t) for t in line)
+    lines = list(scene.get("lines", []))
+    if scene.get("line") is not None:
+        lines = [scene["line"]] + lines
+    if len(lines) > 4:
+        raise ValueError("at most 4 half-planes")
+    sc.nlines = len(lines)
+    for l, (a, b, c) in enumerate(lines):
+        sc.la[l], sc.lb[l], sc.lc[l] = float(a), float(b), float(c)
     notches = scene.get("notches")
     if notches:
         nb = np.ascontiguousarray(np.asarray(notches, np.float64).reshape(-1, 4))
@@ -204,8 +208,9 @@ def init(nx, ny, dx, scene, prec=FP64) -> State:
     """Colour vertices and markers of a scene (Sec. 3.2 initialisation).
 
     scene: dict with optional "circles" (n,3) [xc, yc, r], "curve"
-    {"y0", "amp", "phase"} (reference phase below y = h(x)) and "line"
-    (a, b, c) (toggles where a x + b y <= c)."""
+    {"y0", "amp", "phase"} (reference phase below y = h(x)), "line"
+    (a, b, c) and "lines" [(a, b, c), ...] (each toggles where
+    a x + b y <= c; four at most) and "notches"."""
     S = State(nx, ny, dx, prec)
     keep = []
     sc = _scene_struct(scene, keep)

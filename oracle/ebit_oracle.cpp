@@ -911,7 +911,7 @@ struct Scene {
     return acc;
   }
   bool in_curve(double x, double y) const { return y <= curve_h(x); }
-  bool in_line(double x, double y) const { return s->la * x + s->lb * y <= s->lc; }
+  bool in_line(int l, double x, double y) const { return s->la[l] * x + s->lb[l] * y <= s->lc[l]; }
   bool in_circle(int c, double x, double y) const {
     const double ddx = x - s->xc[c], ddy = y - s->yc[c];
     return ddx * ddx + ddy * ddy <= s->r[c] * s->r[c];
@@ -923,12 +923,12 @@ struct Scene {
     }
     return false;
   }
-  // The scene's phase at a point: curve, line and circles toggle it, then
-  // the notches cut it out.
+  // The scene's phase at a point: curve, half-planes and circles toggle it,
+  // then the notches cut it out.
   bool inside(double x, double y) const {
     bool p = false;
     if (s->has_curve) p ^= in_curve(x, y);
-    if (s->has_line) p ^= in_line(x, y);
+    for (int l = 0; l < s->nlines; ++l) p ^= in_line(l, x, y);
     for (int c = 0; c < s->ncircles; ++c) p ^= in_circle(c, x, y);
     return p && !in_notch(x, y);
   }
@@ -947,8 +947,8 @@ template <typename R>
 void init(State<R>& S, double dx, const orc_scene* sc) {
   const int nx = S.nx, ny = S.ny;
   const Scene P{sc};
-  // colour of every vertex and cell centre: curve, line, then each circle
-  // toggles inside itself
+  // colour of every vertex and cell centre: curve, half-planes, then each
+  // circle toggles inside itself
   std::vector<double> hcol(nx + 1);
   if (sc->has_curve)
     for (int i = 0; i <= nx; ++i) hcol[i] = P.curve_h(i * dx);
@@ -956,7 +956,7 @@ void init(State<R>& S, double dx, const orc_scene* sc) {
     for (int i = 0; i <= nx; ++i) {
       int p = 0;
       if (sc->has_curve) p ^= (j * dx) <= hcol[i];
-      if (sc->has_line) p ^= P.in_line(i * dx, j * dx);
+      for (int l = 0; l < sc->nlines; ++l) p ^= P.in_line(l, i * dx, j * dx);
       S.k(i, j) = (uint8_t)p;
     }
   for (int j = 0; j < ny; ++j)
@@ -964,7 +964,7 @@ void init(State<R>& S, double dx, const orc_scene* sc) {
       const double x = (i + 0.5) * dx, y = (j + 0.5) * dx;
       int p = 0;
       if (sc->has_curve) p ^= P.in_curve(x, y);
-      if (sc->has_line) p ^= P.in_line(x, y);
+      for (int l = 0; l < sc->nlines; ++l) p ^= P.in_line(l, x, y);
       S.z(i, j) = (uint8_t)p;
     }
   auto bbox = [&](int c, int* i0, int* i1, int* j0, int* j1) {
@@ -990,9 +990,9 @@ void init(State<R>& S, double dx, const orc_scene* sc) {
         if (i < nx && j < ny && P.in_notch((i + 0.5) * dx, (j + 0.5) * dx)) S.z(i, j) = 0;
       }
   // Owner of each edge's marker: a notch when the edge touches one of the
-  // boxes, else the curve, then the line, then the circle of lowest index
-  // whose own inside test differs at the two ends of the edge.
-  const int OWN_NOTCH = -4, OWN_NONE = -3, OWN_CURVE = -2, OWN_LINE = -1;
+  // boxes, else the curve, then the half-plane and then the circle of lowest
+  // index whose own inside test differs at the two ends of the edge.
+  const int OWN_NOTCH = -4, OWN_NONE = -3, OWN_CURVE = -2, OWN_LINE = -10;  // line l: -10 - l
   std::vector<int32_t> ownH((size_t)nx * (ny + 1), OWN_NONE), ownV((size_t)(nx + 1) * ny, OWN_NONE);
   for (int j = 0; j <= ny; ++j)
     for (int i = 0; i < nx; ++i) {
@@ -1000,7 +1000,12 @@ void init(State<R>& S, double dx, const orc_scene* sc) {
       int32_t& o = ownH[(size_t)j * nx + i];
       if (sc->nnotches && P.touches_notch(i * dx, j * dx, (i + 1) * dx, j * dx)) o = OWN_NOTCH;
       else if (sc->has_curve && ((j * dx) <= hcol[i]) != ((j * dx) <= hcol[i + 1])) o = OWN_CURVE;
-      else if (sc->has_line && P.in_line(i * dx, j * dx) != P.in_line((i + 1) * dx, j * dx)) o = OWN_LINE;
+      else
+        for (int l = 0; l < sc->nlines; ++l)
+          if (P.in_line(l, i * dx, j * dx) != P.in_line(l, (i + 1) * dx, j * dx)) {
+            o = OWN_LINE - l;
+            break;
+          }
     }
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i <= nx; ++i) {
@@ -1008,7 +1013,12 @@ void init(State<R>& S, double dx, const orc_scene* sc) {
       int32_t& o = ownV[(size_t)j * (nx + 1) + i];
       if (sc->nnotches && P.touches_notch(i * dx, j * dx, i * dx, (j + 1) * dx)) o = OWN_NOTCH;
       else if (sc->has_curve && ((j * dx) <= hcol[i]) != (((j + 1) * dx) <= hcol[i])) o = OWN_CURVE;
-      else if (sc->has_line && P.in_line(i * dx, j * dx) != P.in_line(i * dx, (j + 1) * dx)) o = OWN_LINE;
+      else
+        for (int l = 0; l < sc->nlines; ++l)
+          if (P.in_line(l, i * dx, j * dx) != P.in_line(l, i * dx, (j + 1) * dx)) {
+            o = OWN_LINE - l;
+            break;
+          }
     }
   for (int c = 0; c < sc->ncircles; ++c) {
     int i0, i1, j0, j1;
@@ -1056,8 +1066,9 @@ void init(State<R>& S, double dx, const orc_scene* sc) {
           if ((yj <= P.curve_h(xi + mid * dx)) == side0) lo = mid; else hi = mid;
         }
         s = 0.5 * (lo + hi);
-      } else if (o == OWN_LINE) {
-        const double x = (sc->lc - sc->lb * yj) / sc->la;
+      } else if (o <= OWN_LINE) {
+        const int l = OWN_LINE - o;
+        const double x = (sc->lc[l] - sc->lb[l] * yj) / sc->la[l];
         s = (x - xi) / dx;
       } else if (o >= 0) {
         const double ddy = yj - sc->yc[o];
@@ -1084,8 +1095,9 @@ void init(State<R>& S, double dx, const orc_scene* sc) {
         s = 0.5 * (lo + hi);
       } else if (o == OWN_CURVE) {
         s = (hcol[i] - yj) / dx;
-      } else if (o == OWN_LINE) {
-        const double y = (sc->lc - sc->la * xi) / sc->lb;
+      } else if (o <= OWN_LINE) {
+        const int l = OWN_LINE - o;
+        const double y = (sc->lc[l] - sc->la[l] * xi) / sc->lb[l];
         s = (y - yj) / dx;
       } else if (o >= 0) {
         const double ddx = xi - sc->xc[o];

@@ -37,8 +37,8 @@ typedef struct {
   double y0;                 /* h(x) = y0 + sum_k amp[k-1] cos(2 pi k x + phase[k-1]) */
   int32_t nmodes;
   const double *amp, *phase;
-  int32_t has_line;          /* toggles the phase where la*x + lb*y <= lc  */
-  double la, lb, lc;
+  int32_t nlines;            /* 0..4 half-planes; each toggles the phase    */
+  double la[4], lb[4], lc[4];/*   where la*x + lb*y <= lc                   */
   int32_t nnotches;          /* boxes cut out of the reference phase after the */
   const double* notch;       /* toggles: x0, x1, y0, y1 per box (closed)       */
 } orc_scene;

@@ -280,6 +280,29 @@ def zalesak_workload(n=64, cfl=math.pi / 16):
     return Workload(f"zalesak_n{n}", n, dx, scene, f, dt, steps, {"circle": (0.5, 0.75, 0.15)})
 
 
+def stagnation_workload(n=8, pad=None, D=0.2, dt=1.0 / 64, T=1.0):
+    """Stagnation flow (Sec. 3.1): a film of thickness D between two parallel
+    lines at 45 degrees, x + y = 1 -/+ D/sqrt(2), in the unit square of n x n
+    cells, drained by (u, v) = (0.5 - y, 0.5 - x) about the stagnation point
+    (0.5, 0.5); dt = 1/64 (CFL 0.0625 at n = 8) up to t = T.
+
+    The flow leaves and enters the window through its sides, so the grid
+    extends the window by `pad` cells on every side (default 2n): the grid
+    origin is at (-pad dx, -pad dx), and the scene and field are given in
+    grid coordinates.  The film is the band between the two half-planes
+    (each toggles the phase)."""
+    pad = 2 * n if pad is None else int(pad)
+    N = n + 2 * pad
+    dx = 1.0 / n
+    off = pad * dx
+    h = D / math.sqrt(2.0)
+    lines = [(1.0, 1.0, 1.0 + h + 2.0 * off), (1.0, 1.0, 1.0 - h + 2.0 * off)]
+    f = linear_field(N, N, dx, a=(0.5 + off, 0.0, -1.0), b=(0.5 + off, -1.0, 0.0))
+    steps = int(round(T / dt))
+    return Workload(f"stagnation_n{n}_pad{pad}", N, dx, {"lines": lines}, f, dt, steps,
+                    {"window": (pad, n), "offset": off, "D": D, "c": (1.0 - h, 1.0 + h)})
+
+
 ROT_CENTRE = (0.4841, 0.5477)
 
 

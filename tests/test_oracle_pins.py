@@ -630,6 +630,122 @@ def test_hf_circle_curvature_converges():
 
 
 # ---------------------------------------------------------------------------
+# stagnation flow (Sec. 3.1): a film drained through open sides
+# ---------------------------------------------------------------------------
+def _stagnation_run(prec=oracle.FP64, pad=None, T=1.0, track=None):
+    """The workload's steps; beside them two points per film line (physical
+    coordinates) moved by the same split explicit Euler steps, so that the
+    exact discrete film is the band between the lines through them (the
+    field is linear, so lines stay lines)."""
+    wl = W.stagnation_workload(pad=pad, T=T)
+    S = oracle.init(wl.n, wl.n, wl.dx, wl.scene, prec)
+    P = [np.array([[-0.5, c + 0.5], [1.5, c - 1.5]]) for c in wl.meta["c"]]
+    r = None
+    for k in range(wl.steps):
+        r = oracle.step(S, wl.field.u, wl.field.v, wl.dt)
+        for L in P:
+            for q in L:
+                if k % 2 == 0:
+                    q[0] += (0.5 - q[1]) * wl.dt
+                    q[1] += (0.5 - q[0]) * wl.dt
+                else:
+                    q[1] += (0.5 - q[0]) * wl.dt
+                    q[0] += (0.5 - q[1]) * wl.dt
+        if track is not None:
+            track(k, wl, S, r, P)
+    return wl, S, r, P
+
+
+def _window_markers(wl, S):
+    pad, n = wl.meta["window"]
+    off, dx = wl.meta["offset"], wl.dx
+    pts = []
+    for j, i in np.argwhere(S.hasH):
+        x, y = (i + S.sH[j, i]) * dx - off, j * dx - off
+        if 0 <= x <= 1 and 0 <= y <= 1:
+            pts.append((x, y))
+    for j, i in np.argwhere(S.hasV):
+        x, y = i * dx - off, (j + S.sV[j, i]) * dx - off
+        if 0 <= x <= 1 and 0 <= y <= 1:
+            pts.append((x, y))
+    return np.array(pts)
+
+
+def _band(P):
+    """Unit normal and the two offsets of the film lines: n.x = c."""
+    d = P[0][1] - P[0][0]
+    nrm = np.array([d[1], -d[0]]) / np.hypot(d[0], d[1])
+    return nrm, sorted(float(nrm @ L[0]) for L in P)
+
+
+@pytest.mark.parametrize("prec,tol", [(oracle.FP64, 1e-12), (oracle.FP32, 5e-7)], ids=["fp64", "fp32"])
+def test_stagnation_film_stays_exact(prec, tol):
+    """Under the linear stagnation field straight lines stay straight, and
+    the circle fit through collinear points is the line: after every step
+    every marker in the window lies on the exact discrete film lines, and the
+    reference-phase area in the window equals the exact band area clipped to
+    the window (Sutherland-Hodgman)."""
+    def track(k, wl, S, r, P):
+        pad, n = wl.meta["window"]
+        nrm, (c1, c2) = _band(P)
+        M = _window_markers(wl, S)
+        assert len(M) >= 4
+        d = np.minimum(np.abs(M @ nrm - c1), np.abs(M @ nrm - c2))
+        assert d.max() < tol, (k, d.max())
+        area = r["C"][pad:pad + n, pad:pad + n].sum() * wl.dx ** 2
+        exact = _clip_area(nrm[0], nrm[1], c2) - _clip_area(nrm[0], nrm[1], c1)
+        assert abs(area - exact) < 20 * tol, (k, area, exact)
+    _stagnation_run(prec, track=track)
+
+
+def test_stagnation_subcell_film_kept():
+    """Fig. of Sec. 3.1: by t = 0.5 the film is thinner than a cell diagonal
+    and at t = 1 (0.2/e) it lies inside single cells, yet it is kept: cells
+    holding both lines carry four markers whose centre colour vertex is the
+    reference phase exactly where the centre lies in the film, and every
+    window cell the film's mid-line crosses has C > 0."""
+    seen = {}
+
+    def track(k, wl, S, r, P):
+        t = (k + 1) * wl.dt
+        if abs(t - 0.5) < 1e-12 or abs(t - 1.0) < 1e-12:
+            seen[t] = (S.copy(), r["C"].copy(), [L.copy() for L in P])
+    wl, S, r, P = _stagnation_run(track=track)
+    pad, n = wl.meta["window"]
+    off, dx = wl.meta["offset"], wl.dx
+    for t, (St, C, Pt) in seen.items():
+        nrm, (c1, c2) = _band(Pt)
+        assert c2 - c1 < math.sqrt(2) * dx
+        four = St.four[pad:pad + n, pad:pad + n]
+        assert four.sum() > 0
+        for j, i in np.argwhere(four):
+            xc = np.array([(i + 0.5) * dx, (j + 0.5) * dx])
+            assert St.Z[pad + j, pad + i] == int(c1 < nrm @ xc <= c2)
+        cm = 0.5 * (c1 + c2)
+        for j in range(n):
+            for i in range(n):
+                corners = np.array([[i, j], [i + 1, j], [i + 1, j + 1], [i, j + 1]]) * dx
+                side = np.sign(corners @ nrm - cm)
+                if side.min() < 0 < side.max():
+                    assert C[pad + j, pad + i] > 0.0, (t, i, j)
+
+
+def test_stagnation_margin_is_enough():
+    """The open sides are modelled by extending the grid: with margins of 2n
+    and 3n cells the window's colours, markers and fractions after the run
+    are identical, so nothing from the outer walls reaches the window."""
+    out = []
+    for pad in (16, 24):
+        wl, S, r, P = _stagnation_run(pad=pad)
+        p, n = wl.meta["window"]
+        out.append((S.K[p:p + n + 1, p:p + n + 1], S.Z[p:p + n, p:p + n],
+                    np.where(S.hasH, S.sH, 0)[p:p + n + 1, p:p + n],
+                    np.where(S.hasV, S.sV, 0)[p:p + n, p:p + n + 1], r["C"][p:p + n, p:p + n]))
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
 # generalised height-function fallbacks (Sec. 2.5, the method it cites)
 # ---------------------------------------------------------------------------
 def _frame(rng):
