@@ -79,10 +79,12 @@ typedef struct {
   const ebit_circle* circles;   /* host pointer, ncircles entries (may be NULL if 0) */
   int32_t ncircles;
   const ebit_curve* curve;      /* host pointer or NULL                     */
-  const ebit_halfplane* line;   /* host pointer or NULL                     */
+  const ebit_halfplane* line;   /* host pointer to max(nlines, 1) half-planes, or NULL */
   const ebit_notch* notches;    /* host pointer, nnotches entries (may be NULL if 0);
-                                   applied after the curve, line and circles */
+                                   applied after the curve, half-planes and circles */
   int32_t nnotches;
+  int32_t nlines;               /* half-planes at line (0 or 1: one), at most 4; a
+                                   band between parallel lines is two of them */
 } ebit_scene;
 
 /* Host copy of a state.  K: (ny+1)*(nx+1) bytes, Z: ny*nx bytes (0/1),

@@ -317,10 +317,12 @@ ebit_status init_scene(ebit_ctx* c, const ebit_scene* scene) {
       sc.phase = dcurve + scene->curve->nmodes;
     }
     if (scene->line) {
-      sc.has_line = 1;
-      sc.la = scene->line->a;
-      sc.lb = scene->line->b;
-      sc.lc = scene->line->c;
+      sc.nlines = scene->nlines > 1 ? scene->nlines : 1;
+      for (int l = 0; l < sc.nlines; ++l) {
+        sc.la[l] = scene->line[l].a;
+        sc.lb[l] = scene->line[l].b;
+        sc.lc[l] = scene->line[l].c;
+      }
     }
     const int b = c->cur;
     if (sc.has_curve) ebit::k_curve_cols<<<(c->grid.nx + 1 + 255) / 256, 256, 0, c->stream>>>(sc, c->grid.nx, dx, hv);
@@ -449,7 +451,8 @@ ebit_status ebit_init(ebit_ctx** out, const ebit_grid* grid, const ebit_scene* s
       (scene->curve && (scene->curve->nmodes < 0 || (scene->curve->nmodes > 0 &&
                                                      (!scene->curve->amp || !scene->curve->phase)))) ||
       (scene->line && scene->line->a == 0.0 && scene->line->b == 0.0 && scene->line->c < 0.0) ||
-      scene->nnotches < 0 || (scene->nnotches > 0 && !scene->notches))
+      scene->nnotches < 0 || (scene->nnotches > 0 && !scene->notches) || scene->nlines < 0 ||
+      scene->nlines > 4)
     return fail(EBIT_EINVAL, "invalid scene");
   ebit_status s = new_ctx(out, grid, stream);
   if (s != EBIT_OK) return s;

@@ -170,8 +170,8 @@ struct SceneDev {
   int nmodes;
   const double* amp;
   const double* phase;
-  int has_line;
-  double la, lb, lc;
+  int nlines;  // half-planes, each toggling where la x + lb y <= lc
+  double la[4], lb[4], lc[4];
   const double* notch;  // 4 per notch: x0, x1, y0, y1
   int nnotches;
 };
@@ -190,8 +190,8 @@ __device__ __forceinline__ bool in_circle(const SceneDev& sc, int c, double x, d
   const double r = sc.circ[3 * c + 2];
   return ddx * ddx + ddy * ddy <= r * r;
 }
-__device__ __forceinline__ bool in_line(const SceneDev& sc, double x, double y) {
-  return sc.la * x + sc.lb * y <= sc.lc;
+__device__ __forceinline__ bool in_line(const SceneDev& sc, int l, double x, double y) {
+  return sc.la[l] * x + sc.lb[l] * y <= sc.lc[l];
 }
 __device__ __forceinline__ bool in_notch(const SceneDev& sc, double x, double y) {
   for (int b = 0; b < sc.nnotches; ++b) {
@@ -200,14 +200,21 @@ __device__ __forceinline__ bool in_notch(const SceneDev& sc, double x, double y)
   }
   return false;
 }
-// The scene's phase at a point: curve, line and circles toggle it, then the
-// notches cut it out.
+// The scene's phase at a point: curve, half-planes and circles toggle it,
+// then the notches cut it out.
 __device__ bool scene_inside(const SceneDev& sc, double x, double y) {
   bool p = false;
   if (sc.has_curve) p ^= y <= curve_h(sc, x);
-  if (sc.has_line) p ^= in_line(sc, x, y);
+  for (int l = 0; l < sc.nlines; ++l) p ^= in_line(sc, l, x, y);
   for (int c = 0; c < sc.ncircles; ++c) p ^= in_circle(sc, c, x, y);
   return p && !in_notch(sc, x, y);
+}
+// The first half-plane whose inside test differs at the two ends of an edge, or -1.
+__device__ __forceinline__ int line_crossing(const SceneDev& sc, double xa, double ya, double xb,
+                                             double yb) {
+  for (int l = 0; l < sc.nlines; ++l)
+    if (in_line(sc, l, xa, ya) != in_line(sc, l, xb, yb)) return l;
+  return -1;
 }
 // Does the axis-aligned edge (xa, ya)-(xb, yb), xa <= xb, ya <= yb, touch a notch?
 __device__ __forceinline__ bool touches_notch(const SceneDev& sc, double xa, double ya, double xb,
@@ -236,12 +243,12 @@ k_init_base(SceneDev sc, Dims d, double dx, const double* hv, uint32_t* K, uint3
   int pk = 0, pz = 0;
   if (x <= d.nx && y <= d.ny) {
     if (sc.has_curve) pk ^= (y * dx) <= hv[x];
-    if (sc.has_line) pk ^= in_line(sc, x * dx, y * dx);
+    for (int l = 0; l < sc.nlines; ++l) pk ^= in_line(sc, l, x * dx, y * dx);
   }
   if (x < d.nx && y < d.ny) {
     const double cx = (x + 0.5) * dx, cy = (y + 0.5) * dx;
     if (sc.has_curve) pz ^= cy <= hv[d.nx + 1 + x];
-    if (sc.has_line) pz ^= in_line(sc, cx, cy);
+    for (int l = 0; l < sc.nlines; ++l) pz ^= in_line(sc, l, cx, cy);
   }
   const unsigned wk = __ballot_sync(0xffffffffu, (x <= d.nx && y <= d.ny) && pk);
   const unsigned wz = __ballot_sync(0xffffffffu, (x < d.nx && y < d.ny) && pz);
@@ -343,8 +350,8 @@ k_init_roots(SceneDev sc, Dims d, double dx, const uint32_t* __restrict__ K,
         if ((yj <= curve_h(sc, xi + mid * dx)) == side0) lo = mid; else hi = mid;
       }
       s = 0.5 * (lo + hi);
-    } else if (sc.has_line && in_line(sc, xi, yj) != in_line(sc, (x + 1) * dx, yj)) {
-      const double xr = (sc.lc - sc.lb * yj) / sc.la;
+    } else if (const int l = line_crossing(sc, xi, yj, (x + 1) * dx, yj); l >= 0) {
+      const double xr = (sc.lc[l] - sc.lb[l] * yj) / sc.la[l];
       s = (xr - xi) / dx;
     } else {
       const int o = ownH[(long long)y * d.P + x];
@@ -371,8 +378,8 @@ k_init_roots(SceneDev sc, Dims d, double dx, const uint32_t* __restrict__ K,
       s = 0.5 * (lo + hi);
     } else if (sc.has_curve && ((yj <= hv[x]) != (((y + 1) * dx) <= hv[x]))) {
       s = (hv[x] - yj) / dx;
-    } else if (sc.has_line && in_line(sc, xi, yj) != in_line(sc, xi, (y + 1) * dx)) {
-      const double yr = (sc.lc - sc.la * xi) / sc.lb;
+    } else if (const int l = line_crossing(sc, xi, yj, xi, (y + 1) * dx); l >= 0) {
+      const double yr = (sc.lc[l] - sc.la[l] * xi) / sc.lb[l];
       s = (yr - yj) / dx;
     } else {
       const int o = ownV[(long long)y * d.P + x];

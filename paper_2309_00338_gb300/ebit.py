@@ -63,7 +63,8 @@ class ebit_notch(ctypes.Structure):
 class ebit_scene(ctypes.Structure):
     _fields_ = [("circles", ctypes.POINTER(ebit_circle)), ("ncircles", ctypes.c_int32),
                 ("curve", ctypes.POINTER(ebit_curve)), ("line", ctypes.POINTER(ebit_halfplane)),
-                ("notches", ctypes.POINTER(ebit_notch)), ("nnotches", ctypes.c_int32)]
+                ("notches", ctypes.POINTER(ebit_notch)), ("nnotches", ctypes.c_int32),
+                ("nlines", ctypes.c_int32)]
 
 
 class ebit_fluids(ctypes.Structure):
@@ -158,10 +159,14 @@ def _scene(scene: dict, keep: list):
                        ph.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         keep += [amp, ph, c]
         sc.curve = ctypes.pointer(c)
+    lines = list(scene.get("lines", []))
     if scene.get("line") is not None:
-        hp = ebit_halfplane(*(float(t) for t in scene["line"]))
-        keep.append(hp)
-        sc.line = ctypes.pointer(hp)
+        lines = [scene["line"]] + lines
+    if lines:
+        arr = (ebit_halfplane * len(lines))(*(ebit_halfplane(*(float(t) for t in l)) for l in lines))
+        keep.append(arr)
+        sc.line = ctypes.cast(arr, ctypes.POINTER(ebit_halfplane))
+        sc.nlines = len(lines)
     if scene.get("notches"):
         nb = np.ascontiguousarray(np.asarray(scene["notches"], np.float64).reshape(-1, 4))
         keep.append(nb)

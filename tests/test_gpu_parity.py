@@ -456,3 +456,30 @@ def test_zalesak_64_turn(line_only):
             assert 1.22e-3 / 3 <= e_area <= 3 * 1.22e-3  # Table 5, EBIT, N=64
     finally:
         ebit.ebit_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_stagnation_film_run(prec):
+    """Sec. 3.1's stagnation flow (8x8 window in a grid with 16-cell margins,
+    a film between two half-planes, 64 steps of dt = 1/64): initial state,
+    every 16th state, counters and the final fields equal the oracle's."""
+    wl = W.stagnation_workload()
+    S = oracle.init(wl.n, wl.n, wl.dx, wl.scene, prec)
+    ctx = ebit.ebit_init(wl.n, wl.n, wl.dx, wl.scene, prec)
+    try:
+        g = ebit.ebit_get_state(ctx, wl.n, wl.n)
+        assert np.array_equal(g["Z"], S.Z)
+        assert_same_state(g, S, 1)
+        u, v = dev(wl.field.u, prec), dev(wl.field.v, prec)
+        for k in range(wl.steps):
+            ebit.ebit_step(ctx, u, v, wl.dt)
+            r = oracle.step(S, wl.field.u, wl.field.v, wl.dt)
+            if k % 16 == 15:
+                assert_same_state(ebit.ebit_get_state(ctx, wl.n, wl.n), S, prec)
+                d = ebit.ebit_diagnostics(ctx)
+                assert np.array_equal(d["counters"][:13], r["counters"][:13])
+        assert_same_fields(ctx, S, r, prec)
+        pad, n = wl.meta["window"]
+        assert S.four[pad:pad + n, pad:pad + n].sum() > 0   # the sub-cell film is there
+    finally:
+        ebit.ebit_destroy(ctx)
