@@ -152,15 +152,19 @@ ebit_status launch_coupling(ebit_ctx* c, const ebit_fluids* fl, void* rho, void*
   const Layout& L = c->L;
   const ebit::Fluids<R> f{(R)fl->rho1, (R)fl->rho2, (R)fl->mu1, (R)fl->mu2,
                           (R)fl->sigma / (R)c->grid.dx};
-  const dim3 grid((L.d.nx + 1 + ebit::kCT - 1) / ebit::kCT, (L.d.ny + 1 + ebit::kCR - 1) / ebit::kCR);
   {
     Timed t(c, EBIT_K_COUPLING);
-    if constexpr (sizeof(R) == 8)
+    if constexpr (sizeof(R) == 8) {
+      const dim3 grid((L.d.nx + 1 + ebit::kCT - 1) / ebit::kCT, (L.d.ny + 1 + ebit::kCR - 1) / ebit::kCR);
       ebit::k_coupling_q<<<grid, ebit::kCT, 0, c->stream>>>((const R*)c->C, (const R*)c->kappa, L.d, f,
                                                             (R*)rho, (R*)mu, (R*)fx, (R*)fy);
-    else
+    } else {
+      // column pairs 0..nx/2 (the last pair holds the right wall face)
+      const dim3 grid((L.d.nx / 2 + 1 + ebit::kCT - 1) / ebit::kCT,
+                      (L.d.ny + 1 + ebit::kCR2 - 1) / ebit::kCR2);
       ebit::k_coupling<R><<<grid, ebit::kCT, 0, c->stream>>>((const R*)c->C, (const R*)c->kappa, L.d,
                                                              f, (R*)rho, (R*)mu, (R*)fx, (R*)fy);
+    }
   }
   EBIT_CK(cudaGetLastError());
   return EBIT_OK;

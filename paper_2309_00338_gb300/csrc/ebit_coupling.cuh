@@ -5,17 +5,19 @@
 // heights-based curvatures (one valid: that one; neither: no force).
 //
 // A pure stream: C and kappa are read once, rho, mu, fx and fy written once
-// (24 bytes per cell in float, 48 in double).  One thread per column walks a
-// strip of rows and carries the row below in registers; the left neighbour
-// comes from the next lane down, so only the first row of a strip and lane 0
-// re-read a value, and those hit in cache.
+// (24 bytes per cell in float, 48 in double).  A thread walks a strip of rows
+// and carries the row below in registers; the left neighbour comes from the
+// next lane down, so only the first row of a strip and lane 0 re-read a
+// value, and those hit in cache.
 #pragma once
+#include <type_traits>
+
 #include "ebit_device.cuh"
 
 namespace ebit {
 
-constexpr int kCT = 128;  // columns per block
-constexpr int kCR = 16;   // rows per block
+constexpr int kCT = 128;  // threads per block
+constexpr int kCR = 16;   // rows per block of the double kernel
 
 template <typename R>
 struct Fluids {
@@ -58,69 +60,103 @@ __device__ __forceinline__ R face_force(const Fluids<R>& f, R ka, R kb, R ca, R 
 }
 
 // C, kap: pitched fields (row pitch d.P).  rho, mu: ny x nx; fx: ny x (nx+1);
-// fy: (ny+1) x nx; any output may be null.  Thread column i runs over
-// 0..nx: cell i for i < nx, and the right wall face of fx for i = nx.  Block
-// rows cover 0..ny, row ny carrying only the top wall of fy.  Rows are taken
-// NB at a time, all their loads issued before any is used, so that each
-// thread keeps 2 NB loads in flight.
-template <typename R, int CR = kCR, int NB = 16 / sizeof(R) * 2>
+// fy: (ny+1) x nx; any output may be null.  Thread t owns the column pair
+// i0 = 2t, i0 + 1 (cells below nx; face columns up to nx, so the right wall
+// face belongs to the last pair), reads both with one 8- or 16-byte load
+// (rows are pitched to 32 elements, i0 is even) and, when nx is even, stores
+// the pair of rho, mu and fy with one vector store.  Block rows cover 0..ny,
+// row ny carrying only the top wall of fy.  Rows are taken NB at a time, all
+// their loads issued before any is used.
+constexpr int kCR2 = 8;  // rows per block of the column-pair kernel
+
+template <typename R, int CR = kCR2, int NB = 4>
 __global__ void __launch_bounds__(kCT) k_coupling(const R* __restrict__ C, const R* __restrict__ kap,
                                                   Dims d, Fluids<R> f, R* __restrict__ rho,
                                                   R* __restrict__ mu, R* __restrict__ fx,
                                                   R* __restrict__ fy) {
   static_assert(CR % NB == 0, "strip of whole batches");
-  const int i = blockIdx.x * kCT + threadIdx.x;
+  using R2 = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+  const int i0 = 2 * (blockIdx.x * kCT + threadIdx.x);
   const int lane = threadIdx.x & 31;
   const int j0 = blockIdx.y * CR;
   const int jc = min(j0 + CR, d.ny);      // cell rows of the strip end here
   const int j1 = min(j0 + CR, d.ny + 1);  // face rows end here
-  const bool cell = i < d.nx;
-  const bool left = lane == 0 && cell && i > 0;  // lane 0 reads its left neighbour itself
+  const bool c0 = i0 < d.nx, c1 = i0 + 1 < d.nx;
+  const bool left = lane == 0 && c0 && i0 > 0;  // lane 0 reads its left neighbour itself
   const R nan = R(__int_as_float(0x7fc00000));
   const long long wx = (long long)d.nx + 1;
-  R cb = R(0), kb = nan;  // row below, column i
-  if (j0 > 0 && cell) {
-    cb = __ldg(&C[(long long)(j0 - 1) * d.P + i]);
-    kb = __ldg(&kap[(long long)(j0 - 1) * d.P + i]);
+  const bool pairs = (d.nx & 1) == 0;  // rows of nx elements keep pairs aligned
+  auto load = [&](const R* p, int row, R* a, R* b) {
+    if (c1) {
+      const R2 v = __ldg(reinterpret_cast<const R2*>(p + (long long)row * d.P + i0));
+      *a = v.x;
+      *b = v.y;
+    } else if (c0) {
+      *a = __ldg(p + (long long)row * d.P + i0);
+    }
+  };
+  R cb0 = R(0), kb0 = nan, cb1 = R(0), kb1 = nan;  // row below, columns i0, i0 + 1
+  if (j0 > 0) {
+    load(C, j0 - 1, &cb0, &cb1);
+    load(kap, j0 - 1, &kb0, &kb1);
   }
   for (int jb = j0; jb < j1; jb += NB) {  // trip count uniform across the block
-    R c[NB], k[NB], cl[NB], kl[NB];
+    R ca[NB], cc[NB], ka[NB], kc[NB], cl[NB], kl[NB];
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
       const int j = jb + q;
-      c[q] = R(0);
-      k[q] = nan;
-      cl[q] = R(0);
-      kl[q] = nan;
-      if (j < jc && cell) {
-        c[q] = __ldg(&C[(long long)j * d.P + i]);
-        k[q] = __ldg(&kap[(long long)j * d.P + i]);
+      ca[q] = cc[q] = cl[q] = R(0);
+      ka[q] = kc[q] = kl[q] = nan;
+      if (j < jc) {
+        load(C, j, &ca[q], &cc[q]);
+        load(kap, j, &ka[q], &kc[q]);
       }
       if (j < jc && left) {
-        cl[q] = __ldg(&C[(long long)j * d.P + i - 1]);
-        kl[q] = __ldg(&kap[(long long)j * d.P + i - 1]);
+        cl[q] = __ldg(&C[(long long)j * d.P + i0 - 1]);
+        kl[q] = __ldg(&kap[(long long)j * d.P + i0 - 1]);
       }
     }
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
       const int j = jb + q;
-      const R cs = __shfl_up_sync(0xffffffffu, c[q], 1), ks = __shfl_up_sync(0xffffffffu, k[q], 1);
+      const R cs = __shfl_up_sync(0xffffffffu, cc[q], 1), ks = __shfl_up_sync(0xffffffffu, kc[q], 1);
       if (lane != 0) {
         cl[q] = cs;
         kl[q] = ks;
       }
+      const long long o = (long long)j * d.nx + i0;
       if (j < jc) {
-        if (cell && rho) rho[(long long)j * d.nx + i] = mix(c[q], f.r1, f.r2);
-        if (cell && mu) mu[(long long)j * d.nx + i] = mix(c[q], f.m1, f.m2);
-        if (i <= d.nx && fx)
-          fx[(long long)j * wx + i] =
-              (i == 0 || i == d.nx) ? R(0) : face_force(f, kl[q], k[q], cl[q], c[q]);
+        if (c1 && pairs) {
+          if (rho) *reinterpret_cast<R2*>(rho + o) = R2{mix(ca[q], f.r1, f.r2), mix(cc[q], f.r1, f.r2)};
+          if (mu) *reinterpret_cast<R2*>(mu + o) = R2{mix(ca[q], f.m1, f.m2), mix(cc[q], f.m1, f.m2)};
+        } else {
+          if (c0 && rho) rho[o] = mix(ca[q], f.r1, f.r2);
+          if (c0 && mu) mu[o] = mix(ca[q], f.m1, f.m2);
+          if (c1 && rho) rho[o + 1] = mix(cc[q], f.r1, f.r2);
+          if (c1 && mu) mu[o + 1] = mix(cc[q], f.m1, f.m2);
+        }
+        if (fx) {
+          R* px = fx + (long long)j * wx + i0;
+          if (i0 <= d.nx)
+            px[0] = (i0 == 0 || i0 == d.nx) ? R(0) : face_force(f, kl[q], ka[q], cl[q], ca[q]);
+          if (i0 + 1 <= d.nx) px[1] = (i0 + 1 == d.nx) ? R(0) : face_force(f, ka[q], kc[q], ca[q], cc[q]);
+        }
       }
-      if (j < j1 && cell && fy)
-        fy[(long long)j * d.nx + i] =
-            (j == 0 || j == d.ny) ? R(0) : face_force(f, kb, k[q], cb, c[q]);
-      cb = c[q];
-      kb = k[q];
+      if (fy && j < j1) {
+        const bool wall = j == 0 || j == d.ny;
+        const R y0 = wall ? R(0) : face_force(f, kb0, ka[q], cb0, ca[q]);
+        const R y1 = wall ? R(0) : face_force(f, kb1, kc[q], cb1, cc[q]);
+        if (c1 && pairs) {
+          *reinterpret_cast<R2*>(fy + o) = R2{y0, y1};
+        } else {
+          if (c0) fy[o] = y0;
+          if (c1) fy[o + 1] = y1;
+        }
+      }
+      cb0 = ca[q];
+      kb0 = ka[q];
+      cb1 = cc[q];
+      kb1 = kc[q];
     }
   }
 }
