@@ -4,8 +4,8 @@
 // cells without a valid stencil are left NaN there.  When the context asks
 // for the generalised method, two more launches give those cells a value:
 //
-//   k_ghf_list  a dense pass over kappa and the corner bits that lists the
-//               interface cells whose kappa is NaN (warp-aggregated appends);
+//   k_ghf_list  a pass over the corner bit rows that lists the interface
+//               cells whose kappa is NaN (warp-aggregated appends);
 //   k_ghf_fit   one thread per listed cell, in turn: the standard stencil
 //               along the other direction; a parabola fitted to the valid
 //               heights of both directions ("mixed heights"); a parabola
@@ -32,26 +32,31 @@ __device__ __forceinline__ int kbit(const uint32_t* __restrict__ K, int kw, int 
   return (__ldg(&K[(long long)j * kw + (i >> 5)]) >> (i & 31)) & 1;
 }
 
+// One warp per 32 cells of a row: the interface cells come from the corner
+// bit rows as word operations, and only those lanes read kappa.
 template <typename R>
 __global__ void __launch_bounds__(kGhfListX* kGhfListY)
     k_ghf_list(const uint32_t* __restrict__ K, const R* __restrict__ kappa, Dims d,
                int* __restrict__ list, unsigned* __restrict__ count) {
-  const int i = blockIdx.x * kGhfListX + threadIdx.x;
+  const int lane = threadIdx.x;
+  const int i0 = blockIdx.x * kGhfListX;
   const int j = blockIdx.y * kGhfListY + threadIdx.y;
-  bool need = false;
-  if (i < d.nx && j < d.ny && isnan(__ldg(&kappa[(long long)j * d.P + i]))) {
-    const int c0 = kbit(K, d.kw, i, j), c1 = kbit(K, d.kw, i + 1, j);
-    const int c2 = kbit(K, d.kw, i + 1, j + 1), c3 = kbit(K, d.kw, i, j + 1);
-    need = !(c0 == c1 && c1 == c2 && c2 == c3);
-  }
+  if (j >= d.ny) return;  // the whole warp
+  const uint32_t* r0 = K + (long long)j * d.kw;
+  const uint32_t* r1 = r0 + d.kw;
+  const uint32_t a = row_bits(r0, d.kw, i0), b = row_bits(r0, d.kw, i0 + 1);
+  const uint32_t c = row_bits(r1, d.kw, i0), e = row_bits(r1, d.kw, i0 + 1);
+  uint32_t iface = (a | b | c | e) & ~(a & b & c & e);  // corners not all equal
+  const int ncell = d.nx - i0;
+  if (ncell < 32) iface &= (1u << ncell) - 1u;
+  const bool need = ((iface >> lane) & 1u) && isnan(__ldg(&kappa[(long long)j * d.P + i0 + lane]));
   const unsigned m = __ballot_sync(0xffffffffu, need);
   if (m == 0u) return;
-  const int lane = threadIdx.x & 31;
   const int leader = __ffs(m) - 1;
   unsigned base = 0;
   if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
   base = __shfl_sync(0xffffffffu, base, leader);
-  if (need) list[base + __popc(m & ((1u << lane) - 1u))] = j * d.nx + i;
+  if (need) list[base + __popc(m & ((1u << lane) - 1u))] = j * d.nx + i0 + lane;
 }
 
 // Read-only view of the state and fractions of one context.
@@ -70,24 +75,41 @@ struct GhfView {
   __device__ R v(int i, int j) const { return __ldg(&sV[(long long)j * d.P + i]); }
 };
 
-// The column of seven cells through (i+m, j-3..j+3) (ycol) or the row
-// (i-3..i+3, j+m): its count h of reference-phase cells (summed in that
-// order) and orientation: 1 = reference phase at the low end only, -1 = at
-// the high end only, 0 = not a valid height (mixed end cell, equal ends, or
-// outside the domain).
+// The fractions a listed cell's stencils read: the vertical arm
+// v[m+1][t+3] = C(i+m, j+t) and the horizontal arm h[m+1][t+3] = C(i+t, j+m),
+// m = -1..1, t = -3..3, loaded together (independent loads) for the columns
+// that lie inside the domain (vin / hin).
 template <typename R>
-__device__ int ghf_column(const GhfView<R>& S, int i, int j, int m, bool ycol, R* h) {
-  const bool in = ycol ? (i + m >= 0 && i + m <= S.d.nx - 1 && j - 3 >= 0 && j + 3 <= S.d.ny - 1)
-                       : (j + m >= 0 && j + m <= S.d.ny - 1 && i - 3 >= 0 && i + 3 <= S.d.nx - 1);
-  if (!in) return 0;
-  R acc = R(0);
+struct Cross {
+  R v[3][7], h[3][7];
+  bool vin[3], hin[3];
+  __device__ void load(const GhfView<R>& S, int i, int j) {
 #pragma unroll
-  for (int t = -3; t <= 3; ++t) acc = acc + (ycol ? S.c(i + m, j + t) : S.c(i + t, j + m));
-  *h = acc;
-  const R lo = ycol ? S.c(i + m, j - 3) : S.c(i - 3, j + m);
-  const R hi = ycol ? S.c(i + m, j + 3) : S.c(i + 3, j + m);
-  return (lo == R(1) && hi == R(0)) ? 1 : (lo == R(0) && hi == R(1)) ? -1 : 0;
-}
+    for (int m = -1; m <= 1; ++m) {
+      vin[m + 1] = i + m >= 0 && i + m <= S.d.nx - 1 && j - 3 >= 0 && j + 3 <= S.d.ny - 1;
+      hin[m + 1] = j + m >= 0 && j + m <= S.d.ny - 1 && i - 3 >= 0 && i + 3 <= S.d.nx - 1;
+#pragma unroll
+      for (int t = -3; t <= 3; ++t) {
+        v[m + 1][t + 3] = vin[m + 1] ? S.c(i + m, j + t) : R(0);
+        h[m + 1][t + 3] = hin[m + 1] ? S.c(i + t, j + m) : R(0);
+      }
+    }
+  }
+  // The column of seven cells through (i+m, j-3..j+3) (ycol) or the row
+  // (i-3..i+3, j+m): its count of reference-phase cells (summed in that
+  // order) and orientation: 1 = reference phase at the low end only, -1 = at
+  // the high end only, 0 = not a valid height (mixed end cell, equal ends,
+  // or outside the domain).
+  __device__ __forceinline__ int column(int m, bool ycol, R* hsum) const {
+    if (!(ycol ? vin[m + 1] : hin[m + 1])) return 0;
+    R acc = R(0);
+#pragma unroll
+    for (int t = 0; t < 7; ++t) acc = acc + (ycol ? v[m + 1][t] : h[m + 1][t]);
+    *hsum = acc;
+    const R lo = ycol ? v[m + 1][0] : h[m + 1][0], hi = ycol ? v[m + 1][6] : h[m + 1][6];
+    return (lo == R(1) && hi == R(0)) ? 1 : (lo == R(0) && hi == R(1)) ? -1 : 0;
+  }
+};
 
 // Points of a fit, kept only when at least half a cell from every point
 // already kept, with the least-squares sums (unit weights) accumulated in that
@@ -168,13 +190,15 @@ __global__ void __launch_bounds__(kGhfThreads)
       ax = ax + fabs(px[seg[t][1]] - px[seg[t][0]]);
       ay = ay + fabs(py[seg[t][1]] - py[seg[t][0]]);
     }
+    Cross<R> X;
+    X.load(S, i, j);
     // 1. the standard stencil along the other direction
     const bool ycol = !(ax >= ay);
     {
       R h[3];
       int o[3];
 #pragma unroll
-      for (int m = -1; m <= 1; ++m) o[m + 1] = ghf_column(S, i, j, m, ycol, &h[m + 1]);
+      for (int m = -1; m <= 1; ++m) o[m + 1] = X.column(m, ycol, &h[m + 1]);
       if (o[0] != 0 && o[0] == o[1] && o[1] == o[2]) {
         const R hp = (h[2] - h[0]) * R(0.5);
         const R hpp = (h[2] - h[1]) - (h[1] - h[0]);
@@ -209,11 +233,13 @@ __global__ void __launch_bounds__(kGhfThreads)
     F.ny = n0y / len;
     // 2. mixed heights: the valid columns of both directions' stencils
     F.reset();
+#pragma unroll
     for (int dir = 0; dir < 2; ++dir) {
       const bool yc = dir == 0;
+#pragma unroll
       for (int m = -1; m <= 1; ++m) {
         R h = R(0);
-        const int o = ghf_column(S, i, j, m, yc, &h);
+        const int o = X.column(m, yc, &h);
         if (o == 0) continue;
         const R pos = o == 1 ? R(-3) + h : R(4) - h;
         const R mid = (R)m + R(0.5);
