@@ -112,24 +112,21 @@ ebit_status launch_fields(ebit_ctx* c) {
   const Layout& L = c->L;
   const int b = c->cur;
   const dim3 fgrid((L.d.nx + 1 + ebit::kFX - 1) / ebit::kFX, (L.d.ny + 1 + ebit::kFY - 1) / ebit::kFY);
+  const bool ghf = (c->grid.flags & EBIT_CURV_GHF) != 0;
+  if (ghf) EBIT_CK(cudaMemsetAsync(c->ghf_count, 0, sizeof(unsigned), c->stream));
   {
     Timed t(c, EBIT_K_FIELDS);
     ebit::k_fields_tile<R><<<fgrid, ebit::kFieldThreads, 0, c->stream>>>(
         c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], L.d, (R)c->grid.dx, (R*)c->C,
-        (R*)c->kappa, c->partial, c->ctr);
+        (R*)c->kappa, c->partial, c->ctr, ghf ? c->ghf_list : nullptr, ghf ? c->ghf_count : nullptr);
   }
   {
     Timed t(c, EBIT_K_AREA);
     ebit::k_area<<<1, 256, 0, c->stream>>>(c->partial, (long long)fgrid.x * fgrid.y,
                                            c->grid.dx * c->grid.dx, c->area);
   }
-  if (c->grid.flags & EBIT_CURV_GHF) {
+  if (ghf) {
     Timed t(c, EBIT_K_GHF);
-    EBIT_CK(cudaMemsetAsync(c->ghf_count, 0, sizeof(unsigned), c->stream));
-    const dim3 lgrid((L.d.nx + ebit::kGhfListX - 1) / ebit::kGhfListX,
-                     (L.d.ny + ebit::kGhfListY - 1) / ebit::kGhfListY);
-    ebit::k_ghf_list<R><<<lgrid, dim3(ebit::kGhfListX, ebit::kGhfListY), 0, c->stream>>>(
-        c->K[b], (const R*)c->kappa, L.d, c->ghf_list, c->ghf_count);
     const ebit::GhfView<R> S{c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b],
                              (const R*)c->C, L.d};
     const long long cells = (long long)L.d.nx * L.d.ny;

@@ -79,12 +79,16 @@ __device__ __forceinline__ void store4(double* p, double a, double b, double c, 
 }
 
 // The tile (bx, by) of one grid; its area partial goes to partial[slot].
+// With ghf_list, the interface cells left without a 7x3 stencil are
+// appended to it (ghf_count, zeroed before the launch, counts them): one
+// global atomic per tile reserves its slice.
 template <typename R>
 __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
                                             const uint32_t* __restrict__ Z,
                                             const R* __restrict__ sH, const R* __restrict__ sV,
                                             const Dims& d, R dx, R* C, R* kappa, double* partial,
-                                            long long slot, unsigned long long* ctr, int bx, int by) {
+                                            long long slot, unsigned long long* ctr, int bx, int by,
+                                            int* ghf_list = nullptr, unsigned* ghf_count = nullptr) {
   __shared__ uint32_t kw[kFVY * kFW];  // vertex colours
   __shared__ uint32_t zw[kFRY * kFW];  // centre colours
   __shared__ uint32_t fw[kFRY * kFW];  // full cells
@@ -95,11 +99,15 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
   __shared__ double s_wsum[kFieldThreads / 32];
   __shared__ int s_cnt[D_NUSED];
   __shared__ unsigned long long s_full;
+  __shared__ unsigned s_nghf, s_ghf_base;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i0 = bx * kFX, j0 = by * kFY;
   const int rx0 = i0 - kFH, ry0 = j0 - kFH;
   if (tid < D_NUSED) s_cnt[tid] = 0;
-  if (tid == 0) s_full = 0ull;
+  if (tid == 0) {
+    s_full = 0ull;
+    s_nghf = 0u;
+  }
   // region columns / rows inside the grid
   const int vx0 = max(0, -rx0), vx1 = min(kFVX - 1, d.nx - rx0);  // vertices
   const int cx1 = min(kFRX - 1, d.nx - 1 - rx0);                  // cells
@@ -253,6 +261,10 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
       out = -hpp / den;
     } else {
       cnt[D_HF_INVALID] += 1;
+      if (ghf_list) {  // flag the entry for the generalised fallbacks
+        lst[e] = (uint16_t)(ci | 0x8000);
+        atomicAdd(&s_nghf, 1u);
+      }
     }
     kappa[(long long)j * d.P + i] = out;
   }
@@ -305,15 +317,34 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
     partial[slot] = p;
   }
   if (tid < D_NUSED && s_cnt[tid] != 0) atomicAdd(&ctr[tid], (unsigned long long)s_cnt[tid]);
+  if (ghf_list) {
+    const unsigned nflag = s_nghf;  // final: its atomics precede the last barrier
+    if (nflag != 0u) {              // the same in every thread
+      __syncthreads();              // every thread has read it
+      if (tid == 0) {
+        s_ghf_base = atomicAdd(ghf_count, nflag);
+        s_nghf = 0u;
+      }
+      __syncthreads();
+      for (int e = tid; e < nlist; e += kFieldThreads) {
+        const int ci = lst[e];
+        if (!(ci & 0x8000)) continue;
+        const int t = ci & 0x7fff;
+        const int i = rx0 + t % kFRX, j = ry0 + t / kFRX;
+        ghf_list[s_ghf_base + atomicAdd(&s_nghf, 1u)] = j * d.nx + i;
+      }
+    }
+  }
 }
 
 template <typename R>
 __global__ void __launch_bounds__(kFieldThreads)
 k_fields_tile(const uint32_t* __restrict__ K, const uint32_t* __restrict__ Z,
               const R* __restrict__ sH, const R* __restrict__ sV, Dims d, R dx, R* C, R* kappa,
-              double* partial, unsigned long long* ctr) {
+              double* partial, unsigned long long* ctr, int* ghf_list, unsigned* ghf_count) {
   fields_tile<R>(K, Z, sH, sV, d, dx, C, kappa, partial,
-                 (long long)blockIdx.y * gridDim.x + blockIdx.x, ctr, blockIdx.x, blockIdx.y);
+                 (long long)blockIdx.y * gridDim.x + blockIdx.x, ctr, blockIdx.x, blockIdx.y, ghf_list,
+                 ghf_count);
 }
 
 // Many grids in one launch (work items: grid, tile).

@@ -1,11 +1,12 @@
 // Generalised height-function fallbacks (Sec. 2.5 takes its curvature from
 // the generalised height-function method, Popinet 2009).  The fused fields
 // kernel computes the standard 7x3 height-function curvature; interface
-// cells without a valid stencil are left NaN there.  When the context asks
-// for the generalised method, two more launches give those cells a value:
+// cells without a valid stencil are left NaN there and, when the context
+// asks for the generalised method, listed by that kernel (each tile stages
+// its cells in shared memory and reserves its slice of the list with one
+// atomic; a separate listing pass over kappa was latency-bound at 44-70 us
+// at 4096^2).  One more launch gives the listed cells a value:
 //
-//   k_ghf_list  a pass over the corner bit rows that lists the interface
-//               cells whose kappa is NaN (warp-aggregated appends);
 //   k_ghf_fit   one thread per listed cell, in turn: the standard stencil
 //               along the other direction; a parabola fitted to the valid
 //               heights of both directions ("mixed heights"); a parabola
@@ -25,38 +26,10 @@ namespace ebit {
 constexpr int D_HF_OTHER = 13, D_HF_MIXED = 14, D_HF_MARKERS = 15;
 static_assert(D_NUSED <= D_HF_OTHER && D_HF_MARKERS < kCounters, "counter slots");
 
-constexpr int kGhfListX = 32, kGhfListY = 8;  // k_ghf_list block
-constexpr int kGhfThreads = 128;              // k_ghf_fit block
+constexpr int kGhfThreads = 128;  // k_ghf_fit block
 
 __device__ __forceinline__ int kbit(const uint32_t* __restrict__ K, int kw, int i, int j) {
   return (__ldg(&K[(long long)j * kw + (i >> 5)]) >> (i & 31)) & 1;
-}
-
-// One warp per 32 cells of a row: the interface cells come from the corner
-// bit rows as word operations, and only those lanes read kappa.
-template <typename R>
-__global__ void __launch_bounds__(kGhfListX* kGhfListY)
-    k_ghf_list(const uint32_t* __restrict__ K, const R* __restrict__ kappa, Dims d,
-               int* __restrict__ list, unsigned* __restrict__ count) {
-  const int lane = threadIdx.x;
-  const int i0 = blockIdx.x * kGhfListX;
-  const int j = blockIdx.y * kGhfListY + threadIdx.y;
-  if (j >= d.ny) return;  // the whole warp
-  const uint32_t* r0 = K + (long long)j * d.kw;
-  const uint32_t* r1 = r0 + d.kw;
-  const uint32_t a = row_bits(r0, d.kw, i0), b = row_bits(r0, d.kw, i0 + 1);
-  const uint32_t c = row_bits(r1, d.kw, i0), e = row_bits(r1, d.kw, i0 + 1);
-  uint32_t iface = (a | b | c | e) & ~(a & b & c & e);  // corners not all equal
-  const int ncell = d.nx - i0;
-  if (ncell < 32) iface &= (1u << ncell) - 1u;
-  const bool need = ((iface >> lane) & 1u) && isnan(__ldg(&kappa[(long long)j * d.P + i0 + lane]));
-  const unsigned m = __ballot_sync(0xffffffffu, need);
-  if (m == 0u) return;
-  const int leader = __ffs(m) - 1;
-  unsigned base = 0;
-  if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (need) list[base + __popc(m & ((1u << lane) - 1u))] = j * d.nx + i0 + lane;
 }
 
 // Read-only view of the state and fractions of one context.
