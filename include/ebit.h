@@ -154,6 +154,14 @@ ebit_status ebit_sweep(ebit_ctx* ctx, int axis, const void* vel, double dt);
  * sum C dx^2 (synchronises the stream and reports deferred errors). */
 ebit_status ebit_fraction(ebit_ctx* ctx, void* C_dev, double* area_host);
 
+/* The area sum C dx^2 of the current state copied to area_host (host memory;
+ * pinned memory keeps the copy asynchronous) on the context's stream, without
+ * waiting: the value is there once the stream reaches the copy (after an
+ * event recorded behind it, or ebit_sync).  For callers that read every
+ * step's result while the next step runs.  EBIT_EINVAL for NULL arguments;
+ * deferred device errors are reported by the next synchronising call. */
+ebit_status ebit_area_async(ebit_ctx* ctx, double* area_host);
+
 /* Height-function curvature (Sec. 2.5) of the current state, NaN where the
  * 7x3 stencil is invalid or the cell holds no interface.  kappa_dev: DEVICE
  * buffer of ny*nx elements or NULL; n_invalid_host: if non-NULL receives the

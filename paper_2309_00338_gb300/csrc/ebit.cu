@@ -515,6 +515,12 @@ ebit_status ebit_fraction(ebit_ctx* c, void* C_dev, double* area_host) {
   return EBIT_OK;
 }
 
+ebit_status ebit_area_async(ebit_ctx* c, double* area_host) {
+  if (!c || !area_host) return fail(EBIT_EINVAL, "NULL argument");
+  EBIT_CK(cudaMemcpyAsync(area_host, c->area, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return EBIT_OK;
+}
+
 ebit_status ebit_curvature(ebit_ctx* c, void* kappa_dev, int32_t* n_invalid_host) {
   if (!c) return fail(EBIT_EINVAL, "NULL context");
   const Layout& L = c->L;

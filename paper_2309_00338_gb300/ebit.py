@@ -105,6 +105,7 @@ SIGNATURES = {
     "ebit_timings": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "ebit_fraction_noalloc": (ctypes.c_int, [ctypes.POINTER(ebit_grid), _P, _P, _P, _P, _P, _P, _P, _P]),
     "ebit_coupling": (ctypes.c_int, [_P, ctypes.POINTER(ebit_fluids), _P, _P, _P, _P]),
+    "ebit_area_async": (ctypes.c_int, [_P, _P]),
 }
 
 K_SWEEP, K_CENTRE, K_FIELDS, K_AREA, K_COUPLING, K_GHF = range(6)
@@ -239,6 +240,14 @@ def ebit_fraction(ctx, C=None, want_area=True):
     a = ctypes.c_double(0.0)
     _check(lib().ebit_fraction(ctx, _dev_ptr(C), ctypes.byref(a) if want_area else None), "ebit_fraction")
     return a.value if want_area else None
+
+
+def ebit_area_async(ctx, area_host):
+    """Queue the copy of the area sum into area_host (a pinned CPU tensor of
+    one float64) on the context's stream; valid once the stream gets there."""
+    if area_host.is_cuda or area_host.dtype.itemsize != 8:
+        raise ValueError("expected a host tensor of one float64")
+    _check(lib().ebit_area_async(ctx, ctypes.c_void_p(area_host.data_ptr())), "ebit_area_async")
 
 
 def ebit_curvature(ctx, kappa=None, want_invalid=True):

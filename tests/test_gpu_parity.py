@@ -483,3 +483,25 @@ def test_stagnation_film_run(prec):
         assert S.four[pad:pad + n, pad:pad + n].sum() > 0   # the sub-cell film is there
     finally:
         ebit.ebit_destroy(ctx)
+
+
+def test_area_async_matches_fraction():
+    """ebit_area_async queues the area of the current state; after the stream
+    reaches it the value equals ebit_fraction's, step by step."""
+    S, f, dt = scene_disks(1)
+    ctx = gpu_from(S)
+    try:
+        host = torch.zeros(3, dtype=torch.float64).pin_memory()
+        u, v = dev(f.u, 1), dev(f.v, 1)
+        want = []
+        for k in range(3):
+            ebit.ebit_step(ctx, u, v, dt)
+            ebit.ebit_area_async(ctx, host[k:k + 1])
+            r = oracle.step(S, f.u, f.v, dt)
+            want.append(r["area"])
+        ebit.ebit_sync(ctx)
+        assert host.tolist() == pytest.approx(want, rel=1e-12)
+        assert float(host[2]) == ebit.ebit_fraction(ctx)
+        assert ebit.lib().ebit_area_async(ctx, None) == ebit.EBIT_EINVAL
+    finally:
+        ebit.ebit_destroy(ctx)
