@@ -205,7 +205,17 @@ def cpu_baseline(wl, budget_s=20.0):
             break
     t = time.perf_counter() - t0
     return {"value": wl.n * wl.n * k / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{k} whole steps of the {wl.n}^2 workload (FP32 form) from its initial state"}
+            "sample": f"{k} whole steps of the {wl.n}^2 workload (FP32 form) from its initial state",
+            "host": host_cores()}
+
+
+def host_cores():
+    """The host's cores as the process sees them (the oracle runs on one)."""
+    try:
+        aff = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        aff = None
+    return {"nproc": os.cpu_count(), "affinity": aff}
 
 
 def run_reference(args, wl, world, rank):
@@ -233,7 +243,7 @@ def run_reference(args, wl, world, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": {"workload": wl.name, "grid": [wl.n, wl.n], "prec": "fp32"},
             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cores(),
                              "sample": f"{done} whole steps of the {wl.n}^2 workload after {args.warmup} warm-up steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
