@@ -69,3 +69,26 @@ def test_product_path_has_no_oracle_dependency():
             text = open(path).read()
             assert "import oracle" not in text and "from oracle" not in text, path
             assert "ebit_oracle" not in text and "orc_" not in text, path
+
+
+def test_new_entry_points_check_arguments_without_gpu(libebit):
+    """ebit_coupling, ebit_area_async and the scene checks of ebit_init reject
+    bad arguments before any CUDA call; EBIT_CURV_GHF adds its cell list to
+    the footprint."""
+    from paper_2309_00338_gb300 import ebit
+    L = ebit.lib()
+    fl = ebit.ebit_fluids(1.0, 1.0, 1.0, 1.0, 1.0)
+    assert L.ebit_coupling(None, ctypes.byref(fl), None, None, None, None) == ebit.EBIT_EINVAL
+    assert L.ebit_area_async(None, None) == ebit.EBIT_EINVAL
+    n = 256
+    plain = ebit.ebit_footprint(n, n, 1 / n, ebit.EBIT_FP32)
+    ghf = ebit.ebit_footprint(n, n, 1 / n, ebit.EBIT_FP32, ebit.EBIT_CURV_GHF)
+    assert ghf - plain >= n * n * 4
+    assert ebit.ebit_footprint(n, n, 1 / n, ebit.EBIT_FP32, 4) == 0   # unknown flag
+    keep = []
+    sc = ebit._scene({"lines": [(1.0, 1.0, 0.5)] * 4}, keep)
+    sc.nlines = 5
+    h = ctypes.c_void_p()
+    g = ebit.ebit_grid(n, n, 1 / n, 0, 0)
+    assert L.ebit_init(ctypes.byref(h), ctypes.byref(g), ctypes.byref(sc), None) == ebit.EBIT_EINVAL
+    assert not h.value
