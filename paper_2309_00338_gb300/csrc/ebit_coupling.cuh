@@ -24,8 +24,8 @@ struct Fluids {
   R r1, r2, m1, m2, sh;  // sh = sigma / dx, formed once in R
 };
 
-// Tests on the integer pipe (FP64 compares and arithmetic run on the narrow
-// FP64 pipe, which would otherwise bound the double form).
+// Tests on the integer pipe (FP64 compares run on the narrow FP64 pipe,
+// which the double form keeps for the arithmetic that needs it).
 __device__ __forceinline__ bool nan_bits(float x) { return (__float_as_uint(x) & 0x7fffffffu) > 0x7f800000u; }
 __device__ __forceinline__ bool nan_bits(double x) {
   return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
@@ -39,35 +39,19 @@ __device__ __forceinline__ bool zero_bits(double x) {
   return ((unsigned long long)__double_as_longlong(x) << 1) == 0ull;
 }
 
-// c a + (1 - c) b; a pure cell (c = 1 or c = 0) gives a or b, which is what
-// the expression evaluates to there.
+// rho or mu of a cell: c a + (1 - c) b (Eq. 8 with C for H).
 template <typename R>
 __device__ __forceinline__ R mix(R c, R a, R b) {
-  if (one_bits(c)) return a;
-  if (zero_bits(c)) return b;
   return c * a + (R(1) - c) * b;
 }
 
 // (sigma/dx) kappa_f (C_b - C_a) for the face between cell a (low side) and
-// cell b (high side); NaN marks a cell without a valid curvature.  With no
-// valid curvature on either side kappa_f = 0 and the force is zero.
+// cell b (high side); NaN marks a cell without a valid curvature, and with
+// none on either side kappa_f = 0.  Branch-free for the float form: on the
+// wide FP32 pipe the arithmetic costs less than tests, and the formulas give
+// the pure-phase and zero values themselves.
 template <typename R>
 __device__ __forceinline__ R face_force(const Fluids<R>& f, R ka, R kb, R ca, R cb) {
-  const bool va = !nan_bits(ka), vb = !nan_bits(kb);
-  if (!va && !vb) return R(0);
-  const R kf = va && vb ? (ka + kb) * R(0.5) : va ? ka : kb;
-  return f.sh * kf * (cb - ca);
-}
-
-// The same expressions without the integer shortcuts, for the float form: on
-// the wide FP32 pipe the arithmetic is cheaper than the tests, and it gives
-// the same values (c = 1 or 0 selects a or b; no valid curvature gives 0).
-template <typename R>
-__device__ __forceinline__ R mix_plain(R c, R a, R b) {
-  return c * a + (R(1) - c) * b;
-}
-template <typename R>
-__device__ __forceinline__ R face_plain(const Fluids<R>& f, R ka, R kb, R ca, R cb) {
   const bool va = !nan_bits(ka), vb = !nan_bits(kb);
   const R kf = va ? (vb ? (ka + kb) * R(0.5) : ka) : (vb ? kb : R(0));
   return f.sh * kf * (cb - ca);
@@ -141,25 +125,25 @@ __global__ void __launch_bounds__(kCT) k_coupling(const R* __restrict__ C, const
       const long long o = (long long)j * d.nx + i0;
       if (j < jc) {
         if (c1 && pairs) {
-          if (rho) *reinterpret_cast<R2*>(rho + o) = R2{mix_plain(ca[q], f.r1, f.r2), mix_plain(cc[q], f.r1, f.r2)};
-          if (mu) *reinterpret_cast<R2*>(mu + o) = R2{mix_plain(ca[q], f.m1, f.m2), mix_plain(cc[q], f.m1, f.m2)};
+          if (rho) *reinterpret_cast<R2*>(rho + o) = R2{mix(ca[q], f.r1, f.r2), mix(cc[q], f.r1, f.r2)};
+          if (mu) *reinterpret_cast<R2*>(mu + o) = R2{mix(ca[q], f.m1, f.m2), mix(cc[q], f.m1, f.m2)};
         } else {
-          if (c0 && rho) rho[o] = mix_plain(ca[q], f.r1, f.r2);
-          if (c0 && mu) mu[o] = mix_plain(ca[q], f.m1, f.m2);
-          if (c1 && rho) rho[o + 1] = mix_plain(cc[q], f.r1, f.r2);
-          if (c1 && mu) mu[o + 1] = mix_plain(cc[q], f.m1, f.m2);
+          if (c0 && rho) rho[o] = mix(ca[q], f.r1, f.r2);
+          if (c0 && mu) mu[o] = mix(ca[q], f.m1, f.m2);
+          if (c1 && rho) rho[o + 1] = mix(cc[q], f.r1, f.r2);
+          if (c1 && mu) mu[o + 1] = mix(cc[q], f.m1, f.m2);
         }
         if (fx) {
           R* px = fx + (long long)j * wx + i0;
           if (i0 <= d.nx)
-            px[0] = (i0 == 0 || i0 == d.nx) ? R(0) : face_plain(f, kl[q], ka[q], cl[q], ca[q]);
-          if (i0 + 1 <= d.nx) px[1] = (i0 + 1 == d.nx) ? R(0) : face_plain(f, ka[q], kc[q], ca[q], cc[q]);
+            px[0] = (i0 == 0 || i0 == d.nx) ? R(0) : face_force(f, kl[q], ka[q], cl[q], ca[q]);
+          if (i0 + 1 <= d.nx) px[1] = (i0 + 1 == d.nx) ? R(0) : face_force(f, ka[q], kc[q], ca[q], cc[q]);
         }
       }
       if (fy && j < j1) {
         const bool wall = j == 0 || j == d.ny;
-        const R y0 = wall ? R(0) : face_plain(f, kb0, ka[q], cb0, ca[q]);
-        const R y1 = wall ? R(0) : face_plain(f, kb1, kc[q], cb1, cc[q]);
+        const R y0 = wall ? R(0) : face_force(f, kb0, ka[q], cb0, ca[q]);
+        const R y1 = wall ? R(0) : face_force(f, kb1, kc[q], cb1, cc[q]);
         if (c1 && pairs) {
           *reinterpret_cast<R2*>(fy + o) = R2{y0, y1};
         } else {
