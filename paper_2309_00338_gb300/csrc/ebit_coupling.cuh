@@ -24,21 +24,6 @@ struct Fluids {
   R r1, r2, m1, m2, sh;  // sh = sigma / dx, formed once in R
 };
 
-// Tests on the integer pipe (FP64 compares run on the narrow FP64 pipe,
-// which the double form keeps for the arithmetic that needs it).
-__device__ __forceinline__ bool nan_bits(float x) { return (__float_as_uint(x) & 0x7fffffffu) > 0x7f800000u; }
-__device__ __forceinline__ bool nan_bits(double x) {
-  return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
-}
-__device__ __forceinline__ bool one_bits(float x) { return __float_as_uint(x) == 0x3f800000u; }
-__device__ __forceinline__ bool one_bits(double x) {
-  return (unsigned long long)__double_as_longlong(x) == 0x3ff0000000000000ull;
-}
-__device__ __forceinline__ bool zero_bits(float x) { return (__float_as_uint(x) << 1) == 0u; }
-__device__ __forceinline__ bool zero_bits(double x) {
-  return ((unsigned long long)__double_as_longlong(x) << 1) == 0ull;
-}
-
 // rho or mu of a cell: c a + (1 - c) b (Eq. 8 with C for H).
 template <typename R>
 __device__ __forceinline__ R mix(R c, R a, R b) {

@@ -351,6 +351,21 @@ __device__ __forceinline__ bool d_in01(double x) {
 }
 __device__ __forceinline__ bool d_below_sep(double s) { return dbits(s) < dbits(kMinSep2); }
 
+// Value tests on the integer pipe for either precision (a double compare
+// would take a slot of the narrow FP64 pipe): NaN, exactly 1, +-0.
+__device__ __forceinline__ bool nan_bits(float x) { return (__float_as_uint(x) & 0x7fffffffu) > 0x7f800000u; }
+__device__ __forceinline__ bool nan_bits(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ bool one_bits(float x) { return __float_as_uint(x) == 0x3f800000u; }
+__device__ __forceinline__ bool one_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) == 0x3ff0000000000000ull;
+}
+__device__ __forceinline__ bool zero_bits(float x) { return (__float_as_uint(x) << 1) == 0u; }
+__device__ __forceinline__ bool zero_bits(double x) {
+  return ((unsigned long long)__double_as_longlong(x) << 1) == 0ull;
+}
+
 // Exact conversions to double by integer operations: a float (any finite
 // value) and a small integer.
 __device__ __forceinline__ double f2d(float f) {

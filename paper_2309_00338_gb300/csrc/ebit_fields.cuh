@@ -249,7 +249,7 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
         h[m + 1] = a;
         const R lo = ycol ? cs[(ly - 3) * kFRX + lx + m] : cs[(ly + m) * kFRX + lx - 3];
         const R hi = ycol ? cs[(ly + 3) * kFRX + lx + m] : cs[(ly + m) * kFRX + lx + 3];
-        orient[m + 1] = (lo == R(1) && hi == R(0)) ? 1 : (lo == R(0) && hi == R(1)) ? -1 : 0;
+        orient[m + 1] = (one_bits(lo) && zero_bits(hi)) ? 1 : (zero_bits(lo) && one_bits(hi)) ? -1 : 0;
       }
       valid = orient[0] != 0 && orient[0] == orient[1] && orient[1] == orient[2];
     }

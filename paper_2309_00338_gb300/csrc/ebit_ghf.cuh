@@ -80,7 +80,7 @@ struct Cross {
     for (int t = 0; t < 7; ++t) acc = acc + (ycol ? v[m + 1][t] : h[m + 1][t]);
     *hsum = acc;
     const R lo = ycol ? v[m + 1][0] : h[m + 1][0], hi = ycol ? v[m + 1][6] : h[m + 1][6];
-    return (lo == R(1) && hi == R(0)) ? 1 : (lo == R(0) && hi == R(1)) ? -1 : 0;
+    return (one_bits(lo) && zero_bits(hi)) ? 1 : (zero_bits(lo) && one_bits(hi)) ? -1 : 0;
   }
 };
 
