@@ -141,7 +141,7 @@ struct ParabolaFit {
 };
 
 template <typename R>
-__global__ void __launch_bounds__(kGhfThreads)
+__global__ void __launch_bounds__(kGhfThreads, 6)
     k_ghf_fit(GhfView<R> S, R dx, const int* __restrict__ list, const unsigned* __restrict__ count,
               R* __restrict__ kappa, unsigned long long* __restrict__ ctr) {
   __shared__ unsigned s_cnt[3];
