@@ -122,7 +122,7 @@ ebit_status launch_fields(ebit_ctx* c) {
   }
   {
     Timed t(c, EBIT_K_AREA);
-    ebit::k_area<<<1, 256, 0, c->stream>>>(c->partial, (long long)fgrid.x * fgrid.y,
+    ebit::k_area<<<1, ebit::kAreaThreads, 0, c->stream>>>(c->partial, (long long)fgrid.x * fgrid.y,
                                            c->grid.dx * c->grid.dx, c->area);
   }
   if (ghf) {

@@ -145,14 +145,17 @@ __device__ __forceinline__ int kbit(const uint32_t* K, const Dims& d, int x, int
   return (__ldg(&K[(long long)y * d.kw + (x >> 5)]) >> (x & 31)) & 1;
 }
 
-// Sum of the per-block partials in a fixed order (one block).
-__global__ void k_area(const double* __restrict__ partial, long long n, double scale, double* area) {
-  __shared__ double red[256];
+// Sum of the per-block partials in a fixed order (one block of kAreaThreads;
+// a thread adds every kAreaThreads-th partial, then a tree over the threads).
+constexpr int kAreaThreads = 1024;
+__global__ void __launch_bounds__(kAreaThreads)
+k_area(const double* __restrict__ partial, long long n, double scale, double* area) {
+  __shared__ double red[kAreaThreads];
   double acc = 0.0;
-  for (long long b = threadIdx.x; b < n; b += 256) acc = acc + partial[b];
+  for (long long b = threadIdx.x; b < n; b += kAreaThreads) acc = acc + partial[b];
   red[threadIdx.x] = acc;
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
+  for (int s = kAreaThreads / 2; s > 0; s >>= 1) {
     if ((int)threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
     __syncthreads();
   }

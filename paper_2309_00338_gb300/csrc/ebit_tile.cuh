@@ -42,9 +42,9 @@ constexpr int kNVE = (kTI + 1) * kTJ;  // unaligned edges k in [i0, i0+64], rows
 constexpr int kCandCap = 256;          // candidates per tile; an edge beyond it is done in place
 constexpr uint16_t kKindV = 0x8000;    // marker reference: region index | kKindV if unaligned
 
-// Block shape: 6 warps per tile; tiles resident per SM as shared memory and
-// registers allow (4 in the FP32 form, 3 in the FP64 form).
-template <typename R> __host__ __device__ constexpr int tile_threads() { return 192; }
+// Block shape: 7 warps per tile; tiles resident per SM as shared memory
+// allows (4 in the FP32 form, 3 in the FP64 form).
+template <typename R> __host__ __device__ constexpr int tile_threads() { return 224; }
 template <typename R> __host__ __device__ constexpr int tile_min_blocks();
 template <> __host__ __device__ constexpr int tile_min_blocks<float>() { return 4; }
 template <> __host__ __device__ constexpr int tile_min_blocks<double>() { return 3; }
