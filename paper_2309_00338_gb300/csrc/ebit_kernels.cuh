@@ -147,7 +147,8 @@ __device__ __forceinline__ int kbit(const uint32_t* K, const Dims& d, int x, int
 
 // Sum of the per-block partials in a fixed order (one block of kAreaThreads;
 // a thread adds every kAreaThreads-th partial, then a tree over the threads).
-constexpr int kAreaThreads = 1024;
+// 256 threads: 1024 took 12.6 us at 4096^2 against 10.5.
+constexpr int kAreaThreads = 256;
 __global__ void __launch_bounds__(kAreaThreads)
 k_area(const double* __restrict__ partial, long long n, double scale, double* area) {
   __shared__ double red[kAreaThreads];
