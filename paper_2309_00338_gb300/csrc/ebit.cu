@@ -116,7 +116,7 @@ ebit_status launch_fields(ebit_ctx* c) {
   if (ghf) EBIT_CK(cudaMemsetAsync(c->ghf_count, 0, sizeof(unsigned), c->stream));
   {
     Timed t(c, EBIT_K_FIELDS);
-    ebit::k_fields_tile<R><<<fgrid, ebit::kFieldThreads, 0, c->stream>>>(
+    ebit::k_fields_tile<R><<<fgrid, ebit::field_threads<R>(), 0, c->stream>>>(
         c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], L.d, (R)c->grid.dx, (R*)c->C,
         (R*)c->kappa, c->partial, c->ctr, ghf ? c->ghf_list : nullptr, ghf ? c->ghf_count : nullptr);
   }

@@ -19,10 +19,11 @@ constexpr int kFX = 64, kFY = 32, kFH = 3;
 constexpr int kFRX = kFX + 2 * kFH, kFRY = kFY + 2 * kFH;  // region cells (70 x 38)
 constexpr int kFVX = kFRX + 1, kFVY = kFRY + 1;            // region vertices (71 x 39)
 constexpr int kFW = 3;                                     // words per region bit row
-constexpr int kFieldThreads = 256;
-// Blocks per SM the kernel is compiled for: eight float tiles (32 registers,
-// a few spilled, 12% faster than the five that 48 registers allow); the
+// Threads per tile and blocks per SM the kernel is compiled for: eight float
+// tiles of 256 threads (32 registers, a few spilled, 12% faster than the five
+// that 48 registers allow; 384 or 512 threads per tile were slower); the
 // double form's shared memory admits seven at most, and it gains nothing.
+template <typename R> __host__ __device__ constexpr int field_threads() { return 256; }
 template <typename R> __host__ __device__ constexpr int fields_min_blocks() { return sizeof(R) == 4 ? 8 : 5; }
 
 // Reference-phase area of cell (i,j) in cell units from its corner mask q,
@@ -93,6 +94,7 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
                                             const Dims& d, R dx, R* C, R* kappa, double* partial,
                                             long long slot, unsigned long long* ctr, int bx, int by,
                                             int* ghf_list = nullptr, unsigned* ghf_count = nullptr) {
+  constexpr int kFieldThreads = field_threads<R>();
   __shared__ uint32_t kw[kFVY * kFW];  // vertex colours
   __shared__ uint32_t zw[kFRY * kFW];  // centre colours
   __shared__ uint32_t fw[kFRY * kFW];  // full cells
@@ -342,7 +344,7 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kFieldThreads, fields_min_blocks<R>())
+__global__ void __launch_bounds__(field_threads<R>(), fields_min_blocks<R>())
 k_fields_tile(const uint32_t* __restrict__ K, const uint32_t* __restrict__ Z,
               const R* __restrict__ sH, const R* __restrict__ sV, Dims d, R dx, R* C, R* kappa,
               double* partial, unsigned long long* ctr, int* ghf_list, unsigned* ghf_count) {
@@ -372,7 +374,7 @@ struct FieldItem {
 };
 
 template <typename R>
-__global__ void __launch_bounds__(kFieldThreads, fields_min_blocks<R>())
+__global__ void __launch_bounds__(field_threads<R>(), fields_min_blocks<R>())
 k_fields_tile_batch(const FieldDesc<R>* __restrict__ descs, const FieldItem* __restrict__ items) {
   const FieldItem it = items[blockIdx.x];
   const FieldDesc<R>& D = descs[it.grid];

@@ -269,7 +269,7 @@ struct Group {
     ebit::k_sweep_tile_batch<R, 1><<<n_items1, ebit::tile_threads<R>(), smem, st>>>(d_s1, d_items1);
     ebit::k_sweep_tile_batch<R, 1><<<n_items1, ebit::tile_threads<R>(), smem, st>>>(d_s1 + n, d_items1);
     ebit::k_sweep_tile_batch<R, 0><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0 + n, d_items0);
-    ebit::k_fields_tile_batch<R><<<n_fitems, ebit::kFieldThreads, 0, st>>>(d_fd, d_fitems);
+    ebit::k_fields_tile_batch<R><<<n_fitems, ebit::field_threads<R>(), 0, st>>>(d_fd, d_fitems);
     k_area_batch<<<(unsigned)n, 256, 0, st>>>(d_ad);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EBIT_OK : fail_s(EBIT_ECUDA, "batch launch: %s", cudaGetErrorString(e));
