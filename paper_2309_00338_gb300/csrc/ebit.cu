@@ -448,6 +448,7 @@ ebit_status ebit_create(ebit_ctx** out, const ebit_grid* grid, void* stream) {
 }
 
 ebit_status ebit_init(ebit_ctx** out, const ebit_grid* grid, const ebit_scene* scene, void* stream) {
+  const Range range("ebit_init");
   if (!scene || scene->ncircles < 0 || (scene->ncircles > 0 && !scene->circles) ||
       (scene->curve && (scene->curve->nmodes < 0 || (scene->curve->nmodes > 0 &&
                                                      (!scene->curve->amp || !scene->curve->phase)))) ||
@@ -481,6 +482,7 @@ ebit_status ebit_get_state(ebit_ctx* c, ebit_state_host* st) {
 }
 
 ebit_status ebit_step(ebit_ctx* c, const void* u, const void* v, double dt) {
+  const Range range("ebit_step");
   if (!c || !u || !v) return fail(EBIT_EINVAL, "NULL argument");
   if (!(dt == dt)) return fail(EBIT_EINVAL, "dt is NaN");
   ebit_status s = reset_counters(c);
@@ -540,6 +542,7 @@ ebit_status ebit_curvature(ebit_ctx* c, void* kappa_dev, int32_t* n_invalid_host
 
 ebit_status ebit_coupling(ebit_ctx* c, const ebit_fluids* fl, void* rho, void* mu, void* fx,
                           void* fy) {
+  const Range range("ebit_coupling");
   if (!c || !fl) return fail(EBIT_EINVAL, "NULL argument");
   return c->grid.prec == EBIT_FP32 ? launch_coupling<float>(c, fl, rho, mu, fx, fy)
                                    : launch_coupling<double>(c, fl, rho, mu, fx, fy);

@@ -2,6 +2,7 @@
 // units of libebit.so (not part of the exported interface).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -11,6 +12,15 @@
 #include "ebit_device.cuh"
 
 namespace ebit_detail {
+
+// NVTX range over a host call (visible in profilers that record NVTX; a
+// no-op otherwise).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 constexpr int kMaxSide = 32768;
 constexpr int kBlockX = 32, kBlockY = 8;  // thread blocks of the per-vertex kernels

@@ -402,6 +402,7 @@ void ebit_server::retire(size_t idx) {
 }
 
 ebit_status ebit_server::step() {
+  const ebit_detail::Range range("ebit_server_step");
   std::vector<Instance*> all;
   for (auto& p : active) all.push_back(p.get());
   ebit_status s;
