@@ -505,3 +505,42 @@ def test_area_async_matches_fraction():
         assert ebit.lib().ebit_area_async(ctx, None) == ebit.EBIT_EINVAL
     finally:
         ebit.ebit_destroy(ctx)
+
+
+def test_max_size_grid_fp32():
+    """The largest grid the library accepts (32768^2 cells, FP32 form, ~30 GB
+    of state; every offset above 2^32 bytes): a disk of radius 0.3
+    initialises to its area, keeps it over two steps of solid rotation
+    (properties that hold at any size; the oracle cannot run this grid), and
+    its height-function curvature is 1/r."""
+    if torch.cuda.get_device_properties(0).total_memory < (80 << 30):
+        pytest.skip("needs 80 GB of device memory")
+    n = 32768
+    dx = 1.0 / n
+    r = 0.3
+    ctx = ebit.ebit_init(n, n, dx, {"circles": [(0.5 + 0.37 * dx, 0.5 - 0.21 * dx, r)]}, ebit.EBIT_FP32)
+    try:
+        a0 = ebit.ebit_fraction(ctx)
+        assert abs(a0 - math.pi * r * r) < 1e-8
+        om = 2.0 * math.pi
+        xs = torch.arange(n + 1, device="cuda", dtype=torch.float64) * dx - 0.5
+        u = (-om * xs).to(torch.float32)[:, None].expand(n + 1, n + 1).contiguous()  # -omega (y - 0.5)
+        v = (om * xs).to(torch.float32)[None, :].expand(n + 1, n + 1).contiguous()  # omega (x - 0.5)
+        dt = 0.5 * dx / (0.5 * om)
+        for _ in range(2):
+            ebit.ebit_step(ctx, u, v, dt)
+        del u, v
+        a1 = ebit.ebit_fraction(ctx)
+        assert abs(a1 - a0) / a0 < 1e-8
+        c = ebit.ebit_diagnostics(ctx)["counters"]
+        assert c[ebit.D_CFL] == 0 and c[ebit.D_INVARIANT] == 0
+        assert c[ebit.D_NH] > 2 * r / dx and c[ebit.D_NV] > 2 * r / dx
+        kap = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        ebit.ebit_curvature(ctx, kap)
+        valid = kap[~torch.isnan(kap)]
+        assert valid.numel() > 4 * r / dx
+        assert abs(float(valid.median()) * r - 1.0) < 2e-2
+        del kap, valid
+    finally:
+        ebit.ebit_destroy(ctx)
+        torch.cuda.empty_cache()
