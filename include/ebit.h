@@ -53,8 +53,9 @@ typedef enum { EBIT_FP64 = 0, EBIT_FP32 = 1 } ebit_precision;
  * the stencil along the other direction, else a least-squares parabola
  * through the valid heights of both directions, else one through the markers
  * on the edges of the 3x3 block of cells (fits in the context precision, in
- * cell units relative to the cell).  It costs one more dense pass over kappa and the fits, and a list
- * of nx*ny int32 in the context.  Contexts only (servers reject it). */
+ * cell units relative to the cell).  The fields kernel lists those cells (a
+ * list of nx*ny int32 in the context) and one more launch fits them.  Also
+ * accepted in server requests. */
 #define EBIT_FIT_LINE 1u
 #define EBIT_CURV_GHF 2u
 
@@ -261,7 +262,7 @@ typedef enum {
 typedef struct {
   int32_t n;                   /* grid side, n x n cells, dx = 1/n */
   int32_t prec;                /* ebit_precision */
-  uint32_t flags;              /* EBIT_FIT_LINE or 0 */
+  uint32_t flags;              /* EBIT_FIT_LINE and/or EBIT_CURV_GHF, or 0 */
   const ebit_circle* circles;  /* host array, copied by ebit_submit */
   int32_t ncircles;
   int32_t field;               /* ebit_field_kind */

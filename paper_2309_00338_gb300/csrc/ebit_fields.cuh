@@ -367,6 +367,8 @@ struct FieldDesc {
   double* partial;
   unsigned long long* ctr;
   int tiles_x;
+  int* ghf_list;         // EBIT_CURV_GHF grids: their list of cells without a 7x3 stencil
+  unsigned* ghf_count;   // (null otherwise)
 };
 
 struct FieldItem {
@@ -379,7 +381,7 @@ k_fields_tile_batch(const FieldDesc<R>* __restrict__ descs, const FieldItem* __r
   const FieldItem it = items[blockIdx.x];
   const FieldDesc<R>& D = descs[it.grid];
   fields_tile<R>(D.K, D.Z, D.sH, D.sV, D.d, D.dx, D.C, D.kappa, D.partial,
-                 (long long)it.ty * D.tiles_x + it.tx, D.ctr, it.tx, it.ty);
+                 (long long)it.ty * D.tiles_x + it.tx, D.ctr, it.tx, it.ty, D.ghf_list, D.ghf_count);
 }
 
 }  // namespace ebit

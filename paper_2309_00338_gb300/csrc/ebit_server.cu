@@ -33,6 +33,7 @@
 #include "ebit.h"
 #include "ebit_ctx.hpp"
 #include "ebit_fields.cuh"
+#include "ebit_ghf.cuh"
 #include "ebit_tile.cuh"
 
 namespace {
@@ -83,6 +84,14 @@ struct AreaDesc {
   double scale;
   double* area;
 };
+
+// Zeroes the generalised-HF list counts of the grids that have one, before
+// the batched fields launch lists into them.
+template <typename R>
+__global__ void k_ghf_reset(const ebit::FieldDesc<R>* __restrict__ descs, int n) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n && descs[g].ghf_count) *descs[g].ghf_count = 0u;
+}
 
 __global__ void k_area_batch(const AreaDesc* __restrict__ descs) {
   const AreaDesc D = descs[blockIdx.x];
@@ -145,6 +154,7 @@ struct Group {
   ebit::FieldItem* d_fitems = nullptr;
   AreaDesc* d_ad = nullptr;
   int n_items0 = 0, n_items1 = 0, n_fitems = 0;
+  std::vector<int> ghf;  // grids with EBIT_CURV_GHF (fits after the fields launch)
 
   void release() {
     if (h_s0) cudaFreeHost(h_s0);
@@ -183,8 +193,11 @@ struct Group {
       for (int ty = 0; ty < fy; ++ty)
         for (int tx = 0; tx < fx; ++tx) gf[g].push_back({(int)g, tx, ty});
       const int b = c->cur;
+      const bool gh = (c->grid.flags & EBIT_CURV_GHF) != 0;
       fd[g] = ebit::FieldDesc<R>{c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], d,
-                                 (R)c->grid.dx, (R*)c->C, (R*)c->kappa, c->partial, c->ctr, fx};
+                                 (R)c->grid.dx, (R*)c->C, (R*)c->kappa, c->partial, c->ctr, fx,
+                                 gh ? c->ghf_list : nullptr, gh ? c->ghf_count : nullptr};
+      if (gh) ghf.push_back((int)g);
       ad[g] = AreaDesc{c->partial, (long long)fx * fy, c->grid.dx * c->grid.dx, c->area};
     }
     const std::vector<ebit::WorkItem> it0 = order(g0, schedule), it1 = order(g1, schedule);
@@ -269,8 +282,18 @@ struct Group {
     ebit::k_sweep_tile_batch<R, 1><<<n_items1, ebit::tile_threads<R>(), smem, st>>>(d_s1, d_items1);
     ebit::k_sweep_tile_batch<R, 1><<<n_items1, ebit::tile_threads<R>(), smem, st>>>(d_s1 + n, d_items1);
     ebit::k_sweep_tile_batch<R, 0><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0 + n, d_items0);
+    if (!ghf.empty()) k_ghf_reset<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d_fd, (int)n);
     ebit::k_fields_tile_batch<R><<<n_fitems, ebit::field_threads<R>(), 0, st>>>(d_fd, d_fitems);
     k_area_batch<<<(unsigned)n, 256, 0, st>>>(d_ad);
+    for (const int g : ghf) {  // the state is back in the buffer the plan was built on
+      const ebit_ctx* c = inst[g]->ctx;
+      const int b = c->cur;
+      const ebit::GhfView<R> S{c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], (const R*)c->C, c->L.d};
+      const long long cells = (long long)c->L.d.nx * c->L.d.ny;
+      const int blocks = (int)std::min<long long>((cells + ebit::kGhfThreads - 1) / ebit::kGhfThreads, 152LL * 8);
+      ebit::k_ghf_fit<R><<<blocks, ebit::kGhfThreads, 0, st>>>(S, (R)c->grid.dx, c->ghf_list, c->ghf_count,
+                                                              (R*)c->kappa, c->ctr);
+    }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EBIT_OK : fail_s(EBIT_ECUDA, "batch launch: %s", cudaGetErrorString(e));
   }
@@ -626,7 +649,7 @@ ebit_status ebit_submit(ebit_server* s, const ebit_request* r, uint64_t* ticket)
       r->steps < 0 || !(r->cfl > 0.0 && r->cfl <= 1.0) || r->ncircles < 0 ||
       (r->ncircles > 0 && !r->circles) ||
       (r->field != EBIT_FIELD_VORTEX && r->field != EBIT_FIELD_CELLULAR && r->field != EBIT_FIELD_ROTATION) ||
-      (r->field == EBIT_FIELD_VORTEX && !(r->period > 0.0)) || (r->flags & ~EBIT_FIT_LINE))
+      (r->field == EBIT_FIELD_VORTEX && !(r->period > 0.0)) || (r->flags & ~(EBIT_FIT_LINE | EBIT_CURV_GHF)))
     return fail_s(EBIT_EINVAL, "invalid request");
   auto in = std::make_unique<Instance>();
   in->req = *r;

@@ -144,3 +144,53 @@ def test_vortex_request_returns_to_its_shape():
     finally:
         ebit.ebit_server_destroy(s)
     assert res["status"] == 0 and res["e_area"] < 5e-2
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_served_generalised_hf_matches_oracle(prec):
+    """A request with EBIT_CURV_GHF, served beside plain requests: its
+    fractions equal the oracle's and its fallback counters (summed over the
+    steps) equal the oracle's; the plain requests are unaffected."""
+    n, steps, cfl = 96, 12, 0.5
+    omega, centre, drift = 2 * math.pi, (0.5, 0.5), (0.2, -0.1)
+    rng = W.Rng(77)
+    dx = 1.0 / n
+    circles = W.place_circles(rng, 60, 2.5 * dx, 5 * dx, 2 * dx, lambda x, y, r: True)
+    C = np.zeros(n * n, np.float64 if prec == 0 else np.float32)
+    Cp = np.zeros(n * n, np.float64 if prec == 0 else np.float32)
+    s = ebit.ebit_server_create(4 << 30)
+    try:
+        r, keep = ebit.make_request(n, circles, ebit.EBIT_FIELD_ROTATION, steps, cfl, prec, omega=omega,
+                                    centre=centre, drift=drift, C_out=C, flags=ebit.EBIT_CURV_GHF)
+        rp, keep2 = ebit.make_request(n, circles, ebit.EBIT_FIELD_ROTATION, steps, cfl, prec, omega=omega,
+                                      centre=centre, drift=drift, C_out=Cp)
+        tg, tp = ebit.ebit_submit(s, r), ebit.ebit_submit(s, rp)
+        res = ebit.wait_all(s, [tg, tp])
+    finally:
+        ebit.ebit_server_destroy(s)
+    rg, rpl = res[tg], res[tp]
+    assert rg["status"] == 0 and rpl["status"] == 0
+    umax = 0.0
+    for a in (0, 1):
+        for b in (0, 1):
+            umax = max(umax, abs(-omega * (b - centre[1]) + drift[0]), abs(omega * (a - centre[0]) + drift[1]))
+    dt = cfl * dx / umax
+    f = W.rotation_field(n, n, dx, omega, centre, drift)
+    S = oracle.init(n, n, dx, W.circle_scene(circles), prec)
+    tot = np.zeros(oracle.NCOUNTERS, np.int64)
+    for k in range(steps):
+        out = oracle.step(S, f.u, f.v, dt, ghf=True)
+        tot += out["counters"]
+    got = C.reshape(n, n).astype(np.float64)
+    if prec == 1:
+        assert np.array_equal(got, out["C"])
+    else:
+        assert np.max(np.abs(got - out["C"])) <= 1e-12
+    assert np.array_equal(np.asarray(rg["counters"])[[ebit.D_HF_INVALID, ebit.D_HF_OTHER, ebit.D_HF_MIXED,
+                                                      ebit.D_HF_MARKERS]],
+                          tot[[ebit.D_HF_INVALID, ebit.D_HF_OTHER, ebit.D_HF_MIXED, ebit.D_HF_MARKERS]])
+    assert tot[ebit.D_HF_MIXED] + tot[ebit.D_HF_MARKERS] > 0
+    # the plain request: same fractions, no fallbacks counted
+    assert np.array_equal(Cp, C)
+    assert np.asarray(rpl["counters"])[ebit.D_HF_OTHER:ebit.D_HF_MARKERS + 1].sum() == 0
+    assert rpl["counters"][ebit.D_HF_INVALID] == rg["counters"][ebit.D_HF_INVALID]
