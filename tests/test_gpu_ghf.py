@@ -124,3 +124,21 @@ def test_ghf_full_size_cellular_curve_fp32():
         assert_same_kappa(kappa_of(ctx, S), r["kappa"], 1, wl.dx)
     finally:
         ebit.ebit_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [oracle.FP64, oracle.FP32], ids=["fp64", "fp32"])
+def test_ghf_with_straight_line_fit(prec):
+    """The two flags together (EBIT-SL markers, generalised curvature)."""
+    S, f, dt = packed_disks(prec, n=96, seed=11)
+    ctx = ebit.ebit_create(S.nx, S.ny, S.dx, S.prec, flags=ebit.EBIT_CURV_GHF | ebit.EBIT_FIT_LINE)
+    try:
+        ebit.ebit_load_state(ctx, S.K, S.Z, S.sH, S.sV, S.step_index)
+        for _ in range(3):
+            ebit.ebit_step(ctx, dev(f.u, prec), dev(f.v, prec), dt)
+            r = oracle.step(S, f.u, f.v, dt, line_only=True, ghf=True)
+        d = ebit.ebit_diagnostics(ctx)
+        assert np.array_equal(d["counters"], r["counters"])
+        assert d["counters"][ebit.D_FIT_LINE] > 0 and d["counters"][ebit.D_FIT_TWO] == 0
+        assert_same_kappa(kappa_of(ctx, S), r["kappa"], prec, S.dx)
+    finally:
+        ebit.ebit_destroy(ctx)
