@@ -111,11 +111,13 @@ def test_coupling_null_outputs_untouched():
         ebit.ebit_destroy(ctx)
 
 
-def test_coupling_full_size_cellular_curve_fp32():
-    """4096^2 Fourier curve with 20000 circles, FP32: the launch shape the
-    benchmark times, every output compared."""
+@pytest.mark.parametrize("prec", [oracle.FP32, oracle.FP64], ids=["fp32", "fp64"])
+def test_coupling_full_size_cellular_curve(prec):
+    """4096^2 Fourier curve with 20000 circles: the launch shapes the
+    benchmark times (the column-pair float kernel, the queued double kernel),
+    every output compared."""
     wl = W.cellular_curve_workload()
-    S = oracle.init(wl.n, wl.n, wl.dx, wl.scene, oracle.FP32)
+    S = oracle.init(wl.n, wl.n, wl.dx, wl.scene, prec)
     ctx = gpu_from(S)
     try:
         g = gpu_coupling(ctx, S)

@@ -110,18 +110,19 @@ def test_ghf_off_leaves_standard_path_unchanged():
         ebit.ebit_destroy(b)
 
 
-def test_ghf_full_size_cellular_curve_fp32():
-    """4096^2 Fourier curve with 20000 circles, FP32, one step with the
-    fallbacks: every kappa and counter compared."""
+@pytest.mark.parametrize("prec", [oracle.FP32, oracle.FP64], ids=["fp32", "fp64"])
+def test_ghf_full_size_cellular_curve(prec):
+    """4096^2 Fourier curve with 20000 circles, one step with the fallbacks:
+    every kappa and counter compared."""
     wl = W.cellular_curve_workload()
-    S = oracle.init(wl.n, wl.n, wl.dx, wl.scene, oracle.FP32)
+    S = oracle.init(wl.n, wl.n, wl.dx, wl.scene, prec)
     ctx = gpu_ghf(S)
     try:
-        ebit.ebit_step(ctx, dev(wl.field.u, 1), dev(wl.field.v, 1), wl.dt)
+        ebit.ebit_step(ctx, dev(wl.field.u, prec), dev(wl.field.v, prec), wl.dt)
         r = oracle.step(S, wl.field.u, wl.field.v, wl.dt, ghf=True)
         d = ebit.ebit_diagnostics(ctx)
         assert np.array_equal(d["counters"], r["counters"])
-        assert_same_kappa(kappa_of(ctx, S), r["kappa"], 1, wl.dx)
+        assert_same_kappa(kappa_of(ctx, S), r["kappa"], prec, wl.dx)
     finally:
         ebit.ebit_destroy(ctx)
 
