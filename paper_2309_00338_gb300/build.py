@@ -29,17 +29,26 @@ def _inputs():
     return files
 
 
-def build_library(force: bool = False, verbose: bool = False) -> str:
-    """Compile the CUDA library (idempotent; rebuilds when a source changed)."""
+CHECK_LIB_PATH = os.path.join(OUT_DIR, "libebit_check.so")
+
+
+def build_library(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile the CUDA library (idempotent; rebuilds when a source changed).
+    checked=True builds the debug variant libebit_check.so, compiled with
+    EBIT_CHECK: the step kernels check every global index against its array
+    and record a miss instead of making the access (ebit_check_status)."""
     os.makedirs(OUT_DIR, exist_ok=True)
+    lib_path = CHECK_LIB_PATH if checked else LIB_PATH
     newest = max(os.path.getmtime(f) for f in _inputs())
-    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
-        return LIB_PATH
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= newest:
+        return lib_path
     pid = os.getpid()
+    tag = "chk." if checked else ""
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, f"{os.path.splitext(src)[0]}.{pid}.o")
-        cmd = [nvcc(), *ARCH, *FLAGS, "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(OUT_DIR, f"{os.path.splitext(src)[0]}.{tag}{pid}.o")
+        cmd = [nvcc(), *ARCH, *FLAGS, *(["-DEBIT_CHECK"] if checked else []), "-I", INCLUDE, "-I", CSRC,
+               "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         subprocess.run(cmd, check=True)
@@ -47,12 +56,12 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB_PATH + f".{pid}.tmp"
+    tmp = lib_path + f".{pid}.tmp"
     subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], check=True)
     for o in objs:
         os.unlink(o)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

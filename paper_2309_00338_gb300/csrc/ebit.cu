@@ -517,6 +517,18 @@ ebit_status ebit_fraction(ebit_ctx* c, void* C_dev, double* area_host) {
   return EBIT_OK;
 }
 
+ebit_status ebit_check_status(uint32_t* misses) {
+  if (!misses) return fail(EBIT_EINVAL, "NULL argument");
+#ifdef EBIT_CHECK
+  unsigned w = 0;
+  EBIT_CK(cudaMemcpyFromSymbol(&w, ebit::ebit_check_word, sizeof w));
+  *misses = w;
+#else
+  *misses = 0;
+#endif
+  return EBIT_OK;
+}
+
 ebit_status ebit_area_async(ebit_ctx* c, double* area_host) {
   if (!c || !area_host) return fail(EBIT_EINVAL, "NULL argument");
   EBIT_CK(cudaMemcpyAsync(area_host, c->area, sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -59,6 +59,12 @@ struct Dims {
   int nx, ny;     // cells
   int kw, zw;     // words per row of K and Z
   long long P;    // element pitch of sH, sV, C, kappa
+  // extents of the arrays, in elements
+  __host__ __device__ long long nK() const { return (long long)(ny + 1) * kw; }
+  __host__ __device__ long long nZ() const { return (long long)ny * zw; }
+  __host__ __device__ long long nH() const { return (long long)(ny + 1) * P; }
+  __host__ __device__ long long nV() const { return (long long)ny * P; }  // also C and kappa
+  __host__ __device__ long long nW() const { return (long long)(ny + 1) * (nx + 1); }
 };
 
 struct Mk {
@@ -350,6 +356,21 @@ __device__ __forceinline__ bool d_in01(double x) {
   return b <= 0x3ff0000000000000ull || b == 0x8000000000000000ull;
 }
 __device__ __forceinline__ bool d_below_sep(double s) { return dbits(s) < dbits(kMinSep2); }
+
+// Debug builds (EBIT_CHECK): the step kernels check each global index
+// against the extent of its array; a miss sets the check word (read by
+// ebit_check_status) and the access is skipped.  Release builds compile the
+// checks away.
+#ifdef EBIT_CHECK
+static __device__ unsigned ebit_check_word;
+__device__ __forceinline__ bool in_range(long long idx, long long n) {
+  if (idx >= 0 && idx < n) return true;
+  atomicOr(&ebit_check_word, 1u);
+  return false;
+}
+#else
+__device__ __forceinline__ bool in_range(long long, long long) { return true; }
+#endif
 
 // Value tests on the integer pipe for either precision (a double compare
 // would take a slot of the narrow FP64 pipe): NaN, exactly 1, +-0.
@@ -680,21 +701,26 @@ struct GView {
   __device__ __forceinline__ int tnx() const { return AX ? d.ny : d.nx; }
   __device__ __forceinline__ int tny() const { return AX ? d.nx : d.ny; }
   __device__ __forceinline__ int kreal(int x, int y) const {
-    return (__ldg(&K[(long long)y * d.kw + (x >> 5)]) >> (x & 31)) & 1;
+    const long long q = (long long)y * d.kw + (x >> 5);
+    return in_range(q, d.nK()) ? (__ldg(&K[q]) >> (x & 31)) & 1 : 0;
   }
   __device__ __forceinline__ int k(int i, int j) const { return AX ? kreal(j, i) : kreal(i, j); }
   __device__ __forceinline__ int z(int i, int j) const {
     const int x = AX ? j : i, y = AX ? i : j;
-    return (__ldg(&Z[(long long)y * d.zw + (x >> 5)]) >> (x & 31)) & 1;
+    const long long q = (long long)y * d.zw + (x >> 5);
+    return in_range(q, d.nZ()) ? (__ldg(&Z[q]) >> (x & 31)) & 1 : 0;
   }
   __device__ __forceinline__ R h(int i, int j) const {
-    return AX ? __ldg(&sV[(long long)i * d.P + j]) : __ldg(&sH[(long long)j * d.P + i]);
+    const long long q = AX ? (long long)i * d.P + j : (long long)j * d.P + i;
+    return in_range(q, AX ? d.nV() : d.nH()) ? __ldg(AX ? &sV[q] : &sH[q]) : R(0);
   }
   __device__ __forceinline__ R v(int i, int j) const {
-    return AX ? __ldg(&sH[(long long)i * d.P + j]) : __ldg(&sV[(long long)j * d.P + i]);
+    const long long q = AX ? (long long)i * d.P + j : (long long)j * d.P + i;
+    return in_range(q, AX ? d.nH() : d.nV()) ? __ldg(AX ? &sH[q] : &sV[q]) : R(0);
   }
   __device__ __forceinline__ R vel(int i, int j) const {
-    return AX ? __ldg(&w[(long long)i * (d.nx + 1) + j]) : __ldg(&w[(long long)j * (d.nx + 1) + i]);
+    const long long q = AX ? (long long)i * (d.nx + 1) + j : (long long)j * (d.nx + 1) + i;
+    return in_range(q, d.nW()) ? __ldg(&w[q]) : R(0);
   }
   __device__ AP<R> advect(Mk m, Flags& f) const {
     if (m.kind == 0)

@@ -35,10 +35,11 @@ __device__ double fraction_of(int q, int zc, const R* __restrict__ sH, const R* 
                               const Dims& d, int i, int j) {
   const int em = edge_mask(q);
   // exact conversions on the integer pipe
-  const double s0 = to_d<R>(__ldg(&sH[(long long)j * d.P + i]));
-  const double s1 = to_d<R>(__ldg(&sV[(long long)j * d.P + i + 1]));
-  const double s2 = to_d<R>(__ldg(&sH[(long long)(j + 1) * d.P + i]));
-  const double s3 = to_d<R>(__ldg(&sV[(long long)j * d.P + i]));
+  const long long q0 = (long long)j * d.P + i, q2 = q0 + d.P;  // sH of edges 0, 2; sV of 3, 1 at q0, q0 + 1
+  const double s0 = in_range(q0, d.nH()) ? to_d<R>(__ldg(&sH[q0])) : 0.0;
+  const double s1 = in_range(q0 + 1, d.nV()) ? to_d<R>(__ldg(&sV[q0 + 1])) : 0.0;
+  const double s2 = in_range(q2, d.nH()) ? to_d<R>(__ldg(&sH[q2])) : 0.0;
+  const double s3 = in_range(q0, d.nV()) ? to_d<R>(__ldg(&sV[q0])) : 0.0;
   const double w0 = 1.0 - s0, w1 = 1.0 - s1, w2 = 1.0 - s2, w3 = 1.0 - s3;
   // legs of the triangle cut off at corner c: (s3, s0) (w0, s1) (w1, w2) (s2, w3)
   auto tri = [&](int c) {
@@ -229,8 +230,11 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
     R out = R(NAN);
     int seg[2][2];
     const int ns = segments(q, edge_mask(q) == 15 ? fgetb(zw, lx, ly) : 0, seg);
-    const R px[4] = {__ldg(&sH[(long long)j * d.P + i]), R(1), __ldg(&sH[(long long)(j + 1) * d.P + i]), R(0)};
-    const R py[4] = {R(0), __ldg(&sV[(long long)j * d.P + i + 1]), R(1), __ldg(&sV[(long long)j * d.P + i])};
+    const long long q0 = (long long)j * d.P + i, q2 = q0 + d.P;
+    const R px[4] = {in_range(q0, d.nH()) ? __ldg(&sH[q0]) : R(0), R(1),
+                     in_range(q2, d.nH()) ? __ldg(&sH[q2]) : R(0), R(0)};
+    const R py[4] = {R(0), in_range(q0 + 1, d.nV()) ? __ldg(&sV[q0 + 1]) : R(0), R(1),
+                     in_range(q0, d.nV()) ? __ldg(&sV[q0]) : R(0)};
     R ax = R(0), ay = R(0);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -272,7 +276,7 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
         atomicAdd(&s_nghf, 1u);
       }
     }
-    kappa[(long long)j * d.P + i] = out;
+    if (in_range((long long)j * d.P + i, d.nV())) kappa[(long long)j * d.P + i] = out;
   }
   // dense outputs: C everywhere, kappa = NaN away from the interface (the
   // interface cells' kappa is written above)
@@ -285,6 +289,7 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
     const R* c = &cs[ly * kFRX + lx];
     const uint32_t ib = (iw[ly * kFW + (lx >> 5)] >> (lx & 31)) |
                         ((lx & 31) > 28 ? iw[ly * kFW + (lx >> 5) + 1] << (32 - (lx & 31)) : 0u);
+    if (!in_range((long long)j * d.P + min(i + 3, d.nx - 1), d.nV())) continue;  // this group's last cell
     R* Cp = C + (long long)j * d.P + i;
     R* Kp = kappa + (long long)j * d.P + i;
     if (vec && i + 3 < d.nx) {

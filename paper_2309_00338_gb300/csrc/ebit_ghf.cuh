@@ -28,8 +28,9 @@ static_assert(D_NUSED <= D_HF_OTHER && D_HF_MARKERS < kCounters, "counter slots"
 
 constexpr int kGhfThreads = 128;  // k_ghf_fit block
 
-__device__ __forceinline__ int kbit(const uint32_t* __restrict__ K, int kw, int i, int j) {
-  return (__ldg(&K[(long long)j * kw + (i >> 5)]) >> (i & 31)) & 1;
+__device__ __forceinline__ int kbit(const uint32_t* __restrict__ K, int kw, int i, int j, long long n) {
+  const long long q = (long long)j * kw + (i >> 5);
+  return in_range(q, n) ? (__ldg(&K[q]) >> (i & 31)) & 1 : 0;
 }
 
 // Read-only view of the state and fractions of one context.
@@ -41,11 +42,20 @@ struct GhfView {
   const R* sV;
   const R* C;
   Dims d;
-  __device__ int k(int i, int j) const { return kbit(K, d.kw, i, j); }
-  __device__ int z(int i, int j) const { return kbit(Z, d.zw, i, j); }
-  __device__ R c(int i, int j) const { return __ldg(&C[(long long)j * d.P + i]); }
-  __device__ R h(int i, int j) const { return __ldg(&sH[(long long)j * d.P + i]); }
-  __device__ R v(int i, int j) const { return __ldg(&sV[(long long)j * d.P + i]); }
+  __device__ int k(int i, int j) const { return kbit(K, d.kw, i, j, d.nK()); }
+  __device__ int z(int i, int j) const { return kbit(Z, d.zw, i, j, d.nZ()); }
+  __device__ R c(int i, int j) const {
+    const long long q = (long long)j * d.P + i;
+    return in_range(q, d.nV()) ? __ldg(&C[q]) : R(0);
+  }
+  __device__ R h(int i, int j) const {
+    const long long q = (long long)j * d.P + i;
+    return in_range(q, d.nH()) ? __ldg(&sH[q]) : R(0);
+  }
+  __device__ R v(int i, int j) const {
+    const long long q = (long long)j * d.P + i;
+    return in_range(q, d.nV()) ? __ldg(&sV[q]) : R(0);
+  }
 };
 
 // The fractions a listed cell's stencils read: the vertical arm
@@ -177,7 +187,7 @@ __global__ void __launch_bounds__(kGhfThreads, 6)
         const R hpp = (h[2] - h[1]) - (h[1] - h[0]);
         const R qv = R(1) + hp * hp;
         const R den = dx * (qv * sqrt(qv));
-        kappa[(long long)j * S.d.P + i] = -hpp / den;
+        if (in_range((long long)j * S.d.P + i, S.d.nV())) kappa[(long long)j * S.d.P + i] = -hpp / den;
         ++got[0];
         continue;
       }
@@ -222,7 +232,7 @@ __global__ void __launch_bounds__(kGhfThreads, 6)
     }
     R kv;
     if (F.kappa(dx, &kv)) {
-      kappa[(long long)j * S.d.P + i] = kv;
+      if (in_range((long long)j * S.d.P + i, S.d.nV())) kappa[(long long)j * S.d.P + i] = kv;
       ++got[1];
       continue;
     }
@@ -237,7 +247,7 @@ __global__ void __launch_bounds__(kGhfThreads, 6)
         if (a >= 0 && a <= S.d.nx && b >= 0 && b < S.d.ny && S.k(a, b) != S.k(a, b + 1))
           F.add((R)(a - i), (R)(b - j) + S.v(a, b));
     if (F.kappa(dx, &kv)) {
-      kappa[(long long)j * S.d.P + i] = kv;
+      if (in_range((long long)j * S.d.P + i, S.d.nV())) kappa[(long long)j * S.d.P + i] = kv;
       ++got[2];
     }
   }

@@ -543,8 +543,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
             n_cfl += f.cfl;
             dmax = fmax(dmax, dabs_of<R>(f));
           } else {  // a wall marker normal to the sweep stays
-            if (AX) out.sH[(long long)x * P + y] = p.fy;
-            else out.sV[(long long)y * P + x] = p.fy;
+            if (AX) { if (in_range((long long)x * P + y, G.d.nH())) out.sH[(long long)x * P + y] = p.fy; }
+            else if (in_range((long long)y * P + x, G.d.nV())) out.sV[(long long)y * P + x] = p.fy;
           }
         }
       }
@@ -590,8 +590,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         n_canc += L.cancelled;
         n_inv += L.invariant;
         if (L.present) {
-          if (AX) out.sV[(long long)x * P + y] = L.kept_fx;
-          else out.sH[(long long)y * P + x] = L.kept_fx;
+          if (AX) { if (in_range((long long)x * P + y, G.d.nV())) out.sV[(long long)x * P + y] = L.kept_fx; }
+          else if (in_range((long long)y * P + x, G.d.nH())) out.sH[(long long)y * P + x] = L.kept_fx;
         }
       }
     }
@@ -608,8 +608,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
           bad &= bad - 1;
           const int x = ri0 + 32 * wi + b, y = rj0 + ly;
           n_inv += 1;
-          if (AX) out.sV[(long long)x * P + y] = R(0.5);
-          else out.sH[(long long)y * P + x] = R(0.5);
+          if (AX) { if (in_range((long long)x * P + y, G.d.nV())) out.sV[(long long)x * P + y] = R(0.5); }
+          else if (in_range((long long)y * P + x, G.d.nH())) out.sH[(long long)y * P + x] = R(0.5);
         }
       }
       // interface cells (corner colours not all equal) whose chords can
@@ -869,8 +869,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       }
       M.vrl[e] = verdicts(nv.vr, nv.vl);
       if (own && nv.present) {
-        if (AX) out.sH[(long long)k * P + j] = nv.s;
-        else out.sV[(long long)j * P + k] = nv.s;
+        if (AX) { if (in_range((long long)k * P + j, G.d.nH())) out.sH[(long long)k * P + j] = nv.s; }
+        else if (in_range((long long)j * P + k, G.d.nV())) out.sV[(long long)j * P + k] = nv.s;
       }
     }
     if (tid >= kSplit && 2 + (tid - kSplit) / kRW <= ty1) {  // rows of unaligned edges only
@@ -892,8 +892,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
           if (oc[c]) atomicAdd(&s_cnt[c], oc[c]);
         M.vrl[e] = verdicts(nv.vr, nv.vl);
         if (own && nv.present) {
-          if (AX) out.sH[(long long)k * P + j] = nv.s;
-          else out.sV[(long long)j * P + k] = nv.s;
+          if (AX) { if (in_range((long long)k * P + j, G.d.nH())) out.sH[(long long)k * P + j] = nv.s; }
+          else if (in_range((long long)j * P + k, G.d.nV())) out.sV[(long long)j * P + k] = nv.s;
         }
       }
       // owned interior edges that gain a marker without a candidate: counted,
@@ -905,8 +905,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         miss &= miss - 1;
         const int k = ri0 + 32 * wi + b, j = rj0 + ly;
         n_inv += 1;
-        if (AX) out.sH[(long long)k * P + j] = R(0.5);
-        else out.sV[(long long)j * P + k] = R(0.5);
+        if (AX) { if (in_range((long long)k * P + j, G.d.nH())) out.sH[(long long)k * P + j] = R(0.5); }
+        else if (in_range((long long)j * P + k, G.d.nV())) out.sV[(long long)j * P + k] = R(0.5);
       }
     }
     flush_count(s_cnt, D_CANCELLED, n_canc, lane);

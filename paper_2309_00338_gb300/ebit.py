@@ -106,6 +106,7 @@ SIGNATURES = {
     "ebit_fraction_noalloc": (ctypes.c_int, [ctypes.POINTER(ebit_grid), _P, _P, _P, _P, _P, _P, _P, _P]),
     "ebit_coupling": (ctypes.c_int, [_P, ctypes.POINTER(ebit_fluids), _P, _P, _P, _P]),
     "ebit_area_async": (ctypes.c_int, [_P, _P]),
+    "ebit_check_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
 }
 
 K_SWEEP, K_CENTRE, K_FIELDS, K_AREA, K_COUPLING, K_GHF = range(6)
@@ -118,7 +119,7 @@ def lib(path: str | None = None):
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or LIB_PATH
+    p = path or os.environ.get("EBIT_LIB") or LIB_PATH
     if not os.path.exists(p):
         raise RuntimeError(f"libebit.so not built ({p}); run __graft_entry__.build() first")
     L = ctypes.CDLL(p)
@@ -248,6 +249,14 @@ def ebit_area_async(ctx, area_host):
     if area_host.is_cuda or area_host.dtype.itemsize != 8:
         raise ValueError("expected a host tensor of one float64")
     _check(lib().ebit_area_async(ctx, ctypes.c_void_p(area_host.data_ptr())), "ebit_area_async")
+
+
+def ebit_check_status():
+    """Nonzero if a kernel of the checked build met an index outside its
+    array (always 0 in the release build)."""
+    m = ctypes.c_uint32(0)
+    _check(lib().ebit_check_status(ctypes.byref(m)), "ebit_check_status")
+    return m.value
 
 
 def ebit_curvature(ctx, kappa=None, want_invalid=True):
