@@ -206,8 +206,9 @@ ebit_status ebit_sync(ebit_ctx* ctx);
 void ebit_destroy(ebit_ctx* ctx);
 
 /* Debug builds (libebit_check.so, compiled with EBIT_CHECK) check every
- * global index of the step kernels of contexts (sweeps, fields, fallback
- * fits) against its array and skip an access out of range; *misses receives
+ * global index of the step kernels (sweeps, fields, fallback fits, of
+ * contexts and of servers) against its array and skip an access out of
+ * range; *misses receives
  * nonzero if any happened since the library was loaded.  Release builds
  * report 0.  Synchronous; EBIT_EINVAL for a NULL argument. */
 ebit_status ebit_check_status(uint32_t* misses);

@@ -522,7 +522,7 @@ ebit_status ebit_check_status(uint32_t* misses) {
 #ifdef EBIT_CHECK
   unsigned w = 0;
   EBIT_CK(cudaMemcpyFromSymbol(&w, ebit::ebit_check_word, sizeof w));
-  *misses = w;
+  *misses = w | server_check_misses();
 #else
   *misses = 0;
 #endif

@@ -13,6 +13,9 @@
 
 namespace ebit_detail {
 
+// The index-check word of the server's kernels (debug builds; 0 otherwise).
+unsigned server_check_misses();
+
 // NVTX range over a host call (visible in profilers that record NVTX; a
 // no-op otherwise).
 struct Range {

@@ -299,6 +299,23 @@ struct Group {
   }
 };
 
+}  // namespace
+
+unsigned ebit_detail::server_check_misses() {
+#ifdef EBIT_CHECK
+  unsigned w = 0;
+  if (cudaMemcpyFromSymbol(&w, ebit::ebit_check_word, sizeof w) != cudaSuccess) {
+    cudaGetLastError();
+    return 1u;
+  }
+  return w;
+#else
+  return 0u;
+#endif
+}
+
+namespace {
+
 template <typename R>
 ebit_status set_batch_attributes() {
   constexpr size_t smem = ebit::tile_smem_bytes<R>();

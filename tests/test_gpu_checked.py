@@ -1,5 +1,5 @@
 """The debug build (libebit_check.so, compiled with EBIT_CHECK) on the parity
-scenes: the step kernels check every global index against its array (the
+scenes and a served mix: the step kernels check every global index against its array (the
 bounds checking a sanitizer would do, done by the build itself), no index
 falls outside, and the results still equal the oracle's."""
 import os
@@ -53,6 +53,11 @@ r = oracle.step(S, f.u, f.v, dt, ghf=True)
 assert_same_kappa(kappa_of(ctx, S), r["kappa"], 1, S.dx)
 ebit.ebit_destroy(ctx)
 
+from tests.test_gpu_server import _mix, _run
+specs = _mix()[:4]
+specs[1]["flags"] = ebit.EBIT_CURV_GHF
+res, outs, stats = _run(specs, 8 << 30)
+assert all(r["status"] == 0 for r in res)
 assert ebit.ebit_check_status() == 0, "an index fell outside its array"
 print("checked ok")
 '''
