@@ -981,6 +981,33 @@ def test_coupling_laplace_pressure_jump(drop):
     assert abs(fx.sum()) < 1e-2 * scale and abs(fy.sum()) < 1e-2 * scale
 
 
+def test_rotating_disks_curvature_per_disk():
+    """The 1024^2 rotating-disks workload (1633 placed disks of 2-20 cells):
+    for every disk of radius >= 8 cells the median height-function curvature
+    over the interface cells on its boundary is 1/r (median error < 1%, none
+    above 5%), and the error falls as r grows."""
+    wl = W.rotation_disks_workload()
+    S = oracle.init(wl.n, wl.n, wl.dx, wl.scene)
+    C, _ = oracle.fraction(S)
+    kap, _ = oracle.curvature(S, C)
+    dx = wl.dx
+    js, is_ = np.nonzero(~np.isnan(kap))
+    px, py = (is_ + 0.5) * dx, (js + 0.5) * dx
+    circ = np.asarray(wl.scene["circles"])
+    big = circ[circ[:, 2] >= 8 * dx]
+    assert len(big) > 400
+    err, rad = [], []
+    for xc, yc, r in big:
+        m = (np.abs(px - xc) < r + 2 * dx) & (np.abs(py - yc) < r + 2 * dx)
+        near = np.abs(np.hypot(px[m] - xc, py[m] - yc) - r) < 1.5 * dx
+        assert near.sum() >= 4
+        err.append(abs(np.median(kap[js[m][near], is_[m][near]]) * r - 1))
+        rad.append(r / dx)
+    err, rad = np.array(err), np.array(rad)
+    assert np.median(err) < 1e-2 and err.max() < 5e-2
+    assert np.median(err[rad >= 16]) < np.median(err[rad < 12])
+
+
 # ---------------------------------------------------------------------------
 # initialisation (Sec. 3.2)
 # ---------------------------------------------------------------------------
