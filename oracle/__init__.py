@@ -118,6 +118,8 @@ def _set_signatures(L):
     L.orc_loops.restype = i64
     L.orc_shape_error.argtypes = [i32, i32, f64, P, P, P, f64, f64, f64]
     L.orc_shape_error.restype = f64
+    L.orc_sym_diff.argtypes = [i32, i32, f64, i32, P, P, P, P, P, P, P, P]
+    L.orc_sym_diff.restype = f64
 
 
 def lib():
@@ -337,6 +339,14 @@ def shape_error(S: State, xc, yc, R):
     """E_shape of Eq. 14 against the circle (xc, yc, R)."""
     return float(lib().orc_shape_error(S.nx, S.ny, S.dx, _p(S.K), _p(S.sH), _p(S.sV),
                                        float(xc), float(yc), float(R)))
+
+
+def sym_diff(A: State, B: State):
+    """E_sym of Eqs. 15-16: area of the symmetric difference of the two
+    states' reference-phase regions (domain units)."""
+    assert (A.nx, A.ny, A.prec & 1) == (B.nx, B.ny, B.prec & 1)
+    return float(lib().orc_sym_diff(A.nx, A.ny, A.dx, A.prec, _p(A.K), _p(A.Z), _p(A.sH), _p(A.sV),
+                                    _p(B.K), _p(B.Z), _p(B.sH), _p(B.sV)))
 
 
 def markers(S: State):

@@ -419,6 +419,7 @@ void sweep_x(State<R>& S, const R* u, R lam, bool line_only, int64_t* ctr, doubl
     const bool present = N.hasH(i, j);
     landed[(size_t)j * nx + i] = 1;
     if (present && (n & 1)) {
+      ctr[ORC_CANCELLED] += (int64_t)(n / 2);  // the pairs around the middle one
       const Land& m = land[a + n / 2];
       N.h(i, j) = m.fx;
       keep[(size_t)j * nx + i] = m.src;
@@ -542,6 +543,7 @@ void sweep_x(State<R>& S, const R* u, R lam, bool line_only, int64_t* ctr, doubl
     got[(size_t)j * (nx + 1) + k] = 1;
     const Cand* pick = nullptr;
     if (present && (n & 1)) {
+      ctr[ORC_CANCELLED] += (int64_t)(n / 2);
       pick = &cand[a + n / 2];
     } else if (!present && !(n & 1)) {
       ctr[ORC_CANCELLED] += (int64_t)(n / 2);
@@ -700,6 +702,16 @@ double fraction(const State<R>& S, double dx, double* C) {
 // ("mixed heights"), then a parabola fitted to the markers of the 3x3 block
 // (where the volume-of-fluid form fits interface-fragment centroids, the
 // markers give points that lie on the interface).
+//
+// Precision (reading): the heights and the fits run in the state precision R.
+// Their inputs are the state's own fractions and marker positions, which the
+// FP32 form holds to 2^-24; a three-parameter parabola fitted over a window of
+// about three cells with points at least half a cell apart has normal
+// equations of moderate condition once the ill-determined ones are refused
+// (the regularity test below), so float arithmetic moves kappa by ~1e-6
+// relative (1e-4 at most), while the fit's own error against the curvature of
+// the interface it samples is ~3e-2 (kappa r - 1 on disks of 3-8 cells).  The
+// pins compare the two forms' fallback curvatures to show exactly that.
 // ---------------------------------------------------------------------------
 
 // Curvature of the parabola z = a s^2 + b s + c fitted by weighted least
@@ -708,8 +720,7 @@ double fraction(const State<R>& S, double dx, double* C) {
 // (ny, -nx)), evaluated at s = 0: kappa = -2a / (1 + b^2)^(3/2) / dx, which is
 // +1/R for a reference-phase drop of radius R.  The normal equations are
 // solved by Cramer's rule, in the arithmetic R.  Returns false when the
-// system is singular (|det| <= eps S0^3, eps = 1e-10 in double, 1e-5 in
-// float).
+// system is ill-determined (|det| <= 1e-3 S4 S2 S0).
 template <typename R>
 bool parabola_kappa(int n, const R* X, const R* Y, const R* W, R ox, R oy, R nx, R ny, R dx,
                     R* kappa) {
@@ -733,8 +744,11 @@ bool parabola_kappa(int n, const R* X, const R* Y, const R* W, R ox, R oy, R nx,
   const R m01 = S3 * S0 - S1 * S2;
   const R m02 = S3 * S1 - S2 * S2;
   const R det = S4 * m00 - S3 * m01 + S2 * m02;
-  const R eps = sizeof(R) == 4 ? R(1e-5) : R(1e-10);
-  if (!(std::fabs(det) > eps * (S0 * S0 * S0))) return false;
+  // regular: |det| above 1e-3 of the product of the diagonal of the (positive
+  // definite) normal matrix, which bounds it (Hadamard); the same test in
+  // both precisions
+  const R eps = R(1e-3);
+  if (!(std::fabs(det) > eps * (S4 * S2 * S0))) return false;
   const R u1 = T1 * S0 - S1 * T0;
   const R da = T2 * m00 - S3 * u1 + S2 * (T1 * S1 - S2 * T0);
   const R db = S4 * u1 - T2 * m01 + S2 * (S3 * T0 - T1 * S2);
@@ -1251,6 +1265,104 @@ int64_t loops(const State<R>& S, double dx, int64_t* n_open, double* area, doubl
   return closed;
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric difference of two interface reconstructions (Sec. 3.2, Eqs. 15
+// and 16): E_sym = |A| + |B| - 2 |A n B|, A and B the reference-phase regions
+// bounded by the straight segments joining the markers of two states on the
+// same grid.  Cell by cell, each region is one convex polygon or (a saddle
+// whose centre is not reference phase) two corner triangles, so A n B is a
+// sum of convex-convex intersections (Sutherland-Hodgman clipping).
+// ---------------------------------------------------------------------------
+struct Poly {
+  int n = 0;
+  P2 v[12];
+};
+
+double poly_area(const Poly& p) {
+  double a = 0.0;
+  for (int t = 0; t < p.n; ++t) {
+    const P2 &u = p.v[t], &w = p.v[(t + 1) % p.n];
+    a += u.x * w.y - w.x * u.y;
+  }
+  return 0.5 * a;
+}
+
+// p clipped to the left of the directed edge a->b (the inside of a
+// counter-clockwise convex polygon).
+Poly clip_left(const Poly& p, P2 a, P2 b) {
+  Poly out;
+  auto side = [&](P2 q) { return (b.x - a.x) * (q.y - a.y) - (b.y - a.y) * (q.x - a.x); };
+  for (int t = 0; t < p.n; ++t) {
+    const P2 cur = p.v[t], nxt = p.v[(t + 1) % p.n];
+    const double sc = side(cur), sn = side(nxt);
+    if (sc >= 0.0) out.v[out.n++] = cur;
+    if ((sc >= 0.0) != (sn >= 0.0)) {
+      const double w = sc / (sc - sn);
+      out.v[out.n++] = {cur.x + w * (nxt.x - cur.x), cur.y + w * (nxt.y - cur.y)};
+    }
+  }
+  return out;
+}
+
+double convex_overlap(const Poly& p, const Poly& q) {
+  Poly r = p;
+  for (int t = 0; t < q.n && r.n > 0; ++t) r = clip_left(r, q.v[t], q.v[(t + 1) % q.n]);
+  return r.n >= 3 ? poly_area(r) : 0.0;
+}
+
+// Reference-phase pieces of cell (i,j) in cell units, counter-clockwise.
+template <typename R>
+int cell_pieces(const State<R>& S, int i, int j, Poly out[2]) {
+  int c[4];
+  corners(S, i, j, c);
+  const P2 corner[4] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+  P2 mk[4];
+  int pres[4], n = 0;
+  for (int e = 0; e < 4; ++e) {
+    pres[e] = c[e] != c[(e + 1) & 3];
+    n += pres[e];
+    mk[e] = edge_point(S, i, j, e);
+  }
+  if (n == 4 && S.zc(i, j) == 0) {
+    // two reference-phase corners cut off by their segments
+    int m = 0;
+    for (int q = 0; q < 4; ++q)
+      if (c[q] == 1) {
+        out[m].n = 3;
+        out[m].v[0] = mk[(q + 3) & 3];
+        out[m].v[1] = corner[q];
+        out[m].v[2] = mk[q];
+        ++m;
+      }
+    return m;
+  }
+  // one convex piece: the boundary walked counter-clockwise, keeping the
+  // reference-phase corners and every marker
+  Poly p;
+  for (int q = 0; q < 4; ++q) {
+    if (c[q] == 1) p.v[p.n++] = corner[q];
+    if (pres[q]) p.v[p.n++] = mk[q];
+  }
+  if (p.n < 3) return 0;
+  out[0] = p;
+  return 1;
+}
+
+template <typename R>
+double sym_diff(const State<R>& A, const State<R>& B, double dx) {
+  double a = 0.0, b = 0.0, ab = 0.0;
+  for (int j = 0; j < A.ny; ++j)
+    for (int i = 0; i < A.nx; ++i) {
+      Poly pa[2], pb[2];
+      const int na = cell_pieces(A, i, j, pa), nb = cell_pieces(B, i, j, pb);
+      for (int s = 0; s < na; ++s) a += poly_area(pa[s]);
+      for (int t = 0; t < nb; ++t) b += poly_area(pb[t]);
+      for (int s = 0; s < na; ++s)
+        for (int t = 0; t < nb; ++t) ab += convex_overlap(pa[s], pb[t]);
+    }
+  return (a + b - 2.0 * ab) * (dx * dx);
+}
+
 template <typename R>
 int do_step(int nx, int ny, double dx, int64_t step_index, bool line_only, bool ghf, uint8_t* K,
             uint8_t* Z, double* sH, double* sV, const double* u, const double* v, double dt,
@@ -1372,30 +1484,29 @@ namespace {
 
 // Properties and surface-tension source (the coupling of Sec. 2.5): the
 // fraction C stands in for the Heaviside function of Eq. 8, and the surface
-// term sigma kappa n delta_S of Eq. 6 becomes sigma kappa grad(C)
-// at the faces, with the face curvature the mean of the two cells' valid
-// heights-based curvatures (one valid: that one; none: 0).  The face
-// gradient is (C_b - C_a) times 1/dx, with sigma/dx formed once.
-template <typename R>
+// term sigma kappa n delta_S of Eq. 6 becomes sigma kappa grad(C) at the
+// faces, with the face curvature the mean of the two cells' valid
+// heights-based curvatures (one valid: that one; none: 0) and the face
+// gradient (C_b - C_a) / dx.  The definition written out in double for both
+// precision forms: the library's FP32 form computes the same quantities in
+// float and is compared with this within its rounding.
 void coupling(int nx, int ny, double dx, const double* C, const double* kappa, double rho1,
               double rho2, double mu1, double mu2, double sigma, double* rho, double* mu,
               double* fx, double* fy) {
-  const R r1 = (R)rho1, r2 = (R)rho2, m1 = (R)mu1, m2 = (R)mu2;
-  const R sh = (R)sigma / (R)dx;  // sigma / dx
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
-      const R c = (R)C[(size_t)j * nx + i];
-      rho[(size_t)j * nx + i] = (double)(c * r1 + (R(1) - c) * r2);
-      mu[(size_t)j * nx + i] = (double)(c * m1 + (R(1) - c) * m2);
+      const double c = C[(size_t)j * nx + i];
+      rho[(size_t)j * nx + i] = c * rho1 + (1.0 - c) * rho2;
+      mu[(size_t)j * nx + i] = c * mu1 + (1.0 - c) * mu2;
     }
   auto face = [&](size_t a, size_t b) -> double {  // cells a (low side), b (high side)
-    const R ka = (R)kappa[a], kb = (R)kappa[b];
+    const double ka = kappa[a], kb = kappa[b];
     const bool va = !std::isnan(ka), vb = !std::isnan(kb);
-    R kf = R(0);
-    if (va && vb) kf = (ka + kb) * R(0.5);
+    double kf = 0.0;
+    if (va && vb) kf = 0.5 * (ka + kb);
     else if (va) kf = ka;
     else if (vb) kf = kb;
-    return (double)(sh * kf * ((R)C[b] - (R)C[a]));
+    return sigma * kf * (C[b] - C[a]) / dx;
   };
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i <= nx; ++i)
@@ -1414,8 +1525,8 @@ extern "C" {
 int orc_coupling(int nx, int ny, double dx, int prec, const double* C, const double* kappa,
                  double rho1, double rho2, double mu1, double mu2, double sigma,
                  double* rho, double* mu, double* fx, double* fy) {
-  if ((prec & 1) == 0) coupling<double>(nx, ny, dx, C, kappa, rho1, rho2, mu1, mu2, sigma, rho, mu, fx, fy);
-  else coupling<float>(nx, ny, dx, C, kappa, rho1, rho2, mu1, mu2, sigma, rho, mu, fx, fy);
+  (void)prec;  // the same definition in double for both forms
+  coupling(nx, ny, dx, C, kappa, rho1, rho2, mu1, mu2, sigma, rho, mu, fx, fy);
   return 0;
 }
 
@@ -1433,6 +1544,14 @@ int64_t orc_loops(int nx, int ny, double dx, int prec, const uint8_t* K, const u
   if ((prec & 1) == 0)
     return loops(load<double>(nx, ny, K, Z, sH, sV), dx, n_open, area, xy, cap, n_written);
   return loops(load<float>(nx, ny, K, Z, sH, sV), dx, n_open, area, xy, cap, n_written);
+}
+
+double orc_sym_diff(int nx, int ny, double dx, int prec, const uint8_t* K1, const uint8_t* Z1,
+                    const double* sH1, const double* sV1, const uint8_t* K2, const uint8_t* Z2,
+                    const double* sH2, const double* sV2) {
+  if ((prec & 1) == 0)
+    return sym_diff(load<double>(nx, ny, K1, Z1, sH1, sV1), load<double>(nx, ny, K2, Z2, sH2, sV2), dx);
+  return sym_diff(load<float>(nx, ny, K1, Z1, sH1, sV1), load<float>(nx, ny, K2, Z2, sH2, sV2), dx);
 }
 
 double orc_shape_error(int nx, int ny, double dx, const uint8_t* K, const double* sH,

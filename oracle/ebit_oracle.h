@@ -86,8 +86,10 @@ int orc_fraction(int nx, int ny, double dx, int prec, const uint8_t* K,
 
 /* Curvature of the fractions C; counts[4] (or NULL) receives the interface
  * cells without a valid 7x3 stencil and, with flag 4, how many of them the
- * other direction, mixed heights and the markers of the 3x3 block resolved.  Fallback
- * fits run in double in both precision forms. */
+ * other direction, mixed heights and the markers of the 3x3 block resolved.  The
+ * heights and the fallback fits run in the state precision (double for the FP64
+ * form, float for the FP32 form): their rounding stays far below the error of
+ * the fits themselves (see the curvature section of the implementation). */
 int orc_curvature(int nx, int ny, double dx, int prec, const uint8_t* K,
                   const uint8_t* Z, const double* sH, const double* sV,
                   const double* C, double* kappa, int64_t* counts);
@@ -105,8 +107,8 @@ int orc_parabola_kappa(int n, const double* X, const double* Y, const double* W,
  * rho = C rho1 + (1 - C) rho2 and mu likewise per cell (ny*nx), and the
  * surface-tension source sigma kappa grad(C) on the faces: fx on the
  * (nx+1)*ny vertical faces, fy on the nx*(ny+1) horizontal ones, zero on the
- * walls.  Arithmetic in the state precision: f = (sigma/dx) kappa_f dC with
- * sigma/dx formed once. */
+ * walls: f = sigma kappa_f (C_b - C_a) / dx.  Double arithmetic in both
+ * precision forms (prec is accepted and ignored). */
 int orc_coupling(int nx, int ny, double dx, int prec, const double* C, const double* kappa,
                  double rho1, double rho2, double mu1, double mu2, double sigma,
                  double* rho, double* mu, double* fx, double* fy);
@@ -127,6 +129,13 @@ int64_t orc_loops(int nx, int ny, double dx, int prec, const uint8_t* K,
                   const uint8_t* Z, const double* sH, const double* sV,
                   int64_t* n_open, double* area, double* xy, int64_t cap,
                   int64_t* n_written);
+
+/* E_sym (Eqs. 15-16): |A| + |B| - 2 |A n B| of the reference-phase regions
+ * of two states of the same grid (domain units: dx^2 applied). */
+double orc_sym_diff(int nx, int ny, double dx, int prec, const uint8_t* K1,
+                    const uint8_t* Z1, const double* sH1, const double* sV1,
+                    const uint8_t* K2, const uint8_t* Z2, const double* sH2,
+                    const double* sV2);
 
 /* E_shape (Eq. 14): max over markers of |dist(marker, centre) - R|. */
 double orc_shape_error(int nx, int ny, double dx, const uint8_t* K,

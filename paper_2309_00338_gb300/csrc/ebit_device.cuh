@@ -314,6 +314,7 @@ __device__ __forceinline__ Landing<R> choose_landing3(const bool valid[3], const
   int want = -1;
   if (present && (n & 1)) {
     want = n / 2;
+    L.cancelled = n / 2;  // the pairs around the middle one
   } else if (!present && !(n & 1)) {
     L.cancelled = n / 2;
   } else {
@@ -621,6 +622,7 @@ __device__ NewV<R> select_candidates(int n, double* cy, int* cvr, int* cvl, int*
   int pick = -1;
   if (present && (n & 1)) {
     pick = n / 2;
+    out.cancelled = n / 2;
   } else if (!present && !(n & 1)) {
     out.cancelled = n / 2;
   } else {

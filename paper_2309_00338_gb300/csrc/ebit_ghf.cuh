@@ -138,8 +138,9 @@ struct ParabolaFit {
     const R m01 = S3 * S0 - S1 * S2;
     const R m02 = S3 * S1 - S2 * S2;
     const R det = S4 * m00 - S3 * m01 + S2 * m02;
-    const R eps = sizeof(R) == 4 ? R(1e-5) : R(1e-10);
-    if (!(fabs(det) > eps * (S0 * S0 * S0))) return false;
+    // regular: |det| above 1e-3 of its Hadamard bound S4 S2 S0, in both precisions
+    const R eps = R(1e-3);
+    if (!(fabs(det) > eps * (S4 * S2 * S0))) return false;
     const R u1 = T1 * S0 - S1 * T0;
     const R da = T2 * m00 - S3 * u1 + S2 * (T1 * S1 - S2 * T0);
     const R db = S4 * u1 - T2 * m01 + S2 * (S3 * T0 - T1 * S2);

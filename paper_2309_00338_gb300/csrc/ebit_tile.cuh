@@ -361,6 +361,7 @@ __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int
   int want = -1;  // rank of the kept candidate
   if (present && (n & 1)) {
     want = n / 2;
+    out.cancelled = n / 2;  // the pairs around the middle one
   } else if (!present && !(n & 1)) {
     out.cancelled = n / 2;
   } else {

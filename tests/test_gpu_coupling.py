@@ -1,9 +1,11 @@
 """GPU parity of ebit_coupling (Sec. 2.5: the properties of Eq. 8 and the
 face surface-tension source of Eq. 6) against the oracle, through the C ABI.
 
-Both sides evaluate the same expressions in the context precision on the
-same C and kappa, so the outputs must agree bit for bit; against the oracle's
-own fraction and curvature chain they agree to the fields' tolerance."""
+The oracle evaluates the definitions in double on the GPU's C and kappa; the
+library computes them in the context precision (with sigma/dx formed once),
+so the outputs agree to the rounding of that arithmetic: a few units in the
+last place of float in the FP32 form (16 * 2^-24 of the size of the terms),
+1e-12 relative in the FP64 form."""
 import numpy as np
 import pytest
 
@@ -42,10 +44,24 @@ def gpu_fields(ctx, S):
     return C.double().cpu().numpy(), kap.double().cpu().numpy()
 
 
-def assert_bit_exact(g, o):
+def assert_close(g, o, C, kap, prec, dx, fl=FL):
+    """Outputs g of the library against the oracle's o, computed from the
+    fields C and kap: each within eps times the size of the terms that form
+    it (eps = 16 * 2^-24 for float, 1e-12 for double)."""
+    eps = 16 * 2.0 ** -24 if prec == oracle.FP32 else 1e-12
+    Ca = np.abs(C)
+    scale = {"rho": Ca * abs(fl["rho1"]) + np.abs(1 - C) * abs(fl["rho2"]),
+             "mu": Ca * abs(fl["mu1"]) + np.abs(1 - C) * abs(fl["mu2"])}
+    ka = np.where(np.isnan(kap), 0.0, np.abs(kap))
+    sg = abs(fl["sigma"]) / dx
+    fx = np.zeros((C.shape[0], C.shape[1] + 1))
+    fx[:, 1:-1] = sg * np.maximum(ka[:, :-1], ka[:, 1:]) * np.maximum(Ca[:, :-1], Ca[:, 1:])
+    fy = np.zeros((C.shape[0] + 1, C.shape[1]))
+    fy[1:-1, :] = sg * np.maximum(ka[:-1, :], ka[1:, :]) * np.maximum(Ca[:-1, :], Ca[1:, :])
+    scale["fx"], scale["fy"] = fx, fy
     for name, ref in zip(("rho", "mu", "fx", "fy"), o):
         assert g[name].shape == ref.shape, name
-        bad = np.argwhere(g[name] != ref)
+        bad = np.argwhere(~(np.abs(g[name] - ref) <= eps * scale[name]))
         assert bad.size == 0, f"{name} differs at {bad[:6].tolist()}"
 
 
@@ -59,12 +75,13 @@ def test_coupling_parity_after_step(name, prec):
         r = oracle.step(S, f.u, f.v, dt)
         g = gpu_coupling(ctx, S)
         C, kap = gpu_fields(ctx, S)
-        assert_bit_exact(g, oracle.coupling(S, C, kap, **FL))
-        # against the oracle's own chain: equal in FP32 (fields are bit-exact
-        # there); in FP64 the fields agree to 1e-12 cells and so do these
+        assert_close(g, oracle.coupling(S, C, kap, **FL), C, kap, prec, S.dx)
+        # against the oracle's own chain: in FP32 the fields are bit-exact,
+        # so the same bound holds; in FP64 the fields agree to 1e-12 cells
+        # and so do these
         o = oracle.coupling(S, r["C"], r["kappa"], **FL)
         if prec == oracle.FP32:
-            assert_bit_exact(g, o)
+            assert_close(g, o, r["C"], r["kappa"], prec, S.dx)
         else:
             sc = FL["sigma"] / S.dx ** 2
             for name_, ref in zip(("rho", "mu", "fx", "fy"), o):
@@ -86,7 +103,7 @@ def test_coupling_ragged_grids(nx, ny):
         try:
             g = gpu_coupling(ctx, S)
             C, kap = gpu_fields(ctx, S)
-            assert_bit_exact(g, oracle.coupling(S, C, kap, **FL))
+            assert_close(g, oracle.coupling(S, C, kap, **FL), C, kap, prec, S.dx)
         finally:
             ebit.ebit_destroy(ctx)
 
@@ -103,7 +120,8 @@ def test_coupling_null_outputs_untouched():
         assert torch.all(rho == 7.0)
         C, kap = gpu_fields(ctx, S)
         o = oracle.coupling(S, C, kap, **FL)
-        assert np.array_equal(fx.cpu().numpy(), o[2])
+        g = {"rho": o[0], "mu": o[1], "fx": fx.cpu().numpy(), "fy": o[3]}
+        assert_close(g, o, C, kap, oracle.FP64, S.dx)
         assert ebit.lib().ebit_coupling(ctx, None, None, None, None, None) == ebit.EBIT_EINVAL
         assert ebit.lib().ebit_coupling(None, ebit.ebit_fluids(1, 1, 1, 1, 1), None, None, None,
                                         None) == ebit.EBIT_EINVAL
@@ -122,7 +140,7 @@ def test_coupling_full_size_cellular_curve(prec):
     try:
         g = gpu_coupling(ctx, S)
         C, kap = gpu_fields(ctx, S)
-        assert_bit_exact(g, oracle.coupling(S, C, kap, **FL))
+        assert_close(g, oracle.coupling(S, C, kap, **FL), C, kap, prec, S.dx)
         # the Laplace balance holds on the GPU output too: from the cell that
         # holds a circle's leftmost point to its centre, along the centre's
         # row, the face forces integrate to a pressure jump of sigma / r

@@ -58,6 +58,19 @@ MUTANTS = [
      [("      if (dot > R(0)) {\n        n0x = -n0x;", "      if (dot < R(0)) {\n        n0x = -n0x;")]),
     ("mixed heights measured from the wrong end",
      [("const R pos = o == 1 ? R(-3) + h : R(4) - h;", "const R pos = o == 1 ? R(4) - h : R(-3) + h;")]),
+    ("three landings keep the first instead of the middle one",
+     [("const Land& m = land[a + n / 2];", "const Land& m = land[a];")]),
+    ("three candidates keep the first instead of the middle one",
+     [("pick = &cand[a + n / 2];", "pick = &cand[a];")]),
+    ("centre rule takes the corner at the other end of the edge",
+     [("const int vr = lr < 0 ? -1 : !N.kc(k, lr);",
+       "const int vr = lr < 0 ? -1 : !N.kc(k, lr == j ? j + 1 : j);")]),
+    ("centre rule walks the right cell in the left column",
+     [("const int lr = walk(mB, n4, k);", "const int lr = walk(mB, n4, k - 1);")]),
+    ("symmetric difference: clipping keeps the outside",
+     [("    if (sc >= 0.0) out.v[out.n++] = cur;", "    if (sc <= 0.0) out.v[out.n++] = cur;")]),
+    ("symmetric difference: saddle pieces for the other centre colour",
+     [("  if (n == 4 && S.zc(i, j) == 0) {", "  if (n == 4 && S.zc(i, j) == 1) {")]),
     ("markers fit takes vertical markers one edge off",
      [("add((R)(a - i), (R)(b - j) + S.vc(a, b));", "add((R)(a - i) + R(1), (R)(b - j) + S.vc(a, b));")]),
 ]
@@ -80,6 +93,11 @@ BATTERY = [
     (P.test_hf_circle_curvature_converges, ()),
     (P.test_init_markers_on_shapes, ()),
     (P.test_vortex_T2_table3, (32,)),
+    (P.test_three_landings_keep_the_middle_one, ()),
+    (P.test_sym_diff_closed_forms, ()),
+    (P.test_sym_diff_brute_force, (6,)),
+    (P.test_sweep_commutes_with_reflections, ()),
+    (P.test_centre_colour_of_saddles_follows_the_exact_shape, ()),
     (P.test_parabola_fit_exact_on_parabolas, ()),
     (P.test_parabola_fit_circle_and_singular, ()),
     (P.test_ghf_keeps_standard_values_and_resolves_packed_disks, (0,)),
