@@ -220,8 +220,8 @@ const char* ebit_last_error(void);
  * CUDA events on its stream around every kernel it launches for a step;
  * ebit_timings (synchronous) returns, per kernel kind, the summed duration in
  * milliseconds and the number of launches since the last call, then resets.
- * Kinds: EBIT_K_SWEEP (a split sweep), EBIT_K_CENTRE (second pass of the
- * gather sweep, when selected), EBIT_K_FIELDS (fractions, curvature and area
+ * Kinds: EBIT_K_SWEEP (a split sweep), EBIT_K_CENTRE (reserved, always 0),
+ * EBIT_K_FIELDS (fractions, curvature and area
  * partials), EBIT_K_AREA (area sum), EBIT_K_COUPLING (ebit_coupling),
  * EBIT_K_GHF (list and fits of the generalised fallbacks). */
 enum { EBIT_K_SWEEP = 0, EBIT_K_CENTRE, EBIT_K_FIELDS, EBIT_K_AREA, EBIT_K_COUPLING, EBIT_K_GHF,
@@ -243,9 +243,11 @@ ebit_status ebit_timings(ebit_ctx* ctx, double* ms, int64_t* launches);
  * library holds until exit; it limits grids to 131072 blocks of 32x8 vertices
  * (about 5790x5790 cells) and larger grids return EBIT_EINVAL.  The first call
  * on a device looks up the array's device address (make it before any stream
- * capture); it calls no cudaMalloc/cudaFree.  All calls share the array, so
- * calls that overlap on the GPU (different streams, or other host threads)
- * race and must be serialised by the caller. */
+ * capture) and keeps it for the life of the process: after a cudaDeviceReset
+ * in this process that address is stale, so do not call this entry point on a
+ * device that has been reset.  It calls no cudaMalloc/cudaFree.  All calls
+ * share the array, so calls that overlap on the GPU (different streams, or
+ * other host threads) race and must be serialised by the caller. */
 ebit_status ebit_fraction_noalloc(const ebit_grid* grid, const uint8_t* K, const uint8_t* Z,
                                   const void* sH, const void* sV, void* C, double* area,
                                   int64_t* marker_counts, void* stream);

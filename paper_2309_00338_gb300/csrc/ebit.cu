@@ -87,8 +87,6 @@ ebit_status alloc_ctx(ebit_ctx* c) {
   }
   EBIT_AL(c->C, L.field_bytes);
   EBIT_AL(c->kappa, L.field_bytes);
-  EBIT_AL(c->from_left, L.verdict_bytes);
-  EBIT_AL(c->from_right, L.verdict_bytes);
   EBIT_AL(c->partial, L.partial_count * sizeof(double));
   EBIT_AL(c->area, sizeof(double));
   EBIT_AL(c->ctr, ebit::kCounters * sizeof(unsigned long long));
@@ -175,20 +173,7 @@ ebit_status launch_sweep(ebit_ctx* c, const void* vel, double lam) {
   ebit::GView<R, AX> S{c->K[src], c->Z[src], (const R*)c->sH[src], (const R*)c->sV[src],
                        (const R*)vel, L.d, (R)lam};
   ebit::Buf<R> out{c->K[dst], c->Z[dst], (R*)c->sH[dst], (R*)c->sV[dst]};
-  if (c->gather) {
-    {
-      Timed t(c, EBIT_K_SWEEP);
-      ebit::k_sweep<R, AX><<<L.grid, L.block, 0, c->stream>>>(
-          S, out, line_only, c->from_left, c->from_right, c->ctr, c->cfl_bits, c->status);
-    }
-    ebit::GView<R, AX> Sn{c->K[dst], c->Z[dst], (const R*)c->sH[dst], (const R*)c->sV[dst],
-                          (const R*)vel, L.d, (R)lam};
-    {
-      Timed t(c, EBIT_K_CENTRE);
-      ebit::k_centre<R, AX><<<L.grid, L.block, 0, c->stream>>>(Sn, c->Z[src], c->Z[dst],
-                                                              c->from_left, c->from_right, c->ctr);
-    }
-  } else {
+  {
     constexpr size_t smem = ebit::tile_smem_bytes<R>();
     static bool attr = false;  // once per instantiation and process
     if (!attr) {
@@ -241,8 +226,6 @@ ebit_status new_ctx(ebit_ctx** out, const ebit_grid* grid, void* stream) {
   c->grid = *grid;
   c->L = layout_of(grid);
   c->stream = (cudaStream_t)stream;
-  const char* impl = std::getenv("EBIT_SWEEP");
-  c->gather = impl && std::strcmp(impl, "gather") == 0;
   const ebit_status s = alloc_ctx(c);
   if (s != EBIT_OK) {
     free_ctx(c);

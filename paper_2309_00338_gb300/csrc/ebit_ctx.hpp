@@ -31,10 +31,10 @@ constexpr int kBlockX = 32, kBlockY = 8;  // thread blocks of the per-vertex ker
 struct Layout {
   ebit::Dims d;
   size_t esz;
-  size_t k_bytes, z_bytes, h_bytes, v_bytes, field_bytes, verdict_bytes, partial_count, ghf_bytes;
+  size_t k_bytes, z_bytes, h_bytes, v_bytes, field_bytes, partial_count, ghf_bytes;
   dim3 grid, block;
   size_t total() const {
-    return 2 * (k_bytes + z_bytes + h_bytes + v_bytes) + 2 * field_bytes + 2 * verdict_bytes +
+    return 2 * (k_bytes + z_bytes + h_bytes + v_bytes) + 2 * field_bytes +
            partial_count * sizeof(double) + ghf_bytes + 4096;
   }
 };
@@ -58,7 +58,6 @@ inline Layout layout_of(const ebit_grid* g) {
   L.h_bytes = (size_t)(g->ny + 1) * L.d.P * L.esz;
   L.v_bytes = (size_t)g->ny * L.d.P * L.esz;
   L.field_bytes = (size_t)g->ny * L.d.P * L.esz;
-  L.verdict_bytes = (size_t)g->nx * g->ny;
   L.ghf_bytes = (g->flags & EBIT_CURV_GHF) ? (size_t)g->nx * g->ny * sizeof(int) + 256 : 0;
   L.block = dim3(kBlockX, kBlockY);
   L.grid = dim3((g->nx + 1 + kBlockX - 1) / kBlockX, (g->ny + 1 + kBlockY - 1) / kBlockY);
@@ -79,8 +78,6 @@ struct ebit_ctx {
   int cur = 0;  // buffer holding the current state
   void* C = nullptr;
   void* kappa = nullptr;
-  int8_t* from_left = nullptr;
-  int8_t* from_right = nullptr;
   double* partial = nullptr;
   double* area = nullptr;
   unsigned long long* ctr = nullptr;
@@ -90,9 +87,6 @@ struct ebit_ctx {
   unsigned* ghf_count = nullptr;
   int64_t step_index = 0;
   std::vector<void*> allocs;
-  // EBIT_SWEEP=gather in the environment selects the thread-per-vertex gather
-  // kernels instead of the tiled one (kept for differential testing)
-  bool gather = false;
   // per-kernel event timing (off unless ebit_set_timing)
   bool timing = false;
   struct Mark {

@@ -1,6 +1,5 @@
 // Kernels of the EBIT step besides the tiled sweep and the fused fields: the
-// thread-per-vertex gather sweep (two passes, kept for differential testing),
-// the area sum, initialisation and state I/O.
+// area sum, initialisation and state I/O.
 // Threads map to vertices of the real grid: a warp is 32 consecutive x of one
 // row, aligned to 32, so colour bits pack into 32-bit words with a ballot.
 #pragma once
@@ -9,137 +8,6 @@
 namespace ebit {
 
 constexpr int kBlockY = 8;  // blocks are 32 x kBlockY threads
-
-__device__ __forceinline__ void flush_counters(const int* cnt, unsigned long long* ctr) {
-#pragma unroll
-  for (int c = 0; c < D_NUSED; ++c) {
-    const int v = __reduce_add_sync(0xffffffffu, cnt[c]);
-    if (v != 0 && (threadIdx.x & 31) == 0) atomicAdd(&ctr[c], (unsigned long long)v);
-  }
-}
-
-__device__ __forceinline__ void raise_status(int* status, const int* cnt) {
-  if (cnt[D_CFL]) atomicOr(status, ST_CFL);
-  if (cnt[D_INVARIANT]) atomicOr(status, ST_INVARIANT);
-}
-
-// Pass 1 of a sweep.  Thread at real vertex (x,y) = sweep vertex (i,j):
-//   new corner colour of vertex (i,j), new aligned marker on edge (i,j),
-//   new unaligned marker on edge (i,j) with the centre-rule verdicts it gives
-//   to the cells right (from_left) and left (from_right) of it.
-template <typename R, int AX>
-__global__ void __launch_bounds__(32 * kBlockY)
-k_sweep(GView<R, AX> S, Buf<R> out, int line_only, int8_t* from_left, int8_t* from_right,
-        unsigned long long* ctr, unsigned long long* cfl_bits, int* status) {
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * kBlockY + threadIdx.y;
-  const Dims& d = S.d;
-  const bool in = x <= d.nx && y <= d.ny;
-  const int i = AX ? y : x, j = AX ? x : y;
-  const int tnx = S.tnx(), tny = S.tny();
-  int cnt[D_NUSED];
-#pragma unroll
-  for (int c = 0; c < D_NUSED; ++c) cnt[c] = 0;
-  double dmax = 0.0;
-  int kb = 0;
-  if (in) {
-    kb = S.k(i, j);
-    // Anything to do?  Only if a colour changes along vertex rows j, j+1
-    // within columns i-2..i+2 (all markers this thread looks at live there).
-    bool busy = false;
-    const int c0 = max(i - 2, 0), c1 = min(i + 2, tnx);
-    const int ref = S.k(c0, j);
-    for (int r = j; r <= min(j + 1, tny) && !busy; ++r)
-      for (int c = c0; c <= c1; ++c)
-        if (S.k(c, r) != ref) { busy = true; break; }
-    if (busy) {
-      kb = S.knew(i, j);
-      if (i < tnx) {
-        if (S.k(i, j) != S.k(i + 1, j)) {
-          Flags f;
-          S.advect(Mk{0, i, j}, f);
-          cnt[D_CFL] += f.cfl;
-          cnt[D_WALL_CLAMP] += f.clamp;
-          dmax = fmax(dmax, (double)dabs_of<R>(f));
-        }
-        const Landing<R> L = S.landing(i, j);
-        cnt[D_CANCELLED] += L.cancelled;
-        cnt[D_INVARIANT] += L.invariant;
-        if (L.present) {
-          if (AX) out.sV[(long long)i * d.P + j] = L.kept_fx;
-          else out.sH[(long long)j * d.P + i] = L.kept_fx;
-        }
-      }
-      if (j < tny) {
-        const bool had = S.k(i, j) != S.k(i, j + 1);
-        if (i >= 1 && i <= tnx - 1) {
-          if (had) {
-            Flags f;
-            S.advect(Mk{1, i, j}, f);
-            cnt[D_CFL] += f.cfl;
-            dmax = fmax(dmax, (double)dabs_of<R>(f));
-          }
-          const NewV<R> nv = new_unaligned<R>(S, line_only != 0, i, j, cnt);
-          if (nv.present) {
-            if (AX) out.sH[(long long)i * d.P + j] = nv.s;
-            else out.sV[(long long)j * d.P + i] = nv.s;
-          }
-          // verdict slots are indexed by real cell
-          const long long cr = AX ? (long long)i * d.nx + j : (long long)j * d.nx + i;
-          const long long cl = AX ? (long long)(i - 1) * d.nx + j : (long long)j * d.nx + (i - 1);
-          from_left[cr] = (int8_t)nv.vr;
-          from_right[cl] = (int8_t)nv.vl;
-        } else if (had) {  // wall marker normal to the sweep stays
-          if (AX) out.sH[(long long)i * d.P + j] = S.v(i, j);
-          else out.sV[(long long)j * d.P + i] = S.v(i, j);
-        }
-      }
-    }
-  }
-  const unsigned word = __ballot_sync(0xffffffffu, in && kb);
-  if (threadIdx.x == 0 && y <= d.ny && x <= d.nx) out.K[(long long)y * d.kw + (x >> 5)] = word;
-  flush_counters(cnt, ctr);
-  raise_status(status, cnt);
-  if (dmax > 0.0) atomicMax(cfl_bits, (unsigned long long)__double_as_longlong(dmax));
-}
-
-// Pass 2 of a sweep: centre colour vertices of cells with four markers after
-// the sweep (Sec. 2.3); the verdict from the cell's left (bottom) edge wins.
-template <typename R, int AX>
-__global__ void __launch_bounds__(32 * kBlockY)
-k_centre(GView<R, AX> Snew, const uint32_t* __restrict__ Zold, uint32_t* Zout,
-         const int8_t* __restrict__ from_left, const int8_t* __restrict__ from_right,
-         unsigned long long* ctr) {
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * kBlockY + threadIdx.y;
-  const Dims& d = Snew.d;
-  const bool in = x < d.nx && y < d.ny;
-  int cnt[D_NUSED];
-#pragma unroll
-  for (int c = 0; c < D_NUSED; ++c) cnt[c] = 0;
-  int zb = 0;
-  if (in) {
-    const long long cell = (long long)y * d.nx + x;
-    zb = (__ldg(&Zold[(long long)y * d.zw + (x >> 5)]) >> (x & 31)) & 1;
-    const int i = AX ? y : x, j = AX ? x : y;
-    const int q = corner_mask(Snew, i, j);
-    if (q == 5 || q == 10) {
-      const int a = (i >= 1) ? from_left[cell] : -1;
-      const int b = (i + 1 <= Snew.tnx() - 1) ? from_right[cell] : -1;
-      if (a >= 0) {
-        zb = a;
-        cnt[D_ZSET] += 1;
-        if (b >= 0 && b != a) cnt[D_ZCONFLICT] += 1;
-      } else if (b >= 0) {
-        zb = b;
-        cnt[D_ZSET] += 1;
-      }
-    }
-  }
-  const unsigned word = __ballot_sync(0xffffffffu, in && zb);
-  if (threadIdx.x == 0 && y < d.ny && x < d.nx) Zout[(long long)y * d.zw + (x >> 5)] = word;
-  flush_counters(cnt, ctr);
-}
 
 __device__ __forceinline__ int kbit(const uint32_t* K, const Dims& d, int x, int y) {
   return (__ldg(&K[(long long)y * d.kw + (x >> 5)]) >> (x & 31)) & 1;

@@ -42,7 +42,9 @@ ebit_status fail_na(ebit_status s, const char* fmt, ...) {
 }
 
 // Device address of the scratch array on the current device.  The first call
-// on a device looks it up (with that device current) and caches it.
+// on a device looks it up (with that device current) and caches it for the
+// life of the process; a cudaDeviceReset would make the cached address stale,
+// which the header tells callers.
 ebit_status scratch_address(unsigned long long** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);

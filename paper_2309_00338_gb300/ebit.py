@@ -310,11 +310,33 @@ def ebit_timings(ctx):
     return {KERNEL_NAMES[k]: (ms[k], n[k]) for k in range(len(KERNEL_NAMES))}
 
 
+def _expect(t, name, numel, dtype):
+    """Refuses a tensor whose element count or type does not match what the
+    kernel will read or write, before anything is launched."""
+    if t.numel() != numel or t.dtype != dtype:
+        raise ValueError(f"{name}: expected {numel} elements of {dtype}, got {t.numel()} of {t.dtype}")
+
+
 def ebit_fraction_noalloc(nx, ny, dx, prec, K, Z, sH, sV, C, area, marker_counts=None, stream=None):
     """ebit_fraction_noalloc: fractions of a state in caller-owned device
     tensors (byte colours, fractions of the grid precision) without any
     device allocation; C, area (1 double) and marker_counts (2 int64) are
-    caller-owned device tensors."""
+    caller-owned device tensors.  Sizes and types are checked against nx, ny
+    and prec first (K (ny+1)(nx+1) and Z ny nx uint8, sH (ny+1) nx, sV
+    ny (nx+1) and C ny nx of the precision)."""
+    import torch
+    nx, ny = int(nx), int(ny)
+    if nx < 1 or ny < 1:
+        raise ValueError("nx and ny must be positive")
+    ft = torch.float64 if prec == EBIT_FP64 else torch.float32
+    _expect(K, "K", (ny + 1) * (nx + 1), torch.uint8)
+    _expect(Z, "Z", ny * nx, torch.uint8)
+    _expect(sH, "sH", (ny + 1) * nx, ft)
+    _expect(sV, "sV", ny * (nx + 1), ft)
+    _expect(C, "C", ny * nx, ft)
+    _expect(area, "area", 1, torch.float64)
+    if marker_counts is not None:
+        _expect(marker_counts, "marker_counts", 2, torch.int64)
     g = ebit_grid(nx, ny, dx, prec, 0)
     _check(lib().ebit_fraction_noalloc(ctypes.byref(g), _dev_ptr(K), _dev_ptr(Z), _dev_ptr(sH), _dev_ptr(sV),
                                        _dev_ptr(C), _dev_ptr(area), _dev_ptr(marker_counts), _stream(stream)),

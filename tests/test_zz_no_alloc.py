@@ -62,12 +62,35 @@ def test_noalloc_matches_allocating_fraction_twice(prec):
         assert torch.equal(C, C_ref)
         assert abs(area.item() - area_ref) <= 1e-12 * max(1.0, abs(area_ref))
         assert counts.tolist() == [int(d["counters"][ebit.D_NH]), int(d["counters"][ebit.D_NV])]
+        # and against the oracle's fractions (Sec. 2.5): exact in FP32, where
+        # both round the same double area to float; 1e-12 in FP64; the area
+        # summed in another order agrees to 1e-12
+        C_orc, area_orc = oracle.fraction(S)
+        if prec == 1:
+            assert np.array_equal(C.double().cpu().numpy(), C_orc)
+        else:
+            assert np.max(np.abs(C.cpu().numpy() - C_orc)) <= 1e-12
+        assert abs(area.item() - area_orc) <= 1e-12 * max(1.0, abs(area_orc))
+        assert counts.tolist() == [int(S.hasH.sum()), int(S.hasV.sum())]
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
+    """A grid just past the scratch's limit (5800^2 cells: 132858 blocks of
+    32x8 vertices against 131072) is refused before any launch; the buffers
+    are sized for that grid, so nothing could reach memory outside them."""
+    n = 5800
     dt = torch.float32
-    K = torch.zeros(1, dtype=torch.uint8, device="cuda")
+    K = torch.zeros((n + 1) * (n + 1), dtype=torch.uint8, device="cuda")
+    Z = torch.zeros(n * n, dtype=torch.uint8, device="cuda")
+    sH = torch.zeros((n + 1) * n, dtype=dt, device="cuda")
+    sV = torch.zeros(n * (n + 1), dtype=dt, device="cuda")
+    C = torch.zeros(n * n, dtype=dt, device="cuda")
+    area = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(ebit.EbitError) as e:
-        ebit.ebit_fraction_noalloc(8192, 8192, 1.0 / 8192, 1, K, K, K.to(dt), K.to(dt), K.to(dt),
-                                   torch.zeros(1, dtype=torch.float64, device="cuda"))
+        ebit.ebit_fraction_noalloc(n, n, 1.0 / n, 1, K, Z, sH, sV, C, area)
     assert e.value.status == ebit.EBIT_EINVAL and "scratch" in str(e.value)
+    # the binding refuses buffers that do not match the grid
+    with pytest.raises(ValueError):
+        ebit.ebit_fraction_noalloc(n - 1, n, 1.0 / n, 1, K, Z, sH, sV, C, area)
+    del K, Z, sH, sV, C
+    torch.cuda.empty_cache()
