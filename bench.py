@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-ghf", action="store_true", help="skip the generalised height-function leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--late-from", type=int, default=1000,
+                   help="time a second window from the state after this many steps (0: skip)")
     p.add_argument("--workload", default="cellular_curve_4096",
                    choices=["cellular_curve_4096", "batched", "serving"],
                    help="batched: 512 uneven grids in one batch; serving: Poisson arrivals")
@@ -191,22 +193,33 @@ def traffic_record(kernel):
     return k["dram_bytes_per_cell"], rec
 
 
-def cpu_baseline(wl, budget_s=20.0):
+def cpu_baseline(wl, budget_s=12.0, state=None):
     """The oracle as it stands (FP32-state form, single thread) on whole
-    steps of the same workload from its initial state."""
+    steps of the same workload: from its initial state, and (state given:
+    the GPU's state after step 1000, loaded into the oracle) from there."""
     import oracle
+
+    def timed(S, what):
+        t0 = time.perf_counter()
+        k = 0
+        while True:
+            oracle.step(S, wl.field.u, wl.field.v, wl.dt)
+            k += 1
+            if time.perf_counter() - t0 > budget_s or k >= 8:
+                break
+        t = time.perf_counter() - t0
+        return wl.n * wl.n * k / t, f"{k} whole steps of the {wl.n}^2 workload (FP32 form) from {what}"
+
     S = oracle.init(wl.n, wl.n, wl.dx, wl.scene, oracle.FP32)
-    t0 = time.perf_counter()
-    k = 0
-    while True:
-        oracle.step(S, wl.field.u, wl.field.v, wl.dt)
-        k += 1
-        if time.perf_counter() - t0 > budget_s or k >= 8:
-            break
-    t = time.perf_counter() - t0
-    return {"value": wl.n * wl.n * k / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{k} whole steps of the {wl.n}^2 workload (FP32 form) from its initial state",
-            "host": host_cores()}
+    v0, s0 = timed(S, "its initial state")
+    out = {"value": v0, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": s0, "host": host_cores()}
+    if state is not None:
+        S = oracle.State(wl.n, wl.n, wl.dx, oracle.FP32)
+        S.K[...], S.Z[...], S.sH[...], S.sV[...] = state["K"], state["Z"], state["sH"], state["sV"]
+        S.step_index = state["step_index"]
+        v1, s1 = timed(S, f"the GPU's state after step {state['step_index']}")
+        out["late"] = {"value": v1, "sample": s1}
+    return out
 
 
 def host_cores():
@@ -304,6 +317,90 @@ def timed_steps(torch, ebit, ctx, u, v, dt, K, stream):
     return total, lat
 
 
+def e2e_loop(torch, ebit, ctx, stream, hu, hv, u, v, dt, K, cells, world, barrier, fields):
+    """K steps through the C ABI from host memory: each step's u, v are
+    copied from pinned host buffers (on a second stream, into the other half
+    of a double buffer, while the previous step computes), and each step's
+    area comes back through ebit_area_async; with fields=True its fractions
+    C come back too (ebit_fraction into a device buffer of the caller on the
+    step's stream, then to pinned host memory on the copy stream while the
+    next step runs).  The host takes step k's results once step k+1 is
+    queued.  Returns the e2e record."""
+    n2 = u.shape
+    dbuf = [(torch.empty_like(u), torch.empty_like(v)) for _ in range(2)]
+    copy_stream = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
+    nC = (n2[0] - 1, n2[1] - 1)
+    Cdev = [torch.empty(nC, dtype=u.dtype, device="cuda") for _ in range(2)] if fields else None
+    Chost = [torch.empty(nC, dtype=u.dtype).pin_memory() for _ in range(2)] if fields else None
+    c_ready = [torch.cuda.Event() for _ in range(2)]
+    c_home = [torch.cuda.Event() for _ in range(2)]
+
+    def upload(k):
+        b = k % 2
+        with torch.cuda.stream(copy_stream):
+            if k >= 2:
+                copy_stream.wait_event(freed[b])  # step k-2 has finished with this half
+            dbuf[b][0].copy_(hu, non_blocking=True)
+            dbuf[b][1].copy_(hv, non_blocking=True)
+            copied[b].record(copy_stream)
+
+    areas = torch.zeros(2, dtype=torch.float64).pin_memory()
+    arrived = [torch.cuda.Event() for _ in range(2)]
+    got, csum = [], []
+
+    def take(b):
+        arrived[b].synchronize()
+        got.append(float(areas[b]))
+        if fields:
+            c_home[b].synchronize()
+            csum.append(float(Chost[b][0, 0]) + float(Chost[b][-1, -1]))  # touch the copied values
+
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    copy_stream.wait_event(e0)
+    upload(0)
+    for k in range(K):
+        if k + 1 < K:
+            upload(k + 1)
+        b = k % 2
+        stream.wait_event(copied[b])
+        if fields and k >= 2:
+            stream.wait_event(c_home[b])  # step k-2's C has left this buffer
+        ebit.ebit_step(ctx, dbuf[b][0], dbuf[b][1], dt)
+        freed[b].record(stream)
+        ebit.ebit_area_async(ctx, areas[b:b + 1])
+        arrived[b].record(stream)
+        if fields:
+            ebit.ebit_fraction(ctx, Cdev[b])
+            c_ready[b].record(stream)
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(c_ready[b])
+                Chost[b].copy_(Cdev[b], non_blocking=True)
+                c_home[b].record(copy_stream)
+        if k >= 1:
+            take(1 - b)
+    take((K - 1) % 2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0)), world, "cuda")
+    ebit.ebit_sync(ctx)  # deferred device errors of the e2e steps
+    assert len(got) == K and all(a > 0 for a in got)
+    esz = u.element_size()
+    d2h = 8 + (nC[0] * nC[1] * esz if fields else 0)
+    return {"value": job_value(world, cells, K, ms), "unit": UNIT,
+            "h2d_bytes_per_step": int(hu.numel() * esz + hv.numel() * esz), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": ms / K,
+            "overlap": "inputs of step k+1 copied on a second stream during step k; step k's area"
+                       + (" and fractions C" if fields else "") + " read back while step k+1 runs"}
+
+
 def run_ours(args, wl, world, rank, local):
     import torch
     import torch.distributed as tdist
@@ -368,15 +465,34 @@ def run_ours(args, wl, world, rank, local):
     sm_mhz = clk.get("sm_mhz") or 2070.0
     fp64_peak = FP64_OPS_PER_CLOCK * sm_mhz * 1e6 / 1e9  # Gop/s
     fit_ops = fits_per_launch * FIT_OPS
-    roofline = {"bound": "alu", "pipe": "fp64", "kernel": dom, "achieved": fit_ops / (dom_ms / 1e3) / 1e9,
-                "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
-                "frac": fit_ops / (dom_ms / 1e3) / 1e9 / fp64_peak,
-                "peak_source": f"derived: {FP64_OPS_PER_CLOCK} FP64 ops/clock (152 SMs x 2) x {sm_mhz:.0f} MHz",
-                "algorithmic_flops": fit_ops, "fits_per_launch": fits_per_launch, "flops_per_fit": FIT_OPS,
-                "traffic": None if traffic_cell is None else traffic_cell * cells,
-                "avg_launch_ms": dom_ms,
-                "hbm": {"achieved": dom_gbps, "peak": hbm, "unit": "GB/s", "frac": dom_gbps / hbm,
-                        "algorithmic_bytes": dom_bytes, "peak_source": f"{peak_kind} hbm_gbs (copy)"},
+    # the sweep's own views: its dense byte model against HBM, and its
+    # circle fits against the FP64 pipe, which is what bounds it
+    sweep_view = {"kernel": dom, "avg_launch_ms": dom_ms,
+                  "traffic": None if traffic_cell is None else traffic_cell * cells,
+                  "hbm": {"achieved": dom_gbps, "peak": hbm, "unit": "GB/s", "frac": dom_gbps / hbm,
+                          "algorithmic_bytes": dom_bytes, "bytes_per_cell": kernel_bytes_per_cell(dom, esz),
+                          "peak_source": f"{peak_kind} hbm_gbs (copy)"},
+                  "fp64_pipe": {"bound": "alu", "achieved": fit_ops / (dom_ms / 1e3) / 1e9, "peak": fp64_peak,
+                                "unit": "GFLOP/s (FP64)", "frac": fit_ops / (dom_ms / 1e3) / 1e9 / fp64_peak,
+                                "peak_source": f"derived: {FP64_OPS_PER_CLOCK} FP64 ops/clock (152 SMs x 2) x "
+                                               f"{sm_mhz:.0f} MHz",
+                                "algorithmic_flops": fit_ops, "fits_per_launch": fits_per_launch,
+                                "flops_per_fit": FIT_OPS}}
+    # the metric's roofline: one EBIT step (both sweeps, fields, area) with
+    # the fused-step byte model (32.5 B/cell FP32) against the measured copy
+    # bandwidth; traffic = the ncu DRAM bytes of a step's launches when every
+    # record was taken on the current sources
+    step_model = step_bytes_per_cell(esz) * cells
+    per_step = {k: kt[k][1] / args.steps for k in kt}
+    recs = {k: traffic_record(k)[0] for k in ("sweep", "fields") if per_step.get(k)}
+    step_traffic = (None if any(v is None for v in recs.values())
+                    else sum(recs[k] * per_step[k] * cells for k in recs))
+    roofline = {"bound": "hbm", "kernel": "ebit_step (sweep x2, fields, area)",
+                "achieved": step_model / (ms_per_step / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": step_model / (ms_per_step / 1e3) / 1e9 / hbm,
+                "peak_source": f"{peak_kind} hbm_gbs (copy)", "algorithmic_bytes": step_model,
+                "bytes_per_cell": step_bytes_per_cell(esz), "traffic": step_traffic,
+                "avg_step_ms": ms_per_step, "dominant": sweep_view,
                 "kernels": {k: {"ms_per_launch": (t / max(1, nl)), "launches": nl,
                                 "share": t / max(1e-12, sum(tt for tt, _ in kt.values())),
                                 "GBps": kernel_bytes_per_cell(k, esz) * cells / (t / max(1, nl) / 1e3) / 1e9
@@ -385,68 +501,43 @@ def run_ours(args, wl, world, rank, local):
     c_traffic, _ = traffic_record("coupling")
     coupling = coupling_roofline(kc, n, esz, hbm, peak_kind)
     coupling["traffic"] = None if c_traffic is None else c_traffic * cells
-    step_model = step_bytes_per_cell(esz) * cells
-    step_roof = {"bytes_per_cell": step_bytes_per_cell(esz), "achieved_GBps": step_model / (ms_per_step / 1e3) / 1e9,
-                 "frac": step_model / (ms_per_step / 1e3) / 1e9 / hbm}
 
     # end to end through the C ABI with host buffers: every step copies its
-    # u, v from pinned host memory and reads the step's area back.  The copy
-    # of step k+1's inputs runs on a second stream into the other half of a
-    # double buffer while step k computes (ordered by events), as a caller
-    # that streams its velocities would do.
+    # u, v from pinned host memory and reads the step's results back.  The
+    # copy of step k+1's inputs runs on a second stream into the other half
+    # of a double buffer while step k computes (ordered by events), as a
+    # caller that streams its velocities would do.
     hu = torch.from_numpy(wl.field.u.astype(np.float32)).pin_memory()
     hv = torch.from_numpy(wl.field.v.astype(np.float32)).pin_memory()
-    dbuf = [(torch.empty_like(u), torch.empty_like(v)) for _ in range(2)]
-    copy_stream = torch.cuda.Stream()
-    copied = [torch.cuda.Event() for _ in range(2)]
-    freed = [torch.cuda.Event() for _ in range(2)]
+    e2e = e2e_loop(torch, ebit, ctx, stream, hu, hv, u, v, wl.dt, args.steps, cells, world, barrier,
+                   fields=True)
+    e2e["area_only"] = e2e_loop(torch, ebit, ctx, stream, hu, hv, u, v, wl.dt, args.steps, cells, world,
+                                barrier, fields=False)
 
-    def upload(k):
-        b = k % 2
-        with torch.cuda.stream(copy_stream):
-            if k >= 2:
-                copy_stream.wait_event(freed[b])  # step k-2 has finished with this half
-            dbuf[b][0].copy_(hu, non_blocking=True)
-            dbuf[b][1].copy_(hv, non_blocking=True)
-            copied[b].record(copy_stream)
-
-    # every step's area comes back through ebit_area_async into pinned memory;
-    # the host reads step k's value once step k+1 is queued behind it
-    areas = torch.zeros(2, dtype=torch.float64).pin_memory()
-    arrived = [torch.cuda.Event() for _ in range(2)]
-    got = []
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    copy_stream.wait_event(e0)
-    upload(0)
-    for k in range(args.steps):
-        if k + 1 < args.steps:
-            upload(k + 1)
-        b = k % 2
-        stream.wait_event(copied[b])
-        ebit.ebit_step(ctx, dbuf[b][0], dbuf[b][1], wl.dt)
-        freed[b].record(stream)
-        ebit.ebit_area_async(ctx, areas[b:b + 1])
-        arrived[b].record(stream)
-        if k >= 1:
-            arrived[1 - b].synchronize()
-            got.append(float(areas[1 - b]))
-    arrived[(args.steps - 1) % 2].synchronize()
-    got.append(float(areas[(args.steps - 1) % 2]))
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    e2e_ms = max_over_ranks(max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0)), world, "cuda")
-    ebit.ebit_sync(ctx)  # deferred device errors of the e2e steps
-    assert len(got) == args.steps and all(a > 0 for a in got)
-    e2e = {"value": job_value(world, cells, args.steps, e2e_ms), "unit": UNIT,
-           "h2d_bytes_per_step": int(hu.numel() * 4 + hv.numel() * 4), "d2h_bytes_per_step": 8,
-           "overlap": "inputs of step k+1 copied on a second stream during step k; step k's area "
-                      "read (ebit_area_async) while step k+1 runs"}
+    # a second timed window from the state after 1000 steps, past the first
+    # merges and break-ups of the disks (the steps up to it run untimed)
+    late = None
+    late_state = None
+    done_steps = ebit.ebit_get_state(ctx, n, n)["step_index"]
+    if args.late_from > 0:
+        for _ in range(max(0, args.late_from - done_steps)):
+            ebit.ebit_step(ctx, u, v, wl.dt)
+        ebit.ebit_sync(ctx)
+        torch.cuda.synchronize()
+        barrier()
+        tl, latl = timed_steps(torch, ebit, ctx, u, v, wl.dt, args.steps, stream)
+        barrier()
+        ebit.ebit_sync(ctx)
+        dl = ebit.ebit_diagnostics(ctx)["counters"]
+        tl = max_over_ranks(tl, world, "cuda")
+        late = {"from_step": max(args.late_from, done_steps), "value": job_value(world, cells, args.steps, tl),
+                "unit": UNIT, "ms_per_step": tl / args.steps,
+                "p50_ms": float(np.percentile(latl, 50)), "p99_ms": float(np.percentile(latl, 99)),
+                "step_roofline_frac": step_model / (tl / args.steps / 1e3) / 1e9 / hbm,
+                "last_step": {"cancelled": int(dl[ebit.D_CANCELLED]), "zset": int(dl[ebit.D_ZSET]),
+                              "nH": int(dl[ebit.D_NH]), "nV": int(dl[ebit.D_NV])}}
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            late_state = ebit.ebit_get_state(ctx, n, n)
     ebit.ebit_destroy(ctx)
 
     # the same FP32 steps with the generalised height-function fallbacks on
@@ -500,7 +591,7 @@ def run_ours(args, wl, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl)
+        cpu = cpu_baseline(wl, state=late_state)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -513,7 +604,7 @@ def run_ours(args, wl, world, rank, local):
                            "l2": "working set (~0.45 GB) larger than L2, no flush"},
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(round(launches_per_step * args.steps)),
-                "roofline": roofline, "step_roofline": step_roof, "coupling": coupling, "ghf": ghf,
+                "roofline": roofline, "late_window": late, "coupling": coupling, "ghf": ghf,
                 "fp64": fp64,
                 "cpu_baseline": cpu,
                 "markers": {"nH": int(diag["counters"][0]), "nV": int(diag["counters"][1])}}
