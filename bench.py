@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-ghf", action="store_true", help="skip the generalised height-function leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--record-traffic", nargs="+", metavar="NCU_CSV",
+                   help="write profiles/dram_traffic.json from ncu CSV logs of the headline workload and exit")
     p.add_argument("--late-from", type=int, default=1000,
                    help="time a second window from the state after this many steps (0: skip)")
     p.add_argument("--workload", default="cellular_curve_4096",
@@ -52,8 +54,10 @@ def parse():
                    help="batched: 512 uneven grids in one batch; serving: Poisson arrivals")
     p.add_argument("--instances", type=int, default=512, help="batched: number of grids")
     p.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
-    p.add_argument("--serve-seconds", type=float, default=2.0, help="serving: arrival window")
-    p.add_argument("--serve-cap", type=float, default=90.0, help="serving: wall-clock cap (s)")
+    p.add_argument("--serve-seconds", type=float, default=10.0, help="serving: arrival window")
+    p.add_argument("--serve-cap", type=float, default=180.0, help="serving: wall-clock cap (s)")
+    p.add_argument("--one-at-a-time", type=int, default=64,
+                   help="batched: grids of the random sample run one at a time in plain FP64")
     return p.parse_args()
 
 
@@ -177,6 +181,42 @@ def kernel_source_hash(kernel):
         with open(os.path.join(ROOT, "paper_2309_00338_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
+
+
+def record_traffic(paths, cells, workload, command):
+    """Writes profiles/dram_traffic.json from ncu CSV logs (one per kernel,
+    taken with --metrics dram__bytes_read.sum,dram__bytes_write.sum on the
+    benchmark's workload): per kernel the mean DRAM bytes per launch and per
+    cell, keyed to a hash of the kernel's current sources."""
+    import csv
+    kinds = {"k_sweep_tile": "sweep", "k_fields_tile": "fields", "k_coupling": "coupling"}
+    per = {}
+    for path in paths:
+        with open(path) as f:
+            rows = [r for r in csv.reader(l for l in f if l.startswith('"'))]
+        head, body = rows[0], rows[1:]
+        ik, im, iv = head.index("Kernel Name"), head.index("Metric Name"), head.index("Metric Value")
+        iu = head.index("Metric Unit") if "Metric Unit" in head else None
+        scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+        for r in body:
+            kind = next((v for k, v in kinds.items() if k in r[ik]), None)
+            if kind is None or not r[im].startswith("dram__bytes"):
+                continue
+            val = float(r[iv].replace(",", "")) * (scale.get(r[iu], 1.0) if iu is not None else 1.0)
+            e = per.setdefault(kind, {"kernel": r[ik].split("(")[0].strip(), "read": [], "write": [],
+                                      "path": path})
+            e["read" if "read" in r[im] else "write"].append(val)
+    out = {"workload": workload, "kernels": {}}
+    for kind, e in per.items():
+        rd, wr = float(np.mean(e["read"])), float(np.mean(e["write"]))
+        out["kernels"][kind] = {
+            "kernel": e["kernel"], "launches_captured": len(e["read"]),
+            "dram_bytes_read": rd, "dram_bytes_write": wr, "dram_bytes_per_cell": (rd + wr) / cells,
+            "source": command.get(kind, ""), "sources": KERNEL_SOURCES[kind],
+            "sources_sha256": kernel_source_hash(kind)}
+    with open(os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    return out
 
 
 def traffic_record(kernel):
@@ -683,10 +723,16 @@ def run_batched(args):
                      "e_area_reversed_max": float(np.max(ea)) if ea else None,
                      "autotune": {"schedule": st["schedule"], "tuned_sets": st["tuned_sets"],
                                   "tune_ms": st["tune_ms"]}}
-    sub = specs[:16]
+    # plain FP64 one grid at a time on a seeded random sample of the grids
+    from paper_2309_00338_gb300 import workloads as W
+    pick = W.Rng(230900342)
+    idx = sorted(set(min(len(specs) - 1, int(pick.uniform() * len(specs)))
+                     for _ in range(4 * args.one_at_a_time)))[:args.one_at_a_time]
+    sub = [specs[i] for i in idx]
     res, st, wall = _serve(ebit, sub, 0, budget, max_instances=1)
-    out["fp64_one_at_a_time"] = {"instances": len(sub), "cell_updates": st["cell_updates"],
-                                 "gpu_ms": st["busy_ms"], "value": st["cell_updates"] / (st["busy_ms"] / 1e3)}
+    out["fp64_one_at_a_time"] = {"instances": len(sub), "sample": "seeded random sample (seed 230900342)",
+                                 "cell_updates": st["cell_updates"], "gpu_ms": st["busy_ms"],
+                                 "value": st["cell_updates"] / (st["busy_ms"] / 1e3)}
     total = sum(sp["n"] ** 2 * sp["steps"] for sp in specs)
     line = {"metric": "EBIT cell-updates/s, batched uneven grids", "value": out["fp32"]["value"],
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
@@ -744,8 +790,20 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+TRAFFIC_COMMAND = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                   "--clock-control none -k regex:{k} -s {s} -c {c} --csv --log-file {log} python bench.py "
+                   "--steps 1 --warmup 1 --no-cpu-baseline --no-fp64 --no-ghf --late-from 0")
+
+
 def main():
     args = parse()
+    if args.record_traffic:
+        cmds = {"sweep": TRAFFIC_COMMAND.format(k="k_sweep_tile", s=2, c=2, log="dram_sweep.csv"),
+                "fields": TRAFFIC_COMMAND.format(k="k_fields_tile", s=2, c=1, log="dram_fields.csv"),
+                "coupling": TRAFFIC_COMMAND.format(k="k_coupling", s=3, c=1, log="dram_coupling.csv")}
+        print(json.dumps(record_traffic(args.record_traffic, 4096 * 4096,
+                                        "cellular_curve_n4096 FP32 form (the bench headline)", cmds), indent=1))
+        return
     world, rank, local = dist()
     if args.workload == "batched":
         return run_batched(args)

@@ -41,7 +41,8 @@ typedef enum {
   EBIT_EINVARIANT = -4,  /* colour/marker parity broken (must not happen)    */
   EBIT_ECUDA = -5,       /* CUDA runtime error                               */
   EBIT_ETIMEOUT = -6,    /* a bounded wait ran out                           */
-  EBIT_EFULL = -7        /* request can never fit the server's memory budget */
+  EBIT_EFULL = -7,       /* request can never fit the server's memory budget */
+  EBIT_ECANCELLED = -8   /* the request was cancelled (ebit_cancel)          */
 } ebit_status;
 
 typedef enum { EBIT_FP64 = 0, EBIT_FP32 = 1 } ebit_precision;
@@ -222,7 +223,8 @@ const char* ebit_last_error(void);
  * milliseconds and the number of launches since the last call, then resets.
  * Kinds: EBIT_K_SWEEP (a split sweep), EBIT_K_CENTRE (reserved, always 0),
  * EBIT_K_FIELDS (fractions, curvature and area
- * partials), EBIT_K_AREA (area sum), EBIT_K_COUPLING (ebit_coupling),
+ * sum, added up by the launch's last tile), EBIT_K_AREA (reserved, always 0),
+ * EBIT_K_COUPLING (ebit_coupling),
  * EBIT_K_GHF (list and fits of the generalised fallbacks). */
 enum { EBIT_K_SWEEP = 0, EBIT_K_CENTRE, EBIT_K_FIELDS, EBIT_K_AREA, EBIT_K_COUPLING, EBIT_K_GHF,
        EBIT_K_COUNT = 8 };
@@ -283,10 +285,20 @@ typedef struct {
   void* C_out;                 /* optional HOST buffer of n*n elements (request
                                   precision) receiving the final fractions; must
                                   stay valid until the result has been polled */
+  int32_t fault_after;         /* fault injection for testing the server's failure
+                                  isolation: from step fault_after on, dt is
+                                  multiplied by fault_dt_factor (ignored when
+                                  fault_dt_factor is 0); a factor that takes a
+                                  marker past one cell makes the request fail with
+                                  EBIT_ECFL, which stops it and no other */
+  double fault_dt_factor;
 } ebit_request;
 
 typedef struct {
-  int32_t status;              /* EBIT_OK, or why the request failed */
+  int32_t status;              /* EBIT_OK, or why the request failed or stopped:
+                                  EBIT_ECFL / EBIT_EINVARIANT (detected after the
+                                  batch step that raised it; the request stops
+                                  there), EBIT_ECANCELLED, EBIT_ECUDA */
   int64_t steps;               /* steps done */
   double area0, area;          /* sum C dx^2 at admission and at the end */
   double e_area;               /* |area - area0| / area0 (Eq. 13) */
@@ -337,6 +349,12 @@ ebit_status ebit_submit(ebit_server* s, const ebit_request* req, uint64_t* ticke
 /* EBIT_EAGAIN while the request is queued or running; EBIT_OK with the result
  * once (the result is then released); EBIT_EINVAL for an unknown ticket. */
 ebit_status ebit_poll(ebit_server* s, uint64_t ticket, ebit_result* out);
+/* Cancels a request: a queued one is dropped at once, a running one leaves
+ * the batch before the next batch step (the steps done so far are reported).
+ * Its result (status EBIT_ECANCELLED) is then polled as usual; the other
+ * requests are not affected.  EBIT_EINVAL for an unknown or finished ticket.
+ * Thread-safe. */
+ebit_status ebit_cancel(ebit_server* s, uint64_t ticket);
 ebit_status ebit_server_stats_get(ebit_server* s, ebit_server_stats* out);
 /* Cancels queued requests, finishes nothing further, frees everything. */
 void ebit_server_destroy(ebit_server* s);

@@ -89,6 +89,7 @@ ebit_status alloc_ctx(ebit_ctx* c) {
   EBIT_AL(c->kappa, L.field_bytes);
   EBIT_AL(c->partial, L.partial_count * sizeof(double));
   EBIT_AL(c->area, sizeof(double));
+  EBIT_AL(c->area_done, sizeof(unsigned));
   EBIT_AL(c->ctr, ebit::kCounters * sizeof(unsigned long long));
   EBIT_AL(c->cfl_bits, sizeof(unsigned long long));
   EBIT_AL(c->status, sizeof(int));
@@ -114,14 +115,14 @@ ebit_status launch_fields(ebit_ctx* c) {
   if (ghf) EBIT_CK(cudaMemsetAsync(c->ghf_count, 0, sizeof(unsigned), c->stream));
   {
     Timed t(c, EBIT_K_FIELDS);
+    ebit::AreaSum sum;
+    sum.done = c->area_done;
+    sum.n = (long long)fgrid.x * fgrid.y;
+    sum.scale = c->grid.dx * c->grid.dx;
+    sum.area = c->area;
     ebit::k_fields_tile<R><<<fgrid, ebit::field_threads<R>(), 0, c->stream>>>(
         c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], L.d, (R)c->grid.dx, (R*)c->C,
-        (R*)c->kappa, c->partial, c->ctr, ghf ? c->ghf_list : nullptr, ghf ? c->ghf_count : nullptr);
-  }
-  {
-    Timed t(c, EBIT_K_AREA);
-    ebit::k_area<<<1, ebit::kAreaThreads, 0, c->stream>>>(c->partial, (long long)fgrid.x * fgrid.y,
-                                           c->grid.dx * c->grid.dx, c->area);
+        (R*)c->kappa, c->partial, c->ctr, ghf ? c->ghf_list : nullptr, ghf ? c->ghf_count : nullptr, sum);
   }
   if (ghf) {
     Timed t(c, EBIT_K_GHF);
@@ -259,15 +260,20 @@ ebit_status init_scene(ebit_ctx* c, const ebit_scene* scene) {
     for (int k = 0; k < scene->curve->nmodes; ++k) curve.push_back(scene->curve->amp[k]);
     for (int k = 0; k < scene->curve->nmodes; ++k) curve.push_back(scene->curve->phase[k]);
   }
-  // scene arrays and scratch: freed at the end of the call
+  // scene arrays and scratch: stream-ordered allocations freed at the end of
+  // the call, so that setting up a grid does not wait for work on other
+  // streams (a batch step of the server runs while it admits new grids)
   std::vector<void*> tmp;
   auto talloc = [&](void** p, size_t bytes) -> ebit_status {
-    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
-    if (e != cudaSuccess) { cudaGetLastError(); return fail(EBIT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)); }
+    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, c->stream);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(EBIT_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e)); }
     tmp.push_back(*p);
     return EBIT_OK;
   };
-  auto cleanup = [&]() { cudaStreamSynchronize(c->stream); for (void* p : tmp) cudaFree(p); };
+  auto cleanup = [&]() {
+    for (void* p : tmp) cudaFreeAsync(p, c->stream);
+    cudaStreamSynchronize(c->stream);
+  };
   double *dcirc = nullptr, *dcurve = nullptr, *hv = nullptr, *dnotch = nullptr;
   int *ownH = nullptr, *ownV = nullptr;
   ebit_status s;

@@ -80,6 +80,7 @@ struct ebit_ctx {
   void* kappa = nullptr;
   double* partial = nullptr;
   double* area = nullptr;
+  unsigned* area_done = nullptr;    // tiles of the fields launch done (reset by its last tile)
   unsigned long long* ctr = nullptr;
   unsigned long long* cfl_bits = nullptr;
   int* status = nullptr;

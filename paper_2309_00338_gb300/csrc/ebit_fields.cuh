@@ -1,5 +1,6 @@
 // Fused fields kernel: volume fractions C, height-function curvature kappa,
-// the area partial sums and the marker counts of a state (Sec. 2.5), one
+// the area (per-tile partial sums, added up by the launch's last tile) and
+// the marker counts of a state (Sec. 2.5), one
 // 64x32 tile of cells per block with a 3-cell halo for the 7x3 height
 // stencils.
 //
@@ -84,6 +85,18 @@ __device__ __forceinline__ void store4(double* p, double a, double b, double c, 
   reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
 }
 
+// Where the tiles' area partials are summed: with `done` set, the last tile
+// of the launch to finish (counted on *done, which it then resets to 0) adds
+// all n partials in the order of k_area (thread t takes partials t, t + 256,
+// ..., then a tree over the threads), so the area is the same as a separate
+// k_area launch gives, without that launch.
+struct AreaSum {
+  unsigned* done = nullptr;
+  long long n = 0;
+  double scale = 0.0;
+  double* area = nullptr;
+};
+
 // The tile (bx, by) of one grid; its area partial goes to partial[slot].
 // With ghf_list, the interface cells left without a 7x3 stencil are
 // appended to it (ghf_count, zeroed before the launch, counts them): one
@@ -94,7 +107,8 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
                                             const R* __restrict__ sH, const R* __restrict__ sV,
                                             const Dims& d, R dx, R* C, R* kappa, double* partial,
                                             long long slot, unsigned long long* ctr, int bx, int by,
-                                            int* ghf_list = nullptr, unsigned* ghf_count = nullptr) {
+                                            int* ghf_list = nullptr, unsigned* ghf_count = nullptr,
+                                            AreaSum sum = AreaSum()) {
   constexpr int kFieldThreads = field_threads<R>();
   __shared__ uint32_t kw[kFVY * kFW];  // vertex colours
   __shared__ uint32_t zw[kFRY * kFW];  // centre colours
@@ -107,6 +121,7 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
   __shared__ int s_cnt[D_NUSED];
   __shared__ unsigned long long s_full;
   __shared__ unsigned s_nghf, s_ghf_base;
+  __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i0 = bx * kFX, j0 = by * kFY;
   const int rx0 = i0 - kFH, ry0 = j0 - kFH;
@@ -326,6 +341,11 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
     for (int w = 0; w < kFieldThreads / 32; ++w) p = p + s_wsum[w];
     if (s_full) p = p + (double)s_full;
     partial[slot] = p;
+    s_last = 0;
+    if (sum.done) {
+      __threadfence();  // the partial is visible before the count says so
+      s_last = atomicAdd(sum.done, 1u) == (unsigned)(sum.n - 1);
+    }
   }
   if (tid < D_NUSED && s_cnt[tid] != 0) atomicAdd(&ctr[tid], (unsigned long long)s_cnt[tid]);
   if (ghf_list) {
@@ -346,16 +366,35 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
       }
     }
   }
+  __syncthreads();
+  if (s_last) {  // the same in every thread of the block: set before a barrier
+    static_assert(field_threads<R>() == 256, "the area order of k_area assumes 256 threads");
+    __shared__ double red[256];
+    __threadfence();
+    double a = 0.0;
+    for (long long b = tid; b < sum.n; b += 256) a = a + __ldcg(&partial[b]);
+    red[tid] = a;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (tid < s) red[tid] = red[tid] + red[tid + s];
+      __syncthreads();
+    }
+    if (tid == 0) {
+      *sum.area = red[0] * sum.scale;
+      *sum.done = 0u;  // ready for the next launch (stream order)
+    }
+  }
 }
 
 template <typename R>
 __global__ void __launch_bounds__(field_threads<R>(), fields_min_blocks<R>())
 k_fields_tile(const uint32_t* __restrict__ K, const uint32_t* __restrict__ Z,
               const R* __restrict__ sH, const R* __restrict__ sV, Dims d, R dx, R* C, R* kappa,
-              double* partial, unsigned long long* ctr, int* ghf_list, unsigned* ghf_count) {
+              double* partial, unsigned long long* ctr, int* ghf_list, unsigned* ghf_count,
+              AreaSum sum) {
   fields_tile<R>(K, Z, sH, sV, d, dx, C, kappa, partial,
                  (long long)blockIdx.y * gridDim.x + blockIdx.x, ctr, blockIdx.x, blockIdx.y, ghf_list,
-                 ghf_count);
+                 ghf_count, sum);
 }
 
 // Many grids in one launch (work items: grid, tile).

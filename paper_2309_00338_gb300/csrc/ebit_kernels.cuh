@@ -1,5 +1,5 @@
-// Kernels of the EBIT step besides the tiled sweep and the fused fields: the
-// area sum, initialisation and state I/O.
+// Kernels besides the tiled sweep and the fused fields: initialisation and
+// state I/O.
 // Threads map to vertices of the real grid: a warp is 32 consecutive x of one
 // row, aligned to 32, so colour bits pack into 32-bit words with a ballot.
 #pragma once
@@ -11,24 +11,6 @@ constexpr int kBlockY = 8;  // blocks are 32 x kBlockY threads
 
 __device__ __forceinline__ int kbit(const uint32_t* K, const Dims& d, int x, int y) {
   return (__ldg(&K[(long long)y * d.kw + (x >> 5)]) >> (x & 31)) & 1;
-}
-
-// Sum of the per-block partials in a fixed order (one block of kAreaThreads;
-// a thread adds every kAreaThreads-th partial, then a tree over the threads).
-// 256 threads: 1024 took 12.6 us at 4096^2 against 10.5.
-constexpr int kAreaThreads = 256;
-__global__ void __launch_bounds__(kAreaThreads)
-k_area(const double* __restrict__ partial, long long n, double scale, double* area) {
-  __shared__ double red[kAreaThreads];
-  double acc = 0.0;
-  for (long long b = threadIdx.x; b < n; b += kAreaThreads) acc = acc + partial[b];
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int s = kAreaThreads / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *area = red[0] * scale;
 }
 
 // ---------------------------------------------------------------------------

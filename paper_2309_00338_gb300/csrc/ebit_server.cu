@@ -13,9 +13,15 @@
 // step (first sweep A->B, second B->A).
 //
 // Serving: one worker thread owns the GPU.  Between batch steps it retires
-// finished grids (results copied to the host, memory freed) and admits queued
-// requests, first come first served among those that fit, while the sum of
-// their device footprints stays within the budget: continuous batching.
+// finished, failed and cancelled grids (results copied to the host, memory
+// freed) and admits queued requests, first come first served among those that
+// fit, while the sum of their device footprints stays within the budget:
+// continuous batching.  While a batch step runs on the server's stream, the
+// worker admits the requests that arrived meanwhile on a second stream (their
+// grids join from the next step), so admission overlaps the GPU work.  The
+// last launch of a batch step copies every grid's status word into host-mapped
+// memory; a grid whose step raised a CFL or invariant error leaves the batch
+// with that status, and the others carry on unchanged.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -24,9 +30,11 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <vector>
 
@@ -107,6 +115,13 @@ __global__ void k_area_batch(const AreaDesc* __restrict__ descs) {
   if (threadIdx.x == 0) *D.area = red[0] * D.scale;
 }
 
+// Every grid's status word, gathered into host-mapped memory at the end of a
+// batch step (one thread per grid).
+__global__ void k_status_gather(int* const* __restrict__ status, int n, int* out) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) out[g] = *status[g];
+}
+
 struct Instance {
   uint64_t ticket = 0;
   ebit_request req{};
@@ -120,7 +135,8 @@ struct Instance {
   double area0 = 0.0;
   double t_submit = 0.0, t_admit = 0.0;
   std::vector<float> lat_ms;
-  ebit_status failed = EBIT_OK;  // set when a batch step it took part in failed
+  ebit_status failed = EBIT_OK;  // set when a batch step it took part in failed,
+                                 // its status word reported an error, or it was cancelled
 };
 
 size_t request_bytes(const ebit_request& r) {
@@ -252,7 +268,8 @@ struct Group {
       ebit_ctx* c = in->ctx;
       const int A = c->cur, B = 1 - c->cur;
       const double t = in->done * in->dt;
-      const double dte = in->req.field == EBIT_FIELD_VORTEX ? in->dt * std::cos(M_PI * t / in->req.period) : in->dt;
+      double dte = in->req.field == EBIT_FIELD_VORTEX ? in->dt * std::cos(M_PI * t / in->req.period) : in->dt;
+      if (in->req.fault_dt_factor != 0.0 && in->done >= in->req.fault_after) dte *= in->req.fault_dt_factor;
       const R lam = (R)(dte / c->grid.dx);
       const int x_first = ((c->step_index & 1) == 0);
       const int lo = (c->grid.flags & EBIT_FIT_LINE) ? 1 : 0;
@@ -340,18 +357,27 @@ struct ebit_server {
   std::vector<std::unique_ptr<Instance>> active;
   std::map<uint64_t, ebit_result> done;
   std::map<uint64_t, int> pending;  // tickets queued or running
+  std::set<uint64_t> cancels;       // running tickets to cancel at the next step boundary
   std::thread worker;
   bool started = false;
   // statistics
   int64_t batch_steps = 0, cell_updates = 0;
   double busy_ms = 0.0;
   // worker-only
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;        // batch steps
+  cudaStream_t admit_stream = nullptr;  // initialisation of admitted grids
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   Group<float> g32;
   Group<double> g64;
+  // status words of the grids of the current plan, gathered each step
+  int** d_status = nullptr;  // device array of the grids' status pointers
+  int* h_status = nullptr;   // host-mapped copy written by k_status_gather
+  int* h_status_dev = nullptr;
+  std::vector<Instance*> stepping;  // the grids of the step in flight, plan order
   bool dirty = true;   // the set of grids changed: new plans, new schedule choice
   bool replan = false; // same set, another schedule (autotuning)
   cudaGraphExec_t graph = nullptr;
+  std::function<ebit_status()> launch_plain;  // the step's launches when graphs are off
   // CTA-schedule autotuner: the first kTuneSteps steps of a new set of grids
   // run under each schedule in turn (the work and its results do not depend
   // on the order, so no step is wasted); the fastest is kept for the set and
@@ -369,16 +395,24 @@ struct ebit_server {
   void tune_after(float ms);
 
   void run();
+  void take_admissible(std::vector<std::unique_ptr<Instance>>& out);  // caller holds mu
+  void admit_all(std::vector<std::unique_ptr<Instance>>& admitted);
   ebit_status admit(Instance* in);
   void retire(size_t idx);
-  ebit_status step();
+  ebit_status plan();
+  ebit_status step_launch();
+  ebit_status step_finish();
+  void release_status();
 };
 
 ebit_status ebit_server::admit(Instance* in) {
   const ebit_request& r = in->req;
   ebit_grid g{r.n, r.n, 1.0 / r.n, r.prec, r.flags};
   ebit_scene sc{in->circles.empty() ? nullptr : in->circles.data(), (int32_t)in->circles.size(), nullptr, nullptr};
-  ebit_status s = ebit_init(&in->ctx, &g, &sc, stream);
+  // the grid is set up on the admission stream, so that a batch step in
+  // flight on the server's stream goes on meanwhile; its context keeps that
+  // stream for its own calls (area, status) between batch steps
+  ebit_status s = ebit_init(&in->ctx, &g, &sc, admit_stream);
   if (s != EBIT_OK) return s;
   const size_t esz = r.prec == EBIT_FP32 ? 4 : 8;
   const size_t vb = (size_t)(r.n + 1) * (r.n + 1) * esz;
@@ -388,32 +422,37 @@ ebit_status ebit_server::admit(Instance* in) {
   }
   const int nb = (int)(((long long)(r.n + 1) * (r.n + 1) + 255) / 256);
   if (r.prec == EBIT_FP32)
-    k_velocity<float><<<nb, 256, 0, stream>>>(r.field, r.n, 1.0 / r.n, r.omega, r.cx, r.cy, r.drift_u, r.drift_v, (float*)in->u, (float*)in->v);
+    k_velocity<float><<<nb, 256, 0, admit_stream>>>(r.field, r.n, 1.0 / r.n, r.omega, r.cx, r.cy, r.drift_u, r.drift_v, (float*)in->u, (float*)in->v);
   else
-    k_velocity<double><<<nb, 256, 0, stream>>>(r.field, r.n, 1.0 / r.n, r.omega, r.cx, r.cy, r.drift_u, r.drift_v, (double*)in->u, (double*)in->v);
+    k_velocity<double><<<nb, 256, 0, admit_stream>>>(r.field, r.n, 1.0 / r.n, r.omega, r.cx, r.cy, r.drift_u, r.drift_v, (double*)in->u, (double*)in->v);
   in->dx = 1.0 / r.n;
   in->dt = r.cfl * in->dx / field_umax(r);
   if ((s = ebit_fraction(in->ctx, nullptr, &in->area0)) != EBIT_OK) return s;
-  cudaMemsetAsync(in->ctx->ctr, 0, ebit::kCounters * sizeof(unsigned long long), stream);
+  cudaMemsetAsync(in->ctx->ctr, 0, ebit::kCounters * sizeof(unsigned long long), admit_stream);
+  if (cudaStreamSynchronize(admit_stream) != cudaSuccess) return fail_s(EBIT_ECUDA, "admission");
   in->t_admit = now_ms();
   return EBIT_OK;
 }
 
 void ebit_server::retire(size_t idx) {
   Instance* in = active[idx].get();
+  const cudaStream_t cs = in->ctx->stream;
   ebit_result res{};
   res.status = EBIT_OK;
   res.steps = in->done;
   res.area0 = in->area0;
   unsigned long long ctr[ebit::kCounters] = {0};
   ebit_status s = ebit_fraction(in->ctx, nullptr, &res.area);
+  // a CFL or invariant status was already taken into `failed`; the copy of
+  // the results below still runs
+  if (s == EBIT_ECFL || s == EBIT_EINVARIANT) s = EBIT_OK;
   if (s == EBIT_OK) {
-    cudaMemcpyAsync(ctr, in->ctx->ctr, sizeof ctr, cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(ctr, in->ctx->ctr, sizeof ctr, cudaMemcpyDeviceToHost, cs);
     if (in->req.C_out)
       cudaMemcpy2DAsync(in->req.C_out, (size_t)in->req.n * (in->req.prec == EBIT_FP32 ? 4 : 8),
                         in->ctx->C, (size_t)in->ctx->L.d.P * in->ctx->L.esz,
-                        (size_t)in->req.n * in->ctx->L.esz, in->req.n, cudaMemcpyDeviceToHost, stream);
-    if (cudaStreamSynchronize(stream) != cudaSuccess) s = EBIT_ECUDA;
+                        (size_t)in->req.n * in->ctx->L.esz, in->req.n, cudaMemcpyDeviceToHost, cs);
+    if (cudaStreamSynchronize(cs) != cudaSuccess) s = EBIT_ECUDA;
   }
   res.status = in->failed != EBIT_OK ? in->failed : s;
   for (int t = 0; t < EBIT_D_COUNT; ++t) res.counters[t] = (int64_t)ctr[t];
@@ -434,6 +473,7 @@ void ebit_server::retire(size_t idx) {
     std::lock_guard<std::mutex> lk(mu);
     done[in->ticket] = res;
     pending.erase(in->ticket);
+    cancels.erase(in->ticket);
     in_use -= in->bytes;
   }
   active.erase(active.begin() + idx);
@@ -441,8 +481,16 @@ void ebit_server::retire(size_t idx) {
   cv.notify_all();
 }
 
-ebit_status ebit_server::step() {
-  const ebit_detail::Range range("ebit_server_step");
+void ebit_server::release_status() {
+  if (d_status) cudaFree(d_status);
+  if (h_status) cudaFreeHost(h_status);
+  d_status = nullptr;
+  h_status = nullptr;
+  h_status_dev = nullptr;
+}
+
+// Launch plans (and the captured graph) for the current set of grids.
+ebit_status ebit_server::plan() {
   std::vector<Instance*> all;
   for (auto& p : active) all.push_back(p.get());
   ebit_status s;
@@ -465,52 +513,90 @@ ebit_status ebit_server::step() {
       }
     }
   }
-  if (dirty || replan) {
-    if (graph) {
-      cudaGraphExecDestroy(graph);
-      graph = nullptr;
-    }
-    if ((s = g32.build(all, EBIT_FP32, sched, stream)) != EBIT_OK) return s;
-    if ((s = g64.build(all, EBIT_FP64, sched, stream)) != EBIT_OK) return s;
-    if (opts.use_graphs) {
-      cudaGraph_t gr = nullptr;
-      if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        return fail_s(EBIT_ECUDA, "begin capture");
-      const ebit_status s1 = g32.launch(stream), s2 = g64.launch(stream);
-      if (cudaStreamEndCapture(stream, &gr) != cudaSuccess || s1 != EBIT_OK || s2 != EBIT_OK)
-        return fail_s(EBIT_ECUDA, "capture of the batch step");
-      const cudaError_t e = cudaGraphInstantiate(&graph, gr, 0);
-      cudaGraphDestroy(gr);
-      if (e != cudaSuccess) return fail_s(EBIT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    }
-    dirty = false;
-    replan = false;
+  if (!dirty && !replan) return EBIT_OK;
+  if (graph) {
+    cudaGraphExecDestroy(graph);
+    graph = nullptr;
   }
+  if ((s = g32.build(all, EBIT_FP32, sched, stream)) != EBIT_OK) return s;
+  if ((s = g64.build(all, EBIT_FP64, sched, stream)) != EBIT_OK) return s;
+  // the status words in plan order: the float group's grids, then the double group's
+  stepping.clear();
+  stepping.insert(stepping.end(), g32.inst.begin(), g32.inst.end());
+  stepping.insert(stepping.end(), g64.inst.begin(), g64.inst.end());
+  release_status();
+  const size_t n = stepping.size();
+  std::vector<int*> ptrs(n);
+  for (size_t g = 0; g < n; ++g) ptrs[g] = stepping[g]->ctx->status;
+  if (cudaMalloc((void**)&d_status, n * sizeof(int*)) != cudaSuccess ||
+      cudaHostAlloc((void**)&h_status, n * sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&h_status_dev, h_status, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return fail_s(EBIT_ENOMEM, "status plan");
+  }
+  std::memset(h_status, 0, n * sizeof(int));
+  if (cudaMemcpy(d_status, ptrs.data(), n * sizeof(int*), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail_s(EBIT_ECUDA, "status plan upload");
+  auto launch_all = [&]() -> ebit_status {
+    ebit_status a = g32.launch(stream);
+    if (a != EBIT_OK) return a;
+    if ((a = g64.launch(stream)) != EBIT_OK) return a;
+    k_status_gather<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(d_status, (int)n, h_status_dev);
+    return cudaGetLastError() == cudaSuccess ? EBIT_OK : fail_s(EBIT_ECUDA, "status gather launch");
+  };
+  if (opts.use_graphs) {
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return fail_s(EBIT_ECUDA, "begin capture");
+    const ebit_status s1 = launch_all();
+    if (cudaStreamEndCapture(stream, &gr) != cudaSuccess || s1 != EBIT_OK)
+      return fail_s(EBIT_ECUDA, "capture of the batch step");
+    const cudaError_t e = cudaGraphInstantiate(&graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return fail_s(EBIT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    launch_plain = nullptr;
+  } else {
+    launch_plain = launch_all;
+  }
+  dirty = false;
+  replan = false;
+  return EBIT_OK;
+}
+
+// Enqueues one batch step of the planned grids; returns without waiting.
+ebit_status ebit_server::step_launch() {
+  const ebit_detail::Range range("ebit_server_step");
+  ebit_status s = plan();
+  if (s != EBIT_OK) return s;
   g32.fill();
   g64.fill();
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
-  cudaEventRecord(a, stream);
+  cudaEventRecord(ev_a, stream);
   if (graph) {
     if (cudaGraphLaunch(graph, stream) != cudaSuccess) return fail_s(EBIT_ECUDA, "graph launch");
-  } else {
-    if ((s = g32.launch(stream)) != EBIT_OK) return s;
-    if ((s = g64.launch(stream)) != EBIT_OK) return s;
+  } else if ((s = launch_plain()) != EBIT_OK) {
+    return s;
   }
-  cudaEventRecord(b, stream);
-  if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_s(EBIT_ECUDA, "batch step");
+  cudaEventRecord(ev_b, stream);
+  return EBIT_OK;
+}
+
+// Waits for the step in flight and accounts it; grids whose status word
+// reports an error are marked failed (they leave the batch).
+ebit_status ebit_server::step_finish() {
+  if (cudaEventSynchronize(ev_b) != cudaSuccess) return fail_s(EBIT_ECUDA, "batch step");
   float ms = 0.0f;
-  cudaEventElapsedTime(&ms, a, b);
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
+  cudaEventElapsedTime(&ms, ev_a, ev_b);
   if (tuning) tune_after(ms);
   int64_t cells = 0;
-  for (Instance* in : all) {
+  for (size_t g = 0; g < stepping.size(); ++g) {
+    Instance* in = stepping[g];
     in->lat_ms.push_back(ms);
     in->done += 1;
     in->ctx->step_index += 1;
     cells += (int64_t)in->req.n * in->req.n;
+    const int st = ((volatile int*)h_status)[g];
+    if (st && in->failed == EBIT_OK)
+      in->failed = (st & ebit::ST_INVARIANT) ? EBIT_EINVARIANT : EBIT_ECFL;
   }
   std::lock_guard<std::mutex> lk(mu);
   batch_steps += 1;
@@ -554,9 +640,50 @@ void ebit_server::tune_after(float ms) {
   }
 }
 
+// Moves the queued requests that fit the budget (first come first served
+// among those that fit) to out; the caller holds mu.
+void ebit_server::take_admissible(std::vector<std::unique_ptr<Instance>>& out) {
+  for (auto it = queue.begin(); it != queue.end();) {
+    const bool room = in_use + (*it)->bytes <= budget &&
+                      (opts.max_instances <= 0 ||
+                       (int)(active.size() + out.size()) < opts.max_instances);
+    if (room) {
+      in_use += (*it)->bytes;
+      out.push_back(std::move(*it));
+      it = queue.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+void ebit_server::admit_all(std::vector<std::unique_ptr<Instance>>& admitted) {
+  for (auto& in : admitted) {
+    const ebit_status s = admit(in.get());
+    if (s != EBIT_OK) {
+      ebit_result r{};
+      r.status = s;
+      if (in->ctx) ebit_destroy(in->ctx);
+      if (in->u) cudaFree(in->u);
+      if (in->v) cudaFree(in->v);
+      std::lock_guard<std::mutex> lk(mu);
+      done[in->ticket] = r;
+      pending.erase(in->ticket);
+      in_use -= in->bytes;
+      cv.notify_all();
+      continue;
+    }
+    active.push_back(std::move(in));
+    dirty = true;
+  }
+  admitted.clear();
+}
+
 void ebit_server::run() {
   cudaSetDevice(opts.device);
   if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&admit_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&ev_a) != cudaSuccess || cudaEventCreate(&ev_b) != cudaSuccess ||
       set_batch_attributes<float>() != EBIT_OK || set_batch_attributes<double>() != EBIT_OK) {
     std::lock_guard<std::mutex> lk(mu);
     for (auto& q : queue) {
@@ -571,8 +698,9 @@ void ebit_server::run() {
     return;
   }
   for (;;) {
-    // admission: first come first served among the requests that fit
+    // between batch steps (nothing in flight): admission, cancellations
     std::vector<std::unique_ptr<Instance>> admitted;
+    std::set<uint64_t> cancel_now;
     {
       std::unique_lock<std::mutex> lk(mu);
       if (active.empty())
@@ -588,43 +716,34 @@ void ebit_server::run() {
         }
         queue.clear();
       }
-      for (auto it = queue.begin(); it != queue.end();) {
-        const bool room = in_use + (*it)->bytes <= budget &&
-                          (opts.max_instances <= 0 ||
-                           (int)(active.size() + admitted.size()) < opts.max_instances);
-        if (room) {
-          in_use += (*it)->bytes;
-          admitted.push_back(std::move(*it));
-          it = queue.erase(it);
-        } else {
-          ++it;
-        }
-      }
+      take_admissible(admitted);
+      cancel_now.swap(cancels);
     }
-    for (auto& in : admitted) {
-      const ebit_status s = admit(in.get());
-      if (s != EBIT_OK) {
-        ebit_result r{};
-        r.status = s;
-        if (in->ctx) ebit_destroy(in->ctx);
-        if (in->u) cudaFree(in->u);
-        if (in->v) cudaFree(in->v);
-        std::lock_guard<std::mutex> lk(mu);
-        done[in->ticket] = r;
-        pending.erase(in->ticket);
-        in_use -= in->bytes;
-        cv.notify_all();
-        continue;
+    admit_all(admitted);
+    for (size_t i = active.size(); i-- > 0;)
+      if (cancel_now.count(active[i]->ticket)) {
+        active[i]->failed = EBIT_ECANCELLED;
+        retire(i);
       }
-      active.push_back(std::move(in));
-      dirty = true;
-    }
     if (stop) {
       while (!active.empty()) retire(active.size() - 1);
       continue;
     }
     if (active.empty()) continue;
-    const ebit_status s = step();
+    ebit_status s = step_launch();
+    if (s == EBIT_OK) {
+      // while the step runs: admit what arrived meanwhile (those grids join
+      // from the next step on)
+      std::vector<std::unique_ptr<Instance>> more;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        take_admissible(more);
+      }
+      // the step in flight keeps its own grid list (stepping); the plan is
+      // rebuilt before the next one
+      if (!more.empty()) admit_all(more);
+      s = step_finish();
+    }
     if (s != EBIT_OK) {
       // fail every running request and carry on with an empty set
       for (auto& in : active) {
@@ -633,11 +752,15 @@ void ebit_server::run() {
       }
     }
     for (size_t i = active.size(); i-- > 0;)
-      if (active[i]->done >= active[i]->req.steps) retire(i);
+      if (active[i]->done >= active[i]->req.steps || active[i]->failed != EBIT_OK) retire(i);
   }
   if (graph) cudaGraphExecDestroy(graph);
   g32.release();
   g64.release();
+  release_status();
+  cudaEventDestroy(ev_a);
+  cudaEventDestroy(ev_b);
+  cudaStreamDestroy(admit_stream);
   cudaStreamDestroy(stream);
 }
 
@@ -701,6 +824,26 @@ ebit_status ebit_poll(ebit_server* s, uint64_t ticket, ebit_result* out) {
   }
   if (s->pending.count(ticket)) return EBIT_EAGAIN;
   return fail_s(EBIT_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+}
+
+ebit_status ebit_cancel(ebit_server* s, uint64_t ticket) {
+  if (!s) return fail_s(EBIT_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (!s->pending.count(ticket)) return fail_s(EBIT_EINVAL, "unknown or finished ticket %llu",
+                                               (unsigned long long)ticket);
+  for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+    if ((*it)->ticket == ticket) {  // not admitted yet: dropped at once
+      ebit_result r{};
+      r.status = EBIT_ECANCELLED;
+      r.queue_ms = now_ms() - (*it)->t_submit;
+      s->done[ticket] = r;
+      s->pending.erase(ticket);
+      s->queue.erase(it);
+      s->cv.notify_all();
+      return EBIT_OK;
+    }
+  s->cancels.insert(ticket);  // running: leaves before the next batch step
+  return EBIT_OK;
 }
 
 ebit_status ebit_server_stats_get(ebit_server* s, ebit_server_stats* out) {

@@ -15,8 +15,8 @@ import numpy as np
 from .build import LIB_PATH
 
 EBIT_OK, EBIT_EAGAIN = 0, 1
-EBIT_EINVAL, EBIT_ENOMEM, EBIT_ECFL, EBIT_EINVARIANT, EBIT_ECUDA, EBIT_ETIMEOUT, EBIT_EFULL = \
-    -1, -2, -3, -4, -5, -6, -7
+EBIT_EINVAL, EBIT_ENOMEM, EBIT_ECFL, EBIT_EINVARIANT, EBIT_ECUDA, EBIT_ETIMEOUT, EBIT_EFULL, \
+    EBIT_ECANCELLED = -1, -2, -3, -4, -5, -6, -7, -8
 EBIT_FP64, EBIT_FP32 = 0, 1
 EBIT_FIT_LINE = 1
 EBIT_CURV_GHF = 2
@@ -28,7 +28,7 @@ D_COUNT = 16
 
 _STATUS_NAMES = {0: "EBIT_OK", 1: "EBIT_EAGAIN", -1: "EBIT_EINVAL", -2: "EBIT_ENOMEM",
                  -3: "EBIT_ECFL", -4: "EBIT_EINVARIANT", -5: "EBIT_ECUDA", -6: "EBIT_ETIMEOUT",
-                 -7: "EBIT_EFULL"}
+                 -7: "EBIT_EFULL", -8: "EBIT_ECANCELLED"}
 
 
 class EbitError(RuntimeError):
@@ -355,7 +355,8 @@ class ebit_request(ctypes.Structure):
                 ("field", ctypes.c_int32), ("period", ctypes.c_double),
                 ("omega", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
                 ("drift_u", ctypes.c_double), ("drift_v", ctypes.c_double),
-                ("steps", ctypes.c_int32), ("cfl", ctypes.c_double), ("C_out", ctypes.c_void_p)]
+                ("steps", ctypes.c_int32), ("cfl", ctypes.c_double), ("C_out", ctypes.c_void_p),
+                ("fault_after", ctypes.c_int32), ("fault_dt_factor", ctypes.c_double)]
 
 
 class ebit_result(ctypes.Structure):
@@ -387,11 +388,13 @@ SIGNATURES.update({
     "ebit_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_size_t, ctypes.POINTER(ebit_server_opts)]),
     "ebit_submit": (ctypes.c_int, [_P, ctypes.POINTER(ebit_request), ctypes.POINTER(ctypes.c_uint64)]),
     "ebit_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(ebit_result)]),
+    "ebit_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "ebit_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(ebit_server_stats)]),
     "ebit_server_destroy": (None, [_P]),
 })
 if _lib is not None:  # signatures added after an earlier load
-    for _n in ("ebit_server_create", "ebit_submit", "ebit_poll", "ebit_server_stats_get", "ebit_server_destroy"):
+    for _n in ("ebit_server_create", "ebit_submit", "ebit_poll", "ebit_cancel", "ebit_server_stats_get",
+               "ebit_server_destroy"):
         _f = getattr(_lib, _n)
         _f.restype, _f.argtypes = SIGNATURES[_n]
 
@@ -406,8 +409,11 @@ def ebit_server_create(hbm_budget, max_instances=0, use_graphs=True, device=0, a
 
 
 def make_request(n, circles, field=EBIT_FIELD_CELLULAR, steps=10, cfl=0.5, prec=EBIT_FP64, period=1.0,
-                 omega=0.0, centre=(0.5, 0.5), drift=(0.0, 0.0), C_out=None, flags=0):
-    """Build an ebit_request; returns (request, keep-alive list)."""
+                 omega=0.0, centre=(0.5, 0.5), drift=(0.0, 0.0), C_out=None, flags=0, fault_after=0,
+                 fault_dt_factor=0.0):
+    """Build an ebit_request; returns (request, keep-alive list).
+    fault_after / fault_dt_factor: fault injection for tests of the server's
+    failure isolation (dt times the factor from that step on; 0 = off)."""
     circ = np.ascontiguousarray(np.asarray(circles, np.float64).reshape(-1, 3))
     keep = [circ]
     r = ebit_request()
@@ -418,6 +424,7 @@ def make_request(n, circles, field=EBIT_FIELD_CELLULAR, steps=10, cfl=0.5, prec=
     r.cx, r.cy = (float(t) for t in centre)
     r.drift_u, r.drift_v = (float(t) for t in drift)
     r.steps, r.cfl = int(steps), float(cfl)
+    r.fault_after, r.fault_dt_factor = int(fault_after), float(fault_dt_factor)
     if C_out is not None:
         assert C_out.flags["C_CONTIGUOUS"] and C_out.size == n * n
         r.C_out = C_out.ctypes.data
@@ -443,6 +450,12 @@ def ebit_poll(server, ticket):
             "queue_ms": r.queue_ms, "run_ms": r.run_ms, "step_p50_ms": r.step_p50_ms,
             "step_p99_ms": r.step_p99_ms, "counters": np.array(r.counters[:], np.int64),
             "cell_updates": r.cell_updates}
+
+
+def ebit_cancel(server, ticket):
+    """Cancels a queued or running request (its result then reports
+    EBIT_ECANCELLED); raises EbitError for an unknown or finished ticket."""
+    _check(lib().ebit_cancel(server, ctypes.c_uint64(ticket)), "ebit_cancel")
 
 
 def ebit_server_stats_get(server):

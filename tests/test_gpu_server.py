@@ -4,7 +4,10 @@
   budget that forces queueing, FP32 and FP64 requests together, ragged sizes);
 * a served request equals the oracle run of the same steps (rotation field,
   which both sides evaluate with the same IEEE operations);
-* graph replay and plain launches give identical results."""
+* graph replay and plain launches give identical results;
+* a request that fails mid-run (an injected CFL violation) or is cancelled
+  stops with its status, and every other request's result is still the one
+  it gets alone."""
 import math
 
 import numpy as np
@@ -68,6 +71,84 @@ def test_alone_equals_in_the_mix():
         assert np.array_equal(Ca[0], cm)
         assert np.array_equal(ra["counters"], rm["counters"])
         assert rm["counters"][ebit.D_INVARIANT] == 0 and rm["counters"][ebit.D_CFL] == 0
+
+
+_SOLO = {}
+
+
+def _solo(i, sp, budget):
+    """The result of spec i run alone (cached across tests)."""
+    if i not in _SOLO:
+        r, C, _ = _run([sp], budget)
+        _SOLO[i] = (r[0], C[0])
+    return _SOLO[i]
+
+
+def _assert_unchanged(specs, results, outs, budget, skip=()):
+    for i, (sp, rm, cm) in enumerate(zip(specs, results, outs)):
+        if i in skip:
+            continue
+        ra, ca = _solo(i, sp, budget)
+        assert rm["status"] == 0 and rm["steps"] == sp["steps"]
+        assert ra["area"] == rm["area"] and np.array_equal(ca, cm)
+        assert np.array_equal(ra["counters"], rm["counters"])
+
+
+def test_failing_request_leaves_the_others_unchanged():
+    """One request raises a CFL violation mid-run (fault injection: from its
+    5th step its dt is 4x, taking markers up to two cells per sweep): it
+    stops after that step with EBIT_ECFL, and every other request of the mix
+    returns exactly its solo result."""
+    specs = _mix()
+    bad = dict(specs[1])
+    bad.update(steps=40, fault_after=5, fault_dt_factor=4.0)
+    mixed = specs + [bad]
+    fps = [ebit.ebit_footprint(sp["n"], sp["n"], 1.0 / sp["n"], sp["prec"]) for sp in specs]
+    budget = int(3.5 * max(fps)) + (8 << 20)
+    res, outs, _ = _run(mixed, budget)
+    rb = res[-1]
+    assert rb["status"] == ebit.EBIT_ECFL
+    assert rb["steps"] == 6 and rb["counters"][ebit.D_CFL] > 0
+    _assert_unchanged(specs, res[:-1], outs[:-1], budget)
+
+
+def test_cancel_queued_and_running_requests():
+    """A request cancelled while queued never runs; one cancelled while
+    running stops before the next batch step with the steps it has done; both
+    report EBIT_ECANCELLED and the other requests return their solo
+    results.  A finished or unknown ticket cannot be cancelled."""
+    specs = _mix()
+    long_run = dict(specs[0])
+    long_run.update(steps=100000)   # runs until cancelled
+    queued = dict(specs[2])
+    fps = [ebit.ebit_footprint(sp["n"], sp["n"], 1.0 / sp["n"], sp["prec"]) for sp in specs]
+    budget = int(1.5 * max(fps)) + (8 << 20)      # the last request waits in the queue
+    s = ebit.ebit_server_create(budget)
+    keep, outs, tickets = [], [], []
+    try:
+        for sp in [long_run] + specs + [queued]:
+            C = np.zeros(sp["n"] * sp["n"], np.float64 if sp["prec"] == 0 else np.float32)
+            r, k = ebit.make_request(C_out=C, **sp)
+            keep.append(k)
+            outs.append(C)
+            tickets.append(ebit.ebit_submit(s, r))
+        ebit.ebit_cancel(s, tickets[-1])           # still queued behind the budget
+        import time
+        t0 = time.time()
+        while ebit.ebit_server_stats_get(s)["batch_steps"] < 5 and time.time() - t0 < 60:
+            time.sleep(0.002)
+        ebit.ebit_cancel(s, tickets[0])            # running
+        res = ebit.wait_all(s, tickets)
+        with pytest.raises(ebit.EbitError):
+            ebit.ebit_cancel(s, tickets[1])        # finished
+        with pytest.raises(ebit.EbitError):
+            ebit.ebit_cancel(s, 987654321)         # unknown
+    finally:
+        ebit.ebit_server_destroy(s)
+    r0, rq = res[tickets[0]], res[tickets[-1]]
+    assert r0["status"] == ebit.EBIT_ECANCELLED and 0 < r0["steps"] < 100000
+    assert rq["status"] == ebit.EBIT_ECANCELLED and rq["steps"] == 0
+    _assert_unchanged(specs, [res[t] for t in tickets[1:-1]], outs[1:-1], budget)
 
 
 def test_graphs_and_plain_launches_agree():

@@ -35,6 +35,10 @@ def test_budget_and_validation(ebit):
         with pytest.raises(ebit.EbitError) as e:
             ebit.ebit_poll(s, 12345)
         assert e.value.status == ebit.EBIT_EINVAL
+        with pytest.raises(ebit.EbitError) as e:
+            ebit.ebit_cancel(s, 12345)
+        assert e.value.status == ebit.EBIT_EINVAL
+        assert ebit.lib().ebit_cancel(None, 1) == ebit.EBIT_EINVAL
         st = ebit.ebit_server_stats_get(s)
         assert st["queued"] == 0 and st["batch_steps"] == 0 and st["bytes_in_use"] == 0
     finally:
