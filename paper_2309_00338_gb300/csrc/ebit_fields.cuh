@@ -372,7 +372,15 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
     __shared__ double red[256];
     __threadfence();
     double a = 0.0;
-    for (long long b = tid; b < sum.n; b += 256) a = a + __ldcg(&partial[b]);
+    long long b = tid;
+    for (; b + 7 * 256 < sum.n; b += 8 * 256) {  // eight loads in flight, added in order
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcg(&partial[b + u * 256]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a = a + v[u];
+    }
+    for (; b < sum.n; b += 256) a = a + __ldcg(&partial[b]);
     red[tid] = a;
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {

@@ -30,7 +30,6 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
-#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -377,7 +376,6 @@ struct ebit_server {
   bool dirty = true;   // the set of grids changed: new plans, new schedule choice
   bool replan = false; // same set, another schedule (autotuning)
   cudaGraphExec_t graph = nullptr;
-  std::function<ebit_status()> launch_plain;  // the step's launches when graphs are off
   // CTA-schedule autotuner: the first kTuneSteps steps of a new set of grids
   // run under each schedule in turn (the work and its results do not depend
   // on the order, so no step is wasted); the fastest is kept for the set and
@@ -400,6 +398,7 @@ struct ebit_server {
   ebit_status admit(Instance* in);
   void retire(size_t idx);
   ebit_status plan();
+  ebit_status launch_all();
   ebit_status step_launch();
   ebit_status step_finish();
   void release_status();
@@ -537,13 +536,6 @@ ebit_status ebit_server::plan() {
   std::memset(h_status, 0, n * sizeof(int));
   if (cudaMemcpy(d_status, ptrs.data(), n * sizeof(int*), cudaMemcpyHostToDevice) != cudaSuccess)
     return fail_s(EBIT_ECUDA, "status plan upload");
-  auto launch_all = [&]() -> ebit_status {
-    ebit_status a = g32.launch(stream);
-    if (a != EBIT_OK) return a;
-    if ((a = g64.launch(stream)) != EBIT_OK) return a;
-    k_status_gather<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(d_status, (int)n, h_status_dev);
-    return cudaGetLastError() == cudaSuccess ? EBIT_OK : fail_s(EBIT_ECUDA, "status gather launch");
-  };
   if (opts.use_graphs) {
     cudaGraph_t gr = nullptr;
     if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
@@ -554,13 +546,21 @@ ebit_status ebit_server::plan() {
     const cudaError_t e = cudaGraphInstantiate(&graph, gr, 0);
     cudaGraphDestroy(gr);
     if (e != cudaSuccess) return fail_s(EBIT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    launch_plain = nullptr;
-  } else {
-    launch_plain = launch_all;
   }
   dirty = false;
   replan = false;
   return EBIT_OK;
+}
+
+// The launches of one batch step on the server's stream (captured into the
+// graph, or issued directly when graphs are off).
+ebit_status ebit_server::launch_all() {
+  ebit_status a = g32.launch(stream);
+  if (a != EBIT_OK) return a;
+  if ((a = g64.launch(stream)) != EBIT_OK) return a;
+  const size_t n = stepping.size();
+  k_status_gather<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(d_status, (int)n, h_status_dev);
+  return cudaGetLastError() == cudaSuccess ? EBIT_OK : fail_s(EBIT_ECUDA, "status gather launch");
 }
 
 // Enqueues one batch step of the planned grids; returns without waiting.
@@ -573,7 +573,7 @@ ebit_status ebit_server::step_launch() {
   cudaEventRecord(ev_a, stream);
   if (graph) {
     if (cudaGraphLaunch(graph, stream) != cudaSuccess) return fail_s(EBIT_ECUDA, "graph launch");
-  } else if ((s = launch_plain()) != EBIT_OK) {
+  } else if ((s = launch_all()) != EBIT_OK) {
     return s;
   }
   cudaEventRecord(ev_b, stream);
