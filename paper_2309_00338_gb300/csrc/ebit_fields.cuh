@@ -41,19 +41,23 @@ __device__ double fraction_of(int q, int zc, const R* __restrict__ sH, const R* 
   const double s1 = in_range(q0 + 1, d.nV()) ? to_d<R>(__ldg(&sV[q0 + 1])) : 0.0;
   const double s2 = in_range(q2, d.nH()) ? to_d<R>(__ldg(&sH[q2])) : 0.0;
   const double s3 = in_range(q0, d.nV()) ? to_d<R>(__ldg(&sV[q0])) : 0.0;
-  const double w0 = 1.0 - s0, w1 = 1.0 - s1, w2 = 1.0 - s2, w3 = 1.0 - s3;
-  // legs of the triangle cut off at corner c: (s3, s0) (w0, s1) (w1, w2) (s2, w3)
+  // legs of the triangle cut off at corner c: (s3, s0) (1-s0, s1) (1-s1, 1-s2)
+  // (s2, 1-s3); a one-minus is formed only for the legs that take it
   auto tri = [&](int c) {
-    const double a = c == 0 ? s3 : c == 1 ? w0 : c == 2 ? w1 : s2;
-    const double b = c == 0 ? s0 : c == 1 ? s1 : c == 2 ? w2 : w3;
+    const double xa = c == 0 ? s3 : c == 1 ? s0 : c == 2 ? s1 : s2;
+    const double xb = c == 0 ? s0 : c == 1 ? s1 : c == 2 ? s2 : s3;
+    const double a = (c == 1 || c == 2) ? 1.0 - xa : xa;
+    const double b = (c >= 2) ? 1.0 - xb : xb;
     return 0.5 * (a * b);
   };
   if (em != 15) {
     const int e1 = __ffs(em) - 1, e2 = 31 - __clz(em);
     const int c0 = q & 1;
     if (e2 - e1 == 2) {  // opposite edges: a trapezoid
-      const double a = e1 == 0 ? (c0 ? s0 : w0) : (c0 ? s3 : w3);
-      const double b = e1 == 0 ? (c0 ? s2 : w2) : (c0 ? s1 : w1);
+      const double xa = e1 == 0 ? s0 : s3;
+      const double xb = e1 == 0 ? s2 : s1;
+      const double a = c0 ? xa : 1.0 - xa;
+      const double b = c0 ? xb : 1.0 - xb;
       return 0.5 * (a + b);
     }
     const int c = (e1 == 0 && e2 == 3) ? 0 : e2;

@@ -3,10 +3,10 @@
 //
 // A batch step advances every admitted grid by one EBIT step with a fixed
 // launch sequence per precision: a copy of the per-grid sweep descriptors
-// from pinned host memory, four sweep launches (x-first grids' first sweep,
-// y-first grids' first sweep, then the two second sweeps; a grid that is not
-// due in a launch is skipped by its blocks), the fields launch and the area
-// launch.  Work items are (grid, tile) pairs in the order of a CTA schedule
+// from pinned host memory, two sweep launches (the first sweep of every grid,
+// then the second, each tile in the direction its grid's split order puts
+// there: the grids are square, so their x and y tiles are the same work
+// items), the fields launch and the area launch.  Work items are (grid, tile) pairs in the order of a CTA schedule
 // that an online autotuner picks per set of grids (ebit_schedule).  The
 // sequence is captured once per set of admitted grids (and schedule) as a
 // CUDA graph and replayed every step.  Grids keep their state in the same buffer across a
@@ -164,17 +164,16 @@ struct Group {
   ebit::SweepDesc<R, 0>* d_s0 = nullptr;
   ebit::SweepDesc<R, 1>* d_s1 = nullptr;
   ebit::WorkItem* d_items0 = nullptr;
-  ebit::WorkItem* d_items1 = nullptr;
   ebit::FieldDesc<R>* d_fd = nullptr;
   ebit::FieldItem* d_fitems = nullptr;
   AreaDesc* d_ad = nullptr;
-  int n_items0 = 0, n_items1 = 0, n_fitems = 0;
+  int n_items0 = 0, n_fitems = 0;
   std::vector<int> ghf;  // grids with EBIT_CURV_GHF (fits after the fields launch)
 
   void release() {
     if (h_s0) cudaFreeHost(h_s0);
     if (h_s1) cudaFreeHost(h_s1);
-    for (void* p : {(void*)d_s0, (void*)d_s1, (void*)d_items0, (void*)d_items1, (void*)d_fd,
+    for (void* p : {(void*)d_s0, (void*)d_s1, (void*)d_items0, (void*)d_fd,
                     (void*)d_fitems, (void*)d_ad})
       if (p) cudaFree(p);
     *this = Group<R>();
@@ -193,7 +192,7 @@ struct Group {
                        [](const Instance* a, const Instance* b) { return a->req.n > b->req.n; });
     const size_t n = inst.size();
     // per grid, its tiles in row order; then the CTA schedule orders them
-    std::vector<std::vector<ebit::WorkItem>> g0(n), g1(n);
+    std::vector<std::vector<ebit::WorkItem>> g0(n);
     std::vector<std::vector<ebit::FieldItem>> gf(n);
     std::vector<ebit::FieldDesc<R>> fd(n);
     std::vector<AreaDesc> ad(n);
@@ -202,8 +201,6 @@ struct Group {
       const ebit::Dims& d = c->L.d;
       for (int ty = 0; ty < (d.ny + 1 + ebit::kTJ - 1) / ebit::kTJ; ++ty)
         for (int tx = 0; tx < (d.nx + 1 + ebit::kTI - 1) / ebit::kTI; ++tx) g0[g].push_back({(int)g, tx, ty});
-      for (int ty = 0; ty < (d.nx + 1 + ebit::kTJ - 1) / ebit::kTJ; ++ty)
-        for (int tx = 0; tx < (d.ny + 1 + ebit::kTI - 1) / ebit::kTI; ++tx) g1[g].push_back({(int)g, tx, ty});
       const int fx = (d.nx + 1 + ebit::kFX - 1) / ebit::kFX, fy = (d.ny + 1 + ebit::kFY - 1) / ebit::kFY;
       for (int ty = 0; ty < fy; ++ty)
         for (int tx = 0; tx < fx; ++tx) gf[g].push_back({(int)g, tx, ty});
@@ -215,10 +212,9 @@ struct Group {
       if (gh) ghf.push_back((int)g);
       ad[g] = AreaDesc{c->partial, (long long)fx * fy, c->grid.dx * c->grid.dx, c->area};
     }
-    const std::vector<ebit::WorkItem> it0 = order(g0, schedule), it1 = order(g1, schedule);
+    const std::vector<ebit::WorkItem> it0 = order(g0, schedule);
     const std::vector<ebit::FieldItem> fit = order(gf, schedule);
     n_items0 = (int)it0.size();
-    n_items1 = (int)it1.size();
     n_fitems = (int)fit.size();
     auto dput = [&](void** p, const void* src, size_t bytes) -> ebit_status {
       if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); return fail_s(EBIT_ENOMEM, "cudaMalloc (batch plan)"); }
@@ -228,7 +224,6 @@ struct Group {
     };
     ebit_status s;
     if ((s = dput((void**)&d_items0, it0.data(), it0.size() * sizeof(ebit::WorkItem))) != EBIT_OK) return s;
-    if ((s = dput((void**)&d_items1, it1.data(), it1.size() * sizeof(ebit::WorkItem))) != EBIT_OK) return s;
     if ((s = dput((void**)&d_fitems, fit.data(), fit.size() * sizeof(ebit::FieldItem))) != EBIT_OK) return s;
     if ((s = dput((void**)&d_fd, fd.data(), n * sizeof(ebit::FieldDesc<R>))) != EBIT_OK) return s;
     if ((s = dput((void**)&d_ad, ad.data(), n * sizeof(AreaDesc))) != EBIT_OK) return s;
@@ -294,10 +289,11 @@ struct Group {
     constexpr size_t smem = ebit::tile_smem_bytes<R>();
     cudaMemcpyAsync(d_s0, h_s0, 2 * n * sizeof(ebit::SweepDesc<R, 0>), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_s1, h_s1, 2 * n * sizeof(ebit::SweepDesc<R, 1>), cudaMemcpyHostToDevice, st);
-    ebit::k_sweep_tile_batch<R, 0><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0, d_items0);
-    ebit::k_sweep_tile_batch<R, 1><<<n_items1, ebit::tile_threads<R>(), smem, st>>>(d_s1, d_items1);
-    ebit::k_sweep_tile_batch<R, 1><<<n_items1, ebit::tile_threads<R>(), smem, st>>>(d_s1 + n, d_items1);
-    ebit::k_sweep_tile_batch<R, 0><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0 + n, d_items0);
+    // the requests' grids are square, so the x and y tiles of a grid are the
+    // same work items: the first sweeps of all grids in one launch, then the
+    // second sweeps (each tile in the direction its grid's split order gives)
+    ebit::k_sweep_tile_both<R><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0, d_s1, d_items0);
+    ebit::k_sweep_tile_both<R><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0 + n, d_s1 + n, d_items0);
     if (!ghf.empty()) k_ghf_reset<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d_fd, (int)n);
     ebit::k_fields_tile_batch<R><<<n_fitems, ebit::field_threads<R>(), 0, st>>>(d_fd, d_fitems);
     k_area_batch<<<(unsigned)n, 256, 0, st>>>(d_ad);
@@ -335,8 +331,7 @@ namespace {
 template <typename R>
 ebit_status set_batch_attributes() {
   constexpr size_t smem = ebit::tile_smem_bytes<R>();
-  if (cudaFuncSetAttribute(ebit::k_sweep_tile_batch<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-      cudaFuncSetAttribute(ebit::k_sweep_tile_batch<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (cudaFuncSetAttribute(ebit::k_sweep_tile_both<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return fail_s(EBIT_ECUDA, "cudaFuncSetAttribute (batch)");
   }

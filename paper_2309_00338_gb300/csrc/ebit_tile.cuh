@@ -39,7 +39,8 @@ constexpr int kRX = kTI + 8, kRY = kTJ + 5, kRN = kRX * kRY;
 constexpr int kRW = 3;                 // words per region bit row (72 columns used)
 constexpr int kRB = kRY * kRW;         // words per region bit plane
 constexpr int kNVE = (kTI + 1) * kTJ;  // unaligned edges k in [i0, i0+64], rows j0..j0+31
-constexpr int kCandCap = 256;          // candidates per tile; an edge beyond it is done in place
+constexpr int kCandCap = 255;          // candidates per tile (slot 255 marks no candidate);
+                                       // an edge beyond it is done in place
 constexpr uint16_t kKindV = 0x8000;    // marker reference: region index | kKindV if unaligned
 
 // Block shape: 7 warps per tile; tiles resident per SM as shared memory
@@ -62,36 +63,50 @@ struct Cand {
   int8_t vr, vl, kind;
 };
 
-// Shared memory of one tile (dynamic).
+// Shared memory of one tile (dynamic).  Arrays whose phases do not overlap
+// share storage: the marker lists of P1-P3 with the candidates of P4-P6, the
+// aligned / unaligned marker bit sets of P1-P3 with the candidate bit sets of
+// P4-P6, and the interface-cell list of P3-P4 with the verdicts of P6-P7.
 template <typename R>
 struct TileMem {
   union {
-    Cand cand[kCandCap];   // P4-P6
-    uint16_t ld[kRN];      // P2-P3: claimed landing edges
-  };
+    struct {
+      uint16_t ld[kRN];        // P2-P3: claimed landing edges
+      uint16_t lv[kRN];        // P1-P2: unaligned marker list
+    } p;
+    struct {
+      Cand cand[kCandCap];     // P4-P6
+      int16_t next[kCandCap];  // candidate links
+      uint16_t le[kCandCap];   // P5-P6: unaligned edges with a linked candidate
+    } c;
+  } u;
   R hfx[kRN];              // moved aligned marker: fraction
   R vfx[kRN];              // moved unaligned marker: fraction along the sweep (the one
                            // across it is the marker's own, read from the state)
-  alignas(16) uint32_t head[kNVE / 2];  // first linked candidate of unaligned edges
-                                        // 2m, 2m+1 (16 bits each, 0xffff: none)
+  alignas(16) uint32_t head[kNVE / 4];  // first linked candidate of unaligned edges
+                                        // 4m .. 4m+3 (8 bits each, 0xff: none)
   uint32_t kb[kRB];        // old corner colours
   uint32_t kn[kRB];        // new corner colours
   uint32_t zb[kRB];        // old centre colours (bit lx of row ly: cell (lx, ly))
-  uint32_t hm[kRB];        // aligned markers (bit lx of row ly: edge (lx, ly))
-  uint32_t vm[kRB];        // unaligned markers
+  union {
+    uint32_t hm[kRB];      // P1-P3: aligned markers (bit lx of row ly: edge (lx, ly))
+    uint32_t hc[kRB];      // P4-P6: unaligned edges with a linked candidate
+  };
+  union {
+    uint32_t vm[kRB];      // P1-P3: unaligned markers
+    uint32_t ovf[kRB];     // P4-P6: unaligned edges done in place
+  };
   uint32_t claim[kRB];     // aligned edges some marker lands on
-  uint32_t hc[kRB];        // unaligned edges with a linked candidate
-  uint32_t ovf[kRB];       // unaligned edges done in place
   // 2-bit codes (planes 0 and 1): moved aligned / unaligned marker ix - x + 1,
   // landing kept source - i + 2 (0: none)
   uint32_t hq[2][kRB];
   uint32_t vq[2][kRB];
   uint32_t lq[2][kRB];
-  uint16_t lh[kRN];        // aligned marker list; in P3-P4 the interface-cell list
-  uint16_t lv[kRN];        // unaligned marker list
-  uint16_t le[kCandCap];   // unaligned edges with a linked candidate
-  int16_t next[kCandCap];  // candidate links
-  alignas(16) uint8_t vrl[kNVE];  // centre verdicts of an edge: bits 0-1 right + 1, bits 2-3 left + 1
+  union {
+    uint16_t lh[kRN];      // P1-P2 aligned marker list; P3-P4 the interface-cell list
+    alignas(16) uint8_t vrl[kNVE];  // P5-P7: centre verdicts of an edge: bits 0-1
+                                    // right + 1, bits 2-3 left + 1
+  };
 };
 
 template <typename R>
@@ -302,10 +317,10 @@ struct TViewB {
 // generation order).
 template <typename R>
 __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int present) {
-  if (s >= 0 && M.next[s] < 0 && present) {
+  if (s >= 0 && M.u.c.next[s] < 0 && present) {
     // one candidate on an edge that keeps a marker: it is the marker (the
     // common case, without the ranking below)
-    const Cand& C = M.cand[s];
+    const Cand& C = M.u.c.cand[s];
     NewV<R> one;
     one.present = 1;
     one.vr = C.vr;
@@ -324,7 +339,7 @@ __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     if (s >= 0) {
-      const Cand& C = M.cand[s];
+      const Cand& C = M.u.c.cand[s];
       cy[q] = C.y;
       sf[q] = C.sf;
       key[q] = okey(C.y);
@@ -332,7 +347,7 @@ __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int
       cvr[q] = C.vr;
       cvl[q] = C.vl;
       n = q + 1;
-      s = M.next[s];
+      s = M.u.c.next[s];
     } else {
       cy[q] = 0.0;
       sf[q] = 0.0f;
@@ -478,8 +493,6 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     M.vm[t] = v;
     M.kn[t] = M.kb[t];
     M.claim[t] = 0u;
-    M.hc[t] = 0u;
-    M.ovf[t] = 0u;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       M.hq[q][t] = 0u;
@@ -495,13 +508,11 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     for (int t0 = warp * 32; t0 < kRB; t0 += kTileThreads) {
       const int t = t0 + lane;
       push_bits_warp(t < kRB ? M.hm[t] : 0u, t, M.lh, &s_nh, lane);
-      push_bits_warp(t < kRB ? M.vm[t] : 0u, t, M.lv, &s_nv, lane);
+      push_bits_warp(t < kRB ? M.vm[t] : 0u, t, M.u.p.lv, &s_nv, lane);
     }
     static_assert(kNVE % 16 == 0, "vector initialisation");
-    for (int e = tid; e < kNVE / 8; e += kTileThreads)
-      reinterpret_cast<uint4*>(M.head)[e] = make_uint4(~0u, ~0u, ~0u, ~0u);
     for (int e = tid; e < kNVE / 16; e += kTileThreads)
-      reinterpret_cast<uint4*>(M.vrl)[e] = make_uint4(0u, 0u, 0u, 0u);
+      reinterpret_cast<uint4*>(M.head)[e] = make_uint4(~0u, ~0u, ~0u, ~0u);
     __syncthreads();
 
     // P2: moved points (aligned and unaligned markers in one pass), corner
@@ -533,7 +544,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
           if (!(atomicOr(&M.claim[ly * kRW + (dl >> 5)], bit) & bit)) claimed = ly * kRX + dl;
         }
       } else if (w < nm) {
-        const int id = M.lv[w - nh], lx = id % kRX, ly = id / kRX;
+        const int id = M.u.p.lv[w - nh], lx = id % kRX, ly = id / kRX;
         const int x = ri0 + lx, y = rj0 + ly;
         Flags f;
         const AP<R> p = G.advect(Mk{1, x, y}, f);
@@ -555,7 +566,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         int base = 0;
         if (lane == leader) base = atomicAdd(&s_nd, __popc(cm));
         base = __shfl_sync(kFull, base, leader);
-        if (claimed >= 0) M.ld[base + __popc(cm & ((1u << lane) - 1u))] = (uint16_t)claimed;
+        if (claimed >= 0) M.u.p.ld[base + __popc(cm & ((1u << lane) - 1u))] = (uint16_t)claimed;
       }
     }
     flush_count(s_cnt, D_CFL, n_cfl, lane);
@@ -574,7 +585,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     constexpr int kSplit = kTileThreads - kTJ * kRW;  // 96 words on the last three warps
     static_assert(kSplit > 0 && kSplit % 32 == 0, "warp split");
     for (int w = tid; w < nd && tid < kSplit; w += kSplit) {
-      const int id = M.ld[w], dl = id % kRX, ly = id / kRX;
+      const int id = M.u.p.ld[w], dl = id % kRX, ly = id / kRX;
       const int x = ri0 + dl, y = rj0 + ly;
       bool valid[3];
       R fx[3];
@@ -626,6 +637,12 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     flush_count(s_cnt, D_CANCELLED, n_canc, lane);
     flush_count(s_cnt, D_INVARIANT, n_inv, lane);
     __syncthreads();
+    // the marker sets are dead: their storage becomes the candidate sets
+    for (int t = tid; t < kRB; t += kTileThreads) {
+      M.hc[t] = 0u;
+      M.ovf[t] = 0u;
+    }
+    __syncthreads();
 
     // P4: candidates.  A thread takes one interface cell: counts the grid
     // lines its moved chords cross, takes that many slots, then fills them.
@@ -667,7 +684,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
           }
           const bool a_left = ia[t] < k;
           const Mk mA = a_left ? ma : mb, mB = a_left ? mb : ma;
-          Cand& C = M.cand[slot];
+          Cand& C = M.u.c.cand[slot];
           C.a = TV.ref(mA);
           C.b = TV.ref(mB);
           uint8_t fl = k < i0 + kTI ? CF_OWNED : 0;
@@ -701,16 +718,16 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
           const int ll = walk(TV, mA, n1, k - 1);
           C.vr = (int8_t)(lr < 0 ? -1 : !TV.knew(k, lr));
           C.vl = (int8_t)(ll < 0 ? -1 : !TV.knew(k, ll));
-          {  // push the slot on the edge's list: 16-bit head in a shared word
-            uint32_t* hw = &M.head[e >> 1];
-            const int sh = (e & 1) * 16;
+          {  // push the slot on the edge's list: 8-bit head in a shared word
+            uint32_t* hw = &M.head[e >> 2];
+            const int sh = (e & 3) * 8;
             uint32_t old = *hw, seen;
             do {  // each retry follows another thread's successful update
               seen = old;
-              old = atomicCAS(hw, seen, (seen & ~(0xffffu << sh)) | ((uint32_t)slot << sh));
+              old = atomicCAS(hw, seen, (seen & ~(0xffu << sh)) | ((uint32_t)slot << sh));
             } while (old != seen);
-            const uint32_t prev = (seen >> sh) & 0xffffu;
-            M.next[slot] = prev == 0xffffu ? (int16_t)-1 : (int16_t)prev;
+            const uint32_t prev = (seen >> sh) & 0xffu;
+            M.u.c.next[slot] = prev == 0xffu ? (int16_t)-1 : (int16_t)prev;
           }
           atomicOr(&M.hc[eu], ebit);
         }
@@ -724,17 +741,20 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     // block so that the FP64 work spreads over the SM's sub-partitions.  The
     // last three warps first list the edges with linked candidates.
     const int ncand = min(s_ncand, kCandCap);
+    // the interface-cell list is dead: its storage becomes the verdicts of P6
+    for (int e = tid; e < kNVE / 16; e += kTileThreads)
+      reinterpret_cast<uint4*>(M.vrl)[e] = make_uint4(0u, 0u, 0u, 0u);
     if (warp >= kWarps - 3) {
       const int t = (warp - (kWarps - 3)) * 32 + lane;  // kTJ * kRW = 96 words
       const int u = (2 + t / kRW) * kRW + t % kRW;
-      push_bits_warp(M.hc[u], u, M.le, &s_ne, lane);
+      push_bits_warp(M.hc[u], u, M.u.c.le, &s_ne, lane);
     }
     const int rot = (int)((blockIdx.x + blockIdx.y) & 3u);
     int n_fit[4] = {0, 0, 0, 0};  // D_FIT_ONLINE .. D_FIT_TWO
     const int vt = (((warp + rot) % kWarps) << 5) | lane;
     for (int b0 = 0; b0 < 2 * ncand; b0 += kTileThreads) {
       const int item = b0 + vt, side = item & 1;
-      Cand& C = M.cand[min(item >> 1, kCandCap - 1)];
+      Cand& C = M.u.c.cand[min(item >> 1, kCandCap - 1)];
       int k = 0, j = 0;
       bool act = item < 2 * ncand;
       if (act) {
@@ -856,14 +876,14 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     n_canc = 0;
     n_inv = 0;
     for (int w = tid; w < ne && tid < kSplit; w += kSplit) {
-      const int id = M.le[w], ex = id % kRX, ey = id / kRX;
+      const int id = M.u.c.le[w], ex = id % kRX, ey = id / kRX;
       if (getb(M.ovf, ex, ey)) continue;
       const int k = ri0 + ex, j = rj0 + ey;
       const int e = (j - j0) * (kTI + 1) + (k - i0);
       const bool own = k < i0 + kTI;
       const int present = getb(M.kn, ex, ey) ^ getb(M.kn, ex, ey + 1);
-      const uint32_t hd = (M.head[e >> 1] >> ((e & 1) * 16)) & 0xffffu;
-      const NewV<R> nv = select_linked<R>(M, hd == 0xffffu ? -1 : (int)hd, present);
+      const uint32_t hd = (M.head[e >> 2] >> ((e & 3) * 8)) & 0xffu;
+      const NewV<R> nv = select_linked<R>(M, hd == 0xffu ? -1 : (int)hd, present);
       if (own) {
         n_canc += nv.cancelled;
         n_inv += nv.invariant;
@@ -1012,6 +1032,24 @@ k_sweep_tile_batch(const SweepDesc<R, AX>* __restrict__ descs, const WorkItem* _
   const SweepDesc<R, AX>& D = descs[it.grid];
   if (!D.active) return;
   sweep_tile<R, AX>(D.G, D.out, D.line_only, D.ctr, D.cfl_bits, D.status, it.tx * kTI, it.ty * kTJ);
+}
+
+// Square grids only: a grid's tiles are the same in both sweep directions, so
+// one launch can take the first (or second) sweep of every grid, each tile in
+// the direction its grid's split order puts there (x first on even steps):
+// the x descriptor when it is active for this launch, else the y one.
+template <typename R>
+__global__ void __launch_bounds__(tile_threads<R>(), tile_min_blocks<R>())
+k_sweep_tile_both(const SweepDesc<R, 0>* __restrict__ dx, const SweepDesc<R, 1>* __restrict__ dy,
+                  const WorkItem* __restrict__ items) {
+  const WorkItem it = items[blockIdx.x];
+  const SweepDesc<R, 0>& X = dx[it.grid];
+  if (X.active) {
+    sweep_tile<R, 0>(X.G, X.out, X.line_only, X.ctr, X.cfl_bits, X.status, it.tx * kTI, it.ty * kTJ);
+  } else {
+    const SweepDesc<R, 1>& Y = dy[it.grid];
+    sweep_tile<R, 1>(Y.G, Y.out, Y.line_only, Y.ctr, Y.cfl_bits, Y.status, it.tx * kTI, it.ty * kTJ);
+  }
 }
 
 }  // namespace ebit
