@@ -51,16 +51,19 @@ template <> __host__ __device__ constexpr int tile_min_blocks<float>() { return 
 template <> __host__ __device__ constexpr int tile_min_blocks<double>() { return 3; }
 
 // Candidate of one unaligned edge: chord ends A (left of the line) and B,
-// point 1 (p1) with the next marker beyond it (q1) in case p1 is too close to
-// A, likewise 4; references to moved markers held in the tile.
-enum { CF_P1 = 1, CF_Q1 = 2, CF_P4 = 4, CF_Q4 = 8, CF_OWNED = 16 };
+// points 1 (p1) and 4 (p4); references to moved markers held in the tile.
+// The marker beyond point 1 (or 4), used where that point is too close to A
+// (B), and the centre-rule verdicts, used where the edge borders a new
+// four-marker cell, are rare: they are formed from these references when
+// needed (the chord's cell is k - 2 + ord / 2 of row j).
+enum { CF_P1 = 1, CF_P4 = 4, CF_OWNED = 16 };
 struct Cand {
   double y;
   float sf;  // the crossing as an FP32 marker fraction (FP32 state only)
-  uint16_t a, b, p1, q1, p4, q4;
+  uint16_t a, b, p1, p4;
   uint16_t edge;  // (j - j0) * (kTI + 1) + (k - i0)
   uint8_t fl, ord;
-  int8_t vr, vl, kind;
+  int8_t kind;
 };
 
 // Shared memory of one tile (dynamic).  Arrays whose phases do not overlap
@@ -242,6 +245,22 @@ struct TViewB {
   __device__ __forceinline__ uint16_t ref(Mk mk) const {
     return (uint16_t)((cy(mk.j) * kRX + cx(mk.i)) | (mk.kind ? kKindV : 0));
   }
+  // The marker of a reference.
+  __device__ __forceinline__ Mk mk(uint16_t r) const {
+    const int t = r & (kKindV - 1), ly = t / kRX;
+    return Mk{(r & kKindV) ? 1 : 0, ri0 + t - ly * kRX, rj0 + ly};
+  }
+  // The marker beyond point 1 (side 0) or point 4 (side 1) of candidate C on
+  // the unaligned edge (k, j): points 1 and 4 are the markers beyond A and B
+  // seen from the chord's cell, and this is the one beyond them in turn.
+  template <class CandT>
+  __device__ __forceinline__ Mk next_beyond(const CandT& C, int side, int k, int j) const {
+    const int c = k - 2 + (C.ord >> 1);
+    int ci = 0, cj = 0, oi = 0, oj = 0;
+    const Mk n = beyond(*this, mk(side ? C.b : C.a), c, j, &ci, &cj);
+    if (n.kind < 0) return n;
+    return beyond(*this, n, ci, cj, &oi, &oj);
+  }
   __device__ __forceinline__ AP<R> moved(Mk mk) const {
     const int lx = cx(mk.i), ly = cy(mk.j), t = ly * kRX + lx;
     AP<R> p;
@@ -315,16 +334,20 @@ struct TViewB {
 // One marker per edge from its linked candidates (the rule of
 // select_candidates, Sec. 2.4), in registers: candidates ranked by (position,
 // generation order).
+// *kept receives the slot of the kept candidate (-1: none); its centre-rule
+// verdicts are formed by the caller where they are needed.
 template <typename R>
-__device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int present) {
+__device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int present, int* kept) {
+  *kept = -1;
   if (s >= 0 && M.u.c.next[s] < 0 && present) {
     // one candidate on an edge that keeps a marker: it is the marker (the
     // common case, without the ranking below)
     const Cand& C = M.u.c.cand[s];
     NewV<R> one;
+    *kept = s;
     one.present = 1;
-    one.vr = C.vr;
-    one.vl = C.vl;
+    one.vr = -1;
+    one.vl = -1;
     one.cancelled = 0;
     one.invariant = 0;
     if constexpr (sizeof(R) == 4) one.s = C.sf;
@@ -334,7 +357,7 @@ __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int
   double cy[6];
   float sf[6];
   long long key[6];
-  int ord[6], cvr[6], cvl[6];
+  int ord[6], sl[6];
   int n = 0;
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
@@ -344,8 +367,7 @@ __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int
       sf[q] = C.sf;
       key[q] = okey(C.y);
       ord[q] = C.ord;
-      cvr[q] = C.vr;
-      cvl[q] = C.vl;
+      sl[q] = s;
       n = q + 1;
       s = M.u.c.next[s];
     } else {
@@ -353,8 +375,7 @@ __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int
       sf[q] = 0.0f;
       key[q] = 0;
       ord[q] = 0;
-      cvr[q] = -1;
-      cvl[q] = -1;
+      sl[q] = -1;
     }
   }
   int rank[6];
@@ -402,8 +423,7 @@ __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int
       if (t < n && rank[t] == want) {
         ysel = cy[t];
         fsel = sf[t];
-        out.vr = cvr[t];
-        out.vl = cvl[t];
+        *kept = sl[t];
       }
     if constexpr (sizeof(R) == 4) out.s = fsel;  // to_fraction<float>, taken in the fit phase
     else out.s = to_fraction<R>(ysel);
@@ -694,30 +714,14 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
           if (n1.kind >= 0) {
             C.p1 = TV.ref(n1);
             fl |= CF_P1;
-            int oi, oj;
-            const Mk nn = beyond(TV, n1, c1i, c1j, &oi, &oj);
-            if (nn.kind >= 0) {
-              C.q1 = TV.ref(nn);
-              fl |= CF_Q1;
-            }
           }
           if (n4.kind >= 0) {
             C.p4 = TV.ref(n4);
             fl |= CF_P4;
-            int oi, oj;
-            const Mk nn = beyond(TV, n4, c4i, c4j, &oi, &oj);
-            if (nn.kind >= 0) {
-              C.q4 = TV.ref(nn);
-              fl |= CF_Q4;
-            }
           }
           C.fl = fl;
           C.edge = (uint16_t)e;
           C.ord = (uint8_t)((c - (k - 2)) * 2 + t);
-          const int lr = walk(TV, mB, n4, k);
-          const int ll = walk(TV, mA, n1, k - 1);
-          C.vr = (int8_t)(lr < 0 ? -1 : !TV.knew(k, lr));
-          C.vl = (int8_t)(ll < 0 ? -1 : !TV.knew(k, ll));
           {  // push the slot on the edge's list: 8-bit head in a shared word
             uint32_t* hw = &M.head[e >> 2];
             const int sh = (e & 3) * 8;
@@ -765,14 +769,13 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       // the pair shares the chord: the even lane converts A and forms cx,
       // the odd lane B and cy, and they swap (shuffles instead of FP64 work)
       double px = 0.0, py = 0.0;
-      float pxf = 0.0f, pyf = 0.0f, fy_t = 0.0f, fy_q = 0.0f;
+      float pxf = 0.0f, pyf = 0.0f, fy_t = 0.0f;
       if (act) {
         if constexpr (sizeof(R) == 4) {
           // the state reads this lane needs, issued together
           const uint8_t fl = C.fl;
           const float fy_ab = TV.own_fraction(side ? C.b : C.a);
           if (fl & (side ? CF_P4 : CF_P1)) fy_t = TV.own_fraction(side ? C.p4 : C.p1);
-          if (fl & (side ? CF_Q4 : CF_Q1)) fy_q = TV.own_fraction(side ? C.q4 : C.q1);
           TV.xyf(side ? C.b : C.a, k, j, fy_ab, &px, &py, &pxf, &pyf);
         } else {
           TV.xy(side ? C.b : C.a, k, j, &px, &py);
@@ -819,8 +822,13 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
             third(side ? C.p4 : C.p1, fy_t);
             bool use = true;
             if (side ? !tfar : d_below_sep(r2)) {  // too close to B (A): the next marker
-              if (fl & (side ? CF_Q4 : CF_Q1)) third(side ? C.q4 : C.q1, fy_q);
-              else use = false;
+              const Mk q = TV.next_beyond(C, side, k, j);
+              if (q.kind >= 0) {
+                const uint16_t qr = TV.ref(q);
+                third(qr, TV.own_fraction(qr));
+              } else {
+                use = false;
+              }
             }
             if (use) ok = circle_cross_r(ay, x0, cx, cy, c2, rx, ry, r2, tfar, &ys);
           } else {
@@ -829,8 +837,9 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
             FitPt T = fit_pt(X, Y, ax, ay, bx, by);
             bool use = true;
             if (d_below_sep(side ? T.t2 : T.r2)) {  // too close to A (B): the next marker
-              if (fl & (side ? CF_Q4 : CF_Q1)) {
-                TV.xy(side ? C.q4 : C.q1, k, j, &X, &Y);
+              const Mk q = TV.next_beyond(C, side, k, j);
+              if (q.kind >= 0) {
+                TV.xy(TV.ref(q), k, j, &X, &Y);
                 T = fit_pt(X, Y, ax, ay, bx, by);
               } else {
                 use = false;
@@ -883,12 +892,37 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       const bool own = k < i0 + kTI;
       const int present = getb(M.kn, ex, ey) ^ getb(M.kn, ex, ey + 1);
       const uint32_t hd = (M.head[e >> 2] >> ((e & 3) * 8)) & 0xffu;
-      const NewV<R> nv = select_linked<R>(M, hd == 0xffu ? -1 : (int)hd, present);
+      int kept;
+      const NewV<R> nv = select_linked<R>(M, hd == 0xffu ? -1 : (int)hd, present, &kept);
       if (own) {
         n_canc += nv.cancelled;
         n_inv += nv.invariant;
       }
-      M.vrl[e] = verdicts(nv.vr, nv.vl);
+      // centre-rule verdicts of the kept candidate (Sec. 2.3), for the cells
+      // either side of the edge that have four markers after the sweep (the
+      // only ones whose centre colour the rule sets)
+      int vr = -1, vl = -1;
+      if (kept >= 0) {
+        auto four = [&](int x) {  // cell (x, ey) of the region, new colours
+          const int a = getb(M.kn, x, ey), b = getb(M.kn, x + 1, ey);
+          const int c = getb(M.kn, x + 1, ey + 1), d = getb(M.kn, x, ey + 1);
+          return a != b && b != c && c != d;
+        };
+        const bool fr = four(ex), fl = four(ex - 1);
+        if (fr || fl) {
+          const Cand& C = M.u.c.cand[kept];
+          const Mk none{-1, 0, 0};
+          if (fr) {
+            const int lr = walk(TV, TV.mk(C.b), (C.fl & CF_P4) ? TV.mk(C.p4) : none, k);
+            vr = lr < 0 ? -1 : !TV.knew(k, lr);
+          }
+          if (fl) {
+            const int ll = walk(TV, TV.mk(C.a), (C.fl & CF_P1) ? TV.mk(C.p1) : none, k - 1);
+            vl = ll < 0 ? -1 : !TV.knew(k, ll);
+          }
+        }
+      }
+      M.vrl[e] = verdicts(vr, vl);
       if (own && nv.present) {
         if (AX) { if (in_range((long long)k * P + j, G.d.nH())) out.sH[(long long)k * P + j] = nv.s; }
         else if (in_range((long long)j * P + k, G.d.nV())) out.sV[(long long)j * P + k] = nv.s;
