@@ -78,11 +78,9 @@ def kernel_bytes_per_cell(kind: str, esz: int) -> float:
         # the tiled sweep: reads K, Z, sH, sV and the velocity component,
         # writes K, Z, sH, sV (20.5 B/cell FP32, 40.5 FP64)
         "sweep": (2 * bits + 3 * esz) + (2 * bits + 2 * esz),
-        # reads new K, old Z, verdicts; writes Z
-        "centre": 2 * bits + 2.0 + bits,
-        # reads K, Z, sH, sV; writes C and kappa
+        # reads K, Z, sH, sV; writes C and kappa (the area partials and
+        # their sum are a few KB)
         "fields": 2 * bits + 2 * esz + 2 * esz,
-        "area": 0.0,
         # reads C and kappa; writes rho, mu, fx and fy (the face arrays carry
         # one extra column / row, counted exactly in coupling_bytes)
         "coupling": 6 * esz,
@@ -518,7 +516,7 @@ def run_ours(args, wl, world, rank, local):
                                                f"{sm_mhz:.0f} MHz",
                                 "algorithmic_flops": fit_ops, "fits_per_launch": fits_per_launch,
                                 "flops_per_fit": FIT_OPS}}
-    # the metric's roofline: one EBIT step (both sweeps, fields, area) with
+    # the metric's roofline: one EBIT step (both sweeps, fields) with
     # the fused-step byte model (32.5 B/cell FP32) against the measured copy
     # bandwidth; traffic = the ncu DRAM bytes of a step's launches when every
     # record was taken on the current sources
@@ -527,7 +525,7 @@ def run_ours(args, wl, world, rank, local):
     recs = {k: traffic_record(k)[0] for k in ("sweep", "fields") if per_step.get(k)}
     step_traffic = (None if any(v is None for v in recs.values())
                     else sum(recs[k] * per_step[k] * cells for k in recs))
-    roofline = {"bound": "hbm", "kernel": "ebit_step (sweep x2, fields, area)",
+    roofline = {"bound": "hbm", "kernel": "ebit_step (sweep x2, fields with the area sum)",
                 "achieved": step_model / (ms_per_step / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": step_model / (ms_per_step / 1e3) / 1e9 / hbm,
                 "peak_source": f"{peak_kind} hbm_gbs (copy)", "algorithmic_bytes": step_model,
@@ -536,7 +534,7 @@ def run_ours(args, wl, world, rank, local):
                 "kernels": {k: {"ms_per_launch": (t / max(1, nl)), "launches": nl,
                                 "share": t / max(1e-12, sum(tt for tt, _ in kt.values())),
                                 "GBps": kernel_bytes_per_cell(k, esz) * cells / (t / max(1, nl) / 1e3) / 1e9
-                                if t > 0 and k != "area" else None}
+                                if t > 0 else None}
                             for k, (t, nl) in kt.items()}}
     c_traffic, _ = traffic_record("coupling")
     coupling = coupling_roofline(kc, n, esz, hbm, peak_kind)

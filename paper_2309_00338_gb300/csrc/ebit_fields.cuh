@@ -91,9 +91,9 @@ __device__ __forceinline__ void store4(double* p, double a, double b, double c, 
 
 // Where the tiles' area partials are summed: with `done` set, the last tile
 // of the launch to finish (counted on *done, which it then resets to 0) adds
-// all n partials in the order of k_area (thread t takes partials t, t + 256,
-// ..., then a tree over the threads), so the area is the same as a separate
-// k_area launch gives, without that launch.
+// all n partials in a fixed order (thread t takes partials t, t + 256, ...,
+// then a tree over the threads), so the area does not depend on which tile
+// finishes last, and no separate reduction launch is needed.
 struct AreaSum {
   unsigned* done = nullptr;
   long long n = 0;
@@ -372,7 +372,7 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
   }
   __syncthreads();
   if (s_last) {  // the same in every thread of the block: set before a barrier
-    static_assert(field_threads<R>() == 256, "the area order of k_area assumes 256 threads");
+    static_assert(field_threads<R>() == 256, "the fixed area order assumes 256 threads");
     __shared__ double red[256];
     __threadfence();
     double a = 0.0;

@@ -438,7 +438,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
                                            int* status, const int i0, const int j0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TileMem<R>& M = *reinterpret_cast<TileMem<R>*>(smem_raw);
-  __shared__ int s_nh, s_nv, s_nd, s_nc, s_ncand, s_ne;
+  __shared__ int s_nh, s_nv, s_nd, s_nc, s_ncand, s_ne, s_novf;
   __shared__ int s_cnt[D_NUSED];
   __shared__ unsigned long long s_dmax;
 
@@ -450,7 +450,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
   const long long P = G.d.P;
   if (tid < D_NUSED) s_cnt[tid] = 0;
   if (tid == 0) {
-    s_nh = s_nv = s_nd = s_nc = s_ncand = s_ne = 0;
+    s_nh = s_nv = s_nd = s_nc = s_ncand = s_ne = s_novf = 0;
     s_dmax = 0ull;
   }
   auto owned = [&](int x, int y) { return x >= i0 && x < i0 + kTI && y >= j0 && y < j0 + kTJ; };
@@ -752,6 +752,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       const int t = (warp - (kWarps - 3)) * 32 + lane;  // kTJ * kRW = 96 words
       const int u = (2 + t / kRW) * kRW + t % kRW;
       push_bits_warp(M.hc[u], u, M.u.c.le, &s_ne, lane);
+      const int no = __reduce_add_sync(kFull, __popc(M.ovf[u]));  // edges done in place
+      if (no != 0 && lane == 0) atomicAdd(&s_novf, no);
     }
     const int rot = (int)((blockIdx.x + blockIdx.y) & 3u);
     int n_fit[4] = {0, 0, 0, 0};  // D_FIT_ONLINE .. D_FIT_TWO
@@ -931,26 +933,6 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     if (tid >= kSplit && 2 + (tid - kSplit) / kRW <= ty1) {  // rows of unaligned edges only
       const int t = tid - kSplit;
       const int ly = 2 + t / kRW, wi = t % kRW, u = ly * kRW + wi;
-      // edges whose candidates did not fit in the tile's list: in place
-      uint32_t o = M.ovf[u];
-      while (o) {
-        const int b = __ffs(o) - 1;
-        o &= o - 1;
-        const int k = ri0 + 32 * wi + b, j = rj0 + ly;
-        const int e = (j - j0) * (kTI + 1) + (k - i0);
-        const bool own = k < i0 + kTI;
-        int oc[D_NUSED];
-#pragma unroll
-        for (int c = 0; c < D_NUSED; ++c) oc[c] = 0;
-        const NewV<R> nv = new_unaligned<R>(TV, line_only != 0, k, j, own ? oc : nullptr);
-        for (int c = 0; c < D_NUSED; ++c)
-          if (oc[c]) atomicAdd(&s_cnt[c], oc[c]);
-        M.vrl[e] = verdicts(nv.vr, nv.vl);
-        if (own && nv.present) {
-          if (AX) { if (in_range((long long)k * P + j, G.d.nH())) out.sH[(long long)k * P + j] = nv.s; }
-          else if (in_range((long long)j * P + k, G.d.nV())) out.sV[(long long)j * P + k] = nv.s;
-        }
-      }
       // owned interior edges that gain a marker without a candidate: counted,
       // fraction 0.5
       uint32_t miss = (M.kn[u] ^ M.kn[u + kRW]) & ~M.hc[u] & ~M.ovf[u] &
@@ -962,6 +944,35 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         n_inv += 1;
         if (AX) { if (in_range((long long)k * P + j, G.d.nH())) out.sH[(long long)k * P + j] = R(0.5); }
         else if (in_range((long long)j * P + k, G.d.nV())) out.sV[(long long)j * P + k] = R(0.5);
+      }
+    }
+    // edges whose candidates did not fit in the tile's list are done in
+    // place by the generic logic, spread over all threads: overflow edge m
+    // (in word order) goes to thread m mod the block size
+    for (int m = tid; m < s_novf; m += kTileThreads) {
+      int u = 2 * kRW, r = m;
+      for (; u < kRB; ++u) {
+        const int c = __popc(M.ovf[u]);
+        if (r < c) break;
+        r -= c;
+      }
+      if (u >= kRB) break;  // not reached: s_novf counts these words' bits
+      uint32_t o = M.ovf[u];
+      for (; r > 0; --r) o &= o - 1;
+      const int b = __ffs(o) - 1, ly = u / kRW, wi = u % kRW;
+      const int k = ri0 + 32 * wi + b, j = rj0 + ly;
+      const int e = (j - j0) * (kTI + 1) + (k - i0);
+      const bool own = k < i0 + kTI;
+      int oc[D_NUSED];
+#pragma unroll
+      for (int c = 0; c < D_NUSED; ++c) oc[c] = 0;
+      const NewV<R> nv = new_unaligned<R>(TV, line_only != 0, k, j, own ? oc : nullptr);
+      for (int c = 0; c < D_NUSED; ++c)
+        if (oc[c]) atomicAdd(&s_cnt[c], oc[c]);
+      M.vrl[e] = verdicts(nv.vr, nv.vl);
+      if (own && nv.present) {
+        if (AX) { if (in_range((long long)k * P + j, G.d.nH())) out.sH[(long long)k * P + j] = nv.s; }
+        else if (in_range((long long)j * P + k, G.d.nV())) out.sV[(long long)j * P + k] = nv.s;
       }
     }
     flush_count(s_cnt, D_CANCELLED, n_canc, lane);

@@ -125,7 +125,38 @@ def scene_saddle(prec):
     return S, f, dt
 
 
-SCENES = {"disks": scene_disks, "curve": scene_curve, "vortex": scene_vortex, "saddle": scene_saddle}
+def scene_packed(prec):
+    """Disks of radius about 2 cells on a 5.2-cell lattice, rotating: more
+    crossing candidates than a tile's list holds (255) in most tiles, so the
+    edges beyond it take the in-place path of the sweep."""
+    nx, ny = 130, 70
+    dx = 1.0 / 130
+    rng = W.Rng(43)
+    circles = []
+    L = 5.2
+    for a in range(int(nx / L)):
+        for b in range(int(ny / L)):
+            x = (a + 0.5) * L + (rng.uniform() - 0.5) * 0.8
+            y = (b + 0.5) * L + (rng.uniform() - 0.5) * 0.8
+            circles.append((x * dx, y * dx, (1.9 + 0.4 * rng.uniform()) * dx))
+    f = W.rotation_field(nx, ny, dx, 2 * math.pi, (0.5, 0.27), (0.3, 0.1))
+    dt = 0.5 * dx / f.umax
+    return oracle.init(nx, ny, dx, W.circle_scene(circles), prec), f, dt
+
+
+SCENES = {"disks": scene_disks, "curve": scene_curve, "vortex": scene_vortex, "saddle": scene_saddle,
+          "packed": scene_packed}
+
+
+def test_packed_scene_overflows_the_candidate_list():
+    """Every new unaligned marker of an x sweep comes from a crossing
+    candidate of the tile that owns its edge (64 x 32 edges), so a tile that
+    owns more than 255 of them had more candidates than its list holds."""
+    S, f, dt = scene_packed(oracle.FP32)
+    oracle.sweep(S, 0, f.u, dt / S.dx)
+    per_tile = [int(S.hasV[32 * ty:32 * ty + 32, 64 * tx:64 * tx + 64].sum())
+                for ty in range((S.ny + 31) // 32) for tx in range((S.nx + 1 + 63) // 64)]
+    assert sum(c > 255 for c in per_tile) >= 4, per_tile
 
 
 @pytest.mark.parametrize("prec", [oracle.FP64, oracle.FP32], ids=["fp64", "fp32"])
