@@ -53,6 +53,8 @@ def parse():
                    choices=["cellular_curve_4096", "batched", "serving"],
                    help="batched: 512 uneven grids in one batch; serving: Poisson arrivals")
     p.add_argument("--instances", type=int, default=512, help="batched: number of grids")
+    p.add_argument("--schedule", type=int, default=-1,
+                   help="batched / serving: a fixed ebit_schedule instead of the autotuner's choice")
     p.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
     p.add_argument("--serve-seconds", type=float, default=10.0, help="serving: arrival window")
     p.add_argument("--serve-cap", type=float, default=180.0, help="serving: wall-clock cap (s)")
@@ -667,9 +669,11 @@ def _batched_requests(count, seed=230900340):
     return out
 
 
-def _serve(ebit, specs, prec, budget, max_instances=0, arrivals=None, cap_s=None):
-    """Submit specs (at arrival times if given), wait; returns results + stats."""
-    s = ebit.ebit_server_create(budget, max_instances=max_instances)
+def _serve(ebit, specs, prec, budget, max_instances=0, arrivals=None, cap_s=None, schedule=-1):
+    """Submit specs (at arrival times if given), wait; returns results + stats.
+    schedule >= 0: that ebit_schedule for every batch step (no autotuning)."""
+    s = ebit.ebit_server_create(budget, max_instances=max_instances, autotune=schedule < 0,
+                                schedule=max(0, schedule))
     keep, tickets = [], []
     t0 = time.perf_counter()
     res = {}
@@ -710,7 +714,7 @@ def run_batched(args):
     budget = 200 << 30
     out = {}
     for name, prec in (("fp32", 1), ("fp64", 0)):
-        res, st, wall = _serve(ebit, specs, prec, budget)
+        res, st, wall = _serve(ebit, specs, prec, budget, schedule=args.schedule)
         lat = [r["step_p50_ms"] for r in res if r]
         ea = [r["e_area"] for r, sp in zip(res, specs) if r and sp["vortex"]]
         out[name] = {"cell_updates": st["cell_updates"], "gpu_ms": st["busy_ms"], "wall_s": wall,
@@ -767,7 +771,8 @@ def run_serving(args):
         specs.append(sp)
         arrivals.append(t)
     # a 16 GiB admission budget bounds the batch (and so the step latency)
-    res, st, wall = _serve(ebit, specs, 1, 16 << 30, arrivals=arrivals, cap_s=args.serve_cap)
+    res, st, wall = _serve(ebit, specs, 1, 16 << 30, arrivals=arrivals, cap_s=args.serve_cap,
+                           schedule=args.schedule)
     done = [r for r in res if r is not None]
     lat50 = [r["step_p50_ms"] for r in done]
     lat99 = [r["step_p99_ms"] for r in done]

@@ -292,13 +292,22 @@ typedef struct {
                                   marker past one cell makes the request fail with
                                   EBIT_ECFL, which stops it and no other */
   double fault_dt_factor;
+  int32_t fault_wait;          /* fault injection for the persistent schedules:
+                                  nonzero makes, from step fault_after on, the
+                                  count this grid's second-sweep tiles wait for
+                                  one more than its first sweep can reach; the
+                                  waits run out after the server's wait budget
+                                  and the request stops with EBIT_ETIMEOUT */
 } ebit_request;
 
 typedef struct {
   int32_t status;              /* EBIT_OK, or why the request failed or stopped:
                                   EBIT_ECFL / EBIT_EINVARIANT (detected after the
                                   batch step that raised it; the request stops
-                                  there), EBIT_ECANCELLED, EBIT_ECUDA */
+                                  there), EBIT_ETIMEOUT (a device-side wait of a
+                                  persistent batch step ran out), EBIT_ECANCELLED
+                                  (ebit_cancel, or queued when the server was
+                                  destroyed), EBIT_ECUDA */
   int64_t steps;               /* steps done */
   double area0, area;          /* sum C dx^2 at admission and at the end */
   double e_area;               /* |area - area0| / area0 (Eq. 13) */
@@ -309,13 +318,21 @@ typedef struct {
   int64_t cell_updates;        /* n*n*steps */
 } ebit_result;
 
-/* CTA schedules of the batched launches: the order of the (grid, tile) work
- * items. */
+/* CTA schedules of a batch step: the order of the (grid, tile) work items,
+ * and how the two sweeps run.  The first three issue one launch per sweep
+ * (every grid's first sweep, then every grid's second); the persistent ones
+ * run both sweeps of all grids in one launch of resident blocks that take
+ * the work items in order from a device counter, a grid's second-sweep tiles
+ * starting once its first sweep is done (a device-side wait bounded by the
+ * server's wait budget). */
 typedef enum {
   EBIT_SCHED_LARGEST_FIRST = 0,  /* grid by grid, largest grids first */
   EBIT_SCHED_INTERLEAVED = 1,    /* tile t of every grid, then tile t+1, largest first */
   EBIT_SCHED_SMALLEST_FIRST = 2, /* grid by grid, smallest grids first */
-  EBIT_SCHED_COUNT = 3
+  EBIT_SCHED_PERSISTENT_LARGEST_FIRST = 3,   /* the orders above, persistent */
+  EBIT_SCHED_PERSISTENT_INTERLEAVED = 4,
+  EBIT_SCHED_PERSISTENT_SMALLEST_FIRST = 5,
+  EBIT_SCHED_COUNT = 6
 } ebit_schedule;
 
 typedef struct {
@@ -326,6 +343,8 @@ typedef struct {
                                   grids and keep the fastest (cached per set signature);
                                   0: use `schedule` */
   int32_t schedule;            /* ebit_schedule when autotune is 0 */
+  int32_t wait_budget_ms;      /* bound of each device-side wait of a persistent
+                                  batch step (0: 1000 ms) */
 } ebit_server_opts;
 
 typedef struct {

@@ -35,7 +35,7 @@ enum {
   D_FIT_TWO, D_WALL_CLAMP, D_INVARIANT, D_HF_INVALID, D_CFL, D_NUSED
 };
 constexpr int kCounters = 16;
-enum { ST_CFL = 1, ST_INVARIANT = 2 };
+enum { ST_CFL = 1, ST_INVARIANT = 2, ST_TIMEOUT = 4 };
 
 // Two points closer than 0.01 cell do not define a usable circle (Sec. 2.2).
 constexpr double kMinSep2 = 1e-4;
@@ -106,11 +106,22 @@ __device__ __forceinline__ uint32_t span_mask(int wi, int a, int b) {
   return up & ~((1u << lo) - 1u);
 }
 
+// Loads of the state a kernel advances.  LD = 0: through the read-only
+// (non-coherent) cache, for kernels that never write what they read; LD = 1:
+// cached in L2 only (coherent), for a kernel that reads, after a fenced count
+// of finished tiles, what other blocks of the same launch wrote.
+template <int LD, typename T>
+__device__ __forceinline__ T ld_state(const T* p) {
+  if constexpr (LD != 0) return __ldcg(p);
+  else return __ldg(p);
+}
+
 // Bits x0 .. x0+31 of a stored row of nw words (bits outside the row read 0).
+template <int LD = 0>
 __device__ __forceinline__ uint32_t row_bits(const uint32_t* __restrict__ row, int nw, int x0) {
   const int q = x0 >> 5, r = x0 & 31;
-  const uint32_t a = (q >= 0 && q < nw) ? __ldg(&row[q]) : 0u;
-  const uint32_t b = (q + 1 >= 0 && q + 1 < nw) ? __ldg(&row[q + 1]) : 0u;
+  const uint32_t a = (q >= 0 && q < nw) ? ld_state<LD>(&row[q]) : 0u;
+  const uint32_t b = (q + 1 >= 0 && q + 1 < nw) ? ld_state<LD>(&row[q + 1]) : 0u;
   return r ? ((a >> r) | (b << (32 - r))) : a;
 }
 
@@ -691,7 +702,7 @@ __device__ NewV<R> new_unaligned(const A& S, bool line_only, int k, int j, int* 
 // ---------------------------------------------------------------------------
 // Accessor over a state in global memory (sweep coordinates), recomputing.
 // ---------------------------------------------------------------------------
-template <typename R, int AX>
+template <typename R, int AX, int LD = 0>
 struct GView {
   const uint32_t* __restrict__ K;
   const uint32_t* __restrict__ Z;
@@ -704,21 +715,21 @@ struct GView {
   __device__ __forceinline__ int tny() const { return AX ? d.nx : d.ny; }
   __device__ __forceinline__ int kreal(int x, int y) const {
     const long long q = (long long)y * d.kw + (x >> 5);
-    return in_range(q, d.nK()) ? (__ldg(&K[q]) >> (x & 31)) & 1 : 0;
+    return in_range(q, d.nK()) ? (ld_state<LD>(&K[q]) >> (x & 31)) & 1 : 0;
   }
   __device__ __forceinline__ int k(int i, int j) const { return AX ? kreal(j, i) : kreal(i, j); }
   __device__ __forceinline__ int z(int i, int j) const {
     const int x = AX ? j : i, y = AX ? i : j;
     const long long q = (long long)y * d.zw + (x >> 5);
-    return in_range(q, d.nZ()) ? (__ldg(&Z[q]) >> (x & 31)) & 1 : 0;
+    return in_range(q, d.nZ()) ? (ld_state<LD>(&Z[q]) >> (x & 31)) & 1 : 0;
   }
   __device__ __forceinline__ R h(int i, int j) const {
     const long long q = AX ? (long long)i * d.P + j : (long long)j * d.P + i;
-    return in_range(q, AX ? d.nV() : d.nH()) ? __ldg(AX ? &sV[q] : &sH[q]) : R(0);
+    return in_range(q, AX ? d.nV() : d.nH()) ? ld_state<LD>(AX ? &sV[q] : &sH[q]) : R(0);
   }
   __device__ __forceinline__ R v(int i, int j) const {
     const long long q = AX ? (long long)i * d.P + j : (long long)j * d.P + i;
-    return in_range(q, AX ? d.nH() : d.nV()) ? __ldg(AX ? &sH[q] : &sV[q]) : R(0);
+    return in_range(q, AX ? d.nH() : d.nV()) ? ld_state<LD>(AX ? &sH[q] : &sV[q]) : R(0);
   }
   __device__ __forceinline__ R vel(int i, int j) const {
     const long long q = AX ? (long long)i * (d.nx + 1) + j : (long long)j * (d.nx + 1) + i;

@@ -3,14 +3,17 @@
 //
 // A batch step advances every admitted grid by one EBIT step with a fixed
 // launch sequence per precision: a copy of the per-grid sweep descriptors
-// from pinned host memory, two sweep launches (the first sweep of every grid,
-// then the second, each tile in the direction its grid's split order puts
-// there: the grids are square, so their x and y tiles are the same work
-// items), the fields launch and the area launch.  Work items are (grid, tile) pairs in the order of a CTA schedule
-// that an online autotuner picks per set of grids (ebit_schedule).  The
-// sequence is captured once per set of admitted grids (and schedule) as a
-// CUDA graph and replayed every step.  Grids keep their state in the same buffer across a
-// step (first sweep A->B, second B->A).
+// from pinned host memory, the sweeps (each tile in the direction its grid's
+// split order puts there: the grids are square, so their x and y tiles are
+// the same work items), the fields launch and the area launch.  The sweeps
+// are either one persistent launch for both sweeps of all grids (a grid's
+// second-sweep tiles wait, bounded, for its first sweep) or two launches, the
+// first sweeps of all grids and then the second.  Work items are (grid, tile)
+// pairs in the order of a CTA schedule; an online autotuner picks the order
+// and the persistent or two-launch form per set of grids (ebit_schedule).
+// The sequence is captured once per set of admitted grids (and schedule) as a
+// CUDA graph and replayed every step.  Grids keep their state in the same
+// buffer across a step (first sweep A->B, second B->A).
 //
 // Serving: one worker thread owns the GPU.  Between batch steps it retires
 // finished, failed and cancelled grids (results copied to the host, memory
@@ -41,6 +44,7 @@
 #include "ebit_ctx.hpp"
 #include "ebit_fields.cuh"
 #include "ebit_ghf.cuh"
+#include "ebit_persist.cuh"
 #include "ebit_tile.cuh"
 
 namespace {
@@ -169,12 +173,20 @@ struct Group {
   AreaDesc* d_ad = nullptr;
   int n_items0 = 0, n_fitems = 0;
   std::vector<int> ghf;  // grids with EBIT_CURV_GHF (fits after the fields launch)
+  // persistent schedules: [next item | first-sweep tiles done per grid], the
+  // counts the second sweeps wait for (pinned copy refreshed every step)
+  unsigned* d_ctl = nullptr;
+  unsigned* d_need = nullptr;
+  unsigned* h_need = nullptr;
+  std::vector<unsigned> tiles;  // per grid: tiles of one sweep
+  int persist_blocks = 0;
 
   void release() {
     if (h_s0) cudaFreeHost(h_s0);
     if (h_s1) cudaFreeHost(h_s1);
+    if (h_need) cudaFreeHost(h_need);
     for (void* p : {(void*)d_s0, (void*)d_s1, (void*)d_items0, (void*)d_fd,
-                    (void*)d_fitems, (void*)d_ad})
+                    (void*)d_fitems, (void*)d_ad, (void*)d_ctl, (void*)d_need})
       if (p) cudaFree(p);
     *this = Group<R>();
   }
@@ -196,11 +208,13 @@ struct Group {
     std::vector<std::vector<ebit::FieldItem>> gf(n);
     std::vector<ebit::FieldDesc<R>> fd(n);
     std::vector<AreaDesc> ad(n);
+    tiles.assign(n, 0u);
     for (size_t g = 0; g < n; ++g) {
       const ebit_ctx* c = inst[g]->ctx;
       const ebit::Dims& d = c->L.d;
       for (int ty = 0; ty < (d.ny + 1 + ebit::kTJ - 1) / ebit::kTJ; ++ty)
         for (int tx = 0; tx < (d.nx + 1 + ebit::kTI - 1) / ebit::kTI; ++tx) g0[g].push_back({(int)g, tx, ty});
+      tiles[g] = (unsigned)g0[g].size();
       const int fx = (d.nx + 1 + ebit::kFX - 1) / ebit::kFX, fy = (d.ny + 1 + ebit::kFY - 1) / ebit::kFY;
       for (int ty = 0; ty < fy; ++ty)
         for (int tx = 0; tx < fx; ++tx) gf[g].push_back({(int)g, tx, ty});
@@ -229,11 +243,25 @@ struct Group {
     if ((s = dput((void**)&d_ad, ad.data(), n * sizeof(AreaDesc))) != EBIT_OK) return s;
     if ((s = dput((void**)&d_s0, nullptr, 2 * n * sizeof(ebit::SweepDesc<R, 0>))) != EBIT_OK) return s;
     if ((s = dput((void**)&d_s1, nullptr, 2 * n * sizeof(ebit::SweepDesc<R, 1>))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_ctl, nullptr, (n + 1) * sizeof(unsigned))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_need, nullptr, n * sizeof(unsigned))) != EBIT_OK) return s;
     if (cudaMallocHost((void**)&h_s0, 2 * n * sizeof(ebit::SweepDesc<R, 0>)) != cudaSuccess ||
-        cudaMallocHost((void**)&h_s1, 2 * n * sizeof(ebit::SweepDesc<R, 1>)) != cudaSuccess) {
+        cudaMallocHost((void**)&h_s1, 2 * n * sizeof(ebit::SweepDesc<R, 1>)) != cudaSuccess ||
+        cudaMallocHost((void**)&h_need, n * sizeof(unsigned)) != cudaSuccess) {
       cudaGetLastError();
       return fail_s(EBIT_ENOMEM, "cudaMallocHost (batch plan)");
     }
+    // resident blocks of the persistent launch (more would only wait for a slot)
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ebit::k_sweep_persistent<R>,
+                                                      ebit::tile_threads<R>(),
+                                                      ebit::tile_smem_bytes<R>()) != cudaSuccess) {
+      cudaGetLastError();
+      return fail_s(EBIT_ECUDA, "occupancy of the persistent sweep");
+    }
+    persist_blocks = (int)std::min<long long>(2LL * n_items0, (long long)std::max(1, per_sm) * sms);
     return cudaStreamSynchronize(st) == cudaSuccess ? EBIT_OK : fail_s(EBIT_ECUDA, "plan upload");
   }
 
@@ -279,21 +307,32 @@ struct Group {
       h_s1[g] = ebit::SweepDesc<R, 1>{gv1(A), buf(B), c->ctr, c->cfl_bits, c->status, lo, !x_first};
       h_s1[n + g] = ebit::SweepDesc<R, 1>{gv1(B), buf(A), c->ctr, c->cfl_bits, c->status, lo, x_first};
       h_s0[n + g] = ebit::SweepDesc<R, 0>{gv0(B), buf(A), c->ctr, c->cfl_bits, c->status, lo, !x_first};
+      const bool unreachable = in->req.fault_wait != 0 && in->done >= in->req.fault_after;
+      h_need[g] = tiles[g] + (unreachable ? 1u : 0u);
     }
   }
 
   // The launch sequence of one step on stream st.
-  ebit_status launch(cudaStream_t st) {
+  ebit_status launch(cudaStream_t st, bool persistent, unsigned long long budget_ns) {
     if (inst.empty()) return EBIT_OK;
     const size_t n = inst.size();
     constexpr size_t smem = ebit::tile_smem_bytes<R>();
     cudaMemcpyAsync(d_s0, h_s0, 2 * n * sizeof(ebit::SweepDesc<R, 0>), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_s1, h_s1, 2 * n * sizeof(ebit::SweepDesc<R, 1>), cudaMemcpyHostToDevice, st);
     // the requests' grids are square, so the x and y tiles of a grid are the
-    // same work items: the first sweeps of all grids in one launch, then the
-    // second sweeps (each tile in the direction its grid's split order gives)
-    ebit::k_sweep_tile_both<R><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0, d_s1, d_items0);
-    ebit::k_sweep_tile_both<R><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0 + n, d_s1 + n, d_items0);
+    // same work items (each tile swept in the direction its grid's split
+    // order gives): either one persistent launch for both sweeps of all
+    // grids, or the first sweeps of all grids in one launch and the second
+    // sweeps in the next
+    if (persistent) {
+      cudaMemcpyAsync(d_need, h_need, n * sizeof(unsigned), cudaMemcpyHostToDevice, st);
+      cudaMemsetAsync(d_ctl, 0, (n + 1) * sizeof(unsigned), st);
+      const ebit::PersistCtl P{d_ctl, d_need, n_items0, (int)n, budget_ns};
+      ebit::k_sweep_persistent<R><<<persist_blocks, ebit::tile_threads<R>(), smem, st>>>(d_s0, d_s1, d_items0, P);
+    } else {
+      ebit::k_sweep_tile_both<R><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0, d_s1, d_items0);
+      ebit::k_sweep_tile_both<R><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0 + n, d_s1 + n, d_items0);
+    }
     if (!ghf.empty()) k_ghf_reset<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d_fd, (int)n);
     ebit::k_fields_tile_batch<R><<<n_fitems, ebit::field_threads<R>(), 0, st>>>(d_fd, d_fitems);
     k_area_batch<<<(unsigned)n, 256, 0, st>>>(d_ad);
@@ -331,7 +370,8 @@ namespace {
 template <typename R>
 ebit_status set_batch_attributes() {
   constexpr size_t smem = ebit::tile_smem_bytes<R>();
-  if (cudaFuncSetAttribute(ebit::k_sweep_tile_both<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (cudaFuncSetAttribute(ebit::k_sweep_tile_both<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(ebit::k_sweep_persistent<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return fail_s(EBIT_ECUDA, "cudaFuncSetAttribute (batch)");
   }
@@ -512,8 +552,10 @@ ebit_status ebit_server::plan() {
     cudaGraphExecDestroy(graph);
     graph = nullptr;
   }
-  if ((s = g32.build(all, EBIT_FP32, sched, stream)) != EBIT_OK) return s;
-  if ((s = g64.build(all, EBIT_FP64, sched, stream)) != EBIT_OK) return s;
+  // the work-item order of the schedule (its persistent twin has the same)
+  const int order = sched % EBIT_SCHED_PERSISTENT_LARGEST_FIRST;
+  if ((s = g32.build(all, EBIT_FP32, order, stream)) != EBIT_OK) return s;
+  if ((s = g64.build(all, EBIT_FP64, order, stream)) != EBIT_OK) return s;
   // the status words in plan order: the float group's grids, then the double group's
   stepping.clear();
   stepping.insert(stepping.end(), g32.inst.begin(), g32.inst.end());
@@ -550,9 +592,12 @@ ebit_status ebit_server::plan() {
 // The launches of one batch step on the server's stream (captured into the
 // graph, or issued directly when graphs are off).
 ebit_status ebit_server::launch_all() {
-  ebit_status a = g32.launch(stream);
+  const bool persistent = sched >= EBIT_SCHED_PERSISTENT_LARGEST_FIRST;
+  const unsigned long long budget_ns =
+      (unsigned long long)(opts.wait_budget_ms > 0 ? opts.wait_budget_ms : 1000) * 1000000ull;
+  ebit_status a = g32.launch(stream, persistent, budget_ns);
   if (a != EBIT_OK) return a;
-  if ((a = g64.launch(stream)) != EBIT_OK) return a;
+  if ((a = g64.launch(stream, persistent, budget_ns)) != EBIT_OK) return a;
   const size_t n = stepping.size();
   k_status_gather<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(d_status, (int)n, h_status_dev);
   return cudaGetLastError() == cudaSuccess ? EBIT_OK : fail_s(EBIT_ECUDA, "status gather launch");
@@ -591,7 +636,8 @@ ebit_status ebit_server::step_finish() {
     cells += (int64_t)in->req.n * in->req.n;
     const int st = ((volatile int*)h_status)[g];
     if (st && in->failed == EBIT_OK)
-      in->failed = (st & ebit::ST_INVARIANT) ? EBIT_EINVARIANT : EBIT_ECFL;
+      in->failed = (st & ebit::ST_TIMEOUT) ? EBIT_ETIMEOUT
+                 : (st & ebit::ST_INVARIANT) ? EBIT_EINVARIANT : EBIT_ECFL;
   }
   std::lock_guard<std::mutex> lk(mu);
   batch_steps += 1;
@@ -705,7 +751,7 @@ void ebit_server::run() {
         // cancel what is queued; finish nothing further
         for (auto& q : queue) {
           ebit_result r{};
-          r.status = EBIT_ETIMEOUT;
+          r.status = EBIT_ECANCELLED;
           done[q->ticket] = r;
           pending.erase(q->ticket);
         }

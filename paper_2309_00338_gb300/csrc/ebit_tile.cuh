@@ -226,10 +226,10 @@ __device__ __forceinline__ uint32_t upto32(int c0, int last) {
 // Accessor of the tile for the shared sweep logic (beyond, walk,
 // new_unaligned).  Indices are clamped into the region; the kernel only asks
 // inside it.
-template <typename R, int AX>
+template <typename R, int AX, int LD>
 struct TViewB {
   const TileMem<R>* m;
-  const GView<R, AX>* g;  // an unaligned marker's own fraction is read from the state
+  const GView<R, AX, LD>* g;  // an unaligned marker's own fraction is read from the state
   int ri0, rj0, nx_, ny_;
   __device__ __forceinline__ int tnx() const { return nx_; }
   __device__ __forceinline__ int tny() const { return ny_; }
@@ -432,8 +432,8 @@ __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int
 }
 
 // The tile with origin (i0, j0) of one grid (one block runs it).
-template <typename R, int AX>
-__device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& out, int line_only,
+template <typename R, int AX, int LD>
+__device__ __forceinline__ void sweep_tile(const GView<R, AX, LD>& G, const Buf<R>& out, int line_only,
                                            unsigned long long* ctr, unsigned long long* cfl_bits,
                                            int* status, const int i0, const int j0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -469,9 +469,9 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
       const int y = rj0 + ly, x0 = ri0 + 32 * wi;
       uint32_t v = 0u;
       if (!zpl && ly >= vy0 && ly <= vy1)
-        v = row_bits(G.K + (long long)y * G.d.kw, G.d.kw, x0) & span_mask(wi, vx0, vx1);
+        v = row_bits<LD>(G.K + (long long)y * G.d.kw, G.d.kw, x0) & span_mask(wi, vx0, vx1);
       if (zpl && ly >= vy0 && ly <= ey1)
-        v = row_bits(G.Z + (long long)y * G.d.zw, G.d.zw, x0) & span_mask(wi, vx0, ex1);
+        v = row_bits<LD>(G.Z + (long long)y * G.d.zw, G.d.zw, x0) & span_mask(wi, vx0, ex1);
       (zpl ? M.zb : M.kb)[u] = v;
     }
   } else {
@@ -489,7 +489,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
         const uint32_t* r = base + (long long)yr * nw;
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-          if (c0 + q >= 0 && c0 + q < nw) w[q] = __ldg(&r[c0 + q]);
+          if (c0 + q >= 0 && c0 + q < nw) w[q] = ld_state<LD>(&r[c0 + q]);
       }
       uint32_t* dst = zpl ? M.zb : M.kb;
 #pragma unroll
@@ -522,7 +522,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX>& G, const Buf<R>& 
     mine |= (h | v) != 0u;
   }
   const bool busy = __syncthreads_or(mine) != 0;
-  const TViewB<R, AX> TV{&M, &G, ri0, rj0, tnx, tny};
+  const TViewB<R, AX, LD> TV{&M, &G, ri0, rj0, tnx, tny};
 
   if (busy) {
     for (int t0 = warp * 32; t0 < kRB; t0 += kTileThreads) {

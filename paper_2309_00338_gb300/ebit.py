@@ -357,7 +357,8 @@ class ebit_request(ctypes.Structure):
                 ("omega", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
                 ("drift_u", ctypes.c_double), ("drift_v", ctypes.c_double),
                 ("steps", ctypes.c_int32), ("cfl", ctypes.c_double), ("C_out", ctypes.c_void_p),
-                ("fault_after", ctypes.c_int32), ("fault_dt_factor", ctypes.c_double)]
+                ("fault_after", ctypes.c_int32), ("fault_dt_factor", ctypes.c_double),
+                ("fault_wait", ctypes.c_int32)]
 
 
 class ebit_result(ctypes.Structure):
@@ -368,13 +369,15 @@ class ebit_result(ctypes.Structure):
                 ("counters", ctypes.c_int64 * D_COUNT), ("cell_updates", ctypes.c_int64)]
 
 
-EBIT_SCHED_LARGEST_FIRST, EBIT_SCHED_INTERLEAVED, EBIT_SCHED_SMALLEST_FIRST, EBIT_SCHED_COUNT = range(4)
+(EBIT_SCHED_LARGEST_FIRST, EBIT_SCHED_INTERLEAVED, EBIT_SCHED_SMALLEST_FIRST,
+ EBIT_SCHED_PERSISTENT_LARGEST_FIRST, EBIT_SCHED_PERSISTENT_INTERLEAVED, EBIT_SCHED_PERSISTENT_SMALLEST_FIRST,
+ EBIT_SCHED_COUNT) = range(7)
 
 
 class ebit_server_opts(ctypes.Structure):
     _fields_ = [("max_instances", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("schedule", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("wait_budget_ms", ctypes.c_int32)]
 
 
 class ebit_server_stats(ctypes.Structure):
@@ -401,9 +404,9 @@ if _lib is not None:  # signatures added after an earlier load
 
 
 def ebit_server_create(hbm_budget, max_instances=0, use_graphs=True, device=0, autotune=True,
-                       schedule=EBIT_SCHED_LARGEST_FIRST):
+                       schedule=EBIT_SCHED_LARGEST_FIRST, wait_budget_ms=0):
     o = ebit_server_opts(int(max_instances), int(bool(use_graphs)), int(device), int(bool(autotune)),
-                         int(schedule))
+                         int(schedule), int(wait_budget_ms))
     h = ctypes.c_void_p()
     _check(lib().ebit_server_create(ctypes.byref(h), int(hbm_budget), ctypes.byref(o)), "ebit_server_create")
     return h
@@ -411,10 +414,12 @@ def ebit_server_create(hbm_budget, max_instances=0, use_graphs=True, device=0, a
 
 def make_request(n, circles, field=EBIT_FIELD_CELLULAR, steps=10, cfl=0.5, prec=EBIT_FP64, period=1.0,
                  omega=0.0, centre=(0.5, 0.5), drift=(0.0, 0.0), C_out=None, flags=0, fault_after=0,
-                 fault_dt_factor=0.0):
+                 fault_dt_factor=0.0, fault_wait=False):
     """Build an ebit_request; returns (request, keep-alive list).
     fault_after / fault_dt_factor: fault injection for tests of the server's
-    failure isolation (dt times the factor from that step on; 0 = off)."""
+    failure isolation (dt times the factor from that step on; 0 = off);
+    fault_wait: from step fault_after on, the persistent schedules' wait for
+    this grid's first sweep cannot be met (it runs out: EBIT_ETIMEOUT)."""
     circ = np.ascontiguousarray(np.asarray(circles, np.float64).reshape(-1, 3))
     keep = [circ]
     r = ebit_request()
@@ -426,6 +431,7 @@ def make_request(n, circles, field=EBIT_FIELD_CELLULAR, steps=10, cfl=0.5, prec=
     r.drift_u, r.drift_v = (float(t) for t in drift)
     r.steps, r.cfl = int(steps), float(cfl)
     r.fault_after, r.fault_dt_factor = int(fault_after), float(fault_dt_factor)
+    r.fault_wait = 1 if fault_wait else 0
     if C_out is not None:
         assert C_out.flags["C_CONTIGUOUS"] and C_out.size == n * n
         r.C_out = C_out.ctypes.data

@@ -5,9 +5,10 @@
 * a served request equals the oracle run of the same steps (rotation field,
   which both sides evaluate with the same IEEE operations);
 * graph replay and plain launches give identical results;
-* a request that fails mid-run (an injected CFL violation) or is cancelled
-  stops with its status, and every other request's result is still the one
-  it gets alone."""
+* a request that fails mid-run (an injected CFL violation, or a device-side
+  wait of the persistent schedule made to run out) or is cancelled stops with
+  its status, and every other request's result is still the one it gets
+  alone."""
 import math
 
 import numpy as np
@@ -39,8 +40,9 @@ def _mix():
     return reqs
 
 
-def _run(specs, budget, use_graphs=True, autotune=True, schedule=0):
-    s = ebit.ebit_server_create(budget, use_graphs=use_graphs, autotune=autotune, schedule=schedule)
+def _run(specs, budget, use_graphs=True, autotune=True, schedule=0, wait_budget_ms=0):
+    s = ebit.ebit_server_create(budget, use_graphs=use_graphs, autotune=autotune, schedule=schedule,
+                                wait_budget_ms=wait_budget_ms)
     keep, outs, tickets = [], [], []
     try:
         for sp in specs:
@@ -109,6 +111,28 @@ def test_failing_request_leaves_the_others_unchanged():
     rb = res[-1]
     assert rb["status"] == ebit.EBIT_ECFL
     assert rb["steps"] == 6 and rb["counters"][ebit.D_CFL] > 0
+    _assert_unchanged(specs, res[:-1], outs[:-1], budget)
+
+
+@pytest.mark.parametrize("sched", [ebit.EBIT_SCHED_PERSISTENT_LARGEST_FIRST,
+                                   ebit.EBIT_SCHED_PERSISTENT_INTERLEAVED])
+def test_wait_that_runs_out_stops_only_its_request(sched):
+    """Persistent batch steps: from its 4th step one grid's second-sweep
+    tiles wait for one more first-sweep tile than there are (fault
+    injection from the host; nothing ever sets the count they wait for).
+    Each wait gives up after the 20 ms budget, the tile is skipped, and the
+    request stops after that step with EBIT_ETIMEOUT; the batch step ends,
+    the context stays usable, and every other request of the mix returns
+    exactly its solo result."""
+    specs = _mix()
+    bad = dict(specs[1])
+    bad.update(steps=40, fault_after=3, fault_wait=True)
+    fps = [ebit.ebit_footprint(sp["n"], sp["n"], 1.0 / sp["n"], sp["prec"]) for sp in specs]
+    budget = int(3.5 * max(fps)) + (8 << 20)
+    res, outs, stats = _run(specs + [bad], budget, autotune=False, schedule=sched, wait_budget_ms=20)
+    assert stats["schedule"] == sched
+    rb = res[-1]
+    assert rb["status"] == ebit.EBIT_ETIMEOUT and rb["steps"] == 4
     _assert_unchanged(specs, res[:-1], outs[:-1], budget)
 
 
