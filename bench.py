@@ -357,46 +357,48 @@ def timed_steps(torch, ebit, ctx, u, v, dt, K, stream):
     return total, lat
 
 
-def e2e_loop(torch, ebit, ctx, stream, hu, hv, u, v, dt, K, cells, world, barrier, fields):
+def e2e_loop(torch, ebit, ctx, stream, hu, hv, u, v, dt, K, cells, world, barrier, fields, nb=3):
     """K steps through the C ABI from host memory: each step's u, v are
-    copied from pinned host buffers (on a second stream, into the other half
-    of a double buffer, while the previous step computes), and each step's
-    area comes back through ebit_area_async; with fields=True its fractions
-    C come back too (ebit_fraction into a device buffer of the caller on the
-    step's stream, then to pinned host memory on the copy stream while the
-    next step runs).  The host takes step k's results once step k+1 is
-    queued.  Returns the e2e record."""
+    copied from pinned host buffers (on an upload stream, into one of nb
+    device buffers, while earlier steps compute), and each step's area comes
+    back through ebit_area_async; with fields=True its fractions C come back
+    too (ebit_fraction_to_host: straight into pinned host memory on a
+    download stream while later steps run, so the two directions overlap
+    each other and the steps).
+    With nb buffers a copy has nb - 1 steps to finish; the host takes step
+    k's results once step k+2 is queued.  Returns the e2e record."""
     n2 = u.shape
-    dbuf = [(torch.empty_like(u), torch.empty_like(v)) for _ in range(2)]
-    copy_stream = torch.cuda.Stream()
-    copied = [torch.cuda.Event() for _ in range(2)]
-    freed = [torch.cuda.Event() for _ in range(2)]
+    dbuf = [(torch.empty_like(u), torch.empty_like(v)) for _ in range(nb)]
+    copy_stream = torch.cuda.Stream()   # host -> device
+    down_stream = torch.cuda.Stream()   # device -> host
+    copied = [torch.cuda.Event() for _ in range(nb)]
+    freed = [torch.cuda.Event() for _ in range(nb)]
     nC = (n2[0] - 1, n2[1] - 1)
-    Cdev = [torch.empty(nC, dtype=u.dtype, device="cuda") for _ in range(2)] if fields else None
-    Chost = [torch.empty(nC, dtype=u.dtype).pin_memory() for _ in range(2)] if fields else None
-    c_ready = [torch.cuda.Event() for _ in range(2)]
-    c_home = [torch.cuda.Event() for _ in range(2)]
+    Chost = [torch.empty(nC, dtype=u.dtype).pin_memory() for _ in range(nb)] if fields else None
+    c_home = [torch.cuda.Event() for _ in range(nb)]
 
     def upload(k):
-        b = k % 2
+        b = k % nb
         with torch.cuda.stream(copy_stream):
-            if k >= 2:
-                copy_stream.wait_event(freed[b])  # step k-2 has finished with this half
+            if k >= nb:
+                copy_stream.wait_event(freed[b])  # step k - nb has finished with this buffer
             dbuf[b][0].copy_(hu, non_blocking=True)
             dbuf[b][1].copy_(hv, non_blocking=True)
             copied[b].record(copy_stream)
 
-    areas = torch.zeros(2, dtype=torch.float64).pin_memory()
-    arrived = [torch.cuda.Event() for _ in range(2)]
+    areas = torch.zeros(nb, dtype=torch.float64).pin_memory()
+    arrived = [torch.cuda.Event() for _ in range(nb)]
     got, csum = [], []
 
-    def take(b):
+    def take(k):
+        b = k % nb
         arrived[b].synchronize()
         got.append(float(areas[b]))
         if fields:
             c_home[b].synchronize()
             csum.append(float(Chost[b][0, 0]) + float(Chost[b][-1, -1]))  # touch the copied values
 
+    lag = min(2, nb - 1)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
@@ -404,28 +406,26 @@ def e2e_loop(torch, ebit, ctx, stream, hu, hv, u, v, dt, K, cells, world, barrie
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     copy_stream.wait_event(e0)
+    down_stream.wait_event(e0)
     upload(0)
     for k in range(K):
         if k + 1 < K:
             upload(k + 1)
-        b = k % 2
+        b = k % nb
         stream.wait_event(copied[b])
-        if fields and k >= 2:
-            stream.wait_event(c_home[b])  # step k-2's C has left this buffer
         ebit.ebit_step(ctx, dbuf[b][0], dbuf[b][1], dt)
         freed[b].record(stream)
         ebit.ebit_area_async(ctx, areas[b:b + 1])
         arrived[b].record(stream)
         if fields:
-            ebit.ebit_fraction(ctx, Cdev[b])
-            c_ready[b].record(stream)
-            with torch.cuda.stream(copy_stream):
-                copy_stream.wait_event(c_ready[b])
-                Chost[b].copy_(Cdev[b], non_blocking=True)
-                c_home[b].record(copy_stream)
-        if k >= 1:
-            take(1 - b)
-    take((K - 1) % 2)
+            # C straight into pinned host memory on the download stream; the
+            # library makes the next step's fields launch wait for the copy
+            ebit.ebit_fraction_to_host(ctx, Chost[b], down_stream)
+            c_home[b].record(down_stream)
+        if k >= lag:
+            take(k - lag)
+    for k in range(max(0, K - lag), K):
+        take(k)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -437,8 +437,10 @@ def e2e_loop(torch, ebit, ctx, stream, hu, hv, u, v, dt, K, cells, world, barrie
     return {"value": job_value(world, cells, K, ms), "unit": UNIT,
             "h2d_bytes_per_step": int(hu.numel() * esz + hv.numel() * esz), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": ms / K,
-            "overlap": "inputs of step k+1 copied on a second stream during step k; step k's area"
-                       + (" and fractions C" if fields else "") + " read back while step k+1 runs"}
+            "overlap": f"inputs of step k+1 copied on an upload stream into one of {nb} device buffers while "
+                       "earlier steps run; step k's area"
+                       + (" and fractions C (on a download stream)" if fields else "")
+                       + " read back while later steps run"}
 
 
 def run_ours(args, wl, world, rank, local):

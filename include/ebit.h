@@ -156,6 +156,19 @@ ebit_status ebit_sweep(ebit_ctx* ctx, int axis, const void* vel, double dt);
  * sum C dx^2 (synchronises the stream and reports deferred errors). */
 ebit_status ebit_fraction(ebit_ctx* ctx, void* C_dev, double* area_host);
 
+/* Volume fractions C (Sec. 2.5) of the current state straight into a HOST
+ * buffer, for callers that take C every step: C_host is ny*nx elements
+ * (context precision), row-major, pinned (page-locked) for the copy to run
+ * asynchronously; the caller owns it.  copy_stream: a cudaStream_t of the
+ * caller (NULL: the context's stream) on which the copy runs, ordered after
+ * the work queued so far on the context's stream; the caller learns that
+ * C_host is filled by synchronising copy_stream (or an event recorded on it).
+ * The next fields computation of this context (ebit_step, ebit_fields) waits
+ * on the device for the copy before overwriting C, so the next step's sweeps
+ * overlap the copy.  ebit_destroy waits for a copy still in flight.
+ * Asynchronous; EBIT_EINVAL for a NULL context or buffer. */
+ebit_status ebit_fraction_to_host(ebit_ctx* ctx, void* C_host, void* copy_stream);
+
 /* The area sum C dx^2 of the current state copied to area_host (host memory;
  * pinned memory keeps the copy asynchronous) on the context's stream, without
  * waiting: the value is there once the stream reaches the copy (after an

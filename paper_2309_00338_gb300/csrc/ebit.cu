@@ -112,6 +112,10 @@ ebit_status launch_fields(ebit_ctx* c) {
   const int b = c->cur;
   const dim3 fgrid((L.d.nx + 1 + ebit::kFX - 1) / ebit::kFX, (L.d.ny + 1 + ebit::kFY - 1) / ebit::kFY);
   const bool ghf = (c->grid.flags & EBIT_CURV_GHF) != 0;
+  if (c->c_read_pending) {  // C is still being copied to the host
+    EBIT_CK(cudaStreamWaitEvent(c->stream, c->ev_c_read, 0));
+    c->c_read_pending = false;
+  }
   if (ghf) EBIT_CK(cudaMemsetAsync(c->ghf_count, 0, sizeof(unsigned), c->stream));
   {
     Timed t(c, EBIT_K_FIELDS);
@@ -492,16 +496,58 @@ ebit_status ebit_sweep(ebit_ctx* c, int axis, const void* vel, double dt) {
   return sweep(c, axis, vel, dt / c->grid.dx);
 }
 
+// The context's pitched C or kappa (ny rows of P elements) into the caller's
+// dense ny x nx device array, on the context's stream.
+static ebit_status unpitch(ebit_ctx* c, const void* src, void* dst) {
+  const Layout& L = c->L;
+  const long long row_bytes = (long long)c->grid.nx * L.esz, pitch_bytes = (long long)L.d.P * L.esz;
+  const int h = c->grid.ny;
+  const unsigned gy = (unsigned)std::min(h, 65535);
+  if (row_bytes % 16 == 0 && ((uintptr_t)dst & 15u) == 0) {
+    const long long w = row_bytes / 16;
+    const dim3 grid((unsigned)((w + 255) / 256), gy);
+    ebit::k_unpitch<uint4><<<grid, 256, 0, c->stream>>>((const uint4*)src, pitch_bytes / 16, (uint4*)dst, w, h);
+  } else if (L.esz == 4) {
+    const dim3 grid((unsigned)((c->grid.nx + 255) / 256), gy);
+    ebit::k_unpitch<float><<<grid, 256, 0, c->stream>>>((const float*)src, L.d.P, (float*)dst, c->grid.nx, h);
+  } else {
+    const dim3 grid((unsigned)((c->grid.nx + 255) / 256), gy);
+    ebit::k_unpitch<double><<<grid, 256, 0, c->stream>>>((const double*)src, L.d.P, (double*)dst, c->grid.nx, h);
+  }
+  EBIT_CK(cudaGetLastError());
+  return EBIT_OK;
+}
+
 ebit_status ebit_fraction(ebit_ctx* c, void* C_dev, double* area_host) {
   if (!c) return fail(EBIT_EINVAL, "NULL context");
-  const Layout& L = c->L;
-  if (C_dev)
-    EBIT_CK(cudaMemcpy2DAsync(C_dev, (size_t)c->grid.nx * L.esz, c->C, (size_t)L.d.P * L.esz,
-                              (size_t)c->grid.nx * L.esz, c->grid.ny, cudaMemcpyDeviceToDevice,
-                              c->stream));
+  if (C_dev) {
+    const ebit_status s = unpitch(c, c->C, C_dev);
+    if (s != EBIT_OK) return s;
+  }
   if (area_host) {
     EBIT_CK(cudaMemcpyAsync(area_host, c->area, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     return take_status(c);
+  }
+  return EBIT_OK;
+}
+
+ebit_status ebit_fraction_to_host(ebit_ctx* c, void* C_host, void* copy_stream) {
+  if (!c || !C_host) return fail(EBIT_EINVAL, "NULL argument");
+  const Layout& L = c->L;
+  cudaStream_t cs = copy_stream ? (cudaStream_t)copy_stream : c->stream;
+  if (!c->ev_queued) {
+    EBIT_CK(cudaEventCreateWithFlags(&c->ev_queued, cudaEventDisableTiming));
+    EBIT_CK(cudaEventCreateWithFlags(&c->ev_c_read, cudaEventDisableTiming));
+  }
+  if (cs != c->stream) {
+    EBIT_CK(cudaEventRecord(c->ev_queued, c->stream));
+    EBIT_CK(cudaStreamWaitEvent(cs, c->ev_queued, 0));
+  }
+  EBIT_CK(cudaMemcpy2DAsync(C_host, (size_t)c->grid.nx * L.esz, c->C, (size_t)L.d.P * L.esz,
+                            (size_t)c->grid.nx * L.esz, c->grid.ny, cudaMemcpyDeviceToHost, cs));
+  if (cs != c->stream) {
+    EBIT_CK(cudaEventRecord(c->ev_c_read, cs));
+    c->c_read_pending = true;
   }
   return EBIT_OK;
 }
@@ -526,11 +572,10 @@ ebit_status ebit_area_async(ebit_ctx* c, double* area_host) {
 
 ebit_status ebit_curvature(ebit_ctx* c, void* kappa_dev, int32_t* n_invalid_host) {
   if (!c) return fail(EBIT_EINVAL, "NULL context");
-  const Layout& L = c->L;
-  if (kappa_dev)
-    EBIT_CK(cudaMemcpy2DAsync(kappa_dev, (size_t)c->grid.nx * L.esz, c->kappa,
-                              (size_t)L.d.P * L.esz, (size_t)c->grid.nx * L.esz, c->grid.ny,
-                              cudaMemcpyDeviceToDevice, c->stream));
+  if (kappa_dev) {
+    const ebit_status s = unpitch(c, c->kappa, kappa_dev);
+    if (s != EBIT_OK) return s;
+  }
   if (n_invalid_host) {
     unsigned long long n = 0;
     EBIT_CK(cudaMemcpyAsync(&n, c->ctr + ebit::D_HF_INVALID, sizeof n, cudaMemcpyDeviceToHost, c->stream));
@@ -602,6 +647,11 @@ ebit_status ebit_timings(ebit_ctx* c, double* ms, int64_t* launches) {
 void ebit_destroy(ebit_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->ev_c_read) {  // a copy of C to the host may still run on the caller's stream
+    cudaEventSynchronize(c->ev_c_read);
+    cudaEventDestroy(c->ev_c_read);
+    cudaEventDestroy(c->ev_queued);
+  }
   for (auto& m : c->marks) {
     cudaEventDestroy(m.a);
     cudaEventDestroy(m.b);

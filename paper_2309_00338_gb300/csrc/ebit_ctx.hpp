@@ -87,6 +87,10 @@ struct ebit_ctx {
   int* ghf_list = nullptr;          // EBIT_CURV_GHF: cells left without kappa
   unsigned* ghf_count = nullptr;
   int64_t step_index = 0;
+  // ebit_fraction_to_host: the copy of C on the caller's stream, which the
+  // next fields launch waits for
+  cudaEvent_t ev_queued = nullptr, ev_c_read = nullptr;
+  bool c_read_pending = false;
   std::vector<void*> allocs;
   // per-kernel event timing (off unless ebit_set_timing)
   bool timing = false;

@@ -289,4 +289,17 @@ __global__ void k_store_frac(const R* __restrict__ src, int w, int h, long long 
   dst[t] = (double)src[(long long)y * P + x];
 }
 
+// A pitched field (h rows of `pitch` words of type W) to a dense one (h rows
+// of w words): one word per thread and row, rows by a grid-stride loop (the
+// grid's y extent is capped).  W = uint4 when the dense rows are whole
+// 16-byte words and the destination is 16-byte aligned (the pitched rows
+// always are), else the element type itself.
+template <typename W>
+__global__ void k_unpitch(const W* __restrict__ src, long long pitch, W* __restrict__ dst, long long w,
+                          int h) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= w) return;
+  for (long long y = blockIdx.y; y < h; y += gridDim.y) dst[y * w + x] = src[y * pitch + x];
+}
+
 }  // namespace ebit

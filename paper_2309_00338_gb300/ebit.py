@@ -106,6 +106,7 @@ SIGNATURES = {
     "ebit_fraction_noalloc": (ctypes.c_int, [ctypes.POINTER(ebit_grid), _P, _P, _P, _P, _P, _P, _P, _P]),
     "ebit_coupling": (ctypes.c_int, [_P, ctypes.POINTER(ebit_fluids), _P, _P, _P, _P]),
     "ebit_area_async": (ctypes.c_int, [_P, _P]),
+    "ebit_fraction_to_host": (ctypes.c_int, [_P, _P, _P]),
     "ebit_check_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
 }
 
@@ -250,6 +251,18 @@ def ebit_area_async(ctx, area_host):
     if area_host.is_cuda or area_host.dtype.itemsize != 8:
         raise ValueError("expected a host tensor of one float64")
     _check(lib().ebit_area_async(ctx, ctypes.c_void_p(area_host.data_ptr())), "ebit_area_async")
+
+
+def ebit_fraction_to_host(ctx, C_host, stream=None):
+    """Queue the copy of the current fractions C into C_host (a pinned,
+    contiguous CPU tensor of ny*nx elements of the context precision) on
+    `stream` (a torch.cuda.Stream; None: the context's stream).  C_host is
+    filled once that stream gets there; the context's next fields
+    computation waits for the copy on the device."""
+    if C_host.is_cuda or not C_host.is_contiguous() or not C_host.is_pinned():
+        raise ValueError("expected a pinned, contiguous host tensor")
+    st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(lib().ebit_fraction_to_host(ctx, ctypes.c_void_p(C_host.data_ptr()), st), "ebit_fraction_to_host")
 
 
 def ebit_check_status():

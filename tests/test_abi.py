@@ -72,7 +72,8 @@ def test_product_path_has_no_oracle_dependency():
 
 
 def test_new_entry_points_check_arguments_without_gpu(libebit):
-    """ebit_coupling, ebit_area_async and the scene checks of ebit_init reject
+    """ebit_coupling, ebit_area_async, ebit_fraction_to_host and the scene
+    checks of ebit_init reject
     bad arguments before any CUDA call; EBIT_CURV_GHF adds its cell list to
     the footprint."""
     from paper_2309_00338_gb300 import ebit
@@ -80,6 +81,7 @@ def test_new_entry_points_check_arguments_without_gpu(libebit):
     fl = ebit.ebit_fluids(1.0, 1.0, 1.0, 1.0, 1.0)
     assert L.ebit_coupling(None, ctypes.byref(fl), None, None, None, None) == ebit.EBIT_EINVAL
     assert L.ebit_area_async(None, None) == ebit.EBIT_EINVAL
+    assert L.ebit_fraction_to_host(None, None, None) == ebit.EBIT_EINVAL
     n = 256
     plain = ebit.ebit_footprint(n, n, 1 / n, ebit.EBIT_FP32)
     ghf = ebit.ebit_footprint(n, n, 1 / n, ebit.EBIT_FP32, ebit.EBIT_CURV_GHF)

@@ -614,6 +614,37 @@ def test_stagnation_film_run(prec):
         ebit.ebit_destroy(ctx)
 
 
+@pytest.mark.parametrize("prec", [oracle.FP64, oracle.FP32], ids=["fp64", "fp32"])
+def test_fraction_to_host_every_step(prec):
+    """ebit_fraction_to_host after each of four steps, queued while the GPU
+    runs ahead of the host (the first on the context's stream, the others on
+    a side stream): every host copy holds the C of its own step — the next
+    step's fields launch waits for the copy — and equals the oracle's."""
+    S, f, dt = scene_disks(prec)
+    ctx = gpu_from(S)
+    side = torch.cuda.Stream()
+    dtype = torch.float64 if prec == oracle.FP64 else torch.float32
+    try:
+        u, v = dev(f.u, prec), dev(f.v, prec)
+        hosts = []
+        for k in range(4):
+            ebit.ebit_step(ctx, u, v, dt)
+            h = torch.full((S.ny, S.nx), -1.0, dtype=dtype).pin_memory()
+            ebit.ebit_fraction_to_host(ctx, h, None if k == 0 else side)
+            hosts.append(h)
+        refs = [oracle.step(S, f.u, f.v, dt)["C"].copy() for _ in range(4)]
+        side.synchronize()
+        ebit.ebit_sync(ctx)
+        for h, r in zip(hosts, refs):
+            c = h.double().numpy()
+            if prec == oracle.FP32:
+                assert np.array_equal(c, r)
+            else:
+                assert np.max(np.abs(c - r)) <= TOL64
+    finally:
+        ebit.ebit_destroy(ctx)
+
+
 def test_area_async_matches_fraction():
     """ebit_area_async queues the area of the current state; after the stream
     reaches it the value equals ebit_fraction's, step by step."""
