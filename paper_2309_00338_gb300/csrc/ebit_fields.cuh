@@ -181,6 +181,10 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
       }
     }
   }
+  {
+    const int fsum = __reduce_add_sync(0xffffffffu, full);
+    if (lane == 0 && fsum) atomicAdd(&s_full, (unsigned long long)fsum);
+  }
   __syncthreads();
 
   // interface list in region order: per-warp scans of the word counts
@@ -236,7 +240,30 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
     cs[t] = (R)f;
     if (lx >= kFH && lx < kFH + kFX && ly >= kFH && ly < kFH + kFY) acc = acc + f;
   }
+  // area partial: warps holding interface cells reduce in a fixed shuffle
+  // order (adding 0.0 from the other lanes changes nothing)
+  if (__any_sync(0xffffffffu, !d_eq0(acc))) {
+    for (int o = 16; o > 0; o >>= 1) acc = acc + __shfl_down_sync(0xffffffffu, acc, o);
+  } else {
+    acc = 0.0;
+  }
+  if (lane == 0) s_wsum[warp] = acc;
   __syncthreads();
+  // the tile's partial, and its count towards the launch's last tile, by the
+  // last thread: it has no global stores in flight to fence, and it rarely
+  // has curvature work, so the fence and the counter's round trip overlap
+  // the other threads' curvature
+  if (tid == kFieldThreads - 1) {
+    double p = 0.0;
+    for (int w = 0; w < kFieldThreads / 32; ++w) p = p + s_wsum[w];
+    if (s_full) p = p + (double)s_full;
+    partial[slot] = p;
+    s_last = 0;
+    if (sum.done) {
+      __threadfence();  // the partial is visible before the count says so
+      s_last = atomicAdd(sum.done, 1u) == (unsigned)(sum.n - 1);
+    }
+  }
 
   // height-function curvature of the tile's interface cells
   for (int e = tid; e < nlist; e += kFieldThreads) {
@@ -324,33 +351,12 @@ __device__ __forceinline__ void fields_tile(const uint32_t* __restrict__ K,
       }
     }
   }
-  // area partial: warps holding interface cells reduce in a fixed shuffle
-  // order (adding 0.0 from the other lanes changes nothing)
-  if (__any_sync(0xffffffffu, !d_eq0(acc))) {
-    for (int o = 16; o > 0; o >>= 1) acc = acc + __shfl_down_sync(0xffffffffu, acc, o);
-  } else {
-    acc = 0.0;
-  }
-  if (lane == 0) s_wsum[warp] = acc;
-  const int fsum = __reduce_add_sync(0xffffffffu, full);
-  if (lane == 0 && fsum) atomicAdd(&s_full, (unsigned long long)fsum);
-#pragma unroll
-  for (int c = 0; c < D_NUSED; ++c) {
+  // the counters this kernel keeps (markers, cells without a height stencil)
+  for (const int c : {(int)D_NH, (int)D_NV, (int)D_HF_INVALID}) {
     const int s = __reduce_add_sync(0xffffffffu, cnt[c]);
     if (s != 0 && lane == 0) atomicAdd(&s_cnt[c], s);
   }
   __syncthreads();
-  if (tid == 0) {
-    double p = 0.0;
-    for (int w = 0; w < kFieldThreads / 32; ++w) p = p + s_wsum[w];
-    if (s_full) p = p + (double)s_full;
-    partial[slot] = p;
-    s_last = 0;
-    if (sum.done) {
-      __threadfence();  // the partial is visible before the count says so
-      s_last = atomicAdd(sum.done, 1u) == (unsigned)(sum.n - 1);
-    }
-  }
   if (tid < D_NUSED && s_cnt[tid] != 0) atomicAdd(&ctr[tid], (unsigned long long)s_cnt[tid]);
   if (ghf_list) {
     const unsigned nflag = s_nghf;  // final: its atomics precede the last barrier
