@@ -55,10 +55,12 @@ __device__ __noinline__ void persistent_tile(const SweepDesc<R, 0>& X, const Swe
                                              int tx, int ty) {
   if (X.active) {
     const GView<R, 0, 1> G{X.G.K, X.G.Z, X.G.sH, X.G.sV, X.G.w, X.G.d, X.G.lam};
-    sweep_tile<R, 0, 1>(G, X.out, X.line_only, X.ctr, X.cfl_bits, X.status, tx * kTI, ty * kTJ);
+    sweep_tile<R, 0, 1, batch_cand_cap<R>()>(G, X.out, X.line_only, X.ctr, X.cfl_bits, X.status,
+                                             tx * kTI, ty * kTJ);
   } else {
     const GView<R, 1, 1> G{Y.G.K, Y.G.Z, Y.G.sH, Y.G.sV, Y.G.w, Y.G.d, Y.G.lam};
-    sweep_tile<R, 1, 1>(G, Y.out, Y.line_only, Y.ctr, Y.cfl_bits, Y.status, tx * kTI, ty * kTJ);
+    sweep_tile<R, 1, 1, batch_cand_cap<R>()>(G, Y.out, Y.line_only, Y.ctr, Y.cfl_bits, Y.status,
+                                             tx * kTI, ty * kTJ);
   }
 }
 

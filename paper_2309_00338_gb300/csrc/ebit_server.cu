@@ -257,7 +257,7 @@ struct Group {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ebit::k_sweep_persistent<R>,
                                                       ebit::tile_threads<R>(),
-                                                      ebit::tile_smem_bytes<R>()) != cudaSuccess) {
+                                                      ebit::tile_smem_bytes<R, ebit::batch_cand_cap<R>()>()) != cudaSuccess) {
       cudaGetLastError();
       return fail_s(EBIT_ECUDA, "occupancy of the persistent sweep");
     }
@@ -316,7 +316,7 @@ struct Group {
   ebit_status launch(cudaStream_t st, bool persistent, unsigned long long budget_ns) {
     if (inst.empty()) return EBIT_OK;
     const size_t n = inst.size();
-    constexpr size_t smem = ebit::tile_smem_bytes<R>();
+    constexpr size_t smem = ebit::tile_smem_bytes<R, ebit::batch_cand_cap<R>()>();
     cudaMemcpyAsync(d_s0, h_s0, 2 * n * sizeof(ebit::SweepDesc<R, 0>), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_s1, h_s1, 2 * n * sizeof(ebit::SweepDesc<R, 1>), cudaMemcpyHostToDevice, st);
     // the requests' grids are square, so the x and y tiles of a grid are the
@@ -330,8 +330,8 @@ struct Group {
       const ebit::PersistCtl P{d_ctl, d_need, n_items0, (int)n, budget_ns};
       ebit::k_sweep_persistent<R><<<persist_blocks, ebit::tile_threads<R>(), smem, st>>>(d_s0, d_s1, d_items0, P);
     } else {
-      ebit::k_sweep_tile_both<R><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0, d_s1, d_items0);
-      ebit::k_sweep_tile_both<R><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0 + n, d_s1 + n, d_items0);
+      ebit::k_sweep_tile_both<R, ebit::batch_cand_cap<R>()><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0, d_s1, d_items0);
+      ebit::k_sweep_tile_both<R, ebit::batch_cand_cap<R>()><<<n_items0, ebit::tile_threads<R>(), smem, st>>>(d_s0 + n, d_s1 + n, d_items0);
     }
     if (!ghf.empty()) k_ghf_reset<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d_fd, (int)n);
     ebit::k_fields_tile_batch<R><<<n_fitems, ebit::field_threads<R>(), 0, st>>>(d_fd, d_fitems);
@@ -369,8 +369,8 @@ namespace {
 
 template <typename R>
 ebit_status set_batch_attributes() {
-  constexpr size_t smem = ebit::tile_smem_bytes<R>();
-  if (cudaFuncSetAttribute(ebit::k_sweep_tile_both<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+  constexpr size_t smem = ebit::tile_smem_bytes<R, ebit::batch_cand_cap<R>()>();
+  if (cudaFuncSetAttribute(ebit::k_sweep_tile_both<R, ebit::batch_cand_cap<R>()>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaFuncSetAttribute(ebit::k_sweep_persistent<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return fail_s(EBIT_ECUDA, "cudaFuncSetAttribute (batch)");

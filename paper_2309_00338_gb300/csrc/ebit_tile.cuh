@@ -39,8 +39,14 @@ constexpr int kRX = kTI + 8, kRY = kTJ + 5, kRN = kRX * kRY;
 constexpr int kRW = 3;                 // words per region bit row (72 columns used)
 constexpr int kRB = kRY * kRW;         // words per region bit plane
 constexpr int kNVE = (kTI + 1) * kTJ;  // unaligned edges k in [i0, i0+64], rows j0..j0+31
-constexpr int kCandCap = 255;          // candidates per tile (slot 255 marks no candidate);
-                                       // an edge beyond it is done in place
+constexpr int kCandCap = 255;          // candidates per tile of the one-grid kernels (an
+                                       // edge beyond it is done in place)
+// A candidate list of CAP entries links them through heads of 8 bits (CAP
+// <= 255) or 16 bits; the all-ones head marks an edge without a candidate.
+template <int CAP> __host__ __device__ constexpr int head_bits() { return CAP <= 255 ? 8 : 16; }
+template <int CAP> __host__ __device__ constexpr uint32_t head_none() {
+  return (1u << head_bits<CAP>()) - 1u;
+}
 constexpr uint16_t kKindV = 0x8000;    // marker reference: region index | kKindV if unaligned
 
 // Block shape: 7 warps per tile; tiles resident per SM as shared memory
@@ -49,6 +55,12 @@ template <typename R> __host__ __device__ constexpr int tile_threads() { return 
 template <typename R> __host__ __device__ constexpr int tile_min_blocks();
 template <> __host__ __device__ constexpr int tile_min_blocks<float>() { return 4; }
 template <> __host__ __device__ constexpr int tile_min_blocks<double>() { return 3; }
+// Candidates per tile of the batched kernels: many small grids of uneven
+// sizes hold more interface per tile than one large grid, and the longer
+// list (16-bit heads) still leaves 4 (FP32) / 3 (FP64) tiles per SM.
+template <typename R> __host__ __device__ constexpr int batch_cand_cap() {
+  return sizeof(R) == 4 ? 511 : 383;
+}
 
 // Candidate of one unaligned edge: chord ends A (left of the line) and B,
 // points 1 (p1) and 4 (p4); references to moved markers held in the tile.
@@ -70,23 +82,26 @@ struct Cand {
 // share storage: the marker lists of P1-P3 with the candidates of P4-P6, the
 // aligned / unaligned marker bit sets of P1-P3 with the candidate bit sets of
 // P4-P6, and the interface-cell list of P3-P4 with the verdicts of P6-P7.
-template <typename R>
+template <typename R, int CAP = kCandCap>
 struct TileMem {
+  static_assert(CAP <= 65534, "candidate slots fit the 16-bit heads");
+  static constexpr int kCap = CAP;
   union {
     struct {
       uint16_t ld[kRN];        // P2-P3: claimed landing edges
       uint16_t lv[kRN];        // P1-P2: unaligned marker list
     } p;
     struct {
-      Cand cand[kCandCap];     // P4-P6
-      int16_t next[kCandCap];  // candidate links
-      uint16_t le[kCandCap];   // P5-P6: unaligned edges with a linked candidate
+      Cand cand[CAP];          // P4-P6
+      int16_t next[CAP];       // candidate links
+      uint16_t le[CAP];        // P5-P6: unaligned edges with a linked candidate
     } c;
   } u;
   R hfx[kRN];              // moved aligned marker: fraction
   R vfx[kRN];              // moved unaligned marker: fraction along the sweep (the one
                            // across it is the marker's own, read from the state)
-  alignas(16) uint32_t head[kNVE / 4];  // first linked candidate of unaligned edges
+  alignas(16) uint32_t head[kNVE * head_bits<CAP>() / 32];  // first linked candidate of
+                                                            // unaligned edges
                                         // 4m .. 4m+3 (8 bits each, 0xff: none)
   uint32_t kb[kRB];        // old corner colours
   uint32_t kn[kRB];        // new corner colours
@@ -112,9 +127,9 @@ struct TileMem {
   };
 };
 
-template <typename R>
+template <typename R, int CAP = kCandCap>
 constexpr size_t tile_smem_bytes() {
-  return sizeof(TileMem<R>);
+  return sizeof(TileMem<R, CAP>);
 }
 
 __device__ __forceinline__ int getb(const uint32_t* w, int lx, int ly) {
@@ -226,9 +241,9 @@ __device__ __forceinline__ uint32_t upto32(int c0, int last) {
 // Accessor of the tile for the shared sweep logic (beyond, walk,
 // new_unaligned).  Indices are clamped into the region; the kernel only asks
 // inside it.
-template <typename R, int AX, int LD>
+template <typename R, int AX, int LD, int CAP = kCandCap>
 struct TViewB {
-  const TileMem<R>* m;
+  const TileMem<R, CAP>* m;
   const GView<R, AX, LD>* g;  // an unaligned marker's own fraction is read from the state
   int ri0, rj0, nx_, ny_;
   __device__ __forceinline__ int tnx() const { return nx_; }
@@ -336,8 +351,9 @@ struct TViewB {
 // generation order).
 // *kept receives the slot of the kept candidate (-1: none); its centre-rule
 // verdicts are formed by the caller where they are needed.
-template <typename R>
-__device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int present, int* kept) {
+template <typename R, int CAP>
+__device__ __forceinline__ NewV<R> select_linked(const TileMem<R, CAP>& M, int s, int present,
+                                                 int* kept) {
   *kept = -1;
   if (s >= 0 && M.u.c.next[s] < 0 && present) {
     // one candidate on an edge that keeps a marker: it is the marker (the
@@ -432,12 +448,14 @@ __device__ __forceinline__ NewV<R> select_linked(const TileMem<R>& M, int s, int
 }
 
 // The tile with origin (i0, j0) of one grid (one block runs it).
-template <typename R, int AX, int LD>
+template <typename R, int AX, int LD, int CAP = kCandCap>
 __device__ __forceinline__ void sweep_tile(const GView<R, AX, LD>& G, const Buf<R>& out, int line_only,
                                            unsigned long long* ctr, unsigned long long* cfl_bits,
                                            int* status, const int i0, const int j0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileMem<R>& M = *reinterpret_cast<TileMem<R>*>(smem_raw);
+  TileMem<R, CAP>& M = *reinterpret_cast<TileMem<R, CAP>*>(smem_raw);
+  constexpr int kHB = head_bits<CAP>(), kHPW = 32 / kHB;  // head bits, heads per word
+  constexpr uint32_t kHNone = head_none<CAP>();
   __shared__ int s_nh, s_nv, s_nd, s_nc, s_ncand, s_ne, s_novf;
   __shared__ int s_cnt[D_NUSED];
   __shared__ unsigned long long s_dmax;
@@ -522,7 +540,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX, LD>& G, const Buf<
     mine |= (h | v) != 0u;
   }
   const bool busy = __syncthreads_or(mine) != 0;
-  const TViewB<R, AX, LD> TV{&M, &G, ri0, rj0, tnx, tny};
+  const TViewB<R, AX, LD, CAP> TV{&M, &G, ri0, rj0, tnx, tny};
 
   if (busy) {
     for (int t0 = warp * 32; t0 < kRB; t0 += kTileThreads) {
@@ -530,8 +548,8 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX, LD>& G, const Buf<
       push_bits_warp(t < kRB ? M.hm[t] : 0u, t, M.lh, &s_nh, lane);
       push_bits_warp(t < kRB ? M.vm[t] : 0u, t, M.u.p.lv, &s_nv, lane);
     }
-    static_assert(kNVE % 16 == 0, "vector initialisation");
-    for (int e = tid; e < kNVE / 16; e += kTileThreads)
+    static_assert(sizeof(M.head) % 16 == 0, "vector initialisation");
+    for (int e = tid; e < (int)(sizeof(M.head) / 16); e += kTileThreads)
       reinterpret_cast<uint4*>(M.head)[e] = make_uint4(~0u, ~0u, ~0u, ~0u);
     __syncthreads();
 
@@ -698,7 +716,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX, LD>& G, const Buf<
           const int e = (j - j0) * (kTI + 1) + (k - i0);
           const int ex = k - ri0, eu = ly * kRW + (ex >> 5);
           const uint32_t ebit = 1u << (ex & 31);
-          if (slot >= kCandCap) {
+          if (slot >= CAP) {
             atomicOr(&M.ovf[eu], ebit);
             continue;
           }
@@ -722,16 +740,16 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX, LD>& G, const Buf<
           C.fl = fl;
           C.edge = (uint16_t)e;
           C.ord = (uint8_t)((c - (k - 2)) * 2 + t);
-          {  // push the slot on the edge's list: 8-bit head in a shared word
-            uint32_t* hw = &M.head[e >> 2];
-            const int sh = (e & 3) * 8;
+          {  // push the slot on the edge's list: a head of kHB bits in a shared word
+            uint32_t* hw = &M.head[e / kHPW];
+            const int sh = (e % kHPW) * kHB;
             uint32_t old = *hw, seen;
             do {  // each retry follows another thread's successful update
               seen = old;
-              old = atomicCAS(hw, seen, (seen & ~(0xffu << sh)) | ((uint32_t)slot << sh));
+              old = atomicCAS(hw, seen, (seen & ~(kHNone << sh)) | ((uint32_t)slot << sh));
             } while (old != seen);
-            const uint32_t prev = (seen >> sh) & 0xffu;
-            M.u.c.next[slot] = prev == 0xffu ? (int16_t)-1 : (int16_t)prev;
+            const uint32_t prev = (seen >> sh) & kHNone;
+            M.u.c.next[slot] = prev == kHNone ? (int16_t)-1 : (int16_t)prev;
           }
           atomicOr(&M.hc[eu], ebit);
         }
@@ -744,7 +762,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX, LD>& G, const Buf<
     // as fit_crossing does; the warps that take candidates rotate with the
     // block so that the FP64 work spreads over the SM's sub-partitions.  The
     // last three warps first list the edges with linked candidates.
-    const int ncand = min(s_ncand, kCandCap);
+    const int ncand = min(s_ncand, CAP);
     // the interface-cell list is dead: its storage becomes the verdicts of P6
     for (int e = tid; e < kNVE / 16; e += kTileThreads)
       reinterpret_cast<uint4*>(M.vrl)[e] = make_uint4(0u, 0u, 0u, 0u);
@@ -760,7 +778,7 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX, LD>& G, const Buf<
     const int vt = (((warp + rot) % kWarps) << 5) | lane;
     for (int b0 = 0; b0 < 2 * ncand; b0 += kTileThreads) {
       const int item = b0 + vt, side = item & 1;
-      Cand& C = M.u.c.cand[min(item >> 1, kCandCap - 1)];
+      Cand& C = M.u.c.cand[min(item >> 1, CAP - 1)];
       int k = 0, j = 0;
       bool act = item < 2 * ncand;
       if (act) {
@@ -893,9 +911,9 @@ __device__ __forceinline__ void sweep_tile(const GView<R, AX, LD>& G, const Buf<
       const int e = (j - j0) * (kTI + 1) + (k - i0);
       const bool own = k < i0 + kTI;
       const int present = getb(M.kn, ex, ey) ^ getb(M.kn, ex, ey + 1);
-      const uint32_t hd = (M.head[e >> 2] >> ((e & 3) * 8)) & 0xffu;
+      const uint32_t hd = (M.head[e / kHPW] >> ((e % kHPW) * kHB)) & kHNone;
       int kept;
-      const NewV<R> nv = select_linked<R>(M, hd == 0xffu ? -1 : (int)hd, present, &kept);
+      const NewV<R> nv = select_linked<R>(M, hd == kHNone ? -1 : (int)hd, present, &kept);
       if (own) {
         n_canc += nv.cancelled;
         n_inv += nv.invariant;
@@ -1083,17 +1101,19 @@ k_sweep_tile_batch(const SweepDesc<R, AX>* __restrict__ descs, const WorkItem* _
 // one launch can take the first (or second) sweep of every grid, each tile in
 // the direction its grid's split order puts there (x first on even steps):
 // the x descriptor when it is active for this launch, else the y one.
-template <typename R>
+template <typename R, int CAP = kCandCap>
 __global__ void __launch_bounds__(tile_threads<R>(), tile_min_blocks<R>())
 k_sweep_tile_both(const SweepDesc<R, 0>* __restrict__ dx, const SweepDesc<R, 1>* __restrict__ dy,
                   const WorkItem* __restrict__ items) {
   const WorkItem it = items[blockIdx.x];
   const SweepDesc<R, 0>& X = dx[it.grid];
   if (X.active) {
-    sweep_tile<R, 0>(X.G, X.out, X.line_only, X.ctr, X.cfl_bits, X.status, it.tx * kTI, it.ty * kTJ);
+    sweep_tile<R, 0, 0, CAP>(X.G, X.out, X.line_only, X.ctr, X.cfl_bits, X.status, it.tx * kTI,
+                             it.ty * kTJ);
   } else {
     const SweepDesc<R, 1>& Y = dy[it.grid];
-    sweep_tile<R, 1>(Y.G, Y.out, Y.line_only, Y.ctr, Y.cfl_bits, Y.status, it.tx * kTI, it.ty * kTJ);
+    sweep_tile<R, 1, 0, CAP>(Y.G, Y.out, Y.line_only, Y.ctr, Y.cfl_bits, Y.status, it.tx * kTI,
+                             it.ty * kTJ);
   }
 }
 
