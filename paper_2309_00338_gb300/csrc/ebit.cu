@@ -542,6 +542,9 @@ ebit_status ebit_fraction_to_host(ebit_ctx* c, void* C_host, void* copy_stream) 
   if (cs != c->stream) {
     EBIT_CK(cudaEventRecord(c->ev_queued, c->stream));
     EBIT_CK(cudaStreamWaitEvent(cs, c->ev_queued, 0));
+    // a copy still pending from an earlier call comes first, so that the
+    // single event the next fields launch waits for covers both
+    if (c->c_read_pending) EBIT_CK(cudaStreamWaitEvent(cs, c->ev_c_read, 0));
   }
   EBIT_CK(cudaMemcpy2DAsync(C_host, (size_t)c->grid.nx * L.esz, c->C, (size_t)L.d.P * L.esz,
                             (size_t)c->grid.nx * L.esz, c->grid.ny, cudaMemcpyDeviceToHost, cs));

@@ -618,11 +618,12 @@ def test_stagnation_film_run(prec):
 def test_fraction_to_host_every_step(prec):
     """ebit_fraction_to_host after each of four steps, queued while the GPU
     runs ahead of the host (the first on the context's stream, the others on
-    a side stream): every host copy holds the C of its own step — the next
-    step's fields launch waits for the copy — and equals the oracle's."""
+    a side stream, each with a second copy on another stream): every host copy
+    holds the C of its own step — the next step's fields launch waits for all
+    copies still pending — and equals the oracle's."""
     S, f, dt = scene_disks(prec)
     ctx = gpu_from(S)
-    side = torch.cuda.Stream()
+    side, side2 = torch.cuda.Stream(), torch.cuda.Stream()
     dtype = torch.float64 if prec == oracle.FP64 else torch.float32
     try:
         u, v = dev(f.u, prec), dev(f.v, prec)
@@ -631,16 +632,23 @@ def test_fraction_to_host_every_step(prec):
             ebit.ebit_step(ctx, u, v, dt)
             h = torch.full((S.ny, S.nx), -1.0, dtype=dtype).pin_memory()
             ebit.ebit_fraction_to_host(ctx, h, None if k == 0 else side)
-            hosts.append(h)
+            mine = [h]
+            if k > 0:  # a second copy of the same step on another stream
+                h2 = torch.full((S.ny, S.nx), -1.0, dtype=dtype).pin_memory()
+                ebit.ebit_fraction_to_host(ctx, h2, side2)
+                mine.append(h2)
+            hosts.append(mine)
         refs = [oracle.step(S, f.u, f.v, dt)["C"].copy() for _ in range(4)]
         side.synchronize()
+        side2.synchronize()
         ebit.ebit_sync(ctx)
-        for h, r in zip(hosts, refs):
-            c = h.double().numpy()
-            if prec == oracle.FP32:
-                assert np.array_equal(c, r)
-            else:
-                assert np.max(np.abs(c - r)) <= TOL64
+        for hs, r in zip(hosts, refs):
+            for h in hs:
+                c = h.double().numpy()
+                if prec == oracle.FP32:
+                    assert np.array_equal(c, r)
+                else:
+                    assert np.max(np.abs(c - r)) <= TOL64
     finally:
         ebit.ebit_destroy(ctx)
 
