@@ -184,6 +184,33 @@ def ebit_footprint(nx, ny, dx, prec=EBIT_FP64, flags=0) -> int:
     return int(lib().ebit_footprint(ctypes.byref(g)))
 
 
+# Grid of every live context (handle value -> (nx, ny, prec)): the binding
+# checks the caller's tensors against it before a call that reads or writes
+# them, so that a wrongly sized buffer is refused instead of being accessed
+# out of range.
+_CTX = {}
+
+
+def _grid_of(ctx):
+    return _CTX.get(ctx.value if isinstance(ctx, ctypes.c_void_p) else ctx)
+
+
+def _check_tensor(ctx, t, name, shape_fn, device):
+    """Refuses t unless it has the element count shape_fn(nx, ny) and the
+    dtype of the context's precision, on the device (or host) expected."""
+    if t is None:
+        return
+    g = _grid_of(ctx)
+    if g is None:
+        return  # a handle the binding did not create: the caller vouches for it
+    nx, ny, prec = g
+    import torch
+    want = torch.float32 if prec == EBIT_FP32 else torch.float64
+    _expect(t, name, shape_fn(nx, ny), want)
+    if bool(t.is_cuda) != device:
+        raise ValueError(f"{name}: expected a {'CUDA' if device else 'host'} tensor")
+
+
 def ebit_init(nx, ny, dx, scene: dict, prec=EBIT_FP64, flags=0, stream=None):
     """ebit_init: returns a context handle (c_void_p)."""
     g = ebit_grid(nx, ny, dx, prec, flags)
@@ -191,6 +218,7 @@ def ebit_init(nx, ny, dx, scene: dict, prec=EBIT_FP64, flags=0, stream=None):
     sc = _scene(scene, keep)
     h = ctypes.c_void_p()
     _check(lib().ebit_init(ctypes.byref(h), ctypes.byref(g), ctypes.byref(sc), _stream(stream)), "ebit_init")
+    _CTX[h.value] = (int(nx), int(ny), int(prec))
     return h
 
 
@@ -198,6 +226,7 @@ def ebit_create(nx, ny, dx, prec=EBIT_FP64, flags=0, stream=None):
     g = ebit_grid(nx, ny, dx, prec, flags)
     h = ctypes.c_void_p()
     _check(lib().ebit_create(ctypes.byref(h), ctypes.byref(g), _stream(stream)), "ebit_create")
+    _CTX[h.value] = (int(nx), int(ny), int(prec))
     return h
 
 
@@ -232,14 +261,19 @@ def _dev_ptr(t):
 
 def ebit_step(ctx, u, v, dt):
     """u, v: contiguous CUDA tensors (ny+1, nx+1) of the context precision."""
+    vertices = lambda nx, ny: (nx + 1) * (ny + 1)  # noqa: E731
+    _check_tensor(ctx, u, "u", vertices, True)
+    _check_tensor(ctx, v, "v", vertices, True)
     _check(lib().ebit_step(ctx, _dev_ptr(u), _dev_ptr(v), float(dt)), "ebit_step")
 
 
 def ebit_sweep(ctx, axis, vel, dt):
+    _check_tensor(ctx, vel, "vel", lambda nx, ny: (nx + 1) * (ny + 1), True)
     _check(lib().ebit_sweep(ctx, int(axis), _dev_ptr(vel), float(dt)), "ebit_sweep")
 
 
 def ebit_fraction(ctx, C=None, want_area=True):
+    _check_tensor(ctx, C, "C", lambda nx, ny: nx * ny, True)
     a = ctypes.c_double(0.0)
     _check(lib().ebit_fraction(ctx, _dev_ptr(C), ctypes.byref(a) if want_area else None), "ebit_fraction")
     return a.value if want_area else None
@@ -261,6 +295,7 @@ def ebit_fraction_to_host(ctx, C_host, stream=None):
     computation waits for the copy on the device."""
     if C_host.is_cuda or not C_host.is_contiguous() or not C_host.is_pinned():
         raise ValueError("expected a pinned, contiguous host tensor")
+    _check_tensor(ctx, C_host, "C_host", lambda nx, ny: nx * ny, False)
     st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
     _check(lib().ebit_fraction_to_host(ctx, ctypes.c_void_p(C_host.data_ptr()), st), "ebit_fraction_to_host")
 
@@ -274,6 +309,7 @@ def ebit_check_status():
 
 
 def ebit_curvature(ctx, kappa=None, want_invalid=True):
+    _check_tensor(ctx, kappa, "kappa", lambda nx, ny: nx * ny, True)
     n = ctypes.c_int32(0)
     _check(lib().ebit_curvature(ctx, _dev_ptr(kappa), ctypes.byref(n) if want_invalid else None),
            "ebit_curvature")
@@ -292,6 +328,10 @@ def ebit_coupling(ctx, rho1, rho2, mu1, mu2, sigma, rho=None, mu=None, fx=None, 
     (ny, nx+1), fy: (ny+1, nx)) from the context's current C and kappa, into
     caller-owned contiguous CUDA tensors of the context precision (None:
     skipped).  Asynchronous on the context's stream."""
+    _check_tensor(ctx, rho, "rho", lambda nx, ny: nx * ny, True)
+    _check_tensor(ctx, mu, "mu", lambda nx, ny: nx * ny, True)
+    _check_tensor(ctx, fx, "fx", lambda nx, ny: ny * (nx + 1), True)
+    _check_tensor(ctx, fy, "fy", lambda nx, ny: (ny + 1) * nx, True)
     fl = ebit_fluids(rho1, rho2, mu1, mu2, sigma)
     _check(lib().ebit_coupling(ctx, ctypes.byref(fl), _dev_ptr(rho), _dev_ptr(mu), _dev_ptr(fx), _dev_ptr(fy)),
            "ebit_coupling")
@@ -309,6 +349,7 @@ def ebit_sync(ctx):
 
 def ebit_destroy(ctx):
     if ctx:
+        _CTX.pop(ctx.value if isinstance(ctx, ctypes.c_void_p) else ctx, None)
         lib().ebit_destroy(ctx)
 
 

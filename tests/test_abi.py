@@ -94,3 +94,34 @@ def test_new_entry_points_check_arguments_without_gpu(libebit):
     g = ebit.ebit_grid(n, n, 1 / n, 0, 0)
     assert L.ebit_init(ctypes.byref(h), ctypes.byref(g), ctypes.byref(sc), None) == ebit.EBIT_EINVAL
     assert not h.value
+
+
+def test_binding_refuses_wrongly_sized_tensors():
+    """The binding checks the caller's tensors against the context's grid
+    before any call that reads or writes them (a handle registered by hand
+    here: the checks fire before the library is reached)."""
+    torch = pytest.importorskip("torch")
+    from paper_2309_00338_gb300 import ebit
+    fake = ctypes.c_void_p(0x5eed)
+    ebit._CTX[fake.value] = (8, 4, ebit.EBIT_FP32)
+    try:
+        verts = 9 * 5
+        with pytest.raises(ValueError, match="u: expected 45"):
+            ebit.ebit_step(fake, torch.zeros(44), torch.zeros(verts), 0.1)
+        with pytest.raises(ValueError, match="float32"):
+            ebit.ebit_step(fake, torch.zeros(verts, dtype=torch.float64), torch.zeros(verts), 0.1)
+        with pytest.raises(ValueError, match="CUDA"):
+            ebit.ebit_step(fake, torch.zeros(verts), torch.zeros(verts), 0.1)
+        with pytest.raises(ValueError, match="vel"):
+            ebit.ebit_sweep(fake, 0, torch.zeros(verts + 1), 0.1)
+        with pytest.raises(ValueError, match="C: expected 32"):
+            ebit.ebit_fraction(fake, torch.zeros(31))
+        with pytest.raises(ValueError, match="kappa"):
+            ebit.ebit_curvature(fake, torch.zeros(33))
+        with pytest.raises(ValueError, match="fx: expected 36"):
+            ebit.ebit_coupling(fake, 1, 1, 1, 1, 1, fx=torch.zeros(32))
+        with pytest.raises(ValueError, match="fy: expected 40"):
+            ebit.ebit_coupling(fake, 1, 1, 1, 1, 1, fy=torch.zeros(36))
+        ebit._check_tensor(fake, torch.zeros(32), "C_host", lambda nx, ny: nx * ny, False)  # accepted
+    finally:
+        ebit._CTX.pop(fake.value, None)
