@@ -236,6 +236,9 @@ def ebit_load_state(ctx, K, Z, sH, sV, step_index=0):
     sH = np.ascontiguousarray(sH, np.float64)
     sV = np.ascontiguousarray(sV, np.float64)
     ny, nx = Z.shape
+    for name, arr, size in (("K", K, (ny + 1) * (nx + 1)), ("sH", sH, (ny + 1) * nx), ("sV", sV, ny * (nx + 1))):
+        if arr.size != size:
+            raise ValueError(f"{name}: expected {size} elements for a {nx} x {ny} grid, got {arr.size}")
     st = ebit_state_host(nx, ny, K.ctypes.data, Z.ctypes.data, sH.ctypes.data, sV.ctypes.data, int(step_index))
     _check(lib().ebit_load_state(ctx, ctypes.byref(st)), "ebit_load_state")
 

@@ -123,5 +123,8 @@ def test_binding_refuses_wrongly_sized_tensors():
         with pytest.raises(ValueError, match="fy: expected 40"):
             ebit.ebit_coupling(fake, 1, 1, 1, 1, 1, fy=torch.zeros(36))
         ebit._check_tensor(fake, torch.zeros(32), "C_host", lambda nx, ny: nx * ny, False)  # accepted
+        import numpy as np
+        with pytest.raises(ValueError, match="sV: expected 36"):
+            ebit.ebit_load_state(fake, np.zeros((5, 9)), np.zeros((4, 8)), np.zeros((5, 8)), np.zeros((4, 8)))
     finally:
         ebit._CTX.pop(fake.value, None)
