@@ -201,6 +201,30 @@ def test_results_do_not_depend_on_the_cta_schedule():
             assert np.array_equal(rt["counters"], rf["counters"])
 
 
+def test_flagged_requests_do_not_depend_on_the_schedule():
+    """Plain, straight-line (EBIT_FIT_LINE) and generalised-HF requests in
+    both precisions, served together under each fixed schedule (two sweep
+    launches or one persistent launch, three orders): every request's
+    fractions, area and counters are the same under all six."""
+    rng = W.Rng(4242)
+    specs = []
+    for prec in (0, 1):
+        for flags, n in ((0, 70), (ebit.EBIT_FIT_LINE, 90), (ebit.EBIT_CURV_GHF, 110)):
+            dx = 1.0 / n
+            circles = W.place_circles(rng, 8, 3 * dx, 0.1, 2 * dx, lambda x, y, r: True, max_tries=80)
+            specs.append(dict(n=n, circles=circles, field=ebit.EBIT_FIELD_ROTATION, prec=prec, steps=15,
+                              cfl=0.5, period=1.0, omega=2 * math.pi, centre=(0.5, 0.5), drift=(0.1, 0.05),
+                              flags=flags))
+    base, Cb, _ = _run(specs, 8 << 30, autotune=False, schedule=ebit.EBIT_SCHED_LARGEST_FIRST)
+    assert all(r["status"] == 0 and r["steps"] == 15 for r in base)
+    for sched in range(1, ebit.EBIT_SCHED_COUNT):
+        res, C, st = _run(specs, 8 << 30, autotune=False, schedule=sched)
+        assert st["schedule"] == sched
+        for rb, r, cb, c in zip(base, res, Cb, C):
+            assert r["status"] == 0 and r["area"] == rb["area"] and np.array_equal(c, cb)
+            assert np.array_equal(r["counters"], rb["counters"])
+
+
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
 def test_served_rotation_matches_oracle(prec):
     n, steps, cfl = 72, 30, 0.5
