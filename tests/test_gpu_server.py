@@ -260,6 +260,48 @@ def test_served_rotation_matches_oracle(prec):
         assert np.max(np.abs(got - out["C"])) <= 1e-12
 
 
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_served_degenerate_grid_sizes_match_oracle(prec):
+    """Grids of 1, 2, 3, 31, 33 and 65 cells a side (a single tile, ragged
+    tile edges, one past a tile) served together in one batch: each equals
+    the oracle's run of the same rotation steps."""
+    sides, steps, cfl = (1, 2, 3, 31, 33, 65), 6, 0.5
+    omega, centre, drift = 2 * math.pi, (0.5, 0.5), (0.2, -0.1)
+    circles = np.array([[0.5, 0.5, 0.3], [0.3, 0.7, 0.12]])
+    outs, keep, tickets = [], [], []
+    s = ebit.ebit_server_create(4 << 30)
+    try:
+        for n in sides:
+            C = np.zeros(n * n, np.float64 if prec == 0 else np.float32)
+            r, k = ebit.make_request(n, circles, ebit.EBIT_FIELD_ROTATION, steps, cfl, prec,
+                                     omega=omega, centre=centre, drift=drift, C_out=C)
+            keep.append(k)
+            outs.append(C)
+            tickets.append(ebit.ebit_submit(s, r))
+        res = ebit.wait_all(s, tickets)
+    finally:
+        ebit.ebit_server_destroy(s)
+    umax = 0.0
+    for a in (0, 1):
+        for b in (0, 1):
+            umax = max(umax, abs(-omega * (b - centre[1]) + drift[0]), abs(omega * (a - centre[0]) + drift[1]))
+    for n, t, C in zip(sides, tickets, outs):
+        dx = 1.0 / n
+        dt = cfl * dx / umax
+        f = W.rotation_field(n, n, dx, omega, centre, drift)
+        S = oracle.init(n, n, dx, W.circle_scene(circles), prec)
+        for _ in range(steps):
+            out = oracle.step(S, f.u, f.v, dt)
+        r = res[t]
+        assert r["status"] == 0 and r["steps"] == steps, n
+        assert abs(r["area"] - out["area"]) <= 1e-12 * max(out["area"], 1e-300), n
+        got = C.reshape(n, n).astype(np.float64)
+        if prec == 1:
+            assert np.array_equal(got, out["C"]), n
+        else:
+            assert np.max(np.abs(got - out["C"])) <= 1e-12, n
+
+
 def test_vortex_request_returns_to_its_shape():
     """A time-reversed vortex request (period = steps * dt) comes back with a
     small area error, as in the single-grid tests."""
