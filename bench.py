@@ -6,7 +6,10 @@ y = 0.5 + sum_{k<=16} (0.01/k^2) cos(2 pi k x + phi_k) plus 20000 seeded
 circles of radius 3-12 cells, steady cellular flow, dt = 0.5 dx.  The headline
 is the FP32-fraction form (FP64 circle fit and area sums); the plain FP64 form
 is timed beside it.  A step is one full EBIT step: both split sweeps, volume
-fractions and height-function curvature.
+fractions and height-function curvature.  The same line carries the batched
+leg (512 uneven grids of 32^2-512^2 in one batch, FP32 and plain FP64, against
+plain FP64 one grid at a time) and the serving leg (Poisson arrivals of grids
+of 64^2-2048^2 at --leg-rate per second over 10 s, FP32 and plain FP64).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -45,6 +48,12 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-ghf", action="store_true", help="skip the generalised height-function leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the batched leg (512 uneven grids) of the headline line")
+    p.add_argument("--no-serving", action="store_true",
+                   help="skip the serving leg (Poisson arrivals at --leg-rate) of the headline line")
+    p.add_argument("--leg-rate", type=float, default=50.0,
+                   help="arrivals per second of the headline line's serving leg")
     p.add_argument("--record-traffic", nargs="+", metavar="NCU_CSV",
                    help="write profiles/dram_traffic.json from ncu CSV logs of the headline workload and exit")
     p.add_argument("--late-from", type=int, default=1000,
@@ -57,6 +66,8 @@ def parse():
                    help="batched / serving: a fixed ebit_schedule instead of the autotuner's choice")
     p.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
     p.add_argument("--serve-seconds", type=float, default=10.0, help="serving: arrival window")
+    p.add_argument("--serve-fp64", action="store_true",
+                   help="serving: also serve the same arrivals in plain FP64")
     p.add_argument("--serve-cap", type=float, default=180.0, help="serving: wall-clock cap (s)")
     p.add_argument("--one-at-a-time", type=int, default=64,
                    help="batched: grids of the random sample run one at a time in plain FP64")
@@ -561,9 +572,17 @@ def run_ours(args, wl, world, rank, local):
     late = None
     late_state = None
     done_steps = ebit.ebit_get_state(ctx, n, n)["step_index"]
+    long_window = None
     if args.late_from > 0:
-        for _ in range(max(0, args.late_from - done_steps)):
-            ebit.ebit_step(ctx, u, v, wl.dt)
+        # the steps up to it carry per-step events: p50/p99 of the step over
+        # hundreds of steps, whatever --steps is
+        nlong = max(0, args.late_from - done_steps)
+        if nlong > 0:
+            tlong, latlong = timed_steps(torch, ebit, ctx, u, v, wl.dt, nlong, stream)
+            long_window = {"steps": [done_steps, done_steps + nlong], "ms_per_step": tlong / nlong,
+                           "p50_ms": float(np.percentile(latlong, 50)),
+                           "p99_ms": float(np.percentile(latlong, 99)),
+                           "max_ms": float(np.max(latlong))}
         ebit.ebit_sync(ctx)
         torch.cuda.synchronize()
         barrier()
@@ -631,6 +650,16 @@ def run_ours(args, wl, world, rank, local):
                 "coupling": coupling_roofline(kc64, n, 8, hbm, peak_kind)}
         ebit.ebit_destroy(ctx64)
 
+    # configs 4 and 5 beside the headline: the batched FP32 form against
+    # plain FP64 (batched, and one grid at a time), and the served FP32 form
+    batched = serving = None
+    if rank == 0 and world == 1:
+        if not args.no_batched:
+            batched = batched_leg(args)
+        if not args.no_serving:
+            serving = serving_leg(args, args.leg_rate, 1)
+            serving["fp64"] = serving_leg(args, args.leg_rate, 0)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, state=late_state)
@@ -647,7 +676,8 @@ def run_ours(args, wl, world, rank, local):
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(round(launches_per_step * args.steps)),
                 "roofline": roofline, "late_window": late, "coupling": coupling, "ghf": ghf,
-                "fp64": fp64,
+                "fp64": fp64, "step_latency_long_window": long_window,
+                "batched": batched, "serving": serving,
                 "cpu_baseline": cpu,
                 "markers": {"nH": int(diag["counters"][0]), "nV": int(diag["counters"][1])}}
         print(json.dumps(line), flush=True)
@@ -655,15 +685,18 @@ def run_ours(args, wl, world, rank, local):
         tdist.destroy_process_group()
 
 
-def _batched_requests(count, seed=230900340):
+def _batched_workloads(count, seed=230900340):
     """Grids of side log-uniform in [32, 512], 1-64 circles of radius
     U[0.05, 0.15] (at least 3 cells), a coin flip between the time-reversed
     vortex (period = steps * dt) and the cellular flow, 200-1000 steps, CFL 0.5."""
     from paper_2309_00338_gb300 import workloads as W
     rng = W.Rng(seed)
+    return [W.random_instance(rng) for _ in range(count)]
+
+
+def _batched_requests(count, seed=230900340):
     out = []
-    for _ in range(count):
-        wl = W.random_instance(rng)
+    for wl in _batched_workloads(count, seed):
         vortex = wl.field.name == "vortex"
         out.append(dict(n=wl.n, circles=wl.scene["circles"], steps=wl.steps, cfl=0.5,
                         field=0 if vortex else 1, period=wl.steps * wl.dt if vortex else 1.0,
@@ -706,9 +739,63 @@ def _serve(ebit, specs, prec, budget, max_instances=0, arrivals=None, cap_s=None
     return [res.get(t) for t in tickets], stats, wall
 
 
-def run_batched(args):
+def batched_cpu_baseline(count, budget_s=10.0, seed=230900343):
+    """The plain CPU baseline of the batched workload: the oracle as it
+    stands (plain FP64), one instance at a time per host thread on every core
+    this process may use.  Each thread takes the next grid of a seeded random
+    order of the grids and runs it from its initial state until its steps end
+    or the time budget does, then takes the next one.  The oracle's steps are
+    single foreign calls that release the interpreter lock, so the threads
+    run in parallel."""
+    import threading
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2309_00338_gb300 import workloads as W
+    wls = _batched_workloads(count)
+    cores = host_cores()["affinity"] or os.cpu_count() or 1
+    pick = W.Rng(seed)
+    order = list(range(len(wls)))
+    for i in range(len(order) - 1, 0, -1):  # seeded Fisher-Yates shuffle
+        j = min(i, int(pick.uniform() * (i + 1)))
+        order[i], order[j] = order[j], order[i]
+    lock = threading.Lock()
+    nxt = [0]
+    t0 = time.perf_counter()
+
+    def run(_):
+        cells = steps = grids = 0
+        while time.perf_counter() - t0 < budget_s:
+            with lock:
+                if nxt[0] >= len(order):
+                    break
+                wl = wls[order[nxt[0]]]
+                nxt[0] += 1
+            S = oracle.init(wl.n, wl.n, wl.dx, wl.scene, oracle.FP64)
+            grids += 1
+            k = 0
+            while k < wl.steps and time.perf_counter() - t0 < budget_s:
+                oracle.step(S, wl.field.u, wl.field.v, wl.field.dt_eff(k, wl.dt))
+                k += 1
+            cells += wl.n * wl.n * k
+            steps += k
+        return cells, steps, grids
+
+    with ThreadPoolExecutor(cores) as ex:
+        done = list(ex.map(run, range(cores)))
+    wall = time.perf_counter() - t0
+    return {"value": sum(d[0] for d in done) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "prec": "fp64",
+            "sample": f"{sum(d[2] for d in done)} grids of the batched workload in a seeded random order "
+                      f"(seed {seed}), one at a time per host thread, {sum(d[1] for d in done)} steps in "
+                      f"{wall:.1f} s (initialisation included)",
+            "host": host_cores()}
+
+
+def batched_leg(args):
     """512 uneven grids advanced together (one captured launch sequence per
-    batch step) in FP32 and FP64, against one-grid-at-a-time plain FP64."""
+    batch step) in FP32 and FP64, against one-grid-at-a-time plain FP64 on a
+    seeded random sample of the grids.  Values are cell-updates over the GPU
+    time of the batch steps (the server's own events)."""
     from paper_2309_00338_gb300 import ebit
     import torch
     torch.cuda.set_device(0)
@@ -738,19 +825,29 @@ def run_batched(args):
                                  "cell_updates": st["cell_updates"], "gpu_ms": st["busy_ms"],
                                  "value": st["cell_updates"] / (st["busy_ms"] / 1e3)}
     total = sum(sp["n"] ** 2 * sp["steps"] for sp in specs)
+    out["config"] = {"workload": f"batched_{len(specs)}_grids_32-512", "cell_updates": total,
+                     "seed": 230900340}
+    out["fp32_over_fp64_one_at_a_time"] = out["fp32"]["value"] / out["fp64_one_at_a_time"]["value"]
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = batched_cpu_baseline(len(specs))
+    return out
+
+
+def run_batched(args):
+    out = batched_leg(args)
     line = {"metric": "EBIT cell-updates/s, batched uneven grids", "value": out["fp32"]["value"],
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": f"batched_{len(specs)}_grids_32-512", "cell_updates": total,
-                       "seed": 230900340},
-            "fp32": out["fp32"], "fp64": out["fp64"], "fp64_one_at_a_time": out["fp64_one_at_a_time"]}
+            "data": "synthetic", "config": out["config"],
+            "fp32": out["fp32"], "fp64": out["fp64"], "fp64_one_at_a_time": out["fp64_one_at_a_time"],
+            "cpu_baseline": out.get("cpu_baseline")}
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args):
+def serving_leg(args, rate, prec=1):
     """Poisson arrivals: grids of side log-uniform in [64, 2048], 1-500
     circles of radius U[3, 30] cells, 50-2000 steps of the vortex, the
-    cellular flow or a solid rotation; FP32 requests."""
+    cellular flow or a solid rotation; every request in precision prec
+    (1: FP32 fractions with the FP64 fit, 0: plain FP64)."""
     from paper_2309_00338_gb300 import ebit
     from paper_2309_00338_gb300 import workloads as W
     import torch
@@ -759,7 +856,7 @@ def run_serving(args):
     specs, arrivals = [], []
     t = 0.0
     while True:
-        t += -math.log(1.0 - rng.uniform()) / args.rate
+        t += -math.log(1.0 - rng.uniform()) / rate
         if t > args.serve_seconds:
             break
         n = int(round(math.exp(rng.uniform(math.log(64), math.log(2048)))))
@@ -773,16 +870,15 @@ def run_serving(args):
         specs.append(sp)
         arrivals.append(t)
     # a 16 GiB admission budget bounds the batch (and so the step latency)
-    res, st, wall = _serve(ebit, specs, 1, 16 << 30, arrivals=arrivals, cap_s=args.serve_cap,
+    res, st, wall = _serve(ebit, specs, prec, 16 << 30, arrivals=arrivals, cap_s=args.serve_cap,
                            schedule=args.schedule)
     done = [r for r in res if r is not None]
     lat50 = [r["step_p50_ms"] for r in done]
     lat99 = [r["step_p99_ms"] for r in done]
     qw = [r["queue_ms"] for r in done]
     offered = sum(sp["n"] ** 2 * sp["steps"] for sp in specs) / args.serve_seconds
-    line = {"metric": "EBIT served cell-updates/s (continuous batching)", "value": st["cell_updates"] / wall,
-            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serving_poisson", "rate_per_s": args.rate, "arrival_window_s": args.serve_seconds,
+    return {"value": st["cell_updates"] / wall, "unit": UNIT, "prec": "fp32" if prec == 1 else "fp64",
+            "config": {"workload": "serving_poisson", "rate_per_s": rate, "arrival_window_s": args.serve_seconds,
                        "requests": len(specs), "offered_cell_updates_per_s": offered, "wall_cap_s": args.serve_cap},
             "completed": len(done), "wall_s": wall, "gpu_busy_s": st["busy_ms"] / 1e3,
             "batch_steps": st["batch_steps"],
@@ -792,6 +888,14 @@ def run_serving(args):
             "queue_ms_p50": float(np.median(qw)) if qw else None,
             "queue_ms_p99": float(np.percentile(qw, 99)) if qw else None,
             "autotune": {"schedule": st["schedule"], "tuned_sets": st["tuned_sets"], "tune_ms": st["tune_ms"]}}
+
+
+def run_serving(args):
+    leg = serving_leg(args, args.rate, 1)
+    line = {"metric": "EBIT served cell-updates/s (continuous batching)", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic", **leg}
+    if args.serve_fp64:
+        line["fp64"] = serving_leg(args, args.rate, 0)
     print(json.dumps(line), flush=True)
 
 
