@@ -887,7 +887,10 @@ def serving_leg(args, rate, prec=1):
             "step_p99_ms": float(np.percentile(lat99, 99)) if lat99 else None,
             "queue_ms_p50": float(np.median(qw)) if qw else None,
             "queue_ms_p99": float(np.percentile(qw, 99)) if qw else None,
-            "autotune": {"schedule": st["schedule"], "tuned_sets": st["tuned_sets"], "tune_ms": st["tune_ms"]}}
+            "autotune": {"schedule": st["schedule"], "tuned_sets": st["tuned_sets"], "tune_ms": st["tune_ms"]},
+            "worker_idle_gpu_ms": {"plans": st["plans"], "plan_ms": st["plan_ms"],
+                                   "plan_graph_ms": st["plan_graph_ms"],
+                                   "admit_ms": st["admit_idle_ms"], "retire_ms": st["retire_ms"]}}
 
 
 def run_serving(args):

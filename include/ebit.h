@@ -367,6 +367,14 @@ typedef struct {
   int32_t schedule;            /* ebit_schedule of the current set of grids */
   int32_t tuned_sets;          /* set signatures whose schedule the autotuner has chosen */
   double tune_ms[EBIT_SCHED_COUNT];  /* step time of each schedule, last tuning (0: not timed) */
+  /* Host time of the worker with no batch step in flight (ms): rebuilding the
+     launch plan and its graph for a new set of grids (plans: how many times;
+     plan_graph_ms: the part spent capturing the launch sequence and updating
+     or instantiating its graph), admitting requests while no grid runs and
+     taking out cancelled ones, and retiring finished grids (results copied
+     out, memory freed). */
+  int64_t plans;
+  double plan_ms, plan_graph_ms, admit_idle_ms, retire_ms;
 } ebit_server_stats;
 
 typedef struct ebit_server ebit_server;

@@ -17,11 +17,14 @@
 //
 // Serving: one worker thread owns the GPU.  Between batch steps it retires
 // finished, failed and cancelled grids (results copied to the host, memory
-// freed) and admits queued requests, first come first served among those that
-// fit, while the sum of their device footprints stays within the budget:
-// continuous batching.  While a batch step runs on the server's stream, the
-// worker admits the requests that arrived meanwhile on a second stream (their
-// grids join from the next step), so admission overlaps the GPU work.  The
+// freed).  It admits queued requests, first come first served among those
+// that fit, while the sum of their device footprints stays within the budget:
+// continuous batching.  With grids running, admission happens while a batch
+// step runs on the server's stream (the new grids are set up on a second
+// stream and join from the next step), so it overlaps the GPU work; only a
+// server with no grid running admits between steps.  The launch plan's
+// buffers only grow and its graph is updated in place where the launch
+// sequence keeps its shape, so a new set of grids costs little host time.  The
 // last launch of a batch step copies every grid's status word into host-mapped
 // memory; a grid whose step raised a CFL or invariant error leaves the batch
 // with that status, and the others carry on unchanged.
@@ -180,19 +183,67 @@ struct Group {
   unsigned* h_need = nullptr;
   std::vector<unsigned> tiles;  // per grid: tiles of one sweep
   int persist_blocks = 0;
+  // Capacities in bytes of the buffers above.  They only grow: a new set of
+  // grids reuses them, so a plan rebuild neither frees (cudaFree waits for
+  // the device) nor pins new host memory (slow) unless the set outgrew them.
+  size_t c_s0 = 0, c_s1 = 0, c_items0 = 0, c_fd = 0, c_fitems = 0, c_ad = 0, c_ctl = 0, c_need = 0;
+  size_t hc_s0 = 0, hc_s1 = 0, hc_need = 0;
+  // pinned staging of the plan's tables (copied to the device buffers above)
+  ebit::WorkItem* h_items0 = nullptr;
+  ebit::FieldItem* h_fitems = nullptr;
+  ebit::FieldDesc<R>* h_fd = nullptr;
+  AreaDesc* h_ad = nullptr;
+  size_t hc_items0 = 0, hc_fitems = 0, hc_fd = 0, hc_ad = 0;
+  int per_sm = -1, sms = 0;  // occupancy of the persistent sweep, queried once
 
   void release() {
-    if (h_s0) cudaFreeHost(h_s0);
-    if (h_s1) cudaFreeHost(h_s1);
-    if (h_need) cudaFreeHost(h_need);
+    for (void* p : {(void*)h_s0, (void*)h_s1, (void*)h_need, (void*)h_items0, (void*)h_fitems,
+                    (void*)h_fd, (void*)h_ad})
+      if (p) cudaFreeHost(p);
     for (void* p : {(void*)d_s0, (void*)d_s1, (void*)d_items0, (void*)d_fd,
                     (void*)d_fitems, (void*)d_ad, (void*)d_ctl, (void*)d_need})
       if (p) cudaFree(p);
     *this = Group<R>();
   }
 
+  // At least `bytes` of device (pinned host) memory at *p, reallocated only
+  // when the capacity is short (then doubled, so that a growing set of grids
+  // reallocates rarely).
+  static ebit_status grow_dev(void** p, size_t* cap, size_t bytes) {
+    if (bytes <= *cap && *p) return EBIT_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    const size_t want = std::max<size_t>(256, 2 * bytes);
+    if (cudaMalloc(p, want) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return fail_s(EBIT_ENOMEM, "cudaMalloc (batch plan)");
+    }
+    *cap = want;
+    return EBIT_OK;
+  }
+  static ebit_status grow_host(void** p, size_t* cap, size_t bytes) {
+    if (bytes <= *cap && *p) return EBIT_OK;
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    *cap = 0;
+    const size_t want = std::max<size_t>(256, 2 * bytes);
+    if (cudaMallocHost(p, want) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return fail_s(EBIT_ENOMEM, "cudaMallocHost (batch plan)");
+    }
+    *cap = want;
+    return EBIT_OK;
+  }
+
   ebit_status build(const std::vector<Instance*>& all, int prec, int schedule, cudaStream_t st) {
-    release();
+    inst.clear();
+    ghf.clear();
+    tiles.clear();
+    n_items0 = n_fitems = 0;
+    persist_blocks = 0;
     for (Instance* in : all)
       if (in->req.prec == prec) inst.push_back(in);
     if (inst.empty()) return EBIT_OK;
@@ -203,83 +254,109 @@ struct Group {
       std::stable_sort(inst.begin(), inst.end(),
                        [](const Instance* a, const Instance* b) { return a->req.n > b->req.n; });
     const size_t n = inst.size();
-    // per grid, its tiles in row order; then the CTA schedule orders them
-    std::vector<std::vector<ebit::WorkItem>> g0(n);
-    std::vector<std::vector<ebit::FieldItem>> gf(n);
-    std::vector<ebit::FieldDesc<R>> fd(n);
-    std::vector<AreaDesc> ad(n);
+    // per grid, its sweep and field tiles (row order within the grid)
     tiles.assign(n, 0u);
+    std::vector<int> ntx(n), nfx(n), nft(n);
+    size_t total0 = 0, totalf = 0;
+    for (size_t g = 0; g < n; ++g) {
+      const ebit::Dims& d = inst[g]->ctx->L.d;
+      ntx[g] = (d.nx + 1 + ebit::kTI - 1) / ebit::kTI;
+      tiles[g] = (unsigned)(ntx[g] * ((d.ny + 1 + ebit::kTJ - 1) / ebit::kTJ));
+      nfx[g] = (d.nx + 1 + ebit::kFX - 1) / ebit::kFX;
+      nft[g] = nfx[g] * ((d.ny + 1 + ebit::kFY - 1) / ebit::kFY);
+      total0 += tiles[g];
+      totalf += (size_t)nft[g];
+    }
+    ebit_status s;
+    if ((s = grow_host((void**)&h_items0, &hc_items0, total0 * sizeof(ebit::WorkItem))) != EBIT_OK) return s;
+    if ((s = grow_host((void**)&h_fitems, &hc_fitems, totalf * sizeof(ebit::FieldItem))) != EBIT_OK) return s;
+    if ((s = grow_host((void**)&h_fd, &hc_fd, n * sizeof(ebit::FieldDesc<R>))) != EBIT_OK) return s;
+    if ((s = grow_host((void**)&h_ad, &hc_ad, n * sizeof(AreaDesc))) != EBIT_OK) return s;
+    // the work items in the order of the CTA schedule, written straight into
+    // pinned memory: grid by grid, or round robin (tile t of every grid
+    // before tile t+1)
+    n_items0 = (int)order_items(h_items0, tiles, ntx, schedule);
+    std::vector<unsigned> nft_u(nft.begin(), nft.end());
+    n_fitems = (int)order_items(h_fitems, nft_u, nfx, schedule);
     for (size_t g = 0; g < n; ++g) {
       const ebit_ctx* c = inst[g]->ctx;
       const ebit::Dims& d = c->L.d;
-      for (int ty = 0; ty < (d.ny + 1 + ebit::kTJ - 1) / ebit::kTJ; ++ty)
-        for (int tx = 0; tx < (d.nx + 1 + ebit::kTI - 1) / ebit::kTI; ++tx) g0[g].push_back({(int)g, tx, ty});
-      tiles[g] = (unsigned)g0[g].size();
-      const int fx = (d.nx + 1 + ebit::kFX - 1) / ebit::kFX, fy = (d.ny + 1 + ebit::kFY - 1) / ebit::kFY;
-      for (int ty = 0; ty < fy; ++ty)
-        for (int tx = 0; tx < fx; ++tx) gf[g].push_back({(int)g, tx, ty});
       const int b = c->cur;
       const bool gh = (c->grid.flags & EBIT_CURV_GHF) != 0;
-      fd[g] = ebit::FieldDesc<R>{c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], d,
-                                 (R)c->grid.dx, (R*)c->C, (R*)c->kappa, c->partial, c->ctr, fx,
-                                 gh ? c->ghf_list : nullptr, gh ? c->ghf_count : nullptr};
+      h_fd[g] = ebit::FieldDesc<R>{c->K[b], c->Z[b], (const R*)c->sH[b], (const R*)c->sV[b], d,
+                                   (R)c->grid.dx, (R*)c->C, (R*)c->kappa, c->partial, c->ctr, nfx[g],
+                                   gh ? c->ghf_list : nullptr, gh ? c->ghf_count : nullptr};
       if (gh) ghf.push_back((int)g);
-      ad[g] = AreaDesc{c->partial, (long long)fx * fy, c->grid.dx * c->grid.dx, c->area};
+      h_ad[g] = AreaDesc{c->partial, (long long)nft[g], c->grid.dx * c->grid.dx, c->area};
     }
-    const std::vector<ebit::WorkItem> it0 = order(g0, schedule);
-    const std::vector<ebit::FieldItem> fit = order(gf, schedule);
-    n_items0 = (int)it0.size();
-    n_fitems = (int)fit.size();
-    auto dput = [&](void** p, const void* src, size_t bytes) -> ebit_status {
-      if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); return fail_s(EBIT_ENOMEM, "cudaMalloc (batch plan)"); }
+    // the copies run on the server's stream before the step's launches; the
+    // pinned sources stay untouched until the next plan, which the worker
+    // builds only once that step has finished
+    auto dput = [&](void** p, size_t* cap, const void* src, size_t bytes) -> ebit_status {
+      const ebit_status g = grow_dev(p, cap, bytes);
+      if (g != EBIT_OK) return g;
       if (src && cudaMemcpyAsync(*p, src, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return fail_s(EBIT_ECUDA, "cudaMemcpyAsync (batch plan)");
       return EBIT_OK;
     };
-    ebit_status s;
-    if ((s = dput((void**)&d_items0, it0.data(), it0.size() * sizeof(ebit::WorkItem))) != EBIT_OK) return s;
-    if ((s = dput((void**)&d_fitems, fit.data(), fit.size() * sizeof(ebit::FieldItem))) != EBIT_OK) return s;
-    if ((s = dput((void**)&d_fd, fd.data(), n * sizeof(ebit::FieldDesc<R>))) != EBIT_OK) return s;
-    if ((s = dput((void**)&d_ad, ad.data(), n * sizeof(AreaDesc))) != EBIT_OK) return s;
-    if ((s = dput((void**)&d_s0, nullptr, 2 * n * sizeof(ebit::SweepDesc<R, 0>))) != EBIT_OK) return s;
-    if ((s = dput((void**)&d_s1, nullptr, 2 * n * sizeof(ebit::SweepDesc<R, 1>))) != EBIT_OK) return s;
-    if ((s = dput((void**)&d_ctl, nullptr, (n + 1) * sizeof(unsigned))) != EBIT_OK) return s;
-    if ((s = dput((void**)&d_need, nullptr, n * sizeof(unsigned))) != EBIT_OK) return s;
-    if (cudaMallocHost((void**)&h_s0, 2 * n * sizeof(ebit::SweepDesc<R, 0>)) != cudaSuccess ||
-        cudaMallocHost((void**)&h_s1, 2 * n * sizeof(ebit::SweepDesc<R, 1>)) != cudaSuccess ||
-        cudaMallocHost((void**)&h_need, n * sizeof(unsigned)) != cudaSuccess) {
-      cudaGetLastError();
-      return fail_s(EBIT_ENOMEM, "cudaMallocHost (batch plan)");
-    }
+    if ((s = dput((void**)&d_items0, &c_items0, h_items0, total0 * sizeof(ebit::WorkItem))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_fitems, &c_fitems, h_fitems, totalf * sizeof(ebit::FieldItem))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_fd, &c_fd, h_fd, n * sizeof(ebit::FieldDesc<R>))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_ad, &c_ad, h_ad, n * sizeof(AreaDesc))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_s0, &c_s0, nullptr, 2 * n * sizeof(ebit::SweepDesc<R, 0>))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_s1, &c_s1, nullptr, 2 * n * sizeof(ebit::SweepDesc<R, 1>))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_ctl, &c_ctl, nullptr, (n + 1) * sizeof(unsigned))) != EBIT_OK) return s;
+    if ((s = dput((void**)&d_need, &c_need, nullptr, n * sizeof(unsigned))) != EBIT_OK) return s;
+    if ((s = grow_host((void**)&h_s0, &hc_s0, 2 * n * sizeof(ebit::SweepDesc<R, 0>))) != EBIT_OK) return s;
+    if ((s = grow_host((void**)&h_s1, &hc_s1, 2 * n * sizeof(ebit::SweepDesc<R, 1>))) != EBIT_OK) return s;
+    if ((s = grow_host((void**)&h_need, &hc_need, n * sizeof(unsigned))) != EBIT_OK) return s;
     // resident blocks of the persistent launch (more would only wait for a slot)
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ebit::k_sweep_persistent<R>,
-                                                      ebit::tile_threads<R>(),
-                                                      ebit::tile_smem_bytes<R, ebit::batch_cand_cap<R>()>()) != cudaSuccess) {
+    int dev = 0;
+    if (per_sm < 0 &&
+        (cudaGetDevice(&dev) != cudaSuccess ||
+         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ebit::k_sweep_persistent<R>,
+                                                       ebit::tile_threads<R>(),
+                                                       ebit::tile_smem_bytes<R, ebit::batch_cand_cap<R>()>()) != cudaSuccess)) {
       cudaGetLastError();
+      per_sm = -1;
       return fail_s(EBIT_ECUDA, "occupancy of the persistent sweep");
     }
     persist_blocks = (int)std::min<long long>(2LL * n_items0, (long long)std::max(1, per_sm) * sms);
-    return cudaStreamSynchronize(st) == cudaSuccess ? EBIT_OK : fail_s(EBIT_ECUDA, "plan upload");
+    return EBIT_OK;
   }
 
-  // The work items of all grids in the order of the CTA schedule: grid by
-  // grid, or round robin (tile t of every grid before tile t+1).
+  // Writes the tiles of all grids to out in the order of the CTA schedule
+  // (grid g has count[g] tiles, ncol[g] per tile row, in row order): grid by
+  // grid, or round robin (tile t of every grid before tile t+1).  Returns
+  // how many it wrote.
   template <typename Item>
-  static std::vector<Item> order(const std::vector<std::vector<Item>>& per_grid, int schedule) {
-    std::vector<Item> out;
+  static size_t order_items(Item* out, const std::vector<unsigned>& count, const std::vector<int>& ncol,
+                            int schedule) {
+    size_t k = 0;
+    const size_t n = count.size();
     if (schedule != EBIT_SCHED_INTERLEAVED) {
-      for (const auto& v : per_grid) out.insert(out.end(), v.begin(), v.end());
-      return out;
+      for (size_t g = 0; g < n; ++g) {
+        const int nr = (int)(count[g] / ncol[g]);
+        for (int ty = 0; ty < nr; ++ty)
+          for (int tx = 0; tx < ncol[g]; ++tx) out[k++] = Item{(int)g, tx, ty};
+      }
+      return k;
     }
-    size_t longest = 0;
-    for (const auto& v : per_grid) longest = std::max(longest, v.size());
-    for (size_t t = 0; t < longest; ++t)
-      for (const auto& v : per_grid)
-        if (t < v.size()) out.push_back(v[t]);
-    return out;
+    // round robin: each grid's next tile (column, row) advanced in turn
+    std::vector<int> cx(n, 0), cy(n, 0);
+    unsigned longest = 0;
+    for (size_t g = 0; g < n; ++g) longest = std::max(longest, count[g]);
+    for (unsigned t = 0; t < longest; ++t)
+      for (size_t g = 0; g < n; ++g) {
+        if (t >= count[g]) continue;
+        out[k++] = Item{(int)g, cx[g], cy[g]};
+        if (++cx[g] == ncol[g]) {
+          cx[g] = 0;
+          ++cy[g];
+        }
+      }
+    return k;
   }
 
   // Descriptors of the coming step: lam and the split order of every grid.
@@ -397,6 +474,9 @@ struct ebit_server {
   // statistics
   int64_t batch_steps = 0, cell_updates = 0;
   double busy_ms = 0.0;
+  // host time the worker spends with no batch step in flight
+  int64_t plans = 0;
+  double plan_ms = 0.0, plan_graph_ms = 0.0, admit_idle_ms = 0.0, retire_ms = 0.0;
   // worker-only
   cudaStream_t stream = nullptr;        // batch steps
   cudaStream_t admit_stream = nullptr;  // initialisation of admitted grids
@@ -407,6 +487,8 @@ struct ebit_server {
   int** d_status = nullptr;  // device array of the grids' status pointers
   int* h_status = nullptr;   // host-mapped copy written by k_status_gather
   int* h_status_dev = nullptr;
+  int** h_status_ptrs = nullptr;  // pinned staging of d_status
+  size_t status_cap = 0;     // grids the two status buffers hold (they only grow)
   std::vector<Instance*> stepping;  // the grids of the step in flight, plan order
   bool dirty = true;   // the set of grids changed: new plans, new schedule choice
   bool replan = false; // same set, another schedule (autotuning)
@@ -518,9 +600,12 @@ void ebit_server::retire(size_t idx) {
 void ebit_server::release_status() {
   if (d_status) cudaFree(d_status);
   if (h_status) cudaFreeHost(h_status);
+  if (h_status_ptrs) cudaFreeHost(h_status_ptrs);
   d_status = nullptr;
   h_status = nullptr;
+  h_status_ptrs = nullptr;
   h_status_dev = nullptr;
+  status_cap = 0;
 }
 
 // Launch plans (and the captured graph) for the current set of grids.
@@ -548,10 +633,20 @@ ebit_status ebit_server::plan() {
     }
   }
   if (!dirty && !replan) return EBIT_OK;
-  if (graph) {
-    cudaGraphExecDestroy(graph);
-    graph = nullptr;
-  }
+  const double t0 = now_ms();
+  // nothing of an earlier plan is still being copied from the pinned staging
+  // (a plan whose step was never launched leaves its copies queued)
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_s(EBIT_ECUDA, "plan: stream");
+  // the previous step's graph is updated in place when the new launch
+  // sequence has its shape (same kernels, same nodes), else replaced; it is
+  // destroyed on every path that does not keep it
+  struct ExecGuard {
+    cudaGraphExec_t e;
+    ~ExecGuard() {
+      if (e) cudaGraphExecDestroy(e);
+    }
+  } old{graph};
+  graph = nullptr;
   // the work-item order of the schedule (its persistent twin has the same)
   const int order = sched % EBIT_SCHED_PERSISTENT_LARGEST_FIRST;
   if ((s = g32.build(all, EBIT_FP32, order, stream)) != EBIT_OK) return s;
@@ -560,19 +655,26 @@ ebit_status ebit_server::plan() {
   stepping.clear();
   stepping.insert(stepping.end(), g32.inst.begin(), g32.inst.end());
   stepping.insert(stepping.end(), g64.inst.begin(), g64.inst.end());
-  release_status();
   const size_t n = stepping.size();
   std::vector<int*> ptrs(n);
   for (size_t g = 0; g < n; ++g) ptrs[g] = stepping[g]->ctx->status;
-  if (cudaMalloc((void**)&d_status, n * sizeof(int*)) != cudaSuccess ||
-      cudaHostAlloc((void**)&h_status, n * sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
-      cudaHostGetDevicePointer((void**)&h_status_dev, h_status, 0) != cudaSuccess) {
-    cudaGetLastError();
-    return fail_s(EBIT_ENOMEM, "status plan");
+  if (n > status_cap) {
+    release_status();
+    const size_t cap = std::max<size_t>(64, 2 * n);
+    if (cudaMalloc((void**)&d_status, cap * sizeof(int*)) != cudaSuccess ||
+        cudaMallocHost((void**)&h_status_ptrs, cap * sizeof(int*)) != cudaSuccess ||
+        cudaHostAlloc((void**)&h_status, cap * sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&h_status_dev, h_status, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return fail_s(EBIT_ENOMEM, "status plan");
+    }
+    status_cap = cap;
   }
   std::memset(h_status, 0, n * sizeof(int));
-  if (cudaMemcpy(d_status, ptrs.data(), n * sizeof(int*), cudaMemcpyHostToDevice) != cudaSuccess)
+  std::memcpy(h_status_ptrs, ptrs.data(), n * sizeof(int*));
+  if (cudaMemcpyAsync(d_status, h_status_ptrs, n * sizeof(int*), cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return fail_s(EBIT_ECUDA, "status plan upload");
+  const double tg = now_ms();
   if (opts.use_graphs) {
     cudaGraph_t gr = nullptr;
     if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
@@ -580,12 +682,33 @@ ebit_status ebit_server::plan() {
     const ebit_status s1 = launch_all();
     if (cudaStreamEndCapture(stream, &gr) != cudaSuccess || s1 != EBIT_OK)
       return fail_s(EBIT_ECUDA, "capture of the batch step");
-    const cudaError_t e = cudaGraphInstantiate(&graph, gr, 0);
+    cudaError_t e = cudaErrorUnknown;
+    if (old.e) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(old.e, gr, &info) == cudaSuccess) {
+        graph = old.e;
+        old.e = nullptr;
+        e = cudaSuccess;
+      } else {
+        cudaGetLastError();  // another shape: instantiated anew below
+      }
+    }
+    if (!graph) e = cudaGraphInstantiate(&graph, gr, 0);
     cudaGraphDestroy(gr);
-    if (e != cudaSuccess) return fail_s(EBIT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+      graph = nullptr;
+      return fail_s(EBIT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
   }
   dirty = false;
   replan = false;
+  {
+    const double t1 = now_ms();
+    std::lock_guard<std::mutex> lk(mu);
+    plans += 1;
+    plan_ms += t1 - t0;
+    plan_graph_ms += t1 - tg;
+  }
   return EBIT_OK;
 }
 
@@ -757,15 +880,22 @@ void ebit_server::run() {
         }
         queue.clear();
       }
-      take_admissible(admitted);
+      // with grids running, what fits is admitted while their next step
+      // runs (below), not here with the GPU idle
+      if (active.empty()) take_admissible(admitted);
       cancel_now.swap(cancels);
     }
+    const double ta = now_ms();
     admit_all(admitted);
     for (size_t i = active.size(); i-- > 0;)
       if (cancel_now.count(active[i]->ticket)) {
         active[i]->failed = EBIT_ECANCELLED;
         retire(i);
       }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      admit_idle_ms += now_ms() - ta;
+    }
     if (stop) {
       while (!active.empty()) retire(active.size() - 1);
       continue;
@@ -792,8 +922,13 @@ void ebit_server::run() {
         in->req.steps = (int32_t)in->done;
       }
     }
+    const double tr = now_ms();
     for (size_t i = active.size(); i-- > 0;)
       if (active[i]->done >= active[i]->req.steps || active[i]->failed != EBIT_OK) retire(i);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      retire_ms += now_ms() - tr;
+    }
   }
   if (graph) cudaGraphExecDestroy(graph);
   g32.release();
@@ -899,6 +1034,11 @@ ebit_status ebit_server_stats_get(ebit_server* s, ebit_server_stats* out) {
   out->schedule = s->sched;
   out->tuned_sets = (int32_t)s->tuned.size();
   for (int q = 0; q < EBIT_SCHED_COUNT; ++q) out->tune_ms[q] = s->last_tune_ms[q];
+  out->plans = s->plans;
+  out->plan_ms = s->plan_ms;
+  out->plan_graph_ms = s->plan_graph_ms;
+  out->admit_idle_ms = s->admit_idle_ms;
+  out->retire_ms = s->retire_ms;
   return EBIT_OK;
 }
 

@@ -442,7 +442,9 @@ class ebit_server_stats(ctypes.Structure):
                 ("batch_steps", ctypes.c_int64), ("cell_updates", ctypes.c_int64),
                 ("busy_ms", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t),
                 ("schedule", ctypes.c_int32), ("tuned_sets", ctypes.c_int32),
-                ("tune_ms", ctypes.c_double * EBIT_SCHED_COUNT)]
+                ("tune_ms", ctypes.c_double * EBIT_SCHED_COUNT),
+                ("plans", ctypes.c_int64), ("plan_ms", ctypes.c_double), ("plan_graph_ms", ctypes.c_double),
+                ("admit_idle_ms", ctypes.c_double), ("retire_ms", ctypes.c_double)]
 
 
 SIGNATURES.update({
@@ -527,7 +529,10 @@ def ebit_server_stats_get(server):
     _check(lib().ebit_server_stats_get(server, ctypes.byref(s)), "ebit_server_stats_get")
     return {"queued": s.queued, "running": s.running, "batch_steps": s.batch_steps,
             "cell_updates": s.cell_updates, "busy_ms": s.busy_ms, "bytes_in_use": s.bytes_in_use,
-            "schedule": s.schedule, "tuned_sets": s.tuned_sets, "tune_ms": list(s.tune_ms)}
+            "schedule": s.schedule, "tuned_sets": s.tuned_sets, "tune_ms": list(s.tune_ms),
+            "plans": s.plans, "plan_ms": s.plan_ms, "plan_graph_ms": s.plan_graph_ms,
+            "admit_idle_ms": s.admit_idle_ms,
+            "retire_ms": s.retire_ms}
 
 
 def ebit_server_destroy(server):
