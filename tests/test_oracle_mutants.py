@@ -73,9 +73,27 @@ MUTANTS = [
      [("  if (n == 4 && S.zc(i, j) == 0) {", "  if (n == 4 && S.zc(i, j) == 1) {")]),
     ("markers fit takes vertical markers one edge off",
      [("add((R)(a - i), (R)(b - j) + S.vc(a, b));", "add((R)(a - i) + R(1), (R)(b - j) + S.vc(a, b));")]),
+    ("chord crossing with the slope's sign flipped",
+     [("const double ystar = A.y + (x0 * (B.y - A.y)) / (B.x - A.x);",
+       "const double ystar = A.y - (x0 * (B.y - A.y)) / (B.x - A.x);")]),
+    ("density law with the phases swapped",
+     [("rho[(size_t)j * nx + i] = c * rho1 + (1.0 - c) * rho2;",
+       "rho[(size_t)j * nx + i] = (1.0 - c) * rho1 + c * rho2;")]),
+    ("face force along minus grad C",
+     [("return sigma * kf * (C[b] - C[a]) / dx;", "return sigma * kf * (C[a] - C[b]) / dx;")]),
+    ("face curvature drops a lone valid neighbour",
+     [("else if (va) kf = ka;", "else if (va) kf = 0.0;")]),
+    ("y faces take the cell to the left instead of the one below",
+     [("(j == 0 || j == ny) ? 0.0 : face((size_t)(j - 1) * nx + i, (size_t)j * nx + i);",
+       "(j == 0 || j == ny) ? 0.0 : face((size_t)j * nx + (i > 0 ? i - 1 : i), (size_t)j * nx + i);")]),
 ]
 
 BATTERY = [
+    (P.test_coupling_properties_pure_phases_and_mass, (0,)),
+    (P.test_coupling_flat_interface_has_no_force, ()),
+    (P.test_coupling_constant_curvature_telescopes, ()),
+    (P.test_coupling_face_curvature_reading, ()),
+    (P.test_coupling_laplace_pressure_jump, (True,)),
     (P.test_fit_exact_on_circle, ()),
     (P.test_fit_collinear_is_the_line_and_degenerate_cases, ()),
     (P.test_translation_table1, (32,)),
