@@ -73,6 +73,8 @@ MUTANTS = [
      [("  if (n == 4 && S.zc(i, j) == 0) {", "  if (n == 4 && S.zc(i, j) == 1) {")]),
     ("markers fit takes vertical markers one edge off",
      [("add((R)(a - i), (R)(b - j) + S.vc(a, b));", "add((R)(a - i) + R(1), (R)(b - j) + S.vc(a, b));")]),
+    ("a near neighbour kept as point 1/4 instead of the marker beyond it",
+     [("q = local(move(nn), k, j);", "q = local(move(nb), k, j);")]),
     ("chord crossing with the slope's sign flipped",
      [("const double ystar = A.y + (x0 * (B.y - A.y)) / (B.x - A.x);",
        "const double ystar = A.y - (x0 * (B.y - A.y)) / (B.x - A.x);")]),
@@ -95,6 +97,7 @@ BATTERY = [
     (P.test_coupling_face_curvature_reading, ()),
     (P.test_coupling_laplace_pressure_jump, (True,)),
     (P.test_fit_exact_on_circle, ()),
+    (P.test_near_vertex_neighbour_is_passed_over_for_the_next_marker, ()),
     (P.test_fit_collinear_is_the_line_and_degenerate_cases, ()),
     (P.test_translation_table1, (32,)),
     (P.test_aligned_markers_follow_linear_field, (0,)),

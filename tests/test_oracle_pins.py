@@ -406,6 +406,32 @@ def test_corner_colour_flips_when_marker_passes(oracle_lib):
     assert np.allclose(xs, 0.52 + 0.8 * dx, atol=1e-15)
 
 
+def test_near_vertex_neighbour_is_passed_over_for_the_next_marker():
+    """Reading of Fig. 3's points 1 and 4 with Sec. 2.2's "whenever possible
+    two circles": a circle that passes a few thousandths of a cell inside a
+    grid vertex cuts off a tiny corner, so the horizontal and the vertical
+    marker next to that vertex almost coincide.  A fit whose point 1 (or 4)
+    would be one of them (closer than 0.01 cell to A' or B') takes the next
+    marker along the interface instead, so every chord of a smooth circle
+    still has both circles: after a translated step no candidate is left
+    with a single circle.  (Keeping the near marker makes its circle
+    degenerate and drops it.)"""
+    n = 48
+    dx = 1.0 / n
+    rng = np.random.default_rng(3)
+    tot = np.zeros(oracle.NCOUNTERS, np.int64)
+    for _ in range(24):
+        vx, vy = (20 + rng.integers(0, 8)) * dx, (20 + rng.integers(0, 8)) * dx
+        R = (6 + 4 * rng.uniform()) * dx
+        ang = rng.uniform(0, 2 * math.pi)
+        d = R - (0.002 + 0.004 * rng.uniform()) * dx   # the vertex 0.002-0.006 cell inside
+        S = oracle.init(n, n, dx, W.circle_scene([(vx - d * math.cos(ang), vy - d * math.sin(ang), R)]))
+        f = W.uniform_field(n, n, dx, 0.37, 0.21)
+        tot += oracle.step(S, f.u, f.v, 0.3 * dx)["counters"]
+    assert tot[oracle.FIT_TWO] > 1000
+    assert tot[oracle.FIT_ONE] == 0
+
+
 def test_cfl_violation_is_flagged():
     n = 16
     dx = 1.0 / n
