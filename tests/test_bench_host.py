@@ -26,3 +26,20 @@ def test_batched_workloads_are_seeded():
     assert [w.steps for w in a] == [w.steps for w in b]
     reqs = bench._batched_requests(4)
     assert [r["n"] for r in reqs] == [w.n for w in a]
+
+
+def test_byte_models_are_the_stated_ones():
+    """The roofline byte models the bench reports against: one EBIT step
+    32.5 B/cell (FP32) and 64.5 (FP64); a sweep 20.5 / 40.5; the fields
+    16.25 / 32.25; the coupling 24 / 48, with its face arrays counted exactly."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.step_bytes_per_cell(4) == 32.5 and bench.step_bytes_per_cell(8) == 64.5
+    assert bench.kernel_bytes_per_cell("sweep", 4) == 20.5
+    assert bench.kernel_bytes_per_cell("sweep", 8) == 40.5
+    assert bench.kernel_bytes_per_cell("fields", 4) == 16.25
+    assert bench.kernel_bytes_per_cell("fields", 8) == 32.25
+    assert bench.kernel_bytes_per_cell("coupling", 4) == 24
+    n = 4096
+    assert bench.coupling_bytes(n, n, 4) == 4 * (6 * n * n + 2 * n)
+    assert bench.FIT_OPS == 81
