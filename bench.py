@@ -739,6 +739,17 @@ def _serve(ebit, specs, prec, budget, max_instances=0, arrivals=None, cap_s=None
     return [res.get(t) for t in tickets], stats, wall
 
 
+def batched_roofline(cell_updates, gpu_ms, esz):
+    """The step's HBM roofline (the dense byte model of step_bytes_per_cell)
+    for cell-updates done in gpu_ms of GPU time, against the measured copy
+    bandwidth."""
+    hbm, kind = peaks()
+    bpc = step_bytes_per_cell(esz)
+    gbps = bpc * cell_updates / (gpu_ms / 1e3) / 1e9 if gpu_ms > 0 else 0.0
+    return {"bound": "hbm", "achieved": gbps, "peak": hbm, "unit": "GB/s", "frac": gbps / hbm,
+            "bytes_per_cell": bpc, "peak_source": f"{kind} hbm_gbs (copy)"}
+
+
 def batched_cpu_baseline(count, budget_s=10.0, seed=230900343):
     """The plain CPU baseline of the batched workload: the oracle as it
     stands (plain FP64), one instance at a time per host thread on every core
@@ -813,7 +824,8 @@ def batched_leg(args):
                      "e_area_reversed_median": float(np.median(ea)) if ea else None,
                      "e_area_reversed_max": float(np.max(ea)) if ea else None,
                      "autotune": {"schedule": st["schedule"], "tuned_sets": st["tuned_sets"],
-                                  "tune_ms": st["tune_ms"]}}
+                                  "tune_ms": st["tune_ms"]},
+                     "roofline": batched_roofline(st["cell_updates"], st["busy_ms"], 4 if prec == 1 else 8)}
     # plain FP64 one grid at a time on a seeded random sample of the grids
     from paper_2309_00338_gb300 import workloads as W
     pick = W.Rng(230900342)

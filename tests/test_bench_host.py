@@ -43,3 +43,16 @@ def test_byte_models_are_the_stated_ones():
     n = 4096
     assert bench.coupling_bytes(n, n, 4) == 4 * (6 * n * n + 2 * n)
     assert bench.FIT_OPS == 81
+
+
+def test_batched_roofline_arithmetic():
+    """The batched legs' roofline: the step's byte model times the
+    cell-updates over the GPU time, against the copy bandwidth."""
+    sys.path.insert(0, ROOT)
+    import bench
+    hbm, _ = bench.peaks()
+    r = bench.batched_roofline(10 ** 10, 500.0, 4)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["bytes_per_cell"] == 32.5
+    assert abs(r["achieved"] - 650.0) < 1e-9 and abs(r["frac"] - 650.0 / hbm) < 1e-12
+    assert bench.batched_roofline(10 ** 10, 500.0, 8)["achieved"] == 2 * 645.0 * 1.0
+    assert bench.batched_roofline(0, 0.0, 4)["achieved"] == 0.0
