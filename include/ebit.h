@@ -217,6 +217,8 @@ ebit_status ebit_diagnostics(ebit_ctx* ctx, ebit_diag* out);
 /* Waits for the context's stream; returns and clears a deferred error. */
 ebit_status ebit_sync(ebit_ctx* ctx);
 
+/* Waits for the context's work (and a fraction copy still in flight), then
+ * frees all its device memory.  NULL is ignored. */
 void ebit_destroy(ebit_ctx* ctx);
 
 /* Debug builds (libebit_check.so, compiled with EBIT_CHECK) check every
@@ -395,6 +397,8 @@ ebit_status ebit_poll(ebit_server* s, uint64_t ticket, ebit_result* out);
  * requests are not affected.  EBIT_EINVAL for an unknown or finished ticket.
  * Thread-safe. */
 ebit_status ebit_cancel(ebit_server* s, uint64_t ticket);
+/* A snapshot of the server's counters (ebit_server_stats).  Thread-safe;
+ * EBIT_EINVAL for NULL arguments. */
 ebit_status ebit_server_stats_get(ebit_server* s, ebit_server_stats* out);
 /* Cancels queued requests, finishes nothing further, frees everything. */
 void ebit_server_destroy(ebit_server* s);
