@@ -862,7 +862,8 @@ void ebit_server::run() {
     return;
   }
   for (;;) {
-    // between batch steps (nothing in flight): admission, cancellations
+    // between batch steps (nothing in flight): cancellations, and admission
+    // when no grid runs
     std::vector<std::unique_ptr<Instance>> admitted;
     std::set<uint64_t> cancel_now;
     {
